@@ -1,0 +1,163 @@
+"""Seeded synthetic inputs for single-pulse detection.
+
+Both the CUDA path's tests/bench and the CPU oracle take their inputs from here,
+so this module holds no step of the search itself: it only draws noise and
+injects pulses.
+
+Signal model (Sec. 2.1 of the paper, "idealized signal model"): white Gaussian
+noise of mean ``mu`` and deviation ``sigma`` plus rectangular pulses of width
+``S`` whose amplitude is ``SNR * sigma / sqrt(S)`` (Eq. amplitudenormalization
+with C = SNR), so that a boxcar matching the pulse exactly recovers ``SNR``.
+
+Randomness: numpy's counter-based Philox generator for host arrays, torch's
+Philox-based CUDA generator for device arrays; every entry point takes an
+explicit seed.  Workload seeds are ``SEED_BASE + k``.
+
+Workloads (synthetic stand-ins: the paper's SKA-MID-like data is an instrument
+rate, not a downloadable set):
+  * exhaustive_small: 64 DM trials x 65,536 samples, N(0,1), eight pulses of
+    widths {1,3,7,16,33,64,100,200} and SNR 10.
+  * ska_mid: 4,096 DM trials x 1,048,576 samples at 64 us, N(0,1), 500 pulses,
+    widths log-uniform in 1..4096, SNR uniform in 6..20.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 1910083240
+
+PULSE_DTYPE = np.dtype([("row", np.int64), ("start", np.int64), ("width", np.int64),
+                        ("snr", np.float64)])
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+def gaussian_noise(ndm: int, nt: int, seed: int, mu: float = 0.0, sigma: float = 1.0,
+                   dtype=np.float32) -> np.ndarray:
+    """``ndm x nt`` white Gaussian noise drawn on the host."""
+    g = rng(seed)
+    x = g.standard_normal((ndm, nt), dtype=np.float64)
+    x *= sigma
+    x += mu
+    return x.astype(dtype, copy=False)
+
+
+def pulse_table(n: int, ndm: int, nt: int, seed: int, widths=None, snrs=None,
+                width_range=(1, 4096), log_uniform: bool = True, snr_range=(6.0, 20.0),
+                min_gap: int = 0) -> np.ndarray:
+    """Random pulse truth table ``(row, start, width, snr)``, sorted by (row, start).
+
+    ``widths``/``snrs`` fix the values (cycled); otherwise widths are drawn
+    log-uniformly (or uniformly) in ``width_range`` and SNRs uniformly in
+    ``snr_range``.  Pulses of one row are at least ``min_gap + width`` apart and
+    lie completely inside the row.
+    """
+    g = rng(seed)
+    out = np.zeros(n, PULSE_DTYPE)
+    placed: dict[int, list[tuple[int, int]]] = {}
+    for i in range(n):
+        if widths is not None:
+            w = int(widths[i % len(widths)])
+        elif log_uniform:
+            lo, hi = math.log(width_range[0]), math.log(width_range[1] + 1)
+            w = int(min(width_range[1], max(width_range[0], math.floor(math.exp(g.uniform(lo, hi))))))
+        else:
+            w = int(g.integers(width_range[0], width_range[1] + 1))
+        snr = float(snrs[i % len(snrs)]) if snrs is not None else float(g.uniform(*snr_range))
+        for _ in range(10000):
+            r = int(g.integers(0, ndm))
+            if nt - w <= 0:
+                raise ValueError("pulse wider than the series")
+            s = int(g.integers(0, nt - w + 1))
+            ok = all(s + w + min_gap <= a or a + b + min_gap <= s for a, b in placed.get(r, []))
+            if ok:
+                placed.setdefault(r, []).append((s, w))
+                break
+        else:
+            raise RuntimeError("could not place pulse %d" % i)
+        out[i] = (r, s, w, snr)
+    out.sort(order=("row", "start"))
+    return out
+
+
+def pulse_amplitude(width, snr, sigma=1.0):
+    """Per-sample amplitude of a rectangular pulse of true SNR ``snr`` (Eq. amplitudenormalization)."""
+    return snr * sigma / math.sqrt(width)
+
+
+def inject(x: np.ndarray, table: np.ndarray, sigma: float = 1.0) -> np.ndarray:
+    """Add the rectangular pulses of ``table`` to the host array ``x`` in place."""
+    for p in table:
+        a = pulse_amplitude(int(p["width"]), float(p["snr"]), sigma)
+        r, s, w = int(p["row"]), int(p["start"]), int(p["width"])
+        seg = x[r, s:s + w].astype(np.float64) + a
+        x[r, s:s + w] = seg.astype(x.dtype)
+    return x
+
+
+def sliding_pulse_rows(S: int, n_shift: int, t0: int, nt: int, C: float = 1.0,
+                       dtype=np.float64) -> np.ndarray:
+    """Noise-free series, one per shift: row k holds a pulse [t0 + k, t0 + k + S).
+
+    This is the test data of Sec. 4.1 (each pulse shift in its own series).
+    """
+    x = np.zeros((n_shift, nt), dtype=np.float64)
+    a = pulse_amplitude(S, C)
+    for k in range(n_shift):
+        x[k, t0 + k:t0 + k + S] = a
+    return x.astype(dtype)
+
+
+# ----------------------------------------------------------------------------- workloads
+def exhaustive_small(seed: int = SEED_BASE + 1, dtype=np.float32):
+    """64 x 65,536 N(0,1) with eight SNR-10 pulses of widths {1,3,7,16,33,64,100,200}."""
+    ndm, nt = 64, 65536
+    x = gaussian_noise(ndm, nt, seed, dtype=np.float64)
+    tab = pulse_table(8, ndm, nt, seed + 7, widths=[1, 3, 7, 16, 33, 64, 100, 200],
+                      snrs=[10.0], min_gap=2 * 256)
+    inject(x, tab)
+    return x.astype(dtype), tab
+
+
+SKA_MID = dict(ndm=4096, nt=1 << 20, t_samp=64e-6, n_pulses=500, width_range=(1, 4096),
+               snr_range=(6.0, 20.0), s_end=8192)
+
+
+def ska_mid_pulses(seed: int = SEED_BASE + 2, ndm: int = SKA_MID["ndm"], nt: int = SKA_MID["nt"],
+                   n: int = SKA_MID["n_pulses"], min_gap: int = 2 * 9216):
+    """The 500-pulse truth table of the SKA-MID-shaped workload."""
+    return pulse_table(n, ndm, nt, seed, width_range=SKA_MID["width_range"],
+                       snr_range=SKA_MID["snr_range"], min_gap=min_gap)
+
+
+def device_noise(ndm: int, nt: int, seed: int, device="cuda", mu: float = 0.0,
+                 sigma: float = 1.0, out=None):
+    """``ndm x nt`` float32 N(mu, sigma^2) drawn on the device with a seeded torch generator."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    if out is None:
+        out = torch.empty((ndm, nt), dtype=torch.float32, device=device)
+    # fill row blocks so that the temporary memory stays bounded
+    step = max(1, (1 << 28) // max(nt, 1))
+    for r0 in range(0, ndm, step):
+        blk = out[r0:r0 + step]
+        torch.randn(blk.shape, generator=g, device=device, dtype=torch.float32, out=blk)
+        if sigma != 1.0:
+            blk.mul_(sigma)
+        if mu != 0.0:
+            blk.add_(mu)
+    return out
+
+
+def device_inject(x, table, sigma: float = 1.0):
+    """Add the pulses of ``table`` to a device tensor ``x`` ([ndm, >= nt]) in place."""
+    for p in table:
+        a = pulse_amplitude(int(p["width"]), float(p["snr"]), sigma)
+        r, s, w = int(p["row"]), int(p["start"]), int(p["width"])
+        x[r, s:s + w] += a
+    return x
