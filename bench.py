@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark of the single-pulse-detection hot path on GB300.
+
+One step = one pass of the whole path over one batch: boxcar search over the
+plan's grid (ingest, per-width SNR, max/argmax, Y/W output) plus threshold /
+peak-find candidates, i.e. one ``spd_search`` call through the C ABI.
+
+Workload (default): SKA-MID-shaped lossy search, 4,096 DM trials x 1,048,576
+samples at 64 us, N(0,1) noise with 500 rectangular pulses (widths log-uniform
+1..4096, SNR U(6,20)), IGRID IG(1) with S_end = 8192, candidates above SNR 6.
+The input (17.2 GB) is larger than L2, so no flush is needed between steps.
+
+Metric: DM x time samples per second (whole job, all ranks); the JSON line also
+carries x-real-time (the paper's SKA definition: samples/s x 64 us / 6000), the
+mean SNR loss measured on the GPU on noise-free copies of the workload's pulses,
+the roofline of the search kernel (CUDA events inside the timed region), the
+end-to-end figure through the public API with host buffers, and the oracle's CPU
+throughput on a bounded sample.
+
+``--impl reference`` times the CPU oracle (the only reference this method has:
+the paper's code is not available) on the same workload shape.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import spd_synth  # noqa: E402
+
+T_SAMP = 64e-6
+SKA_DM = 6000
+BYTES_PER_SAMPLE = 4 + 4 + 2  # f32 in, f32 Y out, u16 W out (algorithmic, once each)
+METRIC = "DM x time samples/s"
+
+ALGOS = {
+    "ig1": dict(algo=2, igrid_depth=1, igrid_layers=4),
+    "ig2": dict(algo=2, igrid_depth=2, igrid_layers=8),
+    "ig3": dict(algo=2, igrid_depth=3, igrid_layers=16),
+    "dit": dict(algo=2, igrid_depth=0, igrid_layers=1),
+    "bd8": dict(algo=1, boxdit_lmax=8),
+    "bd16": dict(algo=1, boxdit_lmax=16),
+    "bd32": dict(algo=1, boxdit_lmax=32),
+    "exh": dict(algo=0),
+}
+# candidates per input sample of each grid (sum over widths of 1/L_s), for the ALU roofline
+SEARCH_SOURCES = ["paper_1910_08324_gb300/csrc/spd_search.cu", "paper_1910_08324_gb300/csrc/spd_internal.h"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="ig1", choices=sorted(ALGOS))
+    ap.add_argument("--ndm", type=int, default=spd_synth.SKA_MID["ndm"])
+    ap.add_argument("--nt", type=int, default=spd_synth.SKA_MID["nt"])
+    ap.add_argument("--s-end", type=int, default=spd_synth.SKA_MID["s_end"])
+    ap.add_argument("--threshold", type=float, default=6.0)
+    ap.add_argument("--radius", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-rows", type=int, default=96)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-loss", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for s in SEARCH_SOURCES:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(algo, ndm, nt):
+    """Per-launch DRAM bytes of the search kernel from the committed ncu summary,
+    if it was taken on the current kernel source and this algorithm; else None."""
+    p = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(algo)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return float(e["bytes_per_sample"]) * ndm * nt
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(x_rows, algo, s_end, threads=0):
+    """The oracle (definition form, FP64, OpenMP over rows) on a bounded sample."""
+    import oracle
+    kw = ALGOS[algo]
+    if kw["algo"] == 2:
+        g = oracle.grid_igrid(kw["igrid_depth"], kw["igrid_layers"], s_end)
+    elif kw["algo"] == 1:
+        g = oracle.grid_boxdit(kw["boxdit_lmax"], s_end)
+    else:
+        g = oracle.grid_exhaustive(s_end)
+    xs = np.ascontiguousarray(x_rows, np.float64)
+    t0 = time.perf_counter()
+    oracle.search(xs, g, 0.0, 1.0, threads=threads)
+    dt = time.perf_counter() - t0
+    return xs.size / dt, dt
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    ndm, nt = args.ndm, args.nt
+    rows = min(args.cpu_rows, ndm)
+    cores = os.cpu_count() or 1
+    times = []
+    for k in range(args.warmup + args.steps):
+        x = spd_synth.gaussian_noise(rows, nt, spd_synth.SEED_BASE + 100 + k, dtype=np.float64)
+        rate, dt = cpu_oracle_rate(x, args.algo, args.s_end)
+        if k >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = rows * nt / (ms / 1e3)
+    sample = "%d of %d rows x %d samples per step (oracle definition form, FP64)" % (rows, ndm, nt)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "ska_mid %dx%d" % (ndm, nt), "algo": args.algo, "s_end": args.s_end},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_1910_08324_gb300 as spd
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ndm, nt = args.ndm, args.nt
+    kw = dict(ALGOS[args.algo])
+    plan = spd.spd_plan_create(ndm=ndm, nt=nt, s_end=args.s_end, **kw)
+    widths, seps = plan.widths()
+    cand_per_sample = float(np.sum(1.0 / seps))
+
+    # inputs: every rank searches its own full-size block of DM trials (weak scaling)
+    seed = spd_synth.SEED_BASE + 2 + 1000 * rank
+    tab = spd_synth.ska_mid_pulses(seed=seed, ndm=ndm, nt=nt)
+    x = spd_synth.device_noise(ndm, nt, seed, device=dev)
+    spd_synth.device_inject(x, tab)
+    mu = torch.zeros(ndm, device=dev)
+    sg = torch.ones(ndm, device=dev)
+    Y = torch.empty((ndm, nt), dtype=torch.float32, device=dev)
+    W = torch.empty((ndm, nt), dtype=torch.int16, device=dev)
+    ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device=dev)
+    cap = 1 << 20
+    out = torch.zeros(cap * 24, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def fused_step():
+        spd.search(plan, x, mu, sg, Y, W, args.threshold, args.radius, out, cnt, ws, stream=sp)
+
+    for _ in range(args.warmup):
+        fused_step()
+    torch.cuda.synchronize(dev)
+
+    # timed region: K fused steps, each bracketed by events; search-kernel events too
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[3 * k].record(stream)
+            spd.spd_execute(plan, x.data_ptr(), mu.data_ptr(), sg.data_ptr(), Y.data_ptr(),
+                            W.data_ptr(), ws.data_ptr(), ws.numel(), sp)
+            ev[3 * k + 1].record(stream)
+            spd.spd_candidates(plan, Y.data_ptr(), W.data_ptr(), args.threshold, args.radius,
+                               out.data_ptr(), cap, cnt.data_ptr(), ws.data_ptr(), ws.numel(), 1, sp)
+            ev[3 * k + 2].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    search_ms = [ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(args.steps)]
+    cand_ms = [ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(args.steps)]
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    samples_step = ndm * nt * world
+    value = samples_step / (ms_per_step / 1e3)
+    n_cand = int(cnt.item())
+
+    # roofline of the dominant kernel (the search): algorithmic bytes / event time
+    peak, peak_kind = measured_peaks()
+    s_avg = statistics.mean(search_ms)
+    achieved = BYTES_PER_SAMPLE * ndm * nt / (s_avg / 1e3) / 1e9
+    traffic = recorded_traffic(args.algo, ndm, nt)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "search (%s)" % args.algo, "kernel_ms": s_avg,
+                "candidates_ms": statistics.mean(cand_ms),
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                if peak_kind == "measured" else "fallback 6800 GB/s"}
+
+    # mean SNR loss on noise-free copies of the workload's pulses (GPU search)
+    loss = None
+    if not args.no_loss and rank == 0:
+        x.zero_()
+        spd_synth.device_inject(x, tab)
+        fused_step()
+        torch.cuda.synchronize(dev)
+        lend = int(widths[-1])
+        rs = []
+        for p in tab:
+            r, s, w = int(p["row"]), int(p["start"]), int(p["width"])
+            a = max(0, s - lend)
+            rs.append(float(Y[r, a:s + w].max().item()) / float(p["snr"]))
+        loss = {"mean_snr_loss": float(1.0 - np.mean(rs)), "pulses": len(rs),
+                "max_snr_loss": float(1.0 - np.min(rs)),
+                "definition": "mean over the workload's pulses, noise-free, of 1 - RSNR/SNR"}
+        x.copy_(spd_synth.device_noise(ndm, nt, seed, device=dev))
+        spd_synth.device_inject(x, tab)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty((ndm, nt), dtype=torch.float32, pin_memory=True)
+        xh.copy_(x)
+        cnt_h = torch.zeros(1, dtype=torch.int64, pin_memory=True)
+        out_h = torch.empty(cap * 24, dtype=torch.uint8, pin_memory=True)
+        torch.cuda.synchronize(dev)
+        d2h = []
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            x.copy_(xh, non_blocking=True)
+            fused_step()
+            cnt_h.copy_(cnt, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            k = min(int(cnt_h.item()), cap)
+            out_h[: k * 24].copy_(out[: k * 24])
+            d2h.append(8 + 24 * k)
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            tt = torch.tensor([dt], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": samples_step / dt, "unit": "samples/s", "h2d_bytes_per_step": 4 * ndm * nt,
+               "d2h_bytes_per_step": int(statistics.mean(d2h)), "steps": args.e2e_steps,
+               "ms_per_step": 1e3 * dt, "api": "torch pinned H2D + spd_search (C ABI) + D2H of count and records"}
+        del xh, out_h
+
+    # oracle on the host cores, bounded sample (rank 0 only)
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        rows = min(args.cpu_rows, ndm)
+        xs = x[:rows].cpu().numpy()
+        rate, dt = cpu_oracle_rate(xs, args.algo, args.s_end)
+        cpu = {"value": rate, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": "%d of %d rows x %d samples, %s grid, definition form FP64, %.1f s wall"
+                         % (rows, ndm, nt, args.algo, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "ska_mid %d DM x %d samples, 64 us, 500 pulses" % (ndm, nt),
+                       "algo": args.algo, "s_end": args.s_end, "l_end": int(widths[-1]),
+                       "n_widths": int(len(widths)), "candidates_per_sample": cand_per_sample,
+                       "threshold": args.threshold, "peak_radius": args.radius,
+                       "candidates_found": n_cand, "parallelism": "dp%d (rows per GPU)" % world,
+                       "l2": "inputs (17.2 GB per GPU) larger than L2; no flush",
+                       "x_realtime_ska": value * T_SAMP / SKA_DM,
+                       "x_realtime_batch": (nt * T_SAMP) / (ms_per_step / 1e3)},
+            "snr_loss": loss,
+            "e2e": e2e,
+            "gpu_launches": 4 * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+/*
+ * spd.h -- C ABI of the GB300 single-pulse-detection library (libspd.so).
+ *
+ * Method: Adamek & Armour, "Single Pulse Detection Algorithms for Real-time
+ * Fast Radio Burst Searches using GPUs" (arXiv:1910.08324).  The library
+ * searches many dedispersed time series (one row per DM trial) with boxcar
+ * filters (Eq. boxcar), normalises every boxcar to an SNR (Eq. SNRlong with the
+ * white-noise statistics of Eq. whitenoise), keeps per start sample the
+ * highest SNR and the width that produced it (Eq. MSD03, all iterations
+ * combined), and selects candidates by threshold and peak finding (Sec. 4.5).
+ * Width grids: every width up to L_max (the ideal search of Sec. 3.1), BoxDIT
+ * (Alg. 1, Sec. 3.1) and IGRID (Sec. 3.2, Eq. boxcarsize, Table 1).
+ *
+ * Conventions
+ *   - All device pointers belong to the caller.  The library never allocates
+ *     device memory: scratch space is passed in as a workspace.  A plan owns
+ *     host memory only.
+ *   - Layout: row r of a [ndm][ld] array starts at element r*ld; samples of a
+ *     row are contiguous in time.  Inputs and outputs share the row stride ld.
+ *   - A boxcar is indexed by its first sample s (Eq. boxcar looks forward).
+ *     Width L is evaluated at s iff s is a multiple of its boxcar separation
+ *     L_s (Sec. 2.2.1) and s + L <= nt; nothing beyond a row is read or
+ *     padded into a sum.  Width 1 is in every grid, so every start s < nt
+ *     has a result.
+ *   - Width indices refer to the plan's ascending width table
+ *     (spd_plan_widths); ties in SNR go to the smallest width.
+ *   - Calls taking a stream are asynchronous and never synchronise unless
+ *     stated.  Validation errors are returned synchronously, before any
+ *     work is queued.  Launch errors are returned as SPD_ERR_CUDA; errors of
+ *     earlier asynchronous work surface in a later call or in
+ *     spd_sync_status().  Nothing aborts, traps or prints.
+ *   - Thread safety: a plan is read-only after creation and may be used from
+ *     several host threads and streams at once.
+ */
+#ifndef SPD_H
+#define SPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPD_VERSION_MAJOR 0
+#define SPD_VERSION_MINOR 1
+
+/* A CUDA stream handle (cudaStream_t).  NULL is the legacy default stream. */
+typedef struct CUstream_st *spd_stream_t;
+
+typedef enum spd_status {
+  SPD_OK = 0,
+  SPD_ERR_INVALID_ARG = 1,         /* a NULL pointer, bad size, bad enum, misaligned buffer */
+  SPD_ERR_UNSUPPORTED = 2,         /* valid request this build does not implement */
+  SPD_ERR_CUDA = 3,                /* a CUDA runtime call or kernel launch failed */
+  SPD_ERR_WORKSPACE_TOO_SMALL = 4, /* ws_bytes below spd_workspace_size() */
+  SPD_ERR_BUFFER_TOO_SMALL = 5,    /* a caller buffer (e.g. the width table) is too small */
+  SPD_ERR_TIMEOUT = 6,             /* a bounded device-side wait gave up */
+  SPD_ERR_HOST_ALLOC = 7           /* host memory for the plan could not be allocated */
+} spd_status;
+
+typedef enum spd_algo {
+  SPD_ALGO_EXHAUSTIVE = 0, /* every width 1..s_end at every sample (ideal search, Sec. 3.1) */
+  SPD_ALGO_BOXDIT = 1,     /* BoxDIT, Alg. 1 with L^i_max = boxdit_lmax for all i, D = 2 */
+  SPD_ALGO_IGRID = 2       /* IGRID IG(d) with P layers per step (Sec. 3.2); d = 0, P = 1 is DIT (Alg. 3) */
+} spd_algo;
+
+typedef enum spd_dtype {
+  SPD_F32 = 0, /* 32-bit IEEE float samples (the paper's input type, Sec. 4) */
+  SPD_F16 = 1, /* reserved: not implemented in this build (SPD_ERR_UNSUPPORTED) */
+  SPD_BF16 = 2,/* reserved: not implemented in this build */
+  SPD_U8 = 3   /* reserved: not implemented in this build */
+} spd_dtype;
+
+/*
+ * Plan description (Sec. 2.2.1: a search is characterised by its width set and
+ * the boxcar separation of every width).
+ *   algo          spd_algo
+ *   dtype         spd_dtype of the input samples
+ *   s_end         widest pulse searched, S_end (Sec. 3).  The last width of the
+ *                 grid is the first one >= s_end ("nearest longer", L_end).
+ *                 For SPD_ALGO_EXHAUSTIVE it is L_max itself (1..4096).
+ *                 L_end must not exceed 32768.
+ *   boxdit_lmax   BoxDIT: widths computed per iteration, L^i_max (Alg. 1);
+ *                 one of 8, 16, 32 (BD-8/16/32 of Sec. 4).
+ *   igrid_depth   IGRID: depth d of Eq. boxcarsize, 0..3.
+ *   igrid_layers  IGRID: layers per step P (power of two, 2^d <= P, P <= 2^(d+1));
+ *                 IG(1), IG(2), IG(3) of Sec. 3.2.1 use 4, 8, 16; DIT uses d=0, P=1.
+ *   ndm, nt, ld   rows (DM trials), samples per row, row stride in elements
+ *                 (ld >= nt).  ndm >= 1, nt >= 1.
+ */
+typedef struct spd_plan_desc {
+  int32_t algo;
+  int32_t dtype;
+  int32_t s_end;
+  int32_t boxdit_lmax;
+  int32_t igrid_depth;
+  int32_t igrid_layers;
+  int64_t ndm;
+  int64_t nt;
+  int64_t ld;
+} spd_plan_desc;
+
+/*
+ * Noise statistics used for the SNR of Eq. SNRlong.
+ *   mode 0 (white): mu[ndm], sigma[ndm] are the mean and standard deviation of
+ *                   each row's samples; a width-L boxcar uses L*mu and
+ *                   sqrt(L)*sigma (Eq. whitenoise).  sigma must be > 0.
+ *   mode 1 (table): reserved for per-width statistics; SPD_ERR_UNSUPPORTED in
+ *                   this build.
+ * Both pointers are device pointers to float32.
+ */
+typedef struct spd_noise {
+  int32_t mode;
+  const float *mu;
+  const float *sigma;
+} spd_noise;
+
+/* One detection (Sec. 4.5 candidate list): row, start sample, SNR and width. */
+typedef struct spd_candidate {
+  int32_t row;       /* DM-trial row */
+  int32_t width_idx; /* index into the plan's width table */
+  int64_t start;     /* first sample of the boxcar (centre = start + width/2) */
+  float snr;         /* Y[row][start] */
+  int32_t width;     /* the width itself, in samples */
+} spd_candidate;
+
+typedef struct spd_plan spd_plan;
+
+/* Human-readable text for a status code (static storage, never NULL). */
+const char *spd_status_string(spd_status status);
+
+/* "major.minor" of this library (static storage). */
+const char *spd_version(void);
+
+/*
+ * Build a plan: validates the description and derives the width grid of the
+ * chosen algorithm (Sec. 3.1 Alg. 1 width formula; Sec. 3.2 Eq. boxcarsize and
+ * Table 1).  Host only: no device work, no device memory.
+ * Errors: SPD_ERR_INVALID_ARG for a NULL pointer or any parameter outside the
+ * ranges documented in spd_plan_desc; SPD_ERR_UNSUPPORTED for a dtype this
+ * build lacks; SPD_ERR_HOST_ALLOC.  *out is NULL on error.
+ */
+spd_status spd_plan_create(const spd_plan_desc *desc, spd_plan **out);
+
+/* Release a plan (NULL is accepted).  No device synchronisation. */
+spd_status spd_plan_destroy(spd_plan *plan);
+
+/*
+ * The plan's width table in ascending order: widths[i] (samples) and the
+ * boxcar separation seps[i] (Sec. 2.2.1).  Either array may be NULL to query
+ * only *n.  SPD_ERR_BUFFER_TOO_SMALL if cap < *n (nothing is written then).
+ */
+spd_status spd_plan_widths(const spd_plan *plan, int32_t *widths, int32_t *seps,
+                           int32_t cap, int32_t *n);
+
+/*
+ * Bytes of device workspace the plan needs for spd_execute, spd_candidates and
+ * spd_search (the largest of the three; 256-byte aligned base required).
+ */
+spd_status spd_workspace_size(const spd_plan *plan, size_t *bytes);
+
+/*
+ * The search (Eq. boxcar, Eq. SNRlong, Eq. MSD03).  For every row r and every
+ * start s in [0, nt):
+ *   snr[r*ld + s]       = max over eligible widths L of (X_L[s] - L mu_r)/(sqrt(L) sigma_r)
+ *   width_idx[r*ld + s] = index of the smallest width reaching that maximum
+ * where X_L[s] is the sum of the L samples starting at s.  Width 1 is in every
+ * grid, so every s has a value.  Samples at s >= nt of a row (the ld - nt
+ * padding) are neither read nor written.
+ *   d_x         device, [ndm][ld] samples of plan dtype, 4-byte aligned (16-byte
+ *               alignment and ld % 4 == 0 enable vector loads)
+ *   noise       host struct holding device pointers (mode 0 only)
+ *   d_snr       device, [ndm][ld] float32 output
+ *   d_width_idx device, [ndm][ld] uint16 output
+ *   d_ws        device workspace of at least spd_workspace_size() bytes, or NULL
+ *               if that size is 0; 256-byte aligned.  On return it holds the
+ *               maximum SNR of every tile of every row (used by spd_search).
+ *   stream      stream all work is queued on
+ * Errors: SPD_ERR_INVALID_ARG (NULL or misaligned pointers), SPD_ERR_UNSUPPORTED
+ * (table noise), SPD_ERR_WORKSPACE_TOO_SMALL, SPD_ERR_CUDA (launch failure).
+ * Outputs are only valid once the stream has reached this work.
+ */
+spd_status spd_execute(const spd_plan *plan, const void *d_x, const spd_noise *noise,
+                       float *d_snr, uint16_t *d_width_idx, void *d_ws, size_t ws_bytes,
+                       spd_stream_t stream);
+
+/*
+ * Candidate selection on the outputs of spd_execute (the peak-finding step of
+ * Sec. 4.5, which the paper does not define).  Start s of row r is a candidate
+ * iff snr[s] >= threshold, snr[s] > snr[s'] for s - R <= s' < s and
+ * snr[s] >= snr[s'] for s < s' <= s + R (s' inside [0, nt)), R = peak_radius
+ * (0 = plain threshold, at most 64).  Records are written in (row, start)
+ * order; the first min(cap, total) are stored in d_out and the total count is
+ * stored in *d_count (device int64).  When *d_count > cap the list is
+ * truncated; the call itself still returns SPD_OK (it does not synchronise).
+ *   d_snr, d_width_idx  device outputs of spd_execute ([ndm][ld])
+ *   d_out               device array of cap records (may be NULL if cap == 0)
+ *   d_ws                workspace as for spd_execute
+ *   use_tile_max        nonzero: d_ws still holds the tile maxima written by the
+ *                       spd_execute call that produced d_snr (same plan, same
+ *                       workspace, d_snr unchanged since); tiles whose maximum is
+ *                       below the threshold are then skipped without being read.
+ *                       0: every tile of d_snr is scanned.
+ * Errors: SPD_ERR_INVALID_ARG, SPD_ERR_WORKSPACE_TOO_SMALL, SPD_ERR_CUDA.
+ */
+spd_status spd_candidates(const spd_plan *plan, const float *d_snr,
+                          const uint16_t *d_width_idx, float threshold, int32_t peak_radius,
+                          spd_candidate *d_out, int64_t cap, int64_t *d_count, void *d_ws,
+                          size_t ws_bytes, int32_t use_tile_max, spd_stream_t stream);
+
+/*
+ * spd_execute followed by spd_candidates(..., use_tile_max = 1) on the same
+ * stream, with the same results: the candidate step reads only the tiles whose
+ * maximum SNR reaches the threshold, so it adds almost no memory traffic.
+ * Arguments and errors as for the two calls.
+ */
+spd_status spd_search(const spd_plan *plan, const void *d_x, const spd_noise *noise,
+                      float *d_snr, uint16_t *d_width_idx, float threshold,
+                      int32_t peak_radius, spd_candidate *d_out, int64_t cap,
+                      int64_t *d_count, void *d_ws, size_t ws_bytes, spd_stream_t stream);
+
+/*
+ * Wait for the stream and report any asynchronous CUDA error of work queued
+ * on it (SPD_ERR_CUDA), else SPD_OK.
+ */
+spd_status spd_sync_status(const spd_plan *plan, spd_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPD_H */

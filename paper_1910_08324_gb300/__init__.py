@@ -1,0 +1,42 @@
+"""GB300-native boxcar single-pulse detection (Adamek & Armour, arXiv:1910.08324).
+
+This package is a thin ctypes binding over ``libspd.so`` (CUDA, sm_103a), whose C
+ABI is declared in ``include/spd.h``.  Every step of the search runs in the
+library's kernels; Python only marshals arguments.  PyTorch is used for device
+memory and streams.  There is no CPU fallback: if the library cannot be built
+or loaded, importing the binding functions raises.
+
+Entry points (same names as the C ABI): ``spd_plan_create``,
+``spd_plan_destroy``, ``spd_plan_widths``, ``spd_workspace_size``,
+``spd_execute``, ``spd_candidates``, ``spd_search``, ``spd_sync_status``,
+``spd_status_string``, ``spd_version``.  Convenience wrappers taking torch
+tensors: ``execute``, ``candidates``, ``search``.
+"""
+from ._binding import (  # noqa: F401
+    CANDIDATE_DTYPE,
+    SPD_ALGO_BOXDIT,
+    SPD_ALGO_EXHAUSTIVE,
+    SPD_ALGO_IGRID,
+    SPD_BF16,
+    SPD_F16,
+    SPD_F32,
+    SPD_U8,
+    Plan,
+    SpdError,
+    candidates,
+    execute,
+    library_path,
+    load_library,
+    records,
+    search,
+    spd_candidates,
+    spd_execute,
+    spd_plan_create,
+    spd_plan_destroy,
+    spd_plan_widths,
+    spd_search,
+    spd_status_string,
+    spd_sync_status,
+    spd_version,
+    spd_workspace_size,
+)

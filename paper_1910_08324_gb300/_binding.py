@@ -1,0 +1,231 @@
+"""ctypes binding of libspd.so (argument marshalling only).
+
+The C ABI (``include/spd.h``) takes plain device pointers and a CUDA stream
+handle.  The ``spd_*`` functions here mirror it one to one and accept integer
+pointers; ``execute``/``candidates``/``search`` accept torch tensors and use the
+current torch stream.  Errors raise ``SpdError`` carrying the status code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SPD_ALGO_EXHAUSTIVE, SPD_ALGO_BOXDIT, SPD_ALGO_IGRID = 0, 1, 2
+SPD_F32, SPD_F16, SPD_BF16, SPD_U8 = 0, 1, 2, 3
+
+_STATUS = {0: "SPD_OK", 1: "SPD_ERR_INVALID_ARG", 2: "SPD_ERR_UNSUPPORTED", 3: "SPD_ERR_CUDA",
+           4: "SPD_ERR_WORKSPACE_TOO_SMALL", 5: "SPD_ERR_BUFFER_TOO_SMALL", 6: "SPD_ERR_TIMEOUT",
+           7: "SPD_ERR_HOST_ALLOC"}
+
+# struct spd_candidate {int32 row; int32 width_idx; int64 start; float snr; int32 width;}
+CANDIDATE_DTYPE = np.dtype([("row", np.int32), ("width_idx", np.int32), ("start", np.int64),
+                            ("snr", np.float32), ("width", np.int32)])
+assert CANDIDATE_DTYPE.itemsize == 24
+
+
+class SpdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, _STATUS.get(status, status),
+                                          spd_status_string(status)))
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("dtype", ctypes.c_int32), ("s_end", ctypes.c_int32),
+                ("boxdit_lmax", ctypes.c_int32), ("igrid_depth", ctypes.c_int32),
+                ("igrid_layers", ctypes.c_int32), ("ndm", ctypes.c_int64), ("nt", ctypes.c_int64),
+                ("ld", ctypes.c_int64)]
+
+
+class _Noise(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("mu", ctypes.c_void_p), ("sigma", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+_SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_destroy",
+            "spd_plan_widths", "spd_workspace_size", "spd_execute", "spd_candidates",
+            "spd_search", "spd_sync_status"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Load libspd.so, building it first if it is missing or stale (needs nvcc)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        lib.spd_status_string.argtypes = [ctypes.c_int]
+        lib.spd_status_string.restype = ctypes.c_char_p
+        lib.spd_version.argtypes = []
+        lib.spd_version.restype = ctypes.c_char_p
+        lib.spd_plan_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(vp)]
+        lib.spd_plan_destroy.argtypes = [vp]
+        lib.spd_plan_widths.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i32)]
+        lib.spd_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+        lib.spd_execute.argtypes = [vp, vp, ctypes.POINTER(_Noise), vp, vp, vp, sz, vp]
+        lib.spd_candidates.argtypes = [vp, vp, vp, ctypes.c_float, i32, vp, i64, vp, vp, sz, i32, vp]
+        lib.spd_search.argtypes = [vp, vp, ctypes.POINTER(_Noise), vp, vp, ctypes.c_float, i32, vp,
+                                   i64, vp, vp, sz, vp]
+        lib.spd_sync_status.argtypes = [vp, vp]
+        for name in _SYMBOLS[2:]:
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise SpdError(status, where)
+
+
+def spd_status_string(status: int) -> str:
+    return load_library().spd_status_string(int(status)).decode()
+
+
+def spd_version() -> str:
+    return load_library().spd_version().decode()
+
+
+class Plan:
+    """Owns an ``spd_plan*``; destroyed with the object."""
+
+    def __init__(self, handle: int, desc: _Desc):
+        self.handle = handle
+        self.desc = desc
+        self.ndm, self.nt, self.ld = int(desc.ndm), int(desc.nt), int(desc.ld)
+
+    def widths(self):
+        return spd_plan_widths(self)
+
+    def workspace_size(self) -> int:
+        return spd_workspace_size(self)
+
+    def close(self):
+        if self.handle:
+            spd_plan_destroy(self)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spd_plan_create(algo: int, s_end: int, ndm: int, nt: int, ld: int | None = None,
+                    boxdit_lmax: int = 0, igrid_depth: int = 0, igrid_layers: int = 0,
+                    dtype: int = SPD_F32) -> Plan:
+    lib = load_library()
+    d = _Desc(int(algo), int(dtype), int(s_end), int(boxdit_lmax), int(igrid_depth),
+              int(igrid_layers), int(ndm), int(nt), int(nt if ld is None else ld))
+    h = ctypes.c_void_p()
+    _check(lib.spd_plan_create(ctypes.byref(d), ctypes.byref(h)), "spd_plan_create")
+    return Plan(h.value, d)
+
+
+def spd_plan_destroy(plan: Plan):
+    _check(load_library().spd_plan_destroy(ctypes.c_void_p(plan.handle)), "spd_plan_destroy")
+
+
+def spd_plan_widths(plan: Plan):
+    lib = load_library()
+    n = ctypes.c_int32()
+    _check(lib.spd_plan_widths(ctypes.c_void_p(plan.handle), None, None, 0, ctypes.byref(n)),
+           "spd_plan_widths")
+    w = np.zeros(n.value, np.int32)
+    s = np.zeros(n.value, np.int32)
+    _check(lib.spd_plan_widths(ctypes.c_void_p(plan.handle), w.ctypes.data, s.ctypes.data,
+                               n.value, ctypes.byref(n)), "spd_plan_widths")
+    return w, s
+
+
+def spd_workspace_size(plan: Plan) -> int:
+    b = ctypes.c_size_t()
+    _check(load_library().spd_workspace_size(ctypes.c_void_p(plan.handle), ctypes.byref(b)),
+           "spd_workspace_size")
+    return int(b.value)
+
+
+def spd_execute(plan: Plan, x: int, mu: int, sigma: int, snr: int, width_idx: int, ws: int,
+                ws_bytes: int, stream: int = 0, noise_mode: int = 0):
+    nz = _Noise(int(noise_mode), mu, sigma)
+    _check(load_library().spd_execute(ctypes.c_void_p(plan.handle), x, ctypes.byref(nz), snr,
+                                      width_idx, ws, ws_bytes, stream or None), "spd_execute")
+
+
+def spd_candidates(plan: Plan, snr: int, width_idx: int, threshold: float, peak_radius: int,
+                   out: int, cap: int, count: int, ws: int, ws_bytes: int, use_tile_max: int = 0,
+                   stream: int = 0):
+    _check(load_library().spd_candidates(ctypes.c_void_p(plan.handle), snr, width_idx,
+                                         float(threshold), int(peak_radius), out or None,
+                                         int(cap), count, ws, ws_bytes, int(use_tile_max),
+                                         stream or None),
+           "spd_candidates")
+
+
+def spd_search(plan: Plan, x: int, mu: int, sigma: int, snr: int, width_idx: int,
+               threshold: float, peak_radius: int, out: int, cap: int, count: int, ws: int,
+               ws_bytes: int, stream: int = 0, noise_mode: int = 0):
+    nz = _Noise(int(noise_mode), mu, sigma)
+    _check(load_library().spd_search(ctypes.c_void_p(plan.handle), x, ctypes.byref(nz), snr,
+                                     width_idx, float(threshold), int(peak_radius), out or None,
+                                     int(cap), count, ws, ws_bytes, stream or None), "spd_search")
+
+
+def spd_sync_status(plan: Plan, stream: int = 0):
+    _check(load_library().spd_sync_status(ctypes.c_void_p(plan.handle), stream or None),
+           "spd_sync_status")
+
+
+# ----------------------------------------------------------------------------- torch helpers
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    return 0 if t is None else int(t.data_ptr())
+
+
+def execute(plan: Plan, x, mu, sigma, snr, width_idx, ws, stream=None):
+    """Run ``spd_execute`` on torch CUDA tensors (x: float32 [ndm, ld]; snr float32; width_idx int16/uint16)."""
+    spd_execute(plan, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(snr), _ptr(width_idx), _ptr(ws),
+                ws.numel() * ws.element_size(), _stream(stream))
+
+
+def candidates(plan: Plan, snr, width_idx, threshold: float, peak_radius: int, out, count, ws,
+               use_tile_max: bool = False, stream=None):
+    """Run ``spd_candidates``; ``out`` is a uint8 CUDA tensor of cap*24 bytes, ``count`` int64[1]."""
+    cap = 0 if out is None else out.numel() * out.element_size() // CANDIDATE_DTYPE.itemsize
+    spd_candidates(plan, _ptr(snr), _ptr(width_idx), threshold, peak_radius, _ptr(out), cap,
+                   _ptr(count), _ptr(ws), ws.numel() * ws.element_size(), int(bool(use_tile_max)),
+                   _stream(stream))
+
+
+def search(plan: Plan, x, mu, sigma, snr, width_idx, threshold: float, peak_radius: int, out, count,
+           ws, stream=None):
+    """Run ``spd_search`` (search + candidates) on torch CUDA tensors."""
+    cap = 0 if out is None else out.numel() * out.element_size() // CANDIDATE_DTYPE.itemsize
+    spd_search(plan, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(snr), _ptr(width_idx), threshold,
+               peak_radius, _ptr(out), cap, _ptr(count), _ptr(ws), ws.numel() * ws.element_size(),
+               _stream(stream))
+
+
+def records(out_tensor, count: int):
+    """Host copy of the first ``count`` candidate records as a numpy structured array."""
+    raw = out_tensor[: count * CANDIDATE_DTYPE.itemsize].cpu().numpy()
+    return raw.view(CANDIDATE_DTYPE)

@@ -1,0 +1,363 @@
+// spd_api.cu -- the C ABI of libspd.so: plan construction (width grids of the
+// paper's algorithms), argument validation and kernel launches.  See
+// include/spd.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <new>
+
+#include "spd_internal.h"
+
+namespace {
+
+using spd::kBoxdit;
+using spd::kExhaustive;
+using spd::kIgrid;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2i(int v) {
+  int i = 0;
+  while ((2 << i) <= v) ++i;
+  return i;
+}
+
+// Appends the widths of one level; stops (returns true) once a width >= s_end
+// has been appended, recording the top level and how many of its widths count.
+bool add_level(spd_plan* p, int level, const int* widths, int n, int sep) {
+  p->lvl_first.push_back((int32_t)p->widths.size());
+  for (int q = 0; q < n; ++q) {
+    p->widths.push_back(widths[q]);
+    p->seps.push_back(sep);
+    if (widths[q] >= p->desc.s_end) {
+      p->top = level;
+      p->n_top = q + 1;
+      return true;
+    }
+  }
+  return false;
+}
+
+// BoxDIT (Alg. 1, D = 2, L^i_max = k): iteration i has separation 2^i and the
+// widths L^{i-1}_MAX + 2^i m, m = 1..k, with L^{i-1}_MAX = k (2^i - 1).
+spd_status build_boxdit(spd_plan* p) {
+  const int k = p->k;
+  int w[64];
+  for (int i = 0; i < spd::kMaxLevels; ++i) {
+    const int64_t c = (int64_t)k * ((1LL << i) - 1);
+    for (int m = 1; m <= k; ++m) {
+      const int64_t v = c + ((int64_t)m << i);
+      if (v > (1LL << 30)) return SPD_ERR_INVALID_ARG;
+      w[m - 1] = (int)v;
+    }
+    p->lvl_base.push_back((int32_t)c);
+    if (add_level(p, i, w, k, 1 << i)) return SPD_OK;
+  }
+  return SPD_ERR_INVALID_ARG;
+}
+
+// IGRID IG(d) with P = 2^p layers (Sec. 3.2).  Steps 0..p all have boxcar
+// separation 2^i / P <= 1, so they form level 0 together: step i contributes
+// 2^i + q max(1, 2^(i-d)) for q < 2^min(i, d).  Step p + j (j >= 1) has
+// separation 2^j and the widths 2^j (2^p + q 2^(p-d)), q < 2^d.
+spd_status build_igrid(spd_plan* p) {
+  const int d = p->d, pl = p->pl;
+  int w[64];
+  int n = 0;
+  for (int i = 0; i <= pl; ++i) {
+    const int cnt = 1 << (i < d ? i : d);
+    const int inc = (i >= d) ? (1 << (i - d)) : 1;
+    for (int q = 0; q < cnt; ++q) w[n++] = (1 << i) + q * inc;
+  }
+  p->lvl_base.push_back(0);
+  if (add_level(p, 0, w, n, 1)) return SPD_OK;
+  const int mbase = 1 << pl, mstep = 1 << (pl - d), mm = 1 << d;
+  for (int j = 1; j < spd::kMaxLevels; ++j) {
+    for (int q = 0; q < mm; ++q) {
+      const int64_t v = (int64_t)(mbase + q * mstep) << j;
+      if (v > (1LL << 30)) return SPD_ERR_INVALID_ARG;
+      w[q] = (int)v;
+    }
+    p->lvl_base.push_back(0);
+    if (add_level(p, j, w, mm, 1 << j)) return SPD_OK;
+  }
+  return SPD_ERR_INVALID_ARG;
+}
+
+spd_status check_cuda(cudaError_t e) { return e == cudaSuccess ? SPD_OK : SPD_ERR_CUDA; }
+
+struct WsLayout {
+  size_t tile_max, counts, offsets, total;
+  explicit WsLayout(const spd_plan& p) {
+    const size_t nt = (size_t)(p.desc.ndm * p.tiles_per_row);
+    tile_max = 0;
+    counts = align_up(tile_max + nt * sizeof(float));
+    offsets = align_up(counts + nt * sizeof(int32_t));
+    total = align_up(offsets + nt * sizeof(int64_t));
+  }
+};
+
+spd_status validate_ws(const spd_plan* plan, void* d_ws, size_t ws_bytes) {
+  const WsLayout wl(*plan);
+  if (ws_bytes < wl.total) return SPD_ERR_WORKSPACE_TOO_SMALL;
+  if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0) return SPD_ERR_INVALID_ARG;
+  return SPD_OK;
+}
+
+spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* noise, float* d_snr,
+                      uint16_t* d_width_idx, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+  if (!plan || !d_x || !noise || !d_snr || !d_width_idx) return SPD_ERR_INVALID_ARG;
+  if (noise->mode != 0) return SPD_ERR_UNSUPPORTED;
+  if (!noise->mu || !noise->sigma) return SPD_ERR_INVALID_ARG;
+  if (((uintptr_t)d_x % 4) || ((uintptr_t)d_snr % 4) || ((uintptr_t)d_width_idx % 2))
+    return SPD_ERR_INVALID_ARG;
+  const spd_status ws = validate_ws(plan, d_ws, ws_bytes);
+  if (ws != SPD_OK) return ws;
+  const WsLayout wl(*plan);
+  spd::SearchParams* sp = new (std::nothrow) spd::SearchParams();
+  if (!sp) return SPD_ERR_HOST_ALLOC;
+  spd::SearchParams& p = *sp;
+  p.x = static_cast<const float*>(d_x);
+  p.snr = d_snr;
+  p.widx = d_width_idx;
+  p.tile_max = reinterpret_cast<float*>(static_cast<char*>(d_ws) + wl.tile_max);
+  p.mu = noise->mu;
+  p.sigma = noise->sigma;
+  p.ndm = plan->desc.ndm;
+  p.nt = plan->desc.nt;
+  p.ld = plan->desc.ld;
+  p.tile = plan->tile;
+  p.tiles_per_row = (int32_t)plan->tiles_per_row;
+  p.halo = plan->halo;
+  p.top = plan->top;
+  p.n_top = plan->n_top;
+  p.vec = ((uintptr_t)d_x % 16 == 0 && (uintptr_t)d_snr % 16 == 0 &&
+           (uintptr_t)d_width_idx % 8 == 0 && plan->desc.ld % 4 == 0)
+              ? 1
+              : 0;
+  p.lmax = plan->lend;
+  for (size_t j = 0; j < plan->lvl_first.size() && j < (size_t)spd::kMaxLevels; ++j) {
+    p.lvl_first[j] = plan->lvl_first[j];
+    p.lvl_scale[j] = (float)std::pow(2.0, -0.5 * (double)j);
+  }
+  for (int m = 1; m < 64; ++m) p.rs[m] = (float)(1.0 / std::sqrt((double)m));
+  if (plan->family == kBoxdit) {
+    for (int j = 0; j <= plan->top; ++j)
+      for (int m = 1; m <= plan->k; ++m)
+        p.bscale[j][m] =
+            (float)(1.0 / std::sqrt((double)plan->lvl_base[j] + (double)m * (double)(1 << j)));
+  }
+  const cudaError_t e = spd::launch_search(*plan, p, stream);
+  delete sp;
+  return check_cuda(e);
+}
+
+spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_t* d_width_idx,
+                         float threshold, int32_t peak_radius, spd_candidate* d_out, int64_t cap,
+                         int64_t* d_count, void* d_ws, size_t ws_bytes, bool use_tile_max,
+                         cudaStream_t stream) {
+  if (!plan || !d_snr || !d_width_idx || !d_count) return SPD_ERR_INVALID_ARG;
+  if (cap < 0 || (cap > 0 && !d_out)) return SPD_ERR_INVALID_ARG;
+  if (peak_radius < 0 || peak_radius > spd::kMaxPeakRadius) return SPD_ERR_INVALID_ARG;
+  if (std::isnan(threshold)) return SPD_ERR_INVALID_ARG;
+  if (((uintptr_t)d_count % 8) || ((uintptr_t)d_out % 8)) return SPD_ERR_INVALID_ARG;
+  const spd_status ws = validate_ws(plan, d_ws, ws_bytes);
+  if (ws != SPD_OK) return ws;
+  const WsLayout wl(*plan);
+  spd::CandParams* cp = new (std::nothrow) spd::CandParams();
+  if (!cp) return SPD_ERR_HOST_ALLOC;
+  spd::CandParams& p = *cp;
+  char* base = static_cast<char*>(d_ws);
+  p.snr = d_snr;
+  p.widx = d_width_idx;
+  p.tile_max = use_tile_max ? reinterpret_cast<const float*>(base + wl.tile_max) : nullptr;
+  p.counts = reinterpret_cast<int32_t*>(base + wl.counts);
+  p.offsets = reinterpret_cast<int64_t*>(base + wl.offsets);
+  p.out = d_out;
+  p.d_count = d_count;
+  p.ndm = plan->desc.ndm;
+  p.nt = plan->desc.nt;
+  p.ld = plan->desc.ld;
+  p.cap = cap;
+  p.tile = plan->tile;
+  p.tiles_per_row = (int32_t)plan->tiles_per_row;
+  p.radius = peak_radius;
+  p.thr = threshold;
+  p.width_mode = plan->family == kExhaustive ? 0 : 1;
+  if (p.width_mode)
+    for (size_t i = 0; i < plan->widths.size() && i < 512; ++i) p.width_tab[i] = plan->widths[i];
+  const cudaError_t e = spd::launch_candidates(*plan, p, stream);
+  delete cp;
+  return check_cuda(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* spd_status_string(spd_status s) {
+  switch (s) {
+    case SPD_OK: return "ok";
+    case SPD_ERR_INVALID_ARG: return "invalid argument";
+    case SPD_ERR_UNSUPPORTED: return "unsupported in this build";
+    case SPD_ERR_CUDA: return "CUDA error";
+    case SPD_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case SPD_ERR_BUFFER_TOO_SMALL: return "buffer too small";
+    case SPD_ERR_TIMEOUT: return "device wait timed out";
+    case SPD_ERR_HOST_ALLOC: return "host allocation failed";
+  }
+  return "unknown status";
+}
+
+const char* spd_version(void) { return "0.1"; }
+
+spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
+  if (!out) return SPD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc) return SPD_ERR_INVALID_ARG;
+  const spd_plan_desc& d = *desc;
+  if (d.ndm < 1 || d.nt < 1 || d.ld < d.nt || d.s_end < 1) return SPD_ERR_INVALID_ARG;
+  if (d.ndm > (int64_t)1 << 24 || d.nt > (int64_t)1 << 40) return SPD_ERR_INVALID_ARG;
+  if (d.dtype < SPD_F32 || d.dtype > SPD_U8) return SPD_ERR_INVALID_ARG;
+  if (d.algo < SPD_ALGO_EXHAUSTIVE || d.algo > SPD_ALGO_IGRID) return SPD_ERR_INVALID_ARG;
+  if (d.dtype != SPD_F32) return SPD_ERR_UNSUPPORTED;
+  spd_plan* p = new (std::nothrow) spd_plan();
+  if (!p) return SPD_ERR_HOST_ALLOC;
+  p->desc = d;
+  spd_status st = SPD_OK;
+  try {
+    if (d.algo == SPD_ALGO_EXHAUSTIVE) {
+      if (d.s_end > spd::kMaxExhaustive) {
+        st = SPD_ERR_INVALID_ARG;
+      } else {
+        p->family = kExhaustive;
+        for (int w = 1; w <= d.s_end; ++w) {
+          p->widths.push_back(w);
+          p->seps.push_back(1);
+        }
+        p->lvl_first.push_back(0);
+        p->lvl_base.push_back(0);
+        p->top = 0;
+        p->n_top = d.s_end;
+      }
+    } else if (d.algo == SPD_ALGO_BOXDIT) {
+      if (d.boxdit_lmax != 8 && d.boxdit_lmax != 16 && d.boxdit_lmax != 32) {
+        st = SPD_ERR_INVALID_ARG;
+      } else {
+        p->family = kBoxdit;
+        p->k = d.boxdit_lmax;
+        st = build_boxdit(p);
+      }
+    } else {
+      const int dd = d.igrid_depth, P = d.igrid_layers;
+      if (dd < 0 || dd > 3 || !is_pow2(P) || P < (1 << dd) || P > (2 << dd)) {
+        st = SPD_ERR_INVALID_ARG;
+      } else {
+        p->family = kIgrid;
+        p->d = dd;
+        p->pl = ilog2i(P);
+        st = build_igrid(p);
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    st = SPD_ERR_HOST_ALLOC;
+  }
+  if (st != SPD_OK) {
+    delete p;
+    return st;
+  }
+  p->lend = p->widths.back();
+  if (p->lend > spd::kMaxLend || p->widths.size() > 65535 ||
+      (p->family != kExhaustive && p->widths.size() > 512) || p->top >= spd::kMaxLevels) {
+    delete p;
+    return SPD_ERR_INVALID_ARG;
+  }
+  if (p->family == kExhaustive) {
+    p->tile = spd::kChunk;
+    p->halo = 0;
+  } else {
+    int64_t T = 16384;
+    int64_t np2 = spd::kChunk;
+    while (np2 < d.nt && np2 < T) np2 <<= 1;
+    T = np2;
+    while (T < ((int64_t)1 << p->top)) T <<= 1;
+    p->tile = (int)T;
+    p->halo = (p->lend + 127) / 128 * 128;
+  }
+  p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
+  if (p->desc.ndm * p->tiles_per_row > ((int64_t)1 << 31) - 1 ||
+      spd::search_smem_bytes(*p) > 227 * 1024) {
+    delete p;
+    return SPD_ERR_UNSUPPORTED;
+  }
+  *out = p;
+  return SPD_OK;
+}
+
+spd_status spd_plan_destroy(spd_plan* plan) {
+  delete plan;
+  return SPD_OK;
+}
+
+spd_status spd_plan_widths(const spd_plan* plan, int32_t* widths, int32_t* seps, int32_t cap,
+                           int32_t* n) {
+  if (!plan || !n) return SPD_ERR_INVALID_ARG;
+  const int32_t cnt = (int32_t)plan->widths.size();
+  *n = cnt;
+  if (!widths && !seps) return SPD_OK;
+  if (cap < cnt) return SPD_ERR_BUFFER_TOO_SMALL;
+  for (int32_t i = 0; i < cnt; ++i) {
+    if (widths) widths[i] = plan->widths[i];
+    if (seps) seps[i] = plan->seps[i];
+  }
+  return SPD_OK;
+}
+
+spd_status spd_workspace_size(const spd_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return SPD_ERR_INVALID_ARG;
+  *bytes = WsLayout(*plan).total;
+  return SPD_OK;
+}
+
+spd_status spd_execute(const spd_plan* plan, const void* d_x, const spd_noise* noise, float* d_snr,
+                       uint16_t* d_width_idx, void* d_ws, size_t ws_bytes, spd_stream_t stream) {
+  return do_execute(plan, d_x, noise, d_snr, d_width_idx, d_ws, ws_bytes,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+spd_status spd_candidates(const spd_plan* plan, const float* d_snr, const uint16_t* d_width_idx,
+                          float threshold, int32_t peak_radius, spd_candidate* d_out, int64_t cap,
+                          int64_t* d_count, void* d_ws, size_t ws_bytes, int32_t use_tile_max,
+                          spd_stream_t stream) {
+  return do_candidates(plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count, d_ws,
+                       ws_bytes, use_tile_max != 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+spd_status spd_search(const spd_plan* plan, const void* d_x, const spd_noise* noise, float* d_snr,
+                      uint16_t* d_width_idx, float threshold, int32_t peak_radius,
+                      spd_candidate* d_out, int64_t cap, int64_t* d_count, void* d_ws,
+                      size_t ws_bytes, spd_stream_t stream) {
+  // validate the candidate arguments before queueing the search
+  if (!d_count || cap < 0 || (cap > 0 && !d_out) || peak_radius < 0 ||
+      peak_radius > spd::kMaxPeakRadius || std::isnan(threshold))
+    return SPD_ERR_INVALID_ARG;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const spd_status st = do_execute(plan, d_x, noise, d_snr, d_width_idx, d_ws, ws_bytes, s);
+  if (st != SPD_OK) return st;
+  return do_candidates(plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count, d_ws,
+                       ws_bytes, true, s);
+}
+
+spd_status spd_sync_status(const spd_plan* plan, spd_stream_t stream) {
+  if (!plan) return SPD_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaPeekAtLastError();
+  return check_cuda(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// spd_internal.h -- plan representation and kernel parameter blocks shared by the
+// host side (spd_api.cu) and the kernels of libspd.so.  Not part of the ABI.
+//
+// The searched grids are all written as "levels" (GPU restatement of the
+// paper's iterations/steps):
+//
+//   level j has unit u = 2^j samples; its start samples are s = p * u
+//   (p = level position, so the boxcar separation is L_s = u), and each
+//   candidate width is   L = base_j + m * u   for the block counts m of the level.
+//
+//   * exhaustive (Sec. 3.1, ideal search): one level, u = 1, base 0, m = 1..L_max.
+//   * BoxDIT BD-K (Alg. 1): level i = iteration i, base c_i = K (2^i - 1)
+//     (= L^{i-1}_MAX), m = 1..K; the base sum X_{c_i}[s] is the previous
+//     level's widest boxcar at the same start (X^{i-1} of Alg. 1).
+//   * IGRID IG(d) with P = 2^p layers (Sec. 3.2): steps i <= p all have L_s = 1
+//     and form level 0, with the widths [1, 2^d) and 2^i + q 2^(i-d)
+//     (q < 2^d, d <= i <= p); step p + j (j >= 1) is level j with unit 2^j and
+//     block counts m = 2^p + q 2^(p-d), q < 2^d (Eq. boxcarsize, Table 1).
+//
+// Widths of level j are larger than those of level j-1, so the plan's
+// ascending width table lists the levels one after the other.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "spd.h"
+
+namespace spd {
+
+constexpr int kThreads = 256;      // threads per search CTA
+constexpr int kChunk = 2048;       // starts per sub-chunk of a tile (fine levels)
+constexpr int kMaxLevels = 24;     // levels a plan may have
+constexpr int kMaxLend = 32768;    // largest width a plan may reach
+constexpr int kMaxExhaustive = 4096;
+constexpr int kCandTile = 4096;    // tile of the standalone candidate pass
+constexpr int kMaxPeakRadius = 64;
+
+enum Family { kExhaustive = 0, kBoxdit = 1, kIgrid = 2 };
+
+// Search kernel parameters (passed by value; lives in the constant bank).
+struct SearchParams {
+  const float* x;
+  float* snr;
+  uint16_t* widx;
+  float* tile_max;      // [ndm * tiles_per_row] or nullptr
+  const float* mu;
+  const float* sigma;
+  int64_t ndm, nt, ld;
+  int32_t tile;         // starts per CTA (multiple of kChunk)
+  int32_t tiles_per_row;
+  int32_t halo;         // samples read past the tile for the coarse levels (multiple of 128)
+  int32_t top;          // index of the last level
+  int32_t n_top;        // block counts used on the last level (a prefix of its set)
+  int32_t vec;          // 1: 16-byte vector loads/stores are legal
+  int32_t lmax;         // exhaustive: widest boxcar
+  int32_t lvl_first[kMaxLevels];  // width-table index of each level's first width
+  float lvl_scale[kMaxLevels];    // IGRID: 2^(-j/2), the unit factor of level j
+  float rs[64];                   // rs[m] = 1/sqrt(m) (IGRID block-count factor)
+  float bscale[kMaxLevels][33];   // BoxDIT: 1/sqrt(c_j + m 2^j), m = 1..K
+};
+
+struct CandParams {
+  const float* snr;
+  const uint16_t* widx;
+  const float* tile_max;   // nullptr: scan every tile
+  int32_t* counts;
+  int64_t* offsets;
+  spd_candidate* out;
+  int64_t* d_count;
+  int64_t ndm, nt, ld, cap;
+  int32_t tile, tiles_per_row;
+  int32_t radius;
+  float thr;
+  int32_t width_mode;      // 0: width = index + 1 (exhaustive); 1: width_tab[index]
+  int32_t width_tab[512];  // plan widths (index -> samples) when width_mode == 1
+};
+
+}  // namespace spd
+
+struct spd_plan {
+  spd_plan_desc desc;
+  int family;
+  int k;          // BoxDIT L^i_max
+  int d, pl;      // IGRID depth and log2(layers)
+  int top;        // last level index
+  int n_top;      // block counts used on the last level
+  int lend;       // largest width
+  int tile;       // starts per search CTA
+  int halo;
+  int64_t tiles_per_row;
+  std::vector<int32_t> widths, seps;
+  std::vector<int32_t> lvl_first;
+  std::vector<int32_t> lvl_base;  // base width of each level (BoxDIT c_j)
+};
+
+namespace spd {
+// kernel launchers (spd_search.cu, spd_candidates.cu)
+cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
+cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
+size_t search_smem_bytes(const spd_plan& plan);
+}  // namespace spd

@@ -1,0 +1,115 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+entry point declared in include/spd.h, validates plans, and its width grids
+equal the oracle's (two independent restatements of the paper)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1910_08324_gb300 as spd
+from conftest import ROOT
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "spd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(spd_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = spd.load_library()
+    names = _declared()
+    assert "spd_execute" in names and "spd_search" in names and len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+        assert ctypes.cast(getattr(lib, n), ctypes.c_void_p).value
+
+
+def test_version_and_status_strings():
+    assert spd.spd_version() == "0.1"
+    for s in range(8):
+        assert spd.spd_status_string(s)
+    assert spd.spd_status_string(0) == "ok"
+
+
+GRIDS = [
+    ("exh256", dict(algo=spd.SPD_ALGO_EXHAUSTIVE, s_end=256), lambda: oracle.grid_exhaustive(256)),
+    ("exh1", dict(algo=spd.SPD_ALGO_EXHAUSTIVE, s_end=1), lambda: oracle.grid_exhaustive(1)),
+] + [
+    ("bd%d_%d" % (k, s), dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=k),
+     (lambda k=k, s=s: oracle.grid_boxdit(k, s)))
+    for k in (8, 16, 32) for s in (1, 5, 32, 33, 100, 8192, 20000)
+] + [
+    ("ig%d_%d_%d" % (d, P, s), dict(algo=spd.SPD_ALGO_IGRID, s_end=s, igrid_depth=d, igrid_layers=P),
+     (lambda d=d, P=P, s=s: oracle.grid_igrid(d, P, s)))
+    for d, P in ((0, 1), (0, 2), (1, 2), (1, 4), (2, 4), (2, 8), (3, 8), (3, 16))
+    for s in (1, 3, 7, 16, 31, 100, 8192, 30000)
+]
+
+
+@pytest.mark.parametrize("name,kw,og", GRIDS, ids=[g[0] for g in GRIDS])
+def test_plan_widths_equal_oracle_grid(name, kw, og):
+    plan = spd.spd_plan_create(ndm=4, nt=100000, **kw)
+    w, s = plan.widths()
+    g = og()
+    assert np.array_equal(w, g.L) and np.array_equal(s, g.Ls)
+    assert plan.workspace_size() > 0
+
+
+@pytest.mark.parametrize("kw", [
+    dict(algo=spd.SPD_ALGO_BOXDIT, s_end=100, boxdit_lmax=12),
+    dict(algo=spd.SPD_ALGO_BOXDIT, s_end=100, boxdit_lmax=7),
+    dict(algo=spd.SPD_ALGO_IGRID, s_end=100, igrid_depth=1, igrid_layers=3),
+    dict(algo=spd.SPD_ALGO_IGRID, s_end=100, igrid_depth=2, igrid_layers=2),
+    dict(algo=spd.SPD_ALGO_IGRID, s_end=100, igrid_depth=4, igrid_layers=16),
+    dict(algo=spd.SPD_ALGO_EXHAUSTIVE, s_end=0),
+    dict(algo=spd.SPD_ALGO_EXHAUSTIVE, s_end=5000),
+    dict(algo=spd.SPD_ALGO_IGRID, s_end=40000, igrid_depth=1, igrid_layers=4),
+    dict(algo=7, s_end=10),
+])
+def test_invalid_plans_rejected(kw):
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_plan_create(ndm=4, nt=1000, **kw)
+    assert e.value.status == 1
+
+
+def test_bad_shapes_and_dtypes():
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_plan_create(spd.SPD_ALGO_IGRID, 64, ndm=4, nt=100, ld=50, igrid_depth=1, igrid_layers=4)
+    assert e.value.status == 1
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_plan_create(spd.SPD_ALGO_IGRID, 64, ndm=0, nt=100, igrid_depth=1, igrid_layers=4)
+    assert e.value.status == 1
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_plan_create(spd.SPD_ALGO_IGRID, 64, ndm=4, nt=100, igrid_depth=1, igrid_layers=4,
+                            dtype=spd.SPD_F16)
+    assert e.value.status == 2
+
+
+def test_execute_validates_before_launch():
+    # NULL pointers and a missing workspace are rejected synchronously, no GPU touched.
+    plan = spd.spd_plan_create(spd.SPD_ALGO_IGRID, 64, ndm=4, nt=1000, igrid_depth=1, igrid_layers=4)
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_execute(plan, 0, 0, 0, 0, 0, 0, 0)
+    assert e.value.status == 1
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_execute(plan, 4096, 4096, 4096, 4096, 4096, 0, 0)
+    assert e.value.status == 4  # workspace too small
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_candidates(plan, 4096, 4096, 6.0, 65, 0, 0, 4096, 0, 0, 0)
+    assert e.value.status == 1  # radius above the maximum
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_execute(plan, 4096, 4096, 4096, 4096, 4096, 4096, 1 << 30, noise_mode=1)
+    assert e.value.status == 2  # table noise not in this build
+
+
+def test_widths_buffer_too_small():
+    plan = spd.spd_plan_create(spd.SPD_ALGO_BOXDIT, 8192, ndm=1, nt=100, boxdit_lmax=32)
+    lib = spd.load_library()
+    n = ctypes.c_int32()
+    buf = np.zeros(10, np.int32)
+    st = lib.spd_plan_widths(ctypes.c_void_p(plan.handle), buf.ctypes.data, None, 10, ctypes.byref(n))
+    assert st == 5 and n.value == 257
