@@ -94,7 +94,7 @@ spd_status check_cuda(cudaError_t e) { return e == cudaSuccess ? SPD_OK : SPD_ER
 struct WsLayout {
   size_t tile_max, counts, offsets, total;
   explicit WsLayout(const spd_plan& p) {
-    const size_t nt = (size_t)(p.desc.ndm * p.tiles_per_row);
+    const size_t nt = (size_t)(p.desc.ndm * p.cand_tiles_per_row);
     tile_max = 0;
     counts = align_up(tile_max + nt * sizeof(float));
     offsets = align_up(counts + nt * sizeof(int32_t));
@@ -133,6 +133,7 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   p.ld = plan->desc.ld;
   p.tile = plan->tile;
   p.tiles_per_row = (int32_t)plan->tiles_per_row;
+  p.cand_tiles_per_row = (int32_t)plan->cand_tiles_per_row;
   p.halo = plan->halo;
   p.top = plan->top;
   p.n_top = plan->n_top;
@@ -152,7 +153,11 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
         p.bscale[j][m] =
             (float)(1.0 / std::sqrt((double)plan->lvl_base[j] + (double)m * (double)(1 << j)));
   }
-  const cudaError_t e = spd::launch_search(*plan, p, stream);
+  // tile maxima start at a key below every float (0x80808080)
+  cudaError_t e = cudaMemsetAsync(p.tile_max, 0x80,
+                                  sizeof(float) * (size_t)(plan->desc.ndm * plan->cand_tiles_per_row),
+                                  stream);
+  if (e == cudaSuccess) e = spd::launch_search(*plan, p, stream);
   delete sp;
   return check_cuda(e);
 }
@@ -184,8 +189,8 @@ spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_
   p.nt = plan->desc.nt;
   p.ld = plan->desc.ld;
   p.cap = cap;
-  p.tile = plan->tile;
-  p.tiles_per_row = (int32_t)plan->tiles_per_row;
+  p.tile = spd::kCandTile;
+  p.tiles_per_row = (int32_t)plan->cand_tiles_per_row;
   p.radius = peak_radius;
   p.thr = threshold;
   p.width_mode = plan->family == kExhaustive ? 0 : 1;
@@ -280,6 +285,13 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
   if (p->family == kExhaustive) {
     p->tile = spd::kChunk;
     p->halo = 0;
+  } else if (p->family == kIgrid) {
+    // one CTA streams a segment of up to 131072 starts (a multiple of the
+    // candidate tile); the halo is the widest boxcar, rounded to whole chunks
+    int64_t T = ((d.nt + spd::kCandTile - 1) / spd::kCandTile) * spd::kCandTile;
+    if (T > 131072) T = 131072;
+    p->tile = (int)T;
+    p->halo = ((p->lend + spd::kChunk - 1) / spd::kChunk) * spd::kChunk;
   } else {
     int64_t T = 16384;
     int64_t np2 = spd::kChunk;
@@ -290,6 +302,7 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
     p->halo = (p->lend + 127) / 128 * 128;
   }
   p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
+  p->cand_tiles_per_row = (d.nt + spd::kCandTile - 1) / spd::kCandTile;
   if (p->desc.ndm * p->tiles_per_row > ((int64_t)1 << 31) - 1 ||
       spd::search_smem_bytes(*p) > 227 * 1024) {
     delete p;

@@ -28,6 +28,8 @@ constexpr int kCandThreads = 256;
 constexpr int kScanThreads = 1024;
 constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ float key_to_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
 __device__ __forceinline__ bool is_cand(const float* __restrict__ y, int64_t s, int64_t nt,
                                         float thr, int R) {
   const float v = y[s];
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(kCandThreads) cand_count_kernel(const CandPara
   const int64_t t = blockIdx.x;
   const int64_t row = t / p.tiles_per_row;
   const int64_t t0 = (t % p.tiles_per_row) * (int64_t)p.tile;
-  if (p.tile_max && !(p.tile_max[t] >= p.thr)) {
+  if (p.tile_max && !(key_to_float(reinterpret_cast<const int*>(p.tile_max)[t]) >= p.thr)) {
     if (threadIdx.x == 0) p.counts[t] = 0;
     return;
   }
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(kCandThreads) cand_write_kernel(const CandPara
 }  // namespace
 
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s) {
-  const int64_t ntiles = plan.desc.ndm * plan.tiles_per_row;
+  const int64_t ntiles = plan.desc.ndm * plan.cand_tiles_per_row;
   cand_count_kernel<<<(unsigned)ntiles, kCandThreads, 0, s>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

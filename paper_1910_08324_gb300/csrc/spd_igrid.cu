@@ -1,0 +1,374 @@
+// spd_igrid.cu -- IGRID / DIT search kernel (Sec. 3.2, Alg. 3, Eq. boxcarsize, Table 1).
+//
+// The IGRID grid, written as levels (spd_internal.h): level 0 holds steps
+// 0..p (separation 1); level j >= 1 is step p + j, with unit 2^j and block
+// counts m = 2^p + q 2^(p-d).  The P layers of a step are the P start phases of
+// one block series, so the paper's binary tree of layers is one aligned block
+// pyramid here.
+//
+// One CTA streams one segment of one DM row, 2048-sample chunks at a time,
+// *backwards in time*: when chunk [a, a + 2048) is processed, every block a
+// window starting in it can reach (up to L_end later) has already been seen.
+// Each sample is therefore loaded, normalised and summed exactly once; the
+// segment's first L_end samples past its end are its only re-read (the halo).
+//   step 1  the chunk's 8 samples per thread (prefetched into registers one
+//           chunk earlier) are normalised and reduced in registers and warp
+//           shuffles into levels 0..3 (shared, triple buffered, each with a
+//           lookahead tail copied from the previous chunk) and into ring
+//           buffers for the coarse levels 4.. (unit >= 16);
+//   step 3  one thread per coarse position of the chunk evaluates it from its
+//           ring (scalar loads), results per level to shared memory;
+//   step 5  each thread owns 8 consecutive starts and evaluates levels 0..3
+//           from register windows (8 + 4 + 2 + 1 positions), merges them and
+//           the coarse results in registers (strict '>' in increasing width
+//           order), and writes 8 SNRs (2 x float4) and 8 widths (uint4).
+// Two barriers per chunk.  Samples past the end of the row are -inf, so a
+// boxcar needing them never wins (the s + L <= nt rule).
+#include "spd_common.cuh"
+
+namespace spd {
+namespace {
+
+constexpr int kC = kChunk;            // starts per chunk
+constexpr int kSpt = kC / kThreads;   // starts per thread
+static_assert(kSpt == 8, "the per-thread level layout assumes 8 starts per thread");
+constexpr int kRing0 = 4;             // first coarse (ring) level
+constexpr int kChunkLog = 11;         // log2(kC): levels above it span several chunks
+static_assert((1 << kChunkLog) == kC, "chunk must be 2^11");
+constexpr int kResHi = 256;           // RES slots of levels > kChunkLog start here
+
+__host__ __device__ constexpr int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+template <int D, int PL>
+struct IgS {
+  using SM = IgM<D, PL>;
+  using S0 = Ig0<D, PL>;
+  static constexpr int MMAX = SM::MMAX;
+  static constexpr int NW0 = cdiv(7 + MMAX, 4);  // float4 window of level 0 (starts 8t..8t+7)
+  static constexpr int NW1 = cdiv(3 + MMAX, 4);  // float4 window of level 1 (4 positions)
+  static constexpr int NW2 = cdiv(1 + MMAX, 2);  // float2 window of level 2 (2 positions)
+  static constexpr int NW3 = MMAX;               // scalar window of level 3 (1 position)
+  static constexpr int TL0 = 4 * NW0 - 8;        // lookahead tails (values past the chunk)
+  static constexpr int TL1 = 4 * NW1 - 4;
+  static constexpr int TL2 = 2 * NW2 - 2;
+  static constexpr int TL3 = NW3 - 1;
+};
+
+// Shared-memory layout: three buffers of levels 0..3 (compile-time strides),
+// then the rings of levels 4..top, the per-chunk coarse results and a small
+// table of ring offsets/masks.
+template <int D, int PL>
+struct IgFix {
+  using S = IgS<D, PL>;
+  static constexpr int O1 = al4(kC + S::TL0);
+  static constexpr int O2 = O1 + al4(kC / 2 + S::TL1);
+  static constexpr int O3 = O2 + al4(kC / 4 + S::TL2);
+  static constexpr int FB = O3 + al4(kC / 8 + S::TL3);  // one buffer of levels 0..3
+  __host__ __device__ static constexpr int f0(int b) { return b * FB; }
+  __host__ __device__ static constexpr int f1(int b) { return b * FB + O1; }
+  __host__ __device__ static constexpr int f2(int b) { return b * FB + O2; }
+  __host__ __device__ static constexpr int f3(int b) { return b * FB + O3; }
+  static constexpr int RINGS = 3 * FB;
+};
+
+__host__ __device__ inline int ring_size(int j, int H, int mmax) {
+  return next_pow2(cdiv(kC + H, 1 << j) + mmax + 2);
+}
+
+// offsets (floats) of: rings end, RES_Y, RES_W, table, total
+struct IgDyn {
+  int res_y, res_w, tab, total;
+  __host__ __device__ IgDyn(int rings, int H, int top, int mmax) {
+    int o = rings;
+    for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, H, mmax));
+    res_y = o;
+    o += kResHi + kMaxLevels;
+    res_w = o;
+    o += (kResHi + kMaxLevels) / 2;
+    tab = o;
+    o += 2 * kMaxLevels;
+    total = o;
+  }
+};
+
+template <int D, int PL, bool COARSE>
+__global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
+    igrid_stream_kernel(const SearchParams p) {
+  using S = IgS<D, PL>;
+  using FX = IgFix<D, PL>;
+  using SM = typename S::SM;
+  using S0 = typename S::S0;
+  constexpr int MMAX = S::MMAX;
+  extern __shared__ __align__(16) float smem[];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t row = blockIdx.x / p.tiles_per_row;
+  const int64_t t0 = (blockIdx.x % p.tiles_per_row) * (int64_t)p.tile;
+  const int top = p.top;
+  const int64_t nt = p.nt;
+  const bool vec = p.vec != 0;
+  const float* __restrict__ xrow = p.x + row * p.ld;
+  float* __restrict__ yrow = p.snr + row * p.ld;
+  uint16_t* __restrict__ wrow = p.widx + row * p.ld;
+  const float mu = p.mu[row];
+  const float inv = 1.0f / p.sigma[row];
+  const IgDyn L(FX::RINGS, p.halo, top, MMAX);
+  auto rsM = [&](auto M) { return p.rs[decltype(M)::value]; };
+  float* RESY = smem + L.res_y;
+  uint16_t* RESW = reinterpret_cast<uint16_t*>(smem + L.res_w);
+  int* RTAB = reinterpret_cast<int*>(smem + L.tab);  // [2j]: ring offset, [2j+1]: mask
+
+  // -inf everywhere a chunk past the end of the row would have written
+  for (int i = t; i < L.tab; i += kThreads) smem[i] = ninf();
+  if (t == 0) {
+    int o = FX::RINGS;
+    for (int j = 0; j < kMaxLevels; ++j) {
+      RTAB[2 * j] = 0;
+      RTAB[2 * j + 1] = 0;
+    }
+    for (int j = kRing0; j <= top; ++j) {
+      const int n = ring_size(j, p.halo, MMAX);
+      RTAB[2 * j] = o;
+      RTAB[2 * j + 1] = n - 1;
+      o += al4(n);
+    }
+  }
+  __syncthreads();
+  int r4 = 0, m4 = 0, r5 = 0, m5 = 0, r6 = 0, m6 = 0, r7 = 0, m7 = 0, r8 = 0, m8 = 0;
+  if (COARSE) {
+    r4 = RTAB[8], m4 = RTAB[9], r5 = RTAB[10], m5 = RTAB[11], r6 = RTAB[12], m6 = RTAB[13];
+    r7 = RTAB[14], m7 = RTAB[15], r8 = RTAB[16], m8 = RTAB[17];
+  }
+
+  const int64_t a_hi = t0 + p.tile + p.halo - kC;
+  int64_t a_first = a_hi;
+  if (a_first >= nt) a_first = ((nt - 1) / kC) * kC;  // chunks at or past nt are all -inf
+  float4 nx0 = make_float4(0.f, 0.f, 0.f, 0.f), nx1 = nx0;
+  if (a_first >= t0) {
+    nx0 = load_x4(xrow, a_first + 8 * t, nt, vec);
+    nx1 = load_x4(xrow, a_first + 8 * t + 4, nt, vec);
+  }
+  float tmax = ninf();
+  int k = (int)((a_hi - a_first) / kC);  // chunk counter (selects the buffer triple)
+  for (int64_t a = a_first; a >= t0; a -= kC, ++k) {
+    const int buf = k % 3, nbuf = (k + 1) % 3;
+    const bool body = a < t0 + p.tile;
+    // ---- step 1: normalise, build levels 0..3 and the ring entries --------
+    const float4 v0 = norm4(nx0, mu, inv), v1 = norm4(nx1, mu, inv);
+    if (a - kC >= t0) {
+      nx0 = load_x4(xrow, a - kC + 8 * t, nt, vec);
+      nx1 = load_x4(xrow, a - kC + 8 * t + 4, nt, vec);
+    }
+    {
+      float* F0 = smem + FX::f0(buf);
+      *reinterpret_cast<float4*>(F0 + 8 * t) = v0;
+      *reinterpret_cast<float4*>(F0 + 8 * t + 4) = v1;
+      if (8 * t < S::TL0) {
+        float* T0 = smem + FX::f0(nbuf) + kC + 8 * t;
+        *reinterpret_cast<float4*>(T0) = v0;
+        if (8 * t + 4 < S::TL0) *reinterpret_cast<float4*>(T0 + 4) = v1;
+      }
+      const float p0 = v0.x + v0.y, p1 = v0.z + v0.w, p2 = v1.x + v1.y, p3 = v1.z + v1.w;
+      const float4 pp = make_float4(p0, p1, p2, p3);
+      *reinterpret_cast<float4*>(smem + FX::f1(buf) + 4 * t) = pp;
+      if (4 * t < S::TL1) *reinterpret_cast<float4*>(smem + FX::f1(nbuf) + kC / 2 + 4 * t) = pp;
+      const float q0 = p0 + p1, q1 = p2 + p3;
+      *reinterpret_cast<float2*>(smem + FX::f2(buf) + 2 * t) = make_float2(q0, q1);
+      if (2 * t < S::TL2) *reinterpret_cast<float2*>(smem + FX::f2(nbuf) + kC / 4 + 2 * t) = make_float2(q0, q1);
+      const float o8 = q0 + q1;
+      smem[FX::f3(buf) + t] = o8;
+      if (t < S::TL3) smem[FX::f3(nbuf) + kC / 8 + t] = o8;
+      if (COARSE) {
+        float s = o8 + __shfl_xor_sync(kFull, o8, 1);
+        if (!(lane & 1)) smem[r4 + (int)(((a >> 4) + (t >> 1)) & m4)] = s;
+        if (top >= 5) {
+          s += __shfl_xor_sync(kFull, s, 2);
+          if (!(lane & 3)) smem[r5 + (int)(((a >> 5) + (t >> 2)) & m5)] = s;
+        }
+        if (top >= 6) {
+          s += __shfl_xor_sync(kFull, s, 4);
+          if (!(lane & 7)) smem[r6 + (int)(((a >> 6) + (t >> 3)) & m6)] = s;
+        }
+        if (top >= 7) {
+          s += __shfl_xor_sync(kFull, s, 8);
+          if (!(lane & 15)) smem[r7 + (int)(((a >> 7) + (t >> 4)) & m7)] = s;
+        }
+        if (top >= 8) {
+          s += __shfl_xor_sync(kFull, s, 16);
+          if (lane == 0) smem[r8 + (int)(((a >> 8) + warp) & m8)] = s;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- step 2/3: blocks of levels 9.. (one warp) and coarse evaluation --
+    if (COARSE) {
+      if (warp == kThreads / 32 - 1 && top >= 9) {
+        for (int j = 9; j <= top; ++j) {
+          const int nb = (j <= kChunkLog) ? (kC >> j) : ((a & ((1LL << j) - 1)) == 0 ? 1 : 0);
+          if (lane < nb) {
+            const int64_t n = (a >> j) + lane;
+            const float* R = smem + RTAB[2 * (j - 1)];
+            const int m = RTAB[2 * (j - 1) + 1];
+            smem[RTAB[2 * j] + (int)(n & RTAB[2 * j + 1])] = R[(int)((2 * n) & m)] + R[(int)((2 * n + 1) & m)];
+          }
+          __syncwarp();
+        }
+      }
+      if (body) {
+        const int ctop = top < kChunkLog ? top : kChunkLog;
+        const int npos = 256 - (1 << (kChunkLog - ctop));  // positions of levels 4..ctop
+        int j = -1, q = 0;
+        if (t < npos) {
+          j = kRing0;
+          int off = 0;
+          while (t >= off + (kC >> j)) {
+            off += kC >> j;
+            ++j;
+          }
+          q = t - off;
+        } else if (t == kThreads - 1 && top > kChunkLog) {
+          j = 0;  // levels above the chunk size: handled below by this thread
+        }
+        auto eval_coarse = [&](int jj, int64_t n, int slot) {
+          float w[MMAX];
+          const float* R = smem + RTAB[2 * jj];
+          const int m = RTAB[2 * jj + 1];
+#pragma unroll
+          for (int i = 0; i < MMAX; ++i) w[i] = R[(int)((n + i) & m)];
+          float bv[1], full[1];
+          int bq[1];
+          const int nu = (jj == top) ? p.n_top : SM::MM;
+          eval_window<1, MMAX, SM, true, false>(w, nu, rsM, nullptr, bv, bq, full);
+          RESY[slot] = bv[0] * p.lvl_scale[jj];
+          RESW[slot] = (uint16_t)(p.lvl_first[jj] + bq[0]);
+        };
+        if (j >= kRing0) {
+          eval_coarse(j, (a >> j) + q, t);
+        } else if (j == 0) {
+          for (int jj = kChunkLog + 1; jj <= top; ++jj)
+            if ((a & ((1LL << jj) - 1)) == 0) eval_coarse(jj, a >> jj, kResHi + jj - kChunkLog - 1);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- step 5: per-thread levels 0..3, merge, write ----------------------
+    if (body) {
+      float y[8];
+      int w[8];
+      {
+        float win[S::NW0 * 4], full[8];
+        load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
+        if (!COARSE && top == 0)
+          eval_window<8, MMAX, S0, true, false>(win, p.n_top, rsM, nullptr, y, w, full);
+        else
+          eval_window<8, MMAX, S0, false, false>(win, p.n_top, rsM, nullptr, y, w, full);
+      }
+      if (COARSE || top >= 1) {
+        float win[S::NW1 * 4], bv[4], full[4];
+        int bq[4];
+        load_window4<S::NW1>(smem + FX::f1(buf) + 4 * t, win);
+        if (!COARSE && top == 1)
+          eval_window<4, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        else
+          eval_window<4, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        const float f = p.lvl_scale[1];
+        const int first = p.lvl_first[1];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) merge1(y[2 * r], w[2 * r], bv[r] * f, first + bq[r]);
+      }
+      if (COARSE || top >= 2) {
+        float win[S::NW2 * 2], bv[2], full[2];
+        int bq[2];
+        load_window2<S::NW2>(smem + FX::f2(buf) + 2 * t, win);
+        if (!COARSE && top == 2)
+          eval_window<2, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        else
+          eval_window<2, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        const float f = p.lvl_scale[2];
+        const int first = p.lvl_first[2];
+        merge1(y[0], w[0], bv[0] * f, first + bq[0]);
+        merge1(y[4], w[4], bv[1] * f, first + bq[1]);
+      }
+      if (COARSE || top >= 3) {
+        float win[S::NW3], bv[1], full[1];
+        int bq[1];
+        load_window1<S::NW3>(smem + FX::f3(buf) + t, win);
+        if (!COARSE && top == 3)
+          eval_window<1, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        else
+          eval_window<1, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        merge1(y[0], w[0], bv[0] * p.lvl_scale[3], p.lvl_first[3] + bq[0]);
+      }
+      if (COARSE) {
+        const int ctop = top < kChunkLog ? top : kChunkLog;
+        for (int j = kRing0; j <= ctop; ++j) {
+          if (t & ((1 << (j - 3)) - 1)) break;
+          const int slot = 256 - (1 << (kChunkLog + 1 - j)) + (t >> (j - 3));
+          merge1(y[0], w[0], RESY[slot], RESW[slot]);
+        }
+        if (t == 0)
+          for (int jj = kChunkLog + 1; jj <= top; ++jj)
+            if ((a & ((1LL << jj) - 1)) == 0) {
+              const int slot = kResHi + jj - kChunkLog - 1;
+              merge1(y[0], w[0], RESY[slot], RESW[slot]);
+            }
+      }
+      const int64_t s0 = a + 8 * t;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (s0 + r < nt) tmax = fmaxf(tmax, y[r]);
+      store8(yrow, wrow, s0, nt, vec, y, w);
+      if ((a % kCandTile) == 0) {  // last chunk of a candidate tile (we walk backwards)
+        tile_max_atomic(p, row, a, tmax);
+        tmax = ninf();
+      }
+    }
+  }
+}
+
+}  // namespace
+
+size_t igrid_smem_bytes(const spd_plan& plan) {
+  switch (plan.d * 8 + plan.pl) {
+#define SPD_IG_CASE(D, PL) \
+  case D * 8 + PL:         \
+    return sizeof(float) * (size_t)IgDyn(IgFix<D, PL>::RINGS, plan.halo, plan.top, IgS<D, PL>::MMAX).total;
+    SPD_IG_CASE(0, 0)
+    SPD_IG_CASE(0, 1)
+    SPD_IG_CASE(1, 1)
+    SPD_IG_CASE(1, 2)
+    SPD_IG_CASE(2, 2)
+    SPD_IG_CASE(2, 3)
+    SPD_IG_CASE(3, 3)
+    SPD_IG_CASE(3, 4)
+#undef SPD_IG_CASE
+    default: return 0;
+  }
+}
+
+cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
+  const size_t smem = igrid_smem_bytes(plan);
+  const int64_t nblk = plan.desc.ndm * plan.tiles_per_row;
+  const bool coarse = plan.top >= kRing0;
+  switch (plan.d * 8 + plan.pl) {
+#define SPD_IG_LAUNCH(D, PL)                                                              \
+  case D * 8 + PL:                                                                        \
+    return coarse ? launch_one(igrid_stream_kernel<D, PL, true>, smem, nblk, p, s)        \
+                  : launch_one(igrid_stream_kernel<D, PL, false>, smem, nblk, p, s);
+    SPD_IG_LAUNCH(0, 0)
+    SPD_IG_LAUNCH(0, 1)
+    SPD_IG_LAUNCH(1, 1)
+    SPD_IG_LAUNCH(1, 2)
+    SPD_IG_LAUNCH(2, 2)
+    SPD_IG_LAUNCH(2, 3)
+    SPD_IG_LAUNCH(3, 3)
+    SPD_IG_LAUNCH(3, 4)
+#undef SPD_IG_LAUNCH
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace spd

@@ -35,7 +35,7 @@ constexpr int kChunk = 2048;       // starts per sub-chunk of a tile (fine level
 constexpr int kMaxLevels = 24;     // levels a plan may have
 constexpr int kMaxLend = 32768;    // largest width a plan may reach
 constexpr int kMaxExhaustive = 4096;
-constexpr int kCandTile = 4096;    // tile of the standalone candidate pass
+constexpr int kCandTile = 16384;   // starts per candidate tile (tile maxima granularity)
 constexpr int kMaxPeakRadius = 64;
 
 enum Family { kExhaustive = 0, kBoxdit = 1, kIgrid = 2 };
@@ -45,12 +45,13 @@ struct SearchParams {
   const float* x;
   float* snr;
   uint16_t* widx;
-  float* tile_max;      // [ndm * tiles_per_row] or nullptr
+  float* tile_max;      // [ndm * cand_tiles_per_row] ordered-int keys of tile maxima (or nullptr)
   const float* mu;
   const float* sigma;
   int64_t ndm, nt, ld;
   int32_t tile;         // starts per CTA (multiple of kChunk)
   int32_t tiles_per_row;
+  int32_t cand_tiles_per_row;  // ceil(nt / kCandTile)
   int32_t halo;         // samples read past the tile for the coarse levels (multiple of 128)
   int32_t top;          // index of the last level
   int32_t n_top;        // block counts used on the last level (a prefix of its set)
@@ -65,7 +66,7 @@ struct SearchParams {
 struct CandParams {
   const float* snr;
   const uint16_t* widx;
-  const float* tile_max;   // nullptr: scan every tile
+  const float* tile_max;   // ordered-int keys (see fkey) of tile maxima; nullptr: scan every tile
   int32_t* counts;
   int64_t* offsets;
   spd_candidate* out;
@@ -90,7 +91,8 @@ struct spd_plan {
   int lend;       // largest width
   int tile;       // starts per search CTA
   int halo;
-  int64_t tiles_per_row;
+  int64_t tiles_per_row;       // search CTAs per row
+  int64_t cand_tiles_per_row;  // candidate tiles (kCandTile starts) per row
   std::vector<int32_t> widths, seps;
   std::vector<int32_t> lvl_first;
   std::vector<int32_t> lvl_base;  // base width of each level (BoxDIT c_j)
@@ -99,6 +101,8 @@ struct spd_plan {
 namespace spd {
 // kernel launchers (spd_search.cu, spd_candidates.cu)
 cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
+cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
+size_t igrid_smem_bytes(const spd_plan& plan);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
 size_t search_smem_bytes(const spd_plan& plan);
 }  // namespace spd

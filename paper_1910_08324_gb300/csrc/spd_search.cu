@@ -25,153 +25,24 @@
 //   * the tile's largest SNR goes to the workspace for the candidate step.
 // Samples past the end of a row load as -inf, so a boxcar that would need
 // them sums to -inf and can never be the maximum: that is the rule s + L <= nt.
-#include <cuda_runtime.h>
-
-#include <cstdint>
-#include <type_traits>
-
-#include "spd_internal.h"
+#include "spd_common.cuh"
 
 namespace spd {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kItems0 = kChunk / 4 / kThreads;  // level-0 items (4 starts) per thread per sub-chunk
 static_assert(kItems0 * 4 * kThreads == kChunk, "sub-chunk must split evenly");
 
-__device__ __forceinline__ float ninf() { return __int_as_float(0xff800000u); }
-
-template <int I, int N, class F>
-__device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (I < N) {
-    f(std::integral_constant<int, I>{});
-    static_for<I + 1, N>(f);
-  }
-}
-
-__host__ __device__ inline int al4(int v) { return (v + 3) & ~3; }
-
-// z-values of samples [pos, pos + 4) of one row; -inf at and past nt.
-__device__ __forceinline__ float4 load_z4(const float* __restrict__ row, int64_t pos, int64_t nt,
-                                          bool vec, float mu, float inv) {
-  float4 v;
-  if (vec && pos + 4 <= nt) {
-    v = __ldg(reinterpret_cast<const float4*>(row + pos));
-    v.x = (v.x - mu) * inv;
-    v.y = (v.y - mu) * inv;
-    v.z = (v.z - mu) * inv;
-    v.w = (v.w - mu) * inv;
-  } else {
-    v.x = (pos + 0 < nt) ? (__ldg(row + pos + 0) - mu) * inv : ninf();
-    v.y = (pos + 1 < nt) ? (__ldg(row + pos + 1) - mu) * inv : ninf();
-    v.z = (pos + 2 < nt) ? (__ldg(row + pos + 2) - mu) * inv : ninf();
-    v.w = (pos + 3 < nt) ? (__ldg(row + pos + 3) - mu) * inv : ninf();
-  }
-  return v;
-}
-
-__device__ __forceinline__ void store4(float* __restrict__ yrow, uint16_t* __restrict__ wrow,
-                                       int64_t s0, int64_t nt, bool vec, const float (&y)[4],
-                                       const int (&w)[4]) {
-  if (vec && s0 + 4 <= nt) {
-    __stcs(reinterpret_cast<float4*>(yrow + s0), make_float4(y[0], y[1], y[2], y[3]));
-    uint2 pk;
-    pk.x = (uint32_t)(w[0] & 0xffff) | ((uint32_t)w[1] << 16);
-    pk.y = (uint32_t)(w[2] & 0xffff) | ((uint32_t)w[3] << 16);
-    __stcs(reinterpret_cast<uint2*>(wrow + s0), pk);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (s0 + k < nt) {
-        yrow[s0 + k] = y[k];
-        wrow[s0 + k] = (uint16_t)w[k];
-      }
-  }
-}
-
-// Candidate block-count sets --------------------------------------------------
-struct AllM {  // every block count 1..MMAX (BoxDIT iterations, the exhaustive search)
-  __host__ __device__ static constexpr bool in(int) { return true; }
-  __host__ __device__ static constexpr int rank(int m) { return m - 1; }
-};
-
-template <int D, int PL>
-struct IgM {  // IGRID levels j >= 1: m = 2^p + q 2^(p-d), q < 2^d (Eq. boxcarsize)
-  static constexpr int MM = 1 << D, MBASE = 1 << PL, MSTEP = 1 << (PL - D);
-  static constexpr int MMAX = MBASE + (MM - 1) * MSTEP;
-  __host__ __device__ static constexpr bool in(int m) {
-    return m >= MBASE && m <= MMAX && (m - MBASE) % MSTEP == 0;
-  }
-  __host__ __device__ static constexpr int rank(int m) { return (m - MBASE) / MSTEP; }
-};
-
-template <int D, int PL>
-struct Ig0 {  // IGRID level 0: steps 0..p, all at separation 1
-  static constexpr int MMAX = IgM<D, PL>::MMAX;
-  __host__ __device__ static constexpr int ilog2(int m) {
-    int i = 0;
-    while ((2 << i) <= m) ++i;
-    return i;
-  }
-  __host__ __device__ static constexpr bool in(int m) {
-    return m >= 1 && m <= MMAX &&
-           (m < (1 << D) ||
-            (ilog2(m) <= PL && ((m - (1 << ilog2(m))) % (1 << (ilog2(m) - D))) == 0));
-  }
-  __host__ __device__ static constexpr int rank(int m) {
-    int r = 0;
-    for (int q = 1; q < m; ++q) r += in(q) ? 1 : 0;
-    return r;
-  }
-};
-
-// Evaluate 4 consecutive positions p0..p0+3 (p0 % 4 == 0) of one level.
-// Running sums over the block series `blk` start from base[r] (or 0) and add
-// block counts m = 1..MMAX in order; at every m of the set the sum times
-// scale(m) is compared (strict '>') against the best so far.  Returns the best
-// value and its rank within the set, and the full MMAX-block sum.
+// Evaluate 4 consecutive positions p0..p0+3 (p0 % 4 == 0) of one level whose
+// block series `blk` is in shared memory (see eval_window).
 template <int MMAX, class Pred, bool PARTIAL, bool HAS_BASE, class Scale>
 __device__ __forceinline__ void eval4(const float* __restrict__ blk, int p0, int n_used,
                                       Scale&& scale, const float (&base)[4], float (&bv)[4],
                                       int (&bq)[4], float (&full)[4]) {
   constexpr int NW = (MMAX + 6) / 4;
   float w[NW * 4];
-  static_for<0, NW>([&](auto K) {
-    constexpr int k = decltype(K)::value;
-    const float4 t = *reinterpret_cast<const float4*>(blk + p0 + 4 * k);
-    w[4 * k + 0] = t.x;
-    w[4 * k + 1] = t.y;
-    w[4 * k + 2] = t.z;
-    w[4 * k + 3] = t.w;
-  });
-  static_for<0, 4>([&](auto R) {
-    constexpr int r = decltype(R)::value;
-    float S = HAS_BASE ? base[r] : 0.0f;
-    float best = ninf();
-    int q = 0;
-    static_for<1, MMAX + 1>([&](auto M) {
-      constexpr int m = decltype(M)::value;
-      S += w[r + m - 1];
-      if constexpr (Pred::in(m)) {
-        constexpr int rk = Pred::rank(m);
-        const float v = S * scale(M);
-        if constexpr (rk == 0) {
-          best = v;
-          q = 0;
-        } else {
-          if (!PARTIAL || rk < n_used) {
-            if (v > best) {
-              best = v;
-              q = rk;
-            }
-          }
-        }
-      }
-    });
-    bv[r] = best;
-    bq[r] = q;
-    full[r] = S;
-  });
+  load_window4<NW>(blk + p0, w);
+  eval_window<4, MMAX, Pred, PARTIAL, HAS_BASE>(w, n_used, scale, base, bv, bq, full);
 }
 
 __device__ __forceinline__ void rmw(float* by, uint16_t* bw, int idx, float y, int w) {
@@ -179,240 +50,6 @@ __device__ __forceinline__ void rmw(float* by, uint16_t* bw, int idx, float y, i
     by[idx] = y;
     bw[idx] = (uint16_t)w;
   }
-}
-
-// Block-wide max of v; thread 0 writes it.
-__device__ __forceinline__ void tile_max_store(float v, float* red, float* out) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float m = red[0];
-    for (int k = 1; k < kThreads / 32; ++k) m = fmaxf(m, red[k]);
-    *out = m;
-  }
-}
-
-// ============================================================================ IGRID
-constexpr int kIgCoarse = 3;  // IGRID levels >= 3 (unit >= 8) are coarse
-
-struct IgLayout {
-  int lvl[kMaxLevels];
-  int bc_y, bc_w, f0, f1, f2, be_y, be_w, red, total;
-  __host__ __device__ IgLayout(int T, int H, int top) {
-    int o = 0;
-    for (int j = 0; j < kMaxLevels; ++j) lvl[j] = 0;
-    bc_y = bc_w = 0;
-    if (top >= kIgCoarse) {
-      for (int j = kIgCoarse; j <= top; ++j) {
-        lvl[j] = o;
-        o += al4(((T + H) >> j) + 40);
-      }
-      bc_y = o;
-      o += al4(T >> kIgCoarse);
-      bc_w = o;
-      o += al4(((T >> kIgCoarse) + 1) / 2);
-    }
-    f0 = o;
-    o += al4(kChunk + 128 + 40);
-    f1 = o;
-    o += al4((kChunk + 128) / 2 + 40);
-    f2 = o;
-    o += al4((kChunk + 128) / 4 + 40);
-    be_y = o;
-    o += kChunk / 2;
-    be_w = o;
-    o += kChunk / 4;
-    red = o;
-    o += 32;
-    total = o;
-  }
-};
-
-template <int D, int PL>
-__global__ void __launch_bounds__(kThreads, 2) igrid_kernel(const SearchParams p) {
-  using SM = IgM<D, PL>;
-  using S0 = Ig0<D, PL>;
-  constexpr int MMAX = SM::MMAX;
-  extern __shared__ __align__(16) float smem[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t row = blockIdx.x / p.tiles_per_row;
-  const int64_t tile = blockIdx.x % p.tiles_per_row;
-  const int T = p.tile, H = p.halo, top = p.top;
-  const int64_t t0 = tile * (int64_t)T;
-  const float* __restrict__ xrow = p.x + row * p.ld;
-  const float mu = p.mu[row];
-  const float inv = 1.0f / p.sigma[row];
-  const bool vec = p.vec != 0;
-  const IgLayout L(T, H, top);
-  const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
-  auto rsM = [&](auto M) { return p.rs[decltype(M)::value]; };
-
-  // ---- coarse levels: one pass over the tile and its halo ------------------
-  float* BCY = smem + L.bc_y;
-  uint16_t* BCW = reinterpret_cast<uint16_t*>(smem + L.bc_w);
-  if (top >= kIgCoarse) {
-    const int nchunk = (T + H) / 128;
-    for (int c = warp; c < nchunk; c += kThreads / 32) {
-      const float4 z = load_z4(xrow, t0 + c * 128 + lane * 4, p.nt, vec, mu, inv);
-      float s = (z.x + z.y) + (z.z + z.w);
-      s += __shfl_xor_sync(kFull, s, 1);
-      if (!(lane & 1)) smem[L.lvl[3] + c * 16 + (lane >> 1)] = s;
-      if (top >= 4) {
-        s += __shfl_xor_sync(kFull, s, 2);
-        if (!(lane & 3)) smem[L.lvl[4] + c * 8 + (lane >> 2)] = s;
-      }
-      if (top >= 5) {
-        s += __shfl_xor_sync(kFull, s, 4);
-        if (!(lane & 7)) smem[L.lvl[5] + c * 4 + (lane >> 3)] = s;
-      }
-      if (top >= 6) {
-        s += __shfl_xor_sync(kFull, s, 8);
-        if (!(lane & 15)) smem[L.lvl[6] + c * 2 + (lane >> 4)] = s;
-      }
-      if (top >= 7) {
-        s += __shfl_xor_sync(kFull, s, 16);
-        if (lane == 0) smem[L.lvl[7] + c] = s;
-      }
-    }
-    __syncthreads();
-    for (int j = 8; j <= top; ++j) {
-      float* dst = smem + L.lvl[j];
-      const float* src = smem + L.lvl[j - 1];
-      const int n = (T + H) >> j;
-      for (int i = tid; i < n; i += kThreads) dst[i] = src[2 * i] + src[2 * i + 1];
-      __syncthreads();
-    }
-    // evaluate every coarse level over the tile, merging bottom-up into BC
-    for (int j = kIgCoarse; j <= top; ++j) {
-      const float* blk = smem + L.lvl[j];
-      const int P = T >> j;
-      const int items = (P + 3) >> 2;
-      const float fj = p.lvl_scale[j];
-      const int first = p.lvl_first[j];
-      for (int it = tid; it < items; it += kThreads) {
-        const int p0 = it * 4;
-        float bv[4], full[4];
-        int bq[4];
-        if (j == top)
-          eval4<MMAX, SM, true, false>(blk, p0, p.n_top, rsM, zero4, bv, bq, full);
-        else
-          eval4<MMAX, SM, false, false>(blk, p0, p.n_top, rsM, zero4, bv, bq, full);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int pp = p0 + r;
-          if (pp < P) {
-            const int idx = pp << (j - kIgCoarse);
-            const float y = bv[r] * fj;
-            if (j == kIgCoarse) {
-              BCY[idx] = y;
-              BCW[idx] = (uint16_t)(first + bq[r]);
-            } else {
-              rmw(BCY, BCW, idx, y, first + bq[r]);
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-
-  // ---- fine levels, one sub-chunk at a time --------------------------------
-  float* F0 = smem + L.f0;
-  float* F1 = smem + L.f1;
-  float* F2 = smem + L.f2;
-  float* BEY = smem + L.be_y;
-  uint16_t* BEW = reinterpret_cast<uint16_t*>(smem + L.be_w);
-  float* yrow = p.snr + row * p.ld;
-  uint16_t* wrow = p.widx + row * p.ld;
-  float tmax = ninf();
-  const int nsub = T / kChunk;
-  for (int sub = 0; sub < nsub; ++sub) {
-    const int64_t sc = t0 + (int64_t)sub * kChunk;
-    if (sc >= p.nt) break;
-    for (int c = warp; c < kChunk / 128 + 1; c += kThreads / 32) {
-      const float4 z = load_z4(xrow, sc + c * 128 + lane * 4, p.nt, vec, mu, inv);
-      *reinterpret_cast<float4*>(F0 + c * 128 + lane * 4) = z;
-      const float a = z.x + z.y, b = z.z + z.w;
-      *reinterpret_cast<float2*>(F1 + c * 64 + lane * 2) = make_float2(a, b);
-      F2[c * 32 + lane] = a + b;
-    }
-    __syncthreads();
-    // level 0 stays in registers until the end of the sub-chunk
-    float y0[kItems0][4];
-    int w0[kItems0][4];
-#pragma unroll
-    for (int k = 0; k < kItems0; ++k) {
-      const int p0 = (tid + k * kThreads) * 4;
-      float full[4];
-      if (top == 0)
-        eval4<MMAX, S0, true, false>(F0, p0, p.n_top, rsM, zero4, y0[k], w0[k], full);
-      else
-        eval4<MMAX, S0, false, false>(F0, p0, p.n_top, rsM, zero4, y0[k], w0[k], full);
-    }
-    if (top >= 1) {  // level 1 -> BE (every even start)
-      const float fj = p.lvl_scale[1];
-      const int first = p.lvl_first[1];
-      for (int it = tid; it < kChunk / 8; it += kThreads) {
-        const int p0 = it * 4;
-        float bv[4], full[4];
-        int bq[4];
-        if (top == 1)
-          eval4<MMAX, SM, true, false>(F1, p0, p.n_top, rsM, zero4, bv, bq, full);
-        else
-          eval4<MMAX, SM, false, false>(F1, p0, p.n_top, rsM, zero4, bv, bq, full);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          BEY[p0 + r] = bv[r] * fj;
-          BEW[p0 + r] = (uint16_t)(first + bq[r]);
-        }
-      }
-    }
-    __syncthreads();
-    if (top >= 2) {  // level 2 -> BE at starts = 0 mod 4
-      const float fj = p.lvl_scale[2];
-      const int first = p.lvl_first[2];
-      for (int it = tid; it < kChunk / 16; it += kThreads) {
-        const int p0 = it * 4;
-        float bv[4], full[4];
-        int bq[4];
-        if (top == 2)
-          eval4<MMAX, SM, true, false>(F2, p0, p.n_top, rsM, zero4, bv, bq, full);
-        else
-          eval4<MMAX, SM, false, false>(F2, p0, p.n_top, rsM, zero4, bv, bq, full);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) rmw(BEY, BEW, 2 * (p0 + r), bv[r] * fj, first + bq[r]);
-      }
-      __syncthreads();
-    }
-    if (top >= kIgCoarse) {  // coarse results at starts = 0 mod 8
-      const int cbase = (int)((sc - t0) >> kIgCoarse);
-      for (int n = tid; n < kChunk / 8; n += kThreads) rmw(BEY, BEW, 4 * n, BCY[cbase + n], BCW[cbase + n]);
-      __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < kItems0; ++k) {
-      const int p0 = (tid + k * kThreads) * 4;
-      if (top >= 1) {
-#pragma unroll
-        for (int r = 0; r < 4; r += 2) {
-          const int idx = (p0 + r) >> 1;
-          if (BEY[idx] > y0[k][r]) {
-            y0[k][r] = BEY[idx];
-            w0[k][r] = BEW[idx];
-          }
-        }
-      }
-      const int64_t s0 = sc + p0;
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if (s0 + r < p.nt) tmax = fmaxf(tmax, y0[k][r]);
-      store4(yrow, wrow, s0, p.nt, vec, y0[k], w0[k]);
-    }
-    __syncthreads();
-  }
-  if (p.tile_max) tile_max_store(tmax, smem + L.red, p.tile_max + blockIdx.x);
 }
 
 // ============================================================================ BoxDIT
@@ -670,9 +307,10 @@ __global__ void __launch_bounds__(kThreads, 2) boxdit_kernel(const SearchParams 
         if (s0 + r < p.nt) tmax = fmaxf(tmax, y0[k][r]);
       store4(yrow, wrow, s0, p.nt, vec, y0[k], w0[k]);
     }
+    tile_max_atomic(p, row, sc, tmax);
+    tmax = ninf();
     __syncthreads();
   }
-  if (p.tile_max) tile_max_store(tmax, smem + L.red, p.tile_max + blockIdx.x);
 }
 
 // ============================================================================ exhaustive
@@ -760,16 +398,7 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
       if (s0 + r < p.nt) tmax = fmaxf(tmax, best[r]);
     store4(yrow, wrow, s0, p.nt, vec, best, q);
   }
-  if (p.tile_max) tile_max_store(tmax, smem + L.red, p.tile_max + blockIdx.x);
-}
-
-template <class KernelT>
-cudaError_t launch_one(KernelT kern, size_t smem, int64_t nblk, const SearchParams& p,
-                       cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)nblk, kThreads, smem, s>>>(p);
-  return cudaGetLastError();
+  tile_max_atomic(p, row, t0, tmax);
 }
 
 }  // namespace
@@ -777,7 +406,7 @@ cudaError_t launch_one(KernelT kern, size_t smem, int64_t nblk, const SearchPara
 size_t search_smem_bytes(const spd_plan& plan) {
   switch (plan.family) {
     case kExhaustive: return sizeof(float) * (size_t)ExLayout(plan.lend).total;
-    case kIgrid: return sizeof(float) * (size_t)IgLayout(plan.tile, plan.halo, plan.top).total;
+    case kIgrid: return igrid_smem_bytes(plan);
     default:
       switch (plan.k) {
         case 8: return sizeof(float) * (size_t)BdLayout<8>(plan.tile, plan.halo, plan.top).total;
@@ -799,18 +428,7 @@ cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStrea
       default: return cudaErrorInvalidValue;
     }
   }
-  const int key = plan.d * 8 + plan.pl;
-  switch (key) {
-    case 0 * 8 + 0: return launch_one(igrid_kernel<0, 0>, smem, nblk, p, s);
-    case 0 * 8 + 1: return launch_one(igrid_kernel<0, 1>, smem, nblk, p, s);
-    case 1 * 8 + 1: return launch_one(igrid_kernel<1, 1>, smem, nblk, p, s);
-    case 1 * 8 + 2: return launch_one(igrid_kernel<1, 2>, smem, nblk, p, s);
-    case 2 * 8 + 2: return launch_one(igrid_kernel<2, 2>, smem, nblk, p, s);
-    case 2 * 8 + 3: return launch_one(igrid_kernel<2, 3>, smem, nblk, p, s);
-    case 3 * 8 + 3: return launch_one(igrid_kernel<3, 3>, smem, nblk, p, s);
-    case 3 * 8 + 4: return launch_one(igrid_kernel<3, 4>, smem, nblk, p, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_igrid(plan, p, s);
 }
 
 }  // namespace spd

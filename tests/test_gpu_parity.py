@@ -48,6 +48,8 @@ CASES = [
     ("ig1", 8192, 3, 50000), ("ig1", 6, 2, 3000), ("ig1", 20, 2, 17000), ("ig1", 5000, 2, 33000),
     ("ig2p4", 4096, 2, 30000), ("ig2", 8192, 3, 40003), ("ig2", 12, 2, 5000),
     ("ig3p8", 4096, 2, 30000), ("ig3", 8192, 2, 40000), ("ig3", 100, 2, 9000),
+    # row stride = 4 (mod 8): W rows are only 8-byte aligned on odd rows
+    ("ig1", 512, 5, 3900), ("ig2", 8192, 3, 20004), ("bd16", 1000, 3, 20004), ("exh", 200, 3, 6004),
 ]
 
 
