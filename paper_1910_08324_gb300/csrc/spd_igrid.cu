@@ -11,19 +11,25 @@
 // window starting in it can reach (up to L_end later) has already been seen.
 // Each sample is therefore loaded, normalised and summed exactly once; the
 // segment's first L_end samples past its end are its only re-read (the halo).
-//   step 1  the chunk's 8 samples per thread (prefetched into registers one
-//           chunk earlier) are normalised and reduced in registers and warp
-//           shuffles into levels 0..3 (shared, triple buffered, each with a
-//           lookahead tail copied from the previous chunk) and into ring
-//           buffers for the coarse levels 4.. (unit >= 16);
-//   step 3  one thread per coarse position of the chunk evaluates it from its
-//           ring (scalar loads), results per level to shared memory;
-//   step 5  each thread owns 8 consecutive starts and evaluates levels 0..3
-//           from register windows (8 + 4 + 2 + 1 positions), merges them and
-//           the coarse results in registers (strict '>' in increasing width
-//           order), and writes 8 SNRs (2 x float4) and 8 widths (uint4).
-// Two barriers per chunk.  Samples past the end of the row are -inf, so a
-// boxcar needing them never wins (the s + L <= nt rule).
+// The chunk loop is software pipelined with one barrier per chunk.  Iteration
+// k (chunks counted in processing order):
+//   build   chunk k+1's 8 samples per thread (prefetched into registers one
+//           iteration earlier) are normalised and reduced in registers and
+//           warp shuffles into levels 0..3 (shared, four buffers, each with a
+//           lookahead tail written by the chunk processed before it) and into
+//           ring buffers for the coarse levels 4.. (unit >= 16); the loads of
+//           chunk k+2 are issued;
+//   barrier
+//   coarse  one thread per coarse position of chunk k+1 evaluates it from its
+//           ring (scalar loads); results go to one of two result buffers;
+//   fine    each thread owns 8 consecutive starts of chunk k and evaluates
+//           levels 0..3 from register windows (8 + 4 + 2 + 1 positions),
+//           merges them and chunk k's coarse results (computed one iteration
+//           earlier) in registers (strict '>' in increasing width order), and
+//           writes 8 SNRs (2 x float4) and 8 widths.
+// The coarse evaluation of one chunk thus overlaps the fine evaluation of the
+// next instead of sitting between two barriers.  Samples past the end of the
+// row are -inf, so a boxcar needing them never wins (the s + L <= nt rule).
 #include "spd_common.cuh"
 
 namespace spd {
@@ -72,11 +78,14 @@ struct IgFix {
   __host__ __device__ static constexpr int f1(int b) { return b * FB + O1; }
   __host__ __device__ static constexpr int f2(int b) { return b * FB + O2; }
   __host__ __device__ static constexpr int f3(int b) { return b * FB + O3; }
-  static constexpr int RINGS = 3 * FB;
+  static constexpr int NBUF = 4;
+  static constexpr int RINGS = NBUF * FB;
 };
 
+// A ring holds every block a window of the chunk being evaluated can reach,
+// plus the blocks of the chunk being built meanwhile.
 __host__ __device__ inline int ring_size(int j, int H, int mmax) {
-  return next_pow2(cdiv(kC + H, 1 << j) + mmax + 2);
+  return next_pow2(cdiv(2 * kC + H, 1 << j) + mmax + 2);
 }
 
 // offsets (floats) of: rings end, RES_Y, RES_W, table, total
@@ -86,9 +95,9 @@ struct IgDyn {
     int o = rings;
     for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, H, mmax));
     res_y = o;
-    o += kResHi + kMaxLevels;
+    o += 2 * (kResHi + kMaxLevels);
     res_w = o;
-    o += (kResHi + kMaxLevels) / 2;
+    o += kResHi + kMaxLevels;
     tab = o;
     o += 2 * kMaxLevels;
     total = o;
@@ -103,19 +112,23 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   using SM = typename S::SM;
   using S0 = typename S::S0;
   constexpr int MMAX = S::MMAX;
+  constexpr int RESN = kResHi + kMaxLevels;  // slots of one result buffer
   extern __shared__ __align__(16) float smem[];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t row = blockIdx.x / p.tiles_per_row;
   const int64_t t0 = (blockIdx.x % p.tiles_per_row) * (int64_t)p.tile;
   const int top = p.top;
-  const int64_t nt = p.nt;
+  const int T = p.tile, H = p.halo;
   const bool vec = p.vec != 0;
-  const float* __restrict__ xrow = p.x + row * p.ld;
-  float* __restrict__ yrow = p.snr + row * p.ld;
-  uint16_t* __restrict__ wrow = p.widx + row * p.ld;
+  // everything below is relative to the segment start t0 (32-bit offsets)
+  const float* __restrict__ xseg = p.x + row * p.ld + t0;
+  float* __restrict__ yseg = p.snr + row * p.ld + t0;
+  uint16_t* __restrict__ wseg = p.widx + row * p.ld + t0;
+  const int64_t nleft = p.nt - t0;
+  const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));  // samples that exist
   const float mu = p.mu[row];
   const float inv = 1.0f / p.sigma[row];
-  const IgDyn L(FX::RINGS, p.halo, top, MMAX);
+  const IgDyn L(FX::RINGS, H, top, MMAX);
   auto rsM = [&](auto M) { return p.rs[decltype(M)::value]; };
   float* RESY = smem + L.res_y;
   uint16_t* RESW = reinterpret_cast<uint16_t*>(smem + L.res_w);
@@ -130,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       RTAB[2 * j + 1] = 0;
     }
     for (int j = kRing0; j <= top; ++j) {
-      const int n = ring_size(j, p.halo, MMAX);
+      const int n = ring_size(j, H, MMAX);
       RTAB[2 * j] = o;
       RTAB[2 * j + 1] = n - 1;
       o += al4(n);
@@ -138,194 +151,219 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   }
   __syncthreads();
   int r4 = 0, m4 = 0, r5 = 0, m5 = 0, r6 = 0, m6 = 0, r7 = 0, m7 = 0, r8 = 0, m8 = 0;
+  // this thread's coarse position per chunk: level cj (0 = none), index cq
+  const int ctop = top < kChunkLog ? top : kChunkLog;
+  int cj = 0, cq = 0;
   if (COARSE) {
     r4 = RTAB[8], m4 = RTAB[9], r5 = RTAB[10], m5 = RTAB[11], r6 = RTAB[12], m6 = RTAB[13];
     r7 = RTAB[14], m7 = RTAB[15], r8 = RTAB[16], m8 = RTAB[17];
+    if (t < 256 - (1 << (kChunkLog - ctop))) {  // positions of levels 4..ctop
+      int j = kRing0, off = 0;
+      while (t >= off + (kC >> j)) {
+        off += kC >> j;
+        ++j;
+      }
+      cj = j;
+      cq = t - off;
+    }
   }
 
-  const int64_t a_hi = t0 + p.tile + p.halo - kC;
-  int64_t a_first = a_hi;
-  if (a_first >= nt) a_first = ((nt - 1) / kC) * kC;  // chunks at or past nt are all -inf
-  float4 nx0 = make_float4(0.f, 0.f, 0.f, 0.f), nx1 = nx0;
-  if (a_first >= t0) {
-    nx0 = load_x4(xrow, a_first + 8 * t, nt, vec);
-    nx1 = load_x4(xrow, a_first + 8 * t + 4, nt, vec);
-  }
-  float tmax = ninf();
-  int k = (int)((a_hi - a_first) / kC);  // chunk counter (selects the buffer triple)
-  for (int64_t a = a_first; a >= t0; a -= kC, ++k) {
-    const int buf = k % 3, nbuf = (k + 1) % 3;
-    const bool body = a < t0 + p.tile;
-    // ---- step 1: normalise, build levels 0..3 and the ring entries --------
-    const float4 v0 = norm4(nx0, mu, inv), v1 = norm4(nx1, mu, inv);
-    if (a - kC >= t0) {
-      nx0 = load_x4(xrow, a - kC + 8 * t, nt, vec);
-      nx1 = load_x4(xrow, a - kC + 8 * t + 4, nt, vec);
+  // chunks at relative starts ar(k) = a0 - k*kC, k = 0..nch-1 (backwards in time)
+  int a0 = T + H - kC;
+  if (a0 >= nrel) a0 = ((nrel - 1) / kC) * kC;  // chunks at or past nt are all -inf
+  const int nch = a0 / kC + 1;
+
+  // ---- building chunk k: levels 0..3 into buffer k % 4, tails, rings 4..8 ----
+  auto build = [&](int k, float4 x0, float4 x1) {
+    const int ar = a0 - k * kC;
+    const int buf = k % FX::NBUF, nbuf = (k + 1) % FX::NBUF;
+    const float4 v0 = norm4(x0, mu, inv), v1 = norm4(x1, mu, inv);
+    float* F0 = smem + FX::f0(buf);
+    *reinterpret_cast<float4*>(F0 + 8 * t) = v0;
+    *reinterpret_cast<float4*>(F0 + 8 * t + 4) = v1;
+    if (8 * t < S::TL0) {
+      float* T0 = smem + FX::f0(nbuf) + kC + 8 * t;
+      *reinterpret_cast<float4*>(T0) = v0;
+      if (8 * t + 4 < S::TL0) *reinterpret_cast<float4*>(T0 + 4) = v1;
     }
-    {
-      float* F0 = smem + FX::f0(buf);
-      *reinterpret_cast<float4*>(F0 + 8 * t) = v0;
-      *reinterpret_cast<float4*>(F0 + 8 * t + 4) = v1;
-      if (8 * t < S::TL0) {
-        float* T0 = smem + FX::f0(nbuf) + kC + 8 * t;
-        *reinterpret_cast<float4*>(T0) = v0;
-        if (8 * t + 4 < S::TL0) *reinterpret_cast<float4*>(T0 + 4) = v1;
-      }
-      const float p0 = v0.x + v0.y, p1 = v0.z + v0.w, p2 = v1.x + v1.y, p3 = v1.z + v1.w;
-      const float4 pp = make_float4(p0, p1, p2, p3);
-      *reinterpret_cast<float4*>(smem + FX::f1(buf) + 4 * t) = pp;
-      if (4 * t < S::TL1) *reinterpret_cast<float4*>(smem + FX::f1(nbuf) + kC / 2 + 4 * t) = pp;
-      const float q0 = p0 + p1, q1 = p2 + p3;
-      *reinterpret_cast<float2*>(smem + FX::f2(buf) + 2 * t) = make_float2(q0, q1);
-      if (2 * t < S::TL2) *reinterpret_cast<float2*>(smem + FX::f2(nbuf) + kC / 4 + 2 * t) = make_float2(q0, q1);
-      const float o8 = q0 + q1;
-      smem[FX::f3(buf) + t] = o8;
-      if (t < S::TL3) smem[FX::f3(nbuf) + kC / 8 + t] = o8;
-      if (COARSE) {
-        float s = o8 + __shfl_xor_sync(kFull, o8, 1);
-        if (!(lane & 1)) smem[r4 + (int)(((a >> 4) + (t >> 1)) & m4)] = s;
-        if (top >= 5) {
-          s += __shfl_xor_sync(kFull, s, 2);
-          if (!(lane & 3)) smem[r5 + (int)(((a >> 5) + (t >> 2)) & m5)] = s;
-        }
-        if (top >= 6) {
-          s += __shfl_xor_sync(kFull, s, 4);
-          if (!(lane & 7)) smem[r6 + (int)(((a >> 6) + (t >> 3)) & m6)] = s;
-        }
-        if (top >= 7) {
-          s += __shfl_xor_sync(kFull, s, 8);
-          if (!(lane & 15)) smem[r7 + (int)(((a >> 7) + (t >> 4)) & m7)] = s;
-        }
-        if (top >= 8) {
-          s += __shfl_xor_sync(kFull, s, 16);
-          if (lane == 0) smem[r8 + (int)(((a >> 8) + warp) & m8)] = s;
-        }
-      }
-    }
-    __syncthreads();
-    // ---- step 2/3: blocks of levels 9.. (one warp) and coarse evaluation --
+    const float p0 = v0.x + v0.y, p1 = v0.z + v0.w, p2 = v1.x + v1.y, p3 = v1.z + v1.w;
+    const float4 pp = make_float4(p0, p1, p2, p3);
+    *reinterpret_cast<float4*>(smem + FX::f1(buf) + 4 * t) = pp;
+    if (4 * t < S::TL1) *reinterpret_cast<float4*>(smem + FX::f1(nbuf) + kC / 2 + 4 * t) = pp;
+    const float q0 = p0 + p1, q1 = p2 + p3;
+    *reinterpret_cast<float2*>(smem + FX::f2(buf) + 2 * t) = make_float2(q0, q1);
+    if (2 * t < S::TL2) *reinterpret_cast<float2*>(smem + FX::f2(nbuf) + kC / 4 + 2 * t) = make_float2(q0, q1);
+    const float o8 = q0 + q1;
+    smem[FX::f3(buf) + t] = o8;
+    if (t < S::TL3) smem[FX::f3(nbuf) + kC / 8 + t] = o8;
     if (COARSE) {
-      if (warp == kThreads / 32 - 1 && top >= 9) {
-        for (int j = 9; j <= top; ++j) {
-          const int nb = (j <= kChunkLog) ? (kC >> j) : ((a & ((1LL << j) - 1)) == 0 ? 1 : 0);
-          if (lane < nb) {
-            const int64_t n = (a >> j) + lane;
-            const float* R = smem + RTAB[2 * (j - 1)];
-            const int m = RTAB[2 * (j - 1) + 1];
-            smem[RTAB[2 * j] + (int)(n & RTAB[2 * j + 1])] = R[(int)((2 * n) & m)] + R[(int)((2 * n + 1) & m)];
-          }
-          __syncwarp();
-        }
+      float s = o8 + __shfl_xor_sync(kFull, o8, 1);
+      if (!(lane & 1)) smem[r4 + (((ar >> 4) + (t >> 1)) & m4)] = s;
+      if (top >= 5) {
+        s += __shfl_xor_sync(kFull, s, 2);
+        if (!(lane & 3)) smem[r5 + (((ar >> 5) + (t >> 2)) & m5)] = s;
       }
-      if (body) {
-        const int ctop = top < kChunkLog ? top : kChunkLog;
-        const int npos = 256 - (1 << (kChunkLog - ctop));  // positions of levels 4..ctop
-        int j = -1, q = 0;
-        if (t < npos) {
-          j = kRing0;
-          int off = 0;
-          while (t >= off + (kC >> j)) {
-            off += kC >> j;
-            ++j;
-          }
-          q = t - off;
-        } else if (t == kThreads - 1 && top > kChunkLog) {
-          j = 0;  // levels above the chunk size: handled below by this thread
-        }
-        auto eval_coarse = [&](int jj, int64_t n, int slot) {
-          float w[MMAX];
-          const float* R = smem + RTAB[2 * jj];
-          const int m = RTAB[2 * jj + 1];
-#pragma unroll
-          for (int i = 0; i < MMAX; ++i) w[i] = R[(int)((n + i) & m)];
-          float bv[1], full[1];
-          int bq[1];
-          const int nu = (jj == top) ? p.n_top : SM::MM;
-          eval_window<1, MMAX, SM, true, false>(w, nu, rsM, nullptr, bv, bq, full);
-          RESY[slot] = bv[0] * p.lvl_scale[jj];
-          RESW[slot] = (uint16_t)(p.lvl_first[jj] + bq[0]);
-        };
-        if (j >= kRing0) {
-          eval_coarse(j, (a >> j) + q, t);
-        } else if (j == 0) {
-          for (int jj = kChunkLog + 1; jj <= top; ++jj)
-            if ((a & ((1LL << jj) - 1)) == 0) eval_coarse(jj, a >> jj, kResHi + jj - kChunkLog - 1);
-        }
+      if (top >= 6) {
+        s += __shfl_xor_sync(kFull, s, 4);
+        if (!(lane & 7)) smem[r6 + (((ar >> 6) + (t >> 3)) & m6)] = s;
+      }
+      if (top >= 7) {
+        s += __shfl_xor_sync(kFull, s, 8);
+        if (!(lane & 15)) smem[r7 + (((ar >> 7) + (t >> 4)) & m7)] = s;
+      }
+      if (top >= 8) {
+        s += __shfl_xor_sync(kFull, s, 16);
+        if (lane == 0) smem[r8 + (((ar >> 8) + warp) & m8)] = s;
       }
     }
-    __syncthreads();
-    // ---- step 5: per-thread levels 0..3, merge, write ----------------------
-    if (body) {
-      float y[8];
-      int w[8];
-      {
-        float win[S::NW0 * 4], full[8];
-        load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
-        if (!COARSE && top == 0)
-          eval_window<8, MMAX, S0, true, false>(win, p.n_top, rsM, nullptr, y, w, full);
-        else
-          eval_window<8, MMAX, S0, false, false>(win, p.n_top, rsM, nullptr, y, w, full);
-      }
-      if (COARSE || top >= 1) {
-        float win[S::NW1 * 4], bv[4], full[4];
-        int bq[4];
-        load_window4<S::NW1>(smem + FX::f1(buf) + 4 * t, win);
-        if (!COARSE && top == 1)
-          eval_window<4, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-        else
-          eval_window<4, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-        const float f = p.lvl_scale[1];
-        const int first = p.lvl_first[1];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) merge1(y[2 * r], w[2 * r], bv[r] * f, first + bq[r]);
-      }
-      if (COARSE || top >= 2) {
-        float win[S::NW2 * 2], bv[2], full[2];
-        int bq[2];
-        load_window2<S::NW2>(smem + FX::f2(buf) + 2 * t, win);
-        if (!COARSE && top == 2)
-          eval_window<2, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-        else
-          eval_window<2, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-        const float f = p.lvl_scale[2];
-        const int first = p.lvl_first[2];
-        merge1(y[0], w[0], bv[0] * f, first + bq[0]);
-        merge1(y[4], w[4], bv[1] * f, first + bq[1]);
-      }
-      if (COARSE || top >= 3) {
-        float win[S::NW3], bv[1], full[1];
-        int bq[1];
-        load_window1<S::NW3>(smem + FX::f3(buf) + t, win);
-        if (!COARSE && top == 3)
-          eval_window<1, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-        else
-          eval_window<1, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-        merge1(y[0], w[0], bv[0] * p.lvl_scale[3], p.lvl_first[3] + bq[0]);
-      }
-      if (COARSE) {
-        const int ctop = top < kChunkLog ? top : kChunkLog;
-        for (int j = kRing0; j <= ctop; ++j) {
-          if (t & ((1 << (j - 3)) - 1)) break;
-          const int slot = 256 - (1 << (kChunkLog + 1 - j)) + (t >> (j - 3));
-          merge1(y[0], w[0], RESY[slot], RESW[slot]);
+  };
+
+  // ---- coarse work of chunk k (after the barrier that follows its build) ----
+  auto coarse = [&](int k) {
+    const int ar = a0 - k * kC;
+    if (warp == kThreads / 32 - 1 && top >= 9) {  // blocks of levels 9.. need every warp's level 8
+      for (int j = 9; j <= top; ++j) {
+        const int nb = (j <= kChunkLog) ? (kC >> j) : ((((ar + (int)(t0 & ((1LL << j) - 1))) & ((1 << j) - 1)) == 0) ? 1 : 0);
+        if (lane < nb) {
+          const int n = (ar >> j) + lane;
+          const float* R = smem + RTAB[2 * (j - 1)];
+          const int m = RTAB[2 * (j - 1) + 1];
+          smem[RTAB[2 * j] + (n & RTAB[2 * j + 1])] = R[(2 * n) & m] + R[(2 * n + 1) & m];
         }
-        if (t == 0)
-          for (int jj = kChunkLog + 1; jj <= top; ++jj)
-            if ((a & ((1LL << jj) - 1)) == 0) {
-              const int slot = kResHi + jj - kChunkLog - 1;
-              merge1(y[0], w[0], RESY[slot], RESW[slot]);
-            }
+        __syncwarp();
       }
-      const int64_t s0 = a + 8 * t;
+    }
+    if (ar >= T) return;  // halo chunk: nothing to evaluate
+    float* RY = RESY + (k & 1) * RESN;
+    uint16_t* RW = RESW + (k & 1) * RESN;
+    auto eval_coarse = [&](int jj, int n, int slot) {
+      float w[MMAX];
+      const float* R = smem + RTAB[2 * jj];
+      const int m = RTAB[2 * jj + 1];
+#pragma unroll
+      for (int i = 0; i < MMAX; ++i) w[i] = R[(n + i) & m];
+      float bv[1], full[1];
+      int bq[1];
+      const int nu = (jj == top) ? p.n_top : SM::MM;
+      eval_window<1, MMAX, SM, true, false>(w, nu, rsM, nullptr, bv, bq, full);
+      RY[slot] = bv[0] * p.lvl_scale[jj];
+      RW[slot] = (uint16_t)(p.lvl_first[jj] + bq[0]);
+    };
+    if (cj) eval_coarse(cj, (ar >> cj) + cq, t);
+    if (t == kThreads - 1)
+      for (int jj = kChunkLog + 1; jj <= top; ++jj)
+        if (((t0 + ar) & ((1LL << jj) - 1)) == 0) eval_coarse(jj, ar >> jj, kResHi + jj - kChunkLog - 1);
+  };
+
+  // ---- fine levels, merge and store of chunk k -----------------------------
+  float tmax = ninf();
+  auto fine = [&](int k) {
+    const int ar = a0 - k * kC;
+    if (ar >= T) return;
+    const int buf = k % FX::NBUF;
+    float y[8];
+    int w[8];
+    {
+      float win[S::NW0 * 4], full[8];
+      load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
+      if (!COARSE && top == 0)
+        eval_window<8, MMAX, S0, true, false>(win, p.n_top, rsM, nullptr, y, w, full);
+      else
+        eval_window<8, MMAX, S0, false, false>(win, p.n_top, rsM, nullptr, y, w, full);
+    }
+    if (COARSE || top >= 1) {
+      float win[S::NW1 * 4], bv[4], full[4];
+      int bq[4];
+      load_window4<S::NW1>(smem + FX::f1(buf) + 4 * t, win);
+      if (!COARSE && top == 1)
+        eval_window<4, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+      else
+        eval_window<4, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+      const float f = p.lvl_scale[1];
+      const int first = p.lvl_first[1];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) merge1(y[2 * r], w[2 * r], bv[r] * f, first + bq[r]);
+    }
+    if (COARSE || top >= 2) {
+      float win[S::NW2 * 2], bv[2], full[2];
+      int bq[2];
+      load_window2<S::NW2>(smem + FX::f2(buf) + 2 * t, win);
+      if (!COARSE && top == 2)
+        eval_window<2, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+      else
+        eval_window<2, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+      const float f = p.lvl_scale[2];
+      const int first = p.lvl_first[2];
+      merge1(y[0], w[0], bv[0] * f, first + bq[0]);
+      merge1(y[4], w[4], bv[1] * f, first + bq[1]);
+    }
+    if (COARSE || top >= 3) {
+      float win[S::NW3], bv[1], full[1];
+      int bq[1];
+      load_window1<S::NW3>(smem + FX::f3(buf) + t, win);
+      if (!COARSE && top == 3)
+        eval_window<1, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+      else
+        eval_window<1, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+      merge1(y[0], w[0], bv[0] * p.lvl_scale[3], p.lvl_first[3] + bq[0]);
+    }
+    if (COARSE) {
+      const float* RY = RESY + (k & 1) * RESN;
+      const uint16_t* RW = RESW + (k & 1) * RESN;
+      for (int j = kRing0; j <= ctop; ++j) {
+        if (t & ((1 << (j - 3)) - 1)) break;
+        const int slot = 256 - (1 << (kChunkLog + 1 - j)) + (t >> (j - 3));
+        merge1(y[0], w[0], RY[slot], RW[slot]);
+      }
+      if (t == 0)
+        for (int jj = kChunkLog + 1; jj <= top; ++jj)
+          if (((t0 + ar) & ((1LL << jj) - 1)) == 0) {
+            const int slot = kResHi + jj - kChunkLog - 1;
+            merge1(y[0], w[0], RY[slot], RW[slot]);
+          }
+    }
+    const int s0 = ar + 8 * t;
+    if (s0 + 8 <= nrel) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) tmax = fmaxf(tmax, y[r]);
+    } else {
 #pragma unroll
       for (int r = 0; r < 8; ++r)
-        if (s0 + r < nt) tmax = fmaxf(tmax, y[r]);
-      store8(yrow, wrow, s0, nt, vec, y, w);
-      if ((a % kCandTile) == 0) {  // last chunk of a candidate tile (we walk backwards)
-        tile_max_atomic(p, row, a, tmax);
-        tmax = ninf();
-      }
+        if (s0 + r < nrel) tmax = fmaxf(tmax, y[r]);
     }
+    store8(yseg, wseg, s0, nrel, vec, y, w);
+    if ((ar & (kCandTile - 1)) == 0) {  // last chunk of a candidate tile (we walk backwards)
+      tile_max_atomic(p, row, t0 + ar, tmax);
+      tmax = ninf();
+    }
+  };
+
+  // ---- pipeline --------------------------------------------------------------
+  float4 n0 = load_x4(xseg, a0 + 8 * t, nrel, vec);
+  float4 n1 = load_x4(xseg, a0 + 8 * t + 4, nrel, vec);
+  {
+    const float4 c0 = n0, c1 = n1;
+    if (nch > 1) {
+      n0 = load_x4(xseg, a0 - kC + 8 * t, nrel, vec);
+      n1 = load_x4(xseg, a0 - kC + 8 * t + 4, nrel, vec);
+    }
+    build(0, c0, c1);
+  }
+  __syncthreads();
+  if (COARSE) coarse(0);
+  for (int k = 0; k < nch; ++k) {
+    const bool more = k + 1 < nch;
+    if (more) {
+      const float4 c0 = n0, c1 = n1;
+      if (k + 2 < nch) {
+        n0 = load_x4(xseg, a0 - (k + 2) * kC + 8 * t, nrel, vec);
+        n1 = load_x4(xseg, a0 - (k + 2) * kC + 8 * t + 4, nrel, vec);
+      }
+      build(k + 1, c0, c1);
+    }
+    __syncthreads();
+    if (COARSE && more) coarse(k + 1);
+    fine(k);
   }
 }
 
