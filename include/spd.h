@@ -221,6 +221,34 @@ spd_status spd_search(const spd_plan *plan, const void *d_x, const spd_noise *no
                       int64_t *d_count, void *d_ws, size_t ws_bytes, spd_stream_t stream);
 
 /*
+ * spd_candidates without a workspace, for callers that cannot allocate device
+ * memory when they call it: a real-time pipeline that reserves all of its
+ * device memory at start-up (a later allocation can stall or fail in the
+ * middle of an observation), or a plain C caller with no allocator of its own
+ * for scratch space.  The paper has no counterpart; this is a deployment
+ * convenience.
+ *
+ * Same rule, arguments, output and errors as spd_candidates with
+ * use_tile_max = 0 (every tile of d_snr is scanned), minus the workspace.  Its
+ * scratch is one array inside the library: per-tile counts and offsets for at
+ * most 262,144 candidate tiles of 16,384 starts (ndm * ceil(nt / 16384) tiles,
+ * 3 MiB, held by every device that loads the library until the process exits).
+ * A plan with more tiles is rejected with SPD_ERR_UNSUPPORTED before any work
+ * is queued.  The call itself allocates nothing.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the array: calls whose work overlaps on the
+ *     GPU (different streams, no ordering between them) race and give wrong
+ *     results.  Calls ordered on one stream are safe; nothing carries over
+ *     from one call to the next.
+ */
+spd_status spd_candidates_static(const spd_plan *plan, const float *d_snr,
+                                 const uint16_t *d_width_idx, float threshold,
+                                 int32_t peak_radius, spd_candidate *d_out, int64_t cap,
+                                 int64_t *d_count, spd_stream_t stream);
+
+/*
  * Wait for the stream and report any asynchronous CUDA error of work queued
  * on it (SPD_ERR_CUDA), else SPD_OK.
  */

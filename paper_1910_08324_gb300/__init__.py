@@ -30,6 +30,7 @@ from ._binding import (  # noqa: F401
     records,
     search,
     spd_candidates,
+    spd_candidates_static,
     spd_execute,
     spd_plan_create,
     spd_plan_destroy,

@@ -50,7 +50,7 @@ _lib = None
 _lock = threading.Lock()
 _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_destroy",
             "spd_plan_widths", "spd_workspace_size", "spd_execute", "spd_candidates",
-            "spd_search", "spd_sync_status"]
+            "spd_search", "spd_sync_status", "spd_candidates_static"]
 
 
 def library_path() -> str:
@@ -79,6 +79,7 @@ def load_library():
         lib.spd_search.argtypes = [vp, vp, ctypes.POINTER(_Noise), vp, vp, ctypes.c_float, i32, vp,
                                    i64, vp, vp, sz, vp]
         lib.spd_sync_status.argtypes = [vp, vp]
+        lib.spd_candidates_static.argtypes = [vp, vp, vp, ctypes.c_float, i32, vp, i64, vp, vp]
         for name in _SYMBOLS[2:]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -173,6 +174,15 @@ def spd_candidates(plan: Plan, snr: int, width_idx: int, threshold: float, peak_
                                          int(cap), count, ws, ws_bytes, int(use_tile_max),
                                          stream or None),
            "spd_candidates")
+
+
+def spd_candidates_static(plan: Plan, snr: int, width_idx: int, threshold: float,
+                          peak_radius: int, out: int, cap: int, count: int, stream: int = 0):
+    """spd_candidates with the library's own static scratch instead of a workspace."""
+    _check(load_library().spd_candidates_static(ctypes.c_void_p(plan.handle), snr, width_idx,
+                                                float(threshold), int(peak_radius), out or None,
+                                                int(cap), count, stream or None),
+           "spd_candidates_static")
 
 
 def spd_search(plan: Plan, x: int, mu: int, sigma: int, snr: int, width_idx: int,

@@ -162,27 +162,23 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   return check_cuda(e);
 }
 
-spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_t* d_width_idx,
-                         float threshold, int32_t peak_radius, spd_candidate* d_out, int64_t cap,
-                         int64_t* d_count, void* d_ws, size_t ws_bytes, bool use_tile_max,
-                         cudaStream_t stream) {
+spd_status check_cand_args(const spd_plan* plan, const float* d_snr, const uint16_t* d_width_idx,
+                           float threshold, int32_t peak_radius, spd_candidate* d_out, int64_t cap,
+                           int64_t* d_count) {
   if (!plan || !d_snr || !d_width_idx || !d_count) return SPD_ERR_INVALID_ARG;
   if (cap < 0 || (cap > 0 && !d_out)) return SPD_ERR_INVALID_ARG;
   if (peak_radius < 0 || peak_radius > spd::kMaxPeakRadius) return SPD_ERR_INVALID_ARG;
   if (std::isnan(threshold)) return SPD_ERR_INVALID_ARG;
   if (((uintptr_t)d_count % 8) || ((uintptr_t)d_out % 8)) return SPD_ERR_INVALID_ARG;
-  const spd_status ws = validate_ws(plan, d_ws, ws_bytes);
-  if (ws != SPD_OK) return ws;
-  const WsLayout wl(*plan);
-  spd::CandParams* cp = new (std::nothrow) spd::CandParams();
-  if (!cp) return SPD_ERR_HOST_ALLOC;
-  spd::CandParams& p = *cp;
-  char* base = static_cast<char*>(d_ws);
+  return SPD_OK;
+}
+
+// Fills everything but the scratch pointers (counts, offsets, tile_max).
+void fill_cand_params(spd::CandParams& p, const spd_plan* plan, const float* d_snr,
+                      const uint16_t* d_width_idx, float threshold, int32_t peak_radius,
+                      spd_candidate* d_out, int64_t cap, int64_t* d_count) {
   p.snr = d_snr;
   p.widx = d_width_idx;
-  p.tile_max = use_tile_max ? reinterpret_cast<const float*>(base + wl.tile_max) : nullptr;
-  p.counts = reinterpret_cast<int32_t*>(base + wl.counts);
-  p.offsets = reinterpret_cast<int64_t*>(base + wl.offsets);
   p.out = d_out;
   p.d_count = d_count;
   p.ndm = plan->desc.ndm;
@@ -196,6 +192,25 @@ spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_
   p.width_mode = plan->family == kExhaustive ? 0 : 1;
   if (p.width_mode)
     for (size_t i = 0; i < plan->widths.size() && i < 512; ++i) p.width_tab[i] = plan->widths[i];
+}
+
+spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_t* d_width_idx,
+                         float threshold, int32_t peak_radius, spd_candidate* d_out, int64_t cap,
+                         int64_t* d_count, void* d_ws, size_t ws_bytes, bool use_tile_max,
+                         cudaStream_t stream) {
+  spd_status st = check_cand_args(plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count);
+  if (st != SPD_OK) return st;
+  st = validate_ws(plan, d_ws, ws_bytes);
+  if (st != SPD_OK) return st;
+  const WsLayout wl(*plan);
+  spd::CandParams* cp = new (std::nothrow) spd::CandParams();
+  if (!cp) return SPD_ERR_HOST_ALLOC;
+  spd::CandParams& p = *cp;
+  fill_cand_params(p, plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count);
+  char* base = static_cast<char*>(d_ws);
+  p.tile_max = use_tile_max ? reinterpret_cast<const float*>(base + wl.tile_max) : nullptr;
+  p.counts = reinterpret_cast<int32_t*>(base + wl.counts);
+  p.offsets = reinterpret_cast<int64_t*>(base + wl.offsets);
   const cudaError_t e = spd::launch_candidates(*plan, p, stream);
   delete cp;
   return check_cuda(e);
@@ -349,6 +364,21 @@ spd_status spd_candidates(const spd_plan* plan, const float* d_snr, const uint16
                           spd_stream_t stream) {
   return do_candidates(plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count, d_ws,
                        ws_bytes, use_tile_max != 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+spd_status spd_candidates_static(const spd_plan* plan, const float* d_snr,
+                                 const uint16_t* d_width_idx, float threshold, int32_t peak_radius,
+                                 spd_candidate* d_out, int64_t cap, int64_t* d_count,
+                                 spd_stream_t stream) {
+  spd_status st = check_cand_args(plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count);
+  if (st != SPD_OK) return st;
+  if (plan->desc.ndm * plan->cand_tiles_per_row > spd::kStaticCandTiles) return SPD_ERR_UNSUPPORTED;
+  spd::CandParams* cp = new (std::nothrow) spd::CandParams();
+  if (!cp) return SPD_ERR_HOST_ALLOC;
+  fill_cand_params(*cp, plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count);
+  const cudaError_t e = spd::launch_candidates_static(*plan, *cp, reinterpret_cast<cudaStream_t>(stream));
+  delete cp;
+  return check_cuda(e);
 }
 
 spd_status spd_search(const spd_plan* plan, const void* d_x, const spd_noise* noise, float* d_snr,

@@ -18,8 +18,16 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "spd_internal.h"
+
+// Scratch of spd_candidates_static: per-tile counts (int32) followed by per-tile
+// offsets (int64) for at most kStaticCandTiles candidate tiles (3 MiB).  Every
+// device that loads the library holds this array until the process exits; all
+// calls on a device share it.
+static __device__ __align__(256) unsigned char
+    g_static_cand_scratch[spd::kStaticCandTiles * (sizeof(int32_t) + sizeof(int64_t))];
 
 namespace spd {
 namespace {
@@ -129,6 +137,40 @@ __global__ void __launch_bounds__(kCandThreads) cand_write_kernel(const CandPara
 }
 
 }  // namespace
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};  // device address of the scratch, per device
+}  // namespace
+
+// The host-side name g_static_cand_scratch is not a device address: the address
+// is looked up once per device (with that device current) and cached.
+cudaError_t static_cand_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* a = nullptr;
+    e = cudaGetSymbolAddress(&a, g_static_cand_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = a;
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s) {
+  void* base = nullptr;
+  const cudaError_t e = static_cand_scratch(&base);
+  if (e != cudaSuccess) return e;
+  p.counts = static_cast<int32_t*>(base);
+  p.offsets = reinterpret_cast<int64_t*>(static_cast<char*>(base) + kStaticCandTiles * sizeof(int32_t));
+  p.tile_max = nullptr;  // no tile maxima without a workspace: every tile is scanned
+  return launch_candidates(plan, p, s);
+}
 
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s) {
   const int64_t ntiles = plan.desc.ndm * plan.cand_tiles_per_row;

@@ -37,6 +37,7 @@ constexpr int kMaxLend = 32768;    // largest width a plan may reach
 constexpr int kMaxExhaustive = 4096;
 constexpr int kCandTile = 16384;   // starts per candidate tile (tile maxima granularity)
 constexpr int kMaxPeakRadius = 64;
+constexpr int64_t kStaticCandTiles = 262144;  // candidate tiles spd_candidates_static can hold
 
 enum Family { kExhaustive = 0, kBoxdit = 1, kIgrid = 2 };
 
@@ -104,5 +105,6 @@ cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStrea
 cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 size_t igrid_smem_bytes(const spd_plan& plan);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
+cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s);
 size_t search_smem_bytes(const spd_plan& plan);
 }  // namespace spd
