@@ -220,6 +220,66 @@ __device__ __forceinline__ void eval_window(const float* w, int n_used, Scale&& 
   });
 }
 
+// Three-input maximum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+template <class Pred, int MMAX>
+__host__ __device__ constexpr int count_in() {
+  int n = 0;
+  for (int m = 1; m <= MMAX; ++m) n += Pred::in(m) ? 1 : 0;
+  return n;
+}
+
+// Maximum of v[0..N) with three-input max instructions.
+template <int N>
+__device__ __forceinline__ float tree_max(const float (&v)[N]) {
+  if constexpr (N == 1) {
+    return v[0];
+  } else if constexpr (N == 2) {
+    return fmaxf(v[0], v[1]);
+  } else {
+    float acc = fmax3(v[0], v[1], v[2]);
+    static_for<0, (N - 3) / 2>([&](auto I) {
+      constexpr int i = 3 + 2 * decltype(I)::value;
+      acc = fmax3(acc, v[i], v[i + 1]);
+    });
+    if constexpr (((N - 3) % 2) == 1) acc = fmaxf(acc, v[N - 1]);
+    return acc;
+  }
+}
+
+// eval_window without a base and without PARTIAL, computed another way: the
+// candidates' scaled sums are kept, their maximum is taken with three-input max
+// instructions, and the rank is the first candidate equal to it (the smallest
+// width on ties, as with the strict '>' scan in increasing width order).
+template <int NP, int MMAX, class Pred, class Scale>
+__device__ __forceinline__ void eval_window_mx(const float* w, Scale&& scale, float (&bv)[NP],
+                                               int (&bq)[NP]) {
+  constexpr int NC = count_in<Pred, MMAX>();
+  static_for<0, NP>([&](auto R) {
+    constexpr int r = decltype(R)::value;
+    float v[NC];
+    float S = 0.0f;
+    static_for<1, MMAX + 1>([&](auto M) {
+      constexpr int m = decltype(M)::value;
+      S += w[r + m - 1];
+      if constexpr (Pred::in(m)) v[Pred::rank(m)] = S * scale(M);
+    });
+    const float best = tree_max<NC>(v);
+    int q = NC - 1;
+    static_for<0, NC - 1>([&](auto C) {
+      constexpr int c = NC - 2 - decltype(C)::value;
+      if (v[c] == best) q = c;
+    });
+    bv[r] = best;
+    bq[r] = q;
+  });
+}
+
 // Load a window of NW float4s from 16-byte aligned shared memory.
 template <int NW>
 __device__ __forceinline__ void load_window4(const float* src, float (&w)[NW * 4]) {

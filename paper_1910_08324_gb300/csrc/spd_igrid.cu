@@ -30,6 +30,8 @@
 // The coarse evaluation of one chunk thus overlaps the fine evaluation of the
 // next instead of sitting between two barriers.  Samples past the end of the
 // row are -inf, so a boxcar needing them never wins (the s + L <= nt rule).
+#include <climits>
+
 #include "spd_common.cuh"
 
 namespace spd {
@@ -88,16 +90,24 @@ __host__ __device__ inline int ring_size(int j, int H, int mmax) {
   return next_pow2(cdiv(2 * kC + H, 1 << j) + mmax + 2);
 }
 
-// offsets (floats) of: rings end, RES_Y, RES_W, table, total
+// offsets (floats) of the rings' end, the coarse results (two buffers of
+// values and widths), the coarse-merge keys (two buffers) and the ring table.
+// Each ring stores mmax extra entries that mirror its first ones, so that a
+// window of mmax consecutive blocks never wraps.
+constexpr int kResN = kResHi + kMaxLevels;  // slots of one coarse-result buffer
+constexpr int kBcm = kC / 16;               // starts = 0 mod 16 in a chunk
+
 struct IgDyn {
-  int res_y, res_w, tab, total;
+  int res_y, res_w, bcm, tab, total;
   __host__ __device__ IgDyn(int rings, int H, int top, int mmax) {
     int o = rings;
-    for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, H, mmax));
+    for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, H, mmax) + mmax);
     res_y = o;
-    o += 2 * (kResHi + kMaxLevels);
+    o += 2 * kResN;
     res_w = o;
-    o += kResHi + kMaxLevels;
+    o += kResN;
+    bcm = o;
+    o += 2 * kBcm;
     tab = o;
     o += 2 * kMaxLevels;
     total = o;
@@ -112,7 +122,6 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   using SM = typename S::SM;
   using S0 = typename S::S0;
   constexpr int MMAX = S::MMAX;
-  constexpr int RESN = kResHi + kMaxLevels;  // slots of one result buffer
   extern __shared__ __align__(16) float smem[];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t row = blockIdx.x / p.tiles_per_row;
@@ -132,10 +141,12 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   auto rsM = [&](auto M) { return p.rs[decltype(M)::value]; };
   float* RESY = smem + L.res_y;
   uint16_t* RESW = reinterpret_cast<uint16_t*>(smem + L.res_w);
+  int* BCM = reinterpret_cast<int*>(smem + L.bcm);   // [2][kBcm] keys of the best coarse level
   int* RTAB = reinterpret_cast<int*>(smem + L.tab);  // [2j]: ring offset, [2j+1]: mask
 
   // -inf everywhere a chunk past the end of the row would have written
-  for (int i = t; i < L.tab; i += kThreads) smem[i] = ninf();
+  for (int i = t; i < L.bcm; i += kThreads) smem[i] = ninf();
+  for (int i = t; i < 2 * kBcm; i += kThreads) BCM[i] = INT_MIN;
   if (t == 0) {
     int o = FX::RINGS;
     for (int j = 0; j < kMaxLevels; ++j) {
@@ -146,14 +157,21 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       const int n = ring_size(j, H, MMAX);
       RTAB[2 * j] = o;
       RTAB[2 * j + 1] = n - 1;
-      o += al4(n);
+      o += al4(n + MMAX);
     }
   }
   __syncthreads();
+  // ring write helper: slot and its mirror
+  auto ring_put = [&](int base, int mask, int n, float v) {
+    const int slot = n & mask;
+    smem[base + slot] = v;
+    if (slot < MMAX) smem[base + slot + mask + 1] = v;
+  };
   int r4 = 0, m4 = 0, r5 = 0, m5 = 0, r6 = 0, m6 = 0, r7 = 0, m7 = 0, r8 = 0, m8 = 0;
   // this thread's coarse position per chunk: level cj (0 = none), index cq
   const int ctop = top < kChunkLog ? top : kChunkLog;
-  int cj = 0, cq = 0;
+  int cj = 0, cq = 0, cbase = 0, cmask = 0, cfirst = 0, cnu = 0, cbcm = 0, ccode = 0;
+  float cf = 0.f;
   if (COARSE) {
     r4 = RTAB[8], m4 = RTAB[9], r5 = RTAB[10], m5 = RTAB[11], r6 = RTAB[12], m6 = RTAB[13];
     r7 = RTAB[14], m7 = RTAB[15], r8 = RTAB[16], m8 = RTAB[17];
@@ -165,6 +183,13 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       }
       cj = j;
       cq = t - off;
+      cbase = RTAB[2 * j];
+      cmask = RTAB[2 * j + 1];
+      cf = p.lvl_scale[j];
+      cfirst = p.lvl_first[j];
+      cnu = (j == top) ? p.n_top : SM::MM;
+      cbcm = cq << (j - 4);   // its start / 16
+      ccode = 15 - (j - 4);   // smaller level wins near-ties of the merge key
     }
   }
 
@@ -198,61 +223,63 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
     if (t < S::TL3) smem[FX::f3(nbuf) + kC / 8 + t] = o8;
     if (COARSE) {
       float s = o8 + __shfl_xor_sync(kFull, o8, 1);
-      if (!(lane & 1)) smem[r4 + (((ar >> 4) + (t >> 1)) & m4)] = s;
+      if (!(lane & 1)) ring_put(r4, m4, (ar >> 4) + (t >> 1), s);
       if (top >= 5) {
         s += __shfl_xor_sync(kFull, s, 2);
-        if (!(lane & 3)) smem[r5 + (((ar >> 5) + (t >> 2)) & m5)] = s;
+        if (!(lane & 3)) ring_put(r5, m5, (ar >> 5) + (t >> 2), s);
       }
       if (top >= 6) {
         s += __shfl_xor_sync(kFull, s, 4);
-        if (!(lane & 7)) smem[r6 + (((ar >> 6) + (t >> 3)) & m6)] = s;
+        if (!(lane & 7)) ring_put(r6, m6, (ar >> 6) + (t >> 3), s);
       }
       if (top >= 7) {
         s += __shfl_xor_sync(kFull, s, 8);
-        if (!(lane & 15)) smem[r7 + (((ar >> 7) + (t >> 4)) & m7)] = s;
+        if (!(lane & 15)) ring_put(r7, m7, (ar >> 7) + (t >> 4), s);
       }
       if (top >= 8) {
         s += __shfl_xor_sync(kFull, s, 16);
-        if (lane == 0) smem[r8 + (((ar >> 8) + warp) & m8)] = s;
+        if (lane == 0) ring_put(r8, m8, (ar >> 8) + warp, s);
       }
     }
   };
 
   // ---- coarse work of chunk k (after the barrier that follows its build) ----
+  // Each result also goes into a per-start key (order-preserving float key with
+  // the level in its 4 low bits) through a shared atomic maximum, so that the
+  // fine step finds the best coarse level of a start with one read.
   auto coarse = [&](int k) {
     const int ar = a0 - k * kC;
     if (warp == kThreads / 32 - 1 && top >= 9) {  // blocks of levels 9.. need every warp's level 8
       for (int j = 9; j <= top; ++j) {
-        const int nb = (j <= kChunkLog) ? (kC >> j) : ((((ar + (int)(t0 & ((1LL << j) - 1))) & ((1 << j) - 1)) == 0) ? 1 : 0);
+        const int nb = (j <= kChunkLog) ? (kC >> j) : ((((t0 + ar) & ((1LL << j) - 1)) == 0) ? 1 : 0);
         if (lane < nb) {
           const int n = (ar >> j) + lane;
           const float* R = smem + RTAB[2 * (j - 1)];
           const int m = RTAB[2 * (j - 1) + 1];
-          smem[RTAB[2 * j] + (n & RTAB[2 * j + 1])] = R[(2 * n) & m] + R[(2 * n + 1) & m];
+          ring_put(RTAB[2 * j], RTAB[2 * j + 1], n, R[(2 * n) & m] + R[(2 * n + 1) & m]);
         }
         __syncwarp();
       }
     }
     if (ar >= T) return;  // halo chunk: nothing to evaluate
-    float* RY = RESY + (k & 1) * RESN;
-    uint16_t* RW = RESW + (k & 1) * RESN;
-    auto eval_coarse = [&](int jj, int n, int slot) {
-      float w[MMAX];
-      const float* R = smem + RTAB[2 * jj];
-      const int m = RTAB[2 * jj + 1];
-#pragma unroll
-      for (int i = 0; i < MMAX; ++i) w[i] = R[(n + i) & m];
+    float* RY = RESY + (k & 1) * kResN;
+    uint16_t* RW = RESW + (k & 1) * kResN;
+    int* KB = BCM + (k & 1) * kBcm;
+    auto eval_one = [&](const float* w, int nu, float f, int first, int slot, int bcm, int code) {
       float bv[1], full[1];
       int bq[1];
-      const int nu = (jj == top) ? p.n_top : SM::MM;
       eval_window<1, MMAX, SM, true, false>(w, nu, rsM, nullptr, bv, bq, full);
-      RY[slot] = bv[0] * p.lvl_scale[jj];
-      RW[slot] = (uint16_t)(p.lvl_first[jj] + bq[0]);
+      const float y = bv[0] * f;
+      RY[slot] = y;
+      RW[slot] = (uint16_t)(first + bq[0]);
+      atomicMax(KB + bcm, (fkey(y) & ~15) | code);
     };
-    if (cj) eval_coarse(cj, (ar >> cj) + cq, t);
+    if (cj) eval_one(smem + cbase + (((ar >> cj) + cq) & cmask), cnu, cf, cfirst, t, cbcm, ccode);
     if (t == kThreads - 1)
       for (int jj = kChunkLog + 1; jj <= top; ++jj)
-        if (((t0 + ar) & ((1LL << jj) - 1)) == 0) eval_coarse(jj, ar >> jj, kResHi + jj - kChunkLog - 1);
+        if (((t0 + ar) & ((1LL << jj) - 1)) == 0)
+          eval_one(smem + RTAB[2 * jj] + ((ar >> jj) & RTAB[2 * jj + 1]), (jj == top) ? p.n_top : SM::MM,
+                   p.lvl_scale[jj], p.lvl_first[jj], kResHi + jj - kChunkLog - 1, 0, 15 - (jj - 4));
   };
 
   // ---- fine levels, merge and store of chunk k -----------------------------
@@ -264,12 +291,14 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
     float y[8];
     int w[8];
     {
-      float win[S::NW0 * 4], full[8];
+      float win[S::NW0 * 4];
       load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
-      if (!COARSE && top == 0)
+      if (!COARSE && top == 0) {
+        float full[8];
         eval_window<8, MMAX, S0, true, false>(win, p.n_top, rsM, nullptr, y, w, full);
-      else
-        eval_window<8, MMAX, S0, false, false>(win, p.n_top, rsM, nullptr, y, w, full);
+      } else {
+        eval_window_mx<8, MMAX, S0>(win, rsM, y, w);
+      }
     }
     if (COARSE || top >= 1) {
       float win[S::NW1 * 4], bv[4], full[4];
@@ -307,20 +336,14 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
         eval_window<1, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
       merge1(y[0], w[0], bv[0] * p.lvl_scale[3], p.lvl_first[3] + bq[0]);
     }
-    if (COARSE) {
-      const float* RY = RESY + (k & 1) * RESN;
-      const uint16_t* RW = RESW + (k & 1) * RESN;
-      for (int j = kRing0; j <= ctop; ++j) {
-        if (t & ((1 << (j - 3)) - 1)) break;
-        const int slot = 256 - (1 << (kChunkLog + 1 - j)) + (t >> (j - 3));
-        merge1(y[0], w[0], RY[slot], RW[slot]);
-      }
-      if (t == 0)
-        for (int jj = kChunkLog + 1; jj <= top; ++jj)
-          if (((t0 + ar) & ((1LL << jj) - 1)) == 0) {
-            const int slot = kResHi + jj - kChunkLog - 1;
-            merge1(y[0], w[0], RY[slot], RW[slot]);
-          }
+    if (COARSE && !(t & 1)) {  // best coarse level at start 8t (= 0 mod 16)
+      int* kp = BCM + (k & 1) * kBcm + (t >> 1);
+      const int key = *kp;
+      *kp = INT_MIN;  // ready for chunk k + 2
+      const int lvl = kRing0 + 15 - (key & 15);
+      const int slot = (lvl <= kChunkLog) ? 256 - (1 << (kChunkLog + 1 - lvl)) + (t >> (lvl - 3))
+                                          : kResHi + lvl - kChunkLog - 1;
+      merge1(y[0], w[0], RESY[(k & 1) * kResN + slot], RESW[(k & 1) * kResN + slot]);
     }
     const int s0 = ar + 8 * t;
     if (s0 + 8 <= nrel) {
