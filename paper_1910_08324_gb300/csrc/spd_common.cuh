@@ -280,6 +280,33 @@ __device__ __forceinline__ void eval_window_mx(const float* w, Scale&& scale, fl
   });
 }
 
+// Like eval_window_mx for one position, but only ranks below n_used count
+// (the last level of a grid); the others are set to -inf without branching.
+template <int MMAX, class Pred, class Scale>
+__device__ __forceinline__ void eval_one_masked(const float* w, int n_used, Scale&& scale,
+                                                float& bv, int& bq) {
+  constexpr int NC = count_in<Pred, MMAX>();
+  float v[NC];
+  float S = 0.0f;
+  static_for<1, MMAX + 1>([&](auto M) {
+    constexpr int m = decltype(M)::value;
+    S += w[m - 1];
+    if constexpr (Pred::in(m)) {
+      constexpr int rk = Pred::rank(m);
+      const float x = S * scale(M);
+      v[rk] = (rk == 0 || rk < n_used) ? x : ninf();
+    }
+  });
+  const float best = tree_max<NC>(v);
+  int q = NC - 1;
+  static_for<0, NC - 1>([&](auto C) {
+    constexpr int c = NC - 2 - decltype(C)::value;
+    if (v[c] == best) q = c;
+  });
+  bv = best;
+  bq = q;
+}
+
 // Load a window of NW float4s from 16-byte aligned shared memory.
 template <int NW>
 __device__ __forceinline__ void load_window4(const float* src, float (&w)[NW * 4]) {

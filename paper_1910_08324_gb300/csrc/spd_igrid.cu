@@ -161,28 +161,40 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
     }
   }
   __syncthreads();
-  // ring write helper: slot and its mirror
+  // ring write: slot and, for the first MMAX slots, its mirror (a select, no branch)
   auto ring_put = [&](int base, int mask, int n, float v) {
     const int slot = n & mask;
     smem[base + slot] = v;
-    if (slot < MMAX) smem[base + slot + mask + 1] = v;
+    smem[base + (slot < MMAX ? slot + mask + 1 : slot)] = v;
   };
-  int r4 = 0, m4 = 0, r5 = 0, m5 = 0, r6 = 0, m6 = 0, r7 = 0, m7 = 0, r8 = 0, m8 = 0;
+  // chunks at relative starts ar(k) = a0 - k*kC, k = 0..nch-1 (backwards in time)
+  int a0 = T + H - kC;
+  if (a0 >= nrel) a0 = ((nrel - 1) / kC) * kC;  // chunks at or past nt are all -inf
+  const int nch = a0 / kC + 1;
+
+  // rings of levels 4..8 get one value per thread and level per chunk (all lanes
+  // of a block write the same value): block index of this thread at chunk 0
+  int rb[5] = {0, 0, 0, 0, 0}, rm[5] = {0, 0, 0, 0, 0}, rn[5] = {0, 0, 0, 0, 0};
   // this thread's coarse position per chunk: level cj (0 = none), index cq
   const int ctop = top < kChunkLog ? top : kChunkLog;
-  int cj = 0, cq = 0, cbase = 0, cmask = 0, cfirst = 0, cnu = 0, cbcm = 0, ccode = 0;
+  int cj = 0, cbase = 0, cmask = 0, cfirst = 0, cnu = 0, cbcm = 0, ccode = 0, cn = 0;
   float cf = 0.f;
   if (COARSE) {
-    r4 = RTAB[8], m4 = RTAB[9], r5 = RTAB[10], m5 = RTAB[11], r6 = RTAB[12], m6 = RTAB[13];
-    r7 = RTAB[14], m7 = RTAB[15], r8 = RTAB[16], m8 = RTAB[17];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int j = kRing0 + i;
+      rb[i] = RTAB[2 * j];
+      rm[i] = RTAB[2 * j + 1];
+      rn[i] = (a0 >> j) + (t >> (j - 3));
+    }
     if (t < 256 - (1 << (kChunkLog - ctop))) {  // positions of levels 4..ctop
       int j = kRing0, off = 0;
       while (t >= off + (kC >> j)) {
         off += kC >> j;
         ++j;
       }
+      const int cq = t - off;
       cj = j;
-      cq = t - off;
       cbase = RTAB[2 * j];
       cmask = RTAB[2 * j + 1];
       cf = p.lvl_scale[j];
@@ -190,13 +202,15 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       cnu = (j == top) ? p.n_top : SM::MM;
       cbcm = cq << (j - 4);   // its start / 16
       ccode = 15 - (j - 4);   // smaller level wins near-ties of the merge key
+      cn = (a0 >> j) + cq;    // its block index at chunk 0 (decreases by kC >> j per chunk)
     }
   }
-
-  // chunks at relative starts ar(k) = a0 - k*kC, k = 0..nch-1 (backwards in time)
-  int a0 = T + H - kC;
-  if (a0 >= nrel) a0 = ((nrel - 1) / kC) * kC;  // chunks at or past nt are all -inf
-  const int nch = a0 / kC + 1;
+  // level-9..11 blocks of a chunk: lane L of the last warp builds block lb of level lj
+  // as the sum of lw level-8 blocks (lanes 0..3: level 9, 4..5: level 10, 6: level 11)
+  const int lj = lane < 4 ? 9 : (lane < 6 ? 10 : 11);
+  const int lb = lane < 4 ? lane : (lane < 6 ? lane - 4 : 0);
+  const int lw = 1 << (lj - 8);
+  const bool lbuild = COARSE && warp == kThreads / 32 - 1 && lane < 7 && lj <= top;
 
   // ---- building chunk k: levels 0..3 into buffer k % 4, tails, rings 4..8 ----
   auto build = [&](int k, float4 x0, float4 x1) {
@@ -222,23 +236,24 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
     smem[FX::f3(buf) + t] = o8;
     if (t < S::TL3) smem[FX::f3(nbuf) + kC / 8 + t] = o8;
     if (COARSE) {
+      const int d = k * kC;  // rn[] hold chunk-0 block indices
       float s = o8 + __shfl_xor_sync(kFull, o8, 1);
-      if (!(lane & 1)) ring_put(r4, m4, (ar >> 4) + (t >> 1), s);
+      ring_put(rb[0], rm[0], rn[0] - (d >> 4), s);
       if (top >= 5) {
         s += __shfl_xor_sync(kFull, s, 2);
-        if (!(lane & 3)) ring_put(r5, m5, (ar >> 5) + (t >> 2), s);
+        ring_put(rb[1], rm[1], rn[1] - (d >> 5), s);
       }
       if (top >= 6) {
         s += __shfl_xor_sync(kFull, s, 4);
-        if (!(lane & 7)) ring_put(r6, m6, (ar >> 6) + (t >> 3), s);
+        ring_put(rb[2], rm[2], rn[2] - (d >> 6), s);
       }
       if (top >= 7) {
         s += __shfl_xor_sync(kFull, s, 8);
-        if (!(lane & 15)) ring_put(r7, m7, (ar >> 7) + (t >> 4), s);
+        ring_put(rb[3], rm[3], rn[3] - (d >> 7), s);
       }
       if (top >= 8) {
         s += __shfl_xor_sync(kFull, s, 16);
-        if (lane == 0) ring_put(r8, m8, (ar >> 8) + warp, s);
+        ring_put(rb[4], rm[4], rn[4] - (d >> 8), s);
       }
     }
   };
@@ -250,31 +265,42 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   auto coarse = [&](int k) {
     const int ar = a0 - k * kC;
     if (warp == kThreads / 32 - 1 && top >= 9) {  // blocks of levels 9.. need every warp's level 8
-      for (int j = 9; j <= top; ++j) {
-        const int nb = (j <= kChunkLog) ? (kC >> j) : ((((t0 + ar) & ((1LL << j) - 1)) == 0) ? 1 : 0);
-        if (lane < nb) {
-          const int n = (ar >> j) + lane;
+      if (lbuild) {
+        const float* R8 = smem + rb[4];
+        const int n8 = (ar >> 8) + lb * lw;
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float v = R8[(n8 + i) & rm[4]];
+          acc += (i < lw) ? v : 0.f;
+        }
+        ring_put(RTAB[2 * lj], RTAB[2 * lj + 1], (ar >> lj) + lb, acc);
+      }
+      for (int j = kChunkLog + 1; j <= top; ++j) {  // blocks longer than a chunk (rare)
+        __syncwarp();
+        if (lane == 0 && (((t0 + ar) & ((1LL << j) - 1)) == 0)) {
+          const int n = ar >> j;
           const float* R = smem + RTAB[2 * (j - 1)];
           const int m = RTAB[2 * (j - 1) + 1];
           ring_put(RTAB[2 * j], RTAB[2 * j + 1], n, R[(2 * n) & m] + R[(2 * n + 1) & m]);
         }
-        __syncwarp();
       }
+      __syncwarp();
     }
     if (ar >= T) return;  // halo chunk: nothing to evaluate
     float* RY = RESY + (k & 1) * kResN;
     uint16_t* RW = RESW + (k & 1) * kResN;
     int* KB = BCM + (k & 1) * kBcm;
     auto eval_one = [&](const float* w, int nu, float f, int first, int slot, int bcm, int code) {
-      float bv[1], full[1];
-      int bq[1];
-      eval_window<1, MMAX, SM, true, false>(w, nu, rsM, nullptr, bv, bq, full);
-      const float y = bv[0] * f;
+      float bv;
+      int bq;
+      eval_one_masked<MMAX, SM>(w, nu, rsM, bv, bq);
+      const float y = bv * f;
       RY[slot] = y;
-      RW[slot] = (uint16_t)(first + bq[0]);
+      RW[slot] = (uint16_t)(first + bq);
       atomicMax(KB + bcm, (fkey(y) & ~15) | code);
     };
-    if (cj) eval_one(smem + cbase + (((ar >> cj) + cq) & cmask), cnu, cf, cfirst, t, cbcm, ccode);
+    if (cj) eval_one(smem + cbase + ((cn - ((k * kC) >> cj)) & cmask), cnu, cf, cfirst, t, cbcm, ccode);
     if (t == kThreads - 1)
       for (int jj = kChunkLog + 1; jj <= top; ++jj)
         if (((t0 + ar) & ((1LL << jj) - 1)) == 0)
@@ -336,14 +362,19 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
         eval_window<1, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
       merge1(y[0], w[0], bv[0] * p.lvl_scale[3], p.lvl_first[3] + bq[0]);
     }
-    if (COARSE && !(t & 1)) {  // best coarse level at start 8t (= 0 mod 16)
+    if (COARSE) {  // best coarse level at start 8t (even t: 8t = 0 mod 16), without branching
       int* kp = BCM + (k & 1) * kBcm + (t >> 1);
       const int key = *kp;
-      *kp = INT_MIN;  // ready for chunk k + 2
+      *kp = INT_MIN;  // ready for chunk k + 2 (both lanes of a pair write the same value)
       const int lvl = kRing0 + 15 - (key & 15);
       const int slot = (lvl <= kChunkLog) ? 256 - (1 << (kChunkLog + 1 - lvl)) + (t >> (lvl - 3))
                                           : kResHi + lvl - kChunkLog - 1;
-      merge1(y[0], w[0], RESY[(k & 1) * kResN + slot], RESW[(k & 1) * kResN + slot]);
+      const bool use = !(t & 1) && key != INT_MIN;
+      const float yv = RESY[(k & 1) * kResN + (use ? slot : 0)];
+      const int wv = RESW[(k & 1) * kResN + (use ? slot : 0)];
+      const bool take = use && yv > y[0];
+      y[0] = take ? yv : y[0];
+      w[0] = take ? wv : w[0];
     }
     const int s0 = ar + 8 * t;
     if (s0 + 8 <= nrel) {
