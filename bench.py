@@ -43,6 +43,8 @@ T_SAMP = 64e-6
 SKA_DM = 6000
 BYTES_PER_SAMPLE = 4 + 4 + 2  # f32 in, f32 Y out, u16 W out (algorithmic, once each)
 METRIC = "DM x time samples/s"
+SM_MAX_HZ = 2070e6          # GB300 maximum SM clock
+ALU_BALANCE_CANDIDATES = 10  # above this many candidates per sample a grid is ALU-bound
 
 ALGOS = {
     "ig1": dict(algo=2, igrid_depth=1, igrid_layers=4),
@@ -54,8 +56,9 @@ ALGOS = {
     "bd32": dict(algo=1, boxdit_lmax=32),
     "exh": dict(algo=0),
 }
-# candidates per input sample of each grid (sum over widths of 1/L_s), for the ALU roofline
-SEARCH_SOURCES = ["paper_1910_08324_gb300/csrc/spd_search.cu", "paper_1910_08324_gb300/csrc/spd_internal.h"]
+SEARCH_SOURCES = ["paper_1910_08324_gb300/csrc/spd_igrid.cu", "paper_1910_08324_gb300/csrc/spd_search.cu",
+                  "paper_1910_08324_gb300/csrc/spd_common.cuh", "paper_1910_08324_gb300/csrc/spd_internal.h"]
+L2_BYTES = 129 * 1024 * 1024
 
 
 def parse():
@@ -64,6 +67,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ska_mid", choices=["ska_mid", "exhaustive_small"],
+                    help="ska_mid: 4096 x 1M lossy search (default); exhaustive_small: 64 x 65536, widths 1..256")
     ap.add_argument("--algo", default="ig1", choices=sorted(ALGOS))
     ap.add_argument("--ndm", type=int, default=spd_synth.SKA_MID["ndm"])
     ap.add_argument("--nt", type=int, default=spd_synth.SKA_MID["nt"])
@@ -220,6 +225,8 @@ def reference_arm(args):
 
 def main():
     args = parse()
+    if args.workload == "exhaustive_small":
+        args.ndm, args.nt, args.s_end, args.algo = 64, 65536, 256, "exh"
     if args.impl == "reference":
         return reference_arm(args)
     import torch
@@ -240,9 +247,13 @@ def main():
 
     # inputs: every rank searches its own full-size block of DM trials (weak scaling)
     seed = spd_synth.SEED_BASE + 2 + 1000 * rank
-    tab = spd_synth.ska_mid_pulses(seed=seed, ndm=ndm, nt=nt)
-    x = spd_synth.device_noise(ndm, nt, seed, device=dev)
-    spd_synth.device_inject(x, tab)
+    if args.workload == "exhaustive_small":
+        xs, tab = spd_synth.exhaustive_small(seed=spd_synth.SEED_BASE + 1 + 1000 * rank)
+        x = torch.from_numpy(xs).to(dev)
+    else:
+        tab = spd_synth.ska_mid_pulses(seed=seed, ndm=ndm, nt=nt)
+        x = spd_synth.device_noise(ndm, nt, seed, device=dev)
+        spd_synth.device_inject(x, tab)
     mu = torch.zeros(ndm, device=dev)
     sg = torch.ones(ndm, device=dev)
     Y = torch.empty((ndm, nt), dtype=torch.float32, device=dev)
@@ -261,16 +272,21 @@ def main():
         fused_step()
     torch.cuda.synchronize(dev)
 
-    # timed region: K fused steps, each bracketed by events; search-kernel events too
+    # timed region: K steps (search + candidates), each bracketed by events on the
+    # launching stream.  When the working set (input + outputs) is smaller than
+    # twice the L2, a 512 MiB buffer is written between steps (outside the events)
+    # so that every step starts from a cold L2.
+    flush = None
+    if BYTES_PER_SAMPLE * ndm * nt < 2 * L2_BYTES:
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
         for k in range(args.steps):
+            if flush is not None:
+                flush.zero_()
             ev[3 * k].record(stream)
             spd.spd_execute(plan, x.data_ptr(), mu.data_ptr(), sg.data_ptr(), Y.data_ptr(),
                             W.data_ptr(), ws.data_ptr(), ws.numel(), sp)
@@ -278,13 +294,12 @@ def main():
             spd.spd_candidates(plan, Y.data_ptr(), W.data_ptr(), args.threshold, args.radius,
                                out.data_ptr(), cap, cnt.data_ptr(), ws.data_ptr(), ws.numel(), 1, sp)
             ev[3 * k + 2].record(stream)
-        t_end.record(stream)
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
-    total_ms = t_start.elapsed_time(t_end)
     search_ms = [ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(args.steps)]
     cand_ms = [ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(args.steps)]
+    total_ms = sum(ev[3 * k].elapsed_time(ev[3 * k + 2]) for k in range(args.steps))
     if world > 1:
         tt = torch.tensor([total_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -294,17 +309,31 @@ def main():
     value = samples_step / (ms_per_step / 1e3)
     n_cand = int(cnt.item())
 
-    # roofline of the dominant kernel (the search): algorithmic bytes / event time
+    # roofline of the dominant kernel (the search): algorithmic work / event time.
+    # A grid is HBM-bound when its candidates per sample fit the ALU budget of
+    # 10 bytes; dense grids are reported against the ALU peak in
+    # candidates/s (3 lane operations per candidate: add, scale, compare).
     peak, peak_kind = measured_peaks()
     s_avg = statistics.mean(search_ms)
-    achieved = BYTES_PER_SAMPLE * ndm * nt / (s_avg / 1e3) / 1e9
     traffic = recorded_traffic(args.algo, ndm, nt)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "search (%s)" % args.algo, "kernel_ms": s_avg,
-                "candidates_ms": statistics.mean(cand_ms),
-                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
-                if peak_kind == "measured" else "fallback 6800 GB/s"}
+    if cand_per_sample <= ALU_BALANCE_CANDIDATES:
+        achieved = BYTES_PER_SAMPLE * ndm * nt / (s_avg / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                    if peak_kind == "measured" else "fallback 6800 GB/s"}
+    else:
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = sm_count * 128 * SM_MAX_HZ / 3.0
+        achieved = cand_per_sample * ndm * nt / (s_avg / 1e3)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "candidates/s",
+                    "frac": achieved / alu_peak, "traffic": traffic,
+                    "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz / 3 ops per candidate"
+                                   % (sm_count, SM_MAX_HZ / 1e6),
+                    "hbm_GBps": BYTES_PER_SAMPLE * ndm * nt / (s_avg / 1e3) / 1e9}
+    roofline.update({"kernel": "search (%s)" % args.algo, "kernel_ms": s_avg,
+                     "candidates_ms": statistics.mean(cand_ms),
+                     "algorithmic_bytes_per_launch": BYTES_PER_SAMPLE * ndm * nt})
 
     # mean SNR loss on noise-free copies of the workload's pulses (GPU search)
     loss = None
@@ -322,8 +351,11 @@ def main():
         loss = {"mean_snr_loss": float(1.0 - np.mean(rs)), "pulses": len(rs),
                 "max_snr_loss": float(1.0 - np.min(rs)),
                 "definition": "mean over the workload's pulses, noise-free, of 1 - RSNR/SNR"}
-        x.copy_(spd_synth.device_noise(ndm, nt, seed, device=dev))
-        spd_synth.device_inject(x, tab)
+        if args.workload == "exhaustive_small":
+            x.copy_(torch.from_numpy(xs).to(dev))
+        else:
+            x.copy_(spd_synth.device_noise(ndm, nt, seed, device=dev))
+            spd_synth.device_inject(x, tab)
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -369,12 +401,15 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "ska_mid %d DM x %d samples, 64 us, 500 pulses" % (ndm, nt),
+            "config": {"workload": ("ska_mid %d DM x %d samples, 64 us, 500 pulses" % (ndm, nt))
+                       if args.workload == "ska_mid" else
+                       "exhaustive_small 64 DM x 65536 samples, 8 SNR-10 pulses, widths 1..256",
                        "algo": args.algo, "s_end": args.s_end, "l_end": int(widths[-1]),
                        "n_widths": int(len(widths)), "candidates_per_sample": cand_per_sample,
                        "threshold": args.threshold, "peak_radius": args.radius,
                        "candidates_found": n_cand, "parallelism": "dp%d (rows per GPU)" % world,
-                       "l2": "inputs (17.2 GB per GPU) larger than L2; no flush",
+                       "l2": ("inputs larger than L2 (%.1f GB per GPU); no flush" % (4 * ndm * nt / 1e9))
+                       if flush is None else "L2 flushed between steps (512 MiB write outside the timed events)",
                        "x_realtime_ska": value * T_SAMP / SKA_DM,
                        "x_realtime_batch": (nt * T_SAMP) / (ms_per_step / 1e3)},
             "snr_loss": loss,
