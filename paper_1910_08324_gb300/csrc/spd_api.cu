@@ -300,21 +300,18 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
   if (p->family == kExhaustive) {
     p->tile = spd::kChunk;
     p->halo = 0;
-  } else if (p->family == kIgrid) {
-    // one CTA streams a segment of up to 131072 starts (a multiple of the
-    // candidate tile); the halo is the widest boxcar, rounded to whole chunks
+  } else {
+    // BoxDIT and IGRID: one CTA streams a segment of up to 131072 starts (a
+    // multiple of the candidate tile); the halo is the widest boxcar, rounded
+    // to whole chunks
+    if (p->family == kBoxdit && p->top > 11) {  // unreachable below kMaxLend; the kernel stops at 11
+      delete p;
+      return SPD_ERR_UNSUPPORTED;
+    }
     int64_t T = ((d.nt + spd::kCandTile - 1) / spd::kCandTile) * spd::kCandTile;
     if (T > 131072) T = 131072;
     p->tile = (int)T;
     p->halo = ((p->lend + spd::kChunk - 1) / spd::kChunk) * spd::kChunk;
-  } else {
-    int64_t T = 16384;
-    int64_t np2 = spd::kChunk;
-    while (np2 < d.nt && np2 < T) np2 <<= 1;
-    T = np2;
-    while (T < ((int64_t)1 << p->top)) T <<= 1;
-    p->tile = (int)T;
-    p->halo = (p->lend + 127) / 128 * 128;
   }
   p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
   p->cand_tiles_per_row = (d.nt + spd::kCandTile - 1) / spd::kCandTile;

@@ -24,6 +24,11 @@ __device__ __forceinline__ void static_for(F&& f) {
 
 __host__ __device__ constexpr int al4(int v) { return (v + 3) & ~3; }
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ constexpr int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
 
 // Order-preserving int key of a float (signed compare): used for atomic maxima.
 __device__ __forceinline__ int fkey(float f) {
@@ -252,18 +257,19 @@ __device__ __forceinline__ float tree_max(const float (&v)[N]) {
   }
 }
 
-// eval_window without a base and without PARTIAL, computed another way: the
-// candidates' scaled sums are kept, their maximum is taken with three-input max
-// instructions, and the rank is the first candidate equal to it (the smallest
-// width on ties, as with the strict '>' scan in increasing width order).
-template <int NP, int MMAX, class Pred, class Scale>
-__device__ __forceinline__ void eval_window_mx(const float* w, Scale&& scale, float (&bv)[NP],
-                                               int (&bq)[NP]) {
+// eval_window without PARTIAL, computed another way: the candidates' scaled
+// sums are kept, their maximum is taken with three-input max instructions, and
+// the rank is the first candidate equal to it (the smallest width on ties, as
+// with the strict '>' scan in increasing width order).  Running sums start from
+// base[r] when HAS_BASE; full[r] receives the MMAX-block sum.
+template <int NP, int MMAX, class Pred, bool HAS_BASE, class Scale>
+__device__ __forceinline__ void eval_window_mxb(const float* w, const float* base, Scale&& scale,
+                                                float (&bv)[NP], int (&bq)[NP], float (&full)[NP]) {
   constexpr int NC = count_in<Pred, MMAX>();
   static_for<0, NP>([&](auto R) {
     constexpr int r = decltype(R)::value;
     float v[NC];
-    float S = 0.0f;
+    float S = HAS_BASE ? base[r] : 0.0f;
     static_for<1, MMAX + 1>([&](auto M) {
       constexpr int m = decltype(M)::value;
       S += w[r + m - 1];
@@ -277,7 +283,15 @@ __device__ __forceinline__ void eval_window_mx(const float* w, Scale&& scale, fl
     });
     bv[r] = best;
     bq[r] = q;
+    full[r] = S;
   });
+}
+
+template <int NP, int MMAX, class Pred, class Scale>
+__device__ __forceinline__ void eval_window_mx(const float* w, Scale&& scale, float (&bv)[NP],
+                                               int (&bq)[NP]) {
+  float full[NP];
+  eval_window_mxb<NP, MMAX, Pred, false>(w, nullptr, scale, bv, bq, full);
 }
 
 // Like eval_window_mx for one position, but only ranks below n_used count

@@ -45,12 +45,6 @@ constexpr int kChunkLog = 11;         // log2(kC): levels above it span several 
 static_assert((1 << kChunkLog) == kC, "chunk must be 2^11");
 constexpr int kResHi = 256;           // RES slots of levels > kChunkLog start here
 
-__host__ __device__ constexpr int next_pow2(int v) {
-  int p = 1;
-  while (p < v) p <<= 1;
-  return p;
-}
-
 template <int D, int PL>
 struct IgS {
   using SM = IgM<D, PL>;

@@ -50,10 +50,10 @@ struct SearchParams {
   const float* mu;
   const float* sigma;
   int64_t ndm, nt, ld;
-  int32_t tile;         // starts per CTA (multiple of kChunk)
+  int32_t tile;         // starts per CTA (multiple of kChunk; streaming kernels: of kCandTile)
   int32_t tiles_per_row;
   int32_t cand_tiles_per_row;  // ceil(nt / kCandTile)
-  int32_t halo;         // samples read past the tile for the coarse levels (multiple of 128)
+  int32_t halo;         // samples read past the segment (widest boxcar, whole 2048-sample chunks)
   int32_t top;          // index of the last level
   int32_t n_top;        // block counts used on the last level (a prefix of its set)
   int32_t vec;          // 1: 16-byte vector loads/stores are legal
@@ -100,10 +100,12 @@ struct spd_plan {
 };
 
 namespace spd {
-// kernel launchers (spd_search.cu, spd_candidates.cu)
+// kernel launchers (spd_search.cu, spd_igrid.cu, spd_boxdit.cu, spd_candidates.cu)
 cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 size_t igrid_smem_bytes(const spd_plan& plan);
+cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
+size_t boxdit_smem_bytes(const spd_plan& plan);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
 cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s);
 size_t search_smem_bytes(const spd_plan& plan);

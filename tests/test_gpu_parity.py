@@ -44,6 +44,11 @@ CASES = [
     ("exh", 256, 3, 9001), ("exh", 64, 2, 4099), ("exh", 1, 2, 513), ("exh", 1000, 2, 5000),
     ("bd8", 8192, 3, 40000), ("bd16", 8192, 2, 40001), ("bd32", 8192, 2, 36003),
     ("bd8", 60, 2, 20000), ("bd16", 300, 2, 18000), ("bd32", 33, 2, 5000), ("bd32", 2000, 2, 33000),
+    # BoxDIT: every top level kind -- fine only (top 0..3), first coarse level (K = 8: with
+    # remainder blocks; K = 16: aligned; K = 32: base of K - 2 blocks), deepest levels, and
+    # rows longer than one 131072-start segment
+    ("bd32", 20, 2, 3000), ("bd16", 100, 2, 6000), ("bd8", 200, 2, 17000), ("bd32", 700, 2, 20000),
+    ("bd8", 20000, 2, 140000), ("bd32", 20000, 2, 50000), ("bd16", 30000, 1, 140001),
     ("dit", 8192, 3, 40000), ("ig0p2", 4096, 2, 30000), ("ig1p2", 4096, 2, 30000),
     ("ig1", 8192, 3, 50000), ("ig1", 6, 2, 3000), ("ig1", 20, 2, 17000), ("ig1", 5000, 2, 33000),
     ("ig2p4", 4096, 2, 30000), ("ig2", 8192, 3, 40003), ("ig2", 12, 2, 5000),
