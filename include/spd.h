@@ -230,9 +230,10 @@ spd_status spd_search(const spd_plan *plan, const void *d_x, const spd_noise *no
  *
  * Same rule, arguments, output and errors as spd_candidates with
  * use_tile_max = 0 (every tile of d_snr is scanned), minus the workspace.  Its
- * scratch is one array inside the library: per-tile counts and offsets for at
- * most 262,144 candidate tiles of 16,384 starts (ndm * ceil(nt / 16384) tiles,
- * 3 MiB, held by every device that loads the library until the process exits).
+ * scratch is one array inside the library: per-tile counts and per-group sums
+ * and offsets for at most 262,144 candidate tiles of 16,384 starts
+ * (ndm * ceil(nt / 16384) tiles; 1.1 MiB, held by every device that loads the
+ * library until the process exits).
  * A plan with more tiles is rejected with SPD_ERR_UNSUPPORTED before any work
  * is queued.  The call itself allocates nothing.
  *   - The first call on a device looks up the array's device address (once per

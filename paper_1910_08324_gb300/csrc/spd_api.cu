@@ -91,14 +91,18 @@ spd_status build_igrid(spd_plan* p) {
 
 spd_status check_cuda(cudaError_t e) { return e == cudaSuccess ? SPD_OK : SPD_ERR_CUDA; }
 
+// Workspace: tile maxima (written by the search, read by the candidate step),
+// per-tile candidate counts, per-group sums and offsets.
 struct WsLayout {
-  size_t tile_max, counts, offsets, total;
+  size_t tile_max, counts, gsum, goff, total;
   explicit WsLayout(const spd_plan& p) {
     const size_t nt = (size_t)(p.desc.ndm * p.cand_tiles_per_row);
+    const size_t ng = (nt + spd::kCandGroup - 1) / spd::kCandGroup;
     tile_max = 0;
     counts = align_up(tile_max + nt * sizeof(float));
-    offsets = align_up(counts + nt * sizeof(int32_t));
-    total = align_up(offsets + nt * sizeof(int64_t));
+    gsum = align_up(counts + nt * sizeof(int32_t));
+    goff = align_up(gsum + ng * sizeof(int32_t));
+    total = align_up(goff + ng * sizeof(int64_t));
   }
 };
 
@@ -173,7 +177,7 @@ spd_status check_cand_args(const spd_plan* plan, const float* d_snr, const uint1
   return SPD_OK;
 }
 
-// Fills everything but the scratch pointers (counts, offsets, tile_max).
+// Fills everything but the scratch pointers (counts, gsum, goff, tile_max).
 void fill_cand_params(spd::CandParams& p, const spd_plan* plan, const float* d_snr,
                       const uint16_t* d_width_idx, float threshold, int32_t peak_radius,
                       spd_candidate* d_out, int64_t cap, int64_t* d_count) {
@@ -210,7 +214,8 @@ spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_
   char* base = static_cast<char*>(d_ws);
   p.tile_max = use_tile_max ? reinterpret_cast<const float*>(base + wl.tile_max) : nullptr;
   p.counts = reinterpret_cast<int32_t*>(base + wl.counts);
-  p.offsets = reinterpret_cast<int64_t*>(base + wl.offsets);
+  p.gsum = reinterpret_cast<int32_t*>(base + wl.gsum);
+  p.goff = reinterpret_cast<int64_t*>(base + wl.goff);
   const cudaError_t e = spd::launch_candidates(*plan, p, stream);
   delete cp;
   return check_cuda(e);

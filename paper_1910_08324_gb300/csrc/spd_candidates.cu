@@ -6,35 +6,50 @@
 // Y[s] >= Y[s'] for s < s' <= s + R (inside the row); the leftmost sample of a
 // plateau wins and R = 0 is a plain threshold.
 //
-// Deterministic compaction in (row, start) order, three launches:
-//   count  -- one CTA per tile counts its candidates (tiles whose maximum SNR,
-//             recorded by the search kernel, is below the threshold are
-//             skipped without reading them);
-//   scan   -- one CTA turns the per-tile counts into int64 offsets and writes
-//             the total to *d_count;
-//   write  -- tiles with candidates re-test their starts 256 at a time and
-//             write their records at offset + block-prefix, keeping the first
-//             cap records overall.
+// Deterministic compaction in (row, start) order.  Candidate tiles (16384
+// starts of one row) are taken 32 at a time by one warp ("groups"):
+//   count  -- a warp reads its group's 32 tile maxima (recorded by the search
+//             kernel) with one load, skips the tiles below the threshold without
+//             reading them, and counts the candidates of the others; it writes
+//             the 32 per-tile counts and their sum;
+//   scan   -- one CTA turns the group sums into int64 group offsets (coalesced
+//             passes of 1024 groups with a running carry) and writes the total
+//             to *d_count;
+//   write  -- a warp scans its group's 32 counts and re-tests the starts of the
+//             tiles that have candidates, writing their records at offset +
+//             prefix (a ballot per 32 consecutive starts keeps the order); only
+//             the first cap records are kept.
+// A warp reads a tile 512 starts at a time (16 independent loads per lane)
+// and runs the peak test only where the threshold is met.
+// Count and write run as a grid of persistent warps (a few per SM) that stride
+// over the groups.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <mutex>
 
-#include "spd_internal.h"
+#include "spd_common.cuh"
 
-// Scratch of spd_candidates_static: per-tile counts (int32) followed by per-tile
-// offsets (int64) for at most kStaticCandTiles candidate tiles (3 MiB).  Every
-// device that loads the library holds this array until the process exits; all
-// calls on a device share it.
+// Scratch of spd_candidates_static: per-tile counts (int32), then per-group sums
+// (int32) and offsets (int64), for at most kStaticCandTiles candidate tiles
+// (1.1 MiB).  Every device that loads the library holds this array until the
+// process exits; all calls on a device share it.
 static __device__ __align__(256) unsigned char
-    g_static_cand_scratch[spd::kStaticCandTiles * (sizeof(int32_t) + sizeof(int64_t))];
+    g_static_cand_scratch[spd::kStaticCandTiles * sizeof(int32_t) +
+                          (spd::kStaticCandTiles / spd::kCandGroup) * (sizeof(int32_t) + sizeof(int64_t))];
 
 namespace spd {
 namespace {
 
 constexpr int kCandThreads = 256;
 constexpr int kScanThreads = 1024;
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCandCtas = 152 * 8;  // persistent CTAs of the count and write passes (upper bound)
+static_assert(kCandGroup == 32, "a group is one tile per lane");
+static_assert(sizeof(spd_candidate) == 24 && offsetof(spd_candidate, row) == 0 &&
+                  offsetof(spd_candidate, width_idx) == 4 && offsetof(spd_candidate, start) == 8 &&
+                  offsetof(spd_candidate, snr) == 16 && offsetof(spd_candidate, width) == 20,
+              "records are written as three 8-byte words");
 
 __device__ __forceinline__ float key_to_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
 
@@ -49,90 +64,145 @@ __device__ __forceinline__ bool is_cand(const float* __restrict__ y, int64_t s, 
   return true;
 }
 
-__global__ void __launch_bounds__(kCandThreads) cand_count_kernel(const CandParams p) {
-  __shared__ int red[kCandThreads / 32];
-  const int64_t t = blockIdx.x;
-  const int64_t row = t / p.tiles_per_row;
-  const int64_t t0 = (t % p.tiles_per_row) * (int64_t)p.tile;
-  if (p.tile_max && !(key_to_float(reinterpret_cast<const int*>(p.tile_max)[t]) >= p.thr)) {
-    if (threadIdx.x == 0) p.counts[t] = 0;
-    return;
-  }
-  const float* y = p.snr + row * p.ld;
-  const int64_t end = (t0 + p.tile < p.nt) ? t0 + p.tile : p.nt;
-  int c = 0;
-  for (int64_t s = t0 + threadIdx.x; s < end; s += kCandThreads) c += is_cand(y, s, p.nt, p.thr, p.radius) ? 1 : 0;
+__device__ __forceinline__ int warp_sum(int v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int tot = 0;
-    for (int k = 0; k < kCandThreads / 32; ++k) tot += red[k];
-    p.counts[t] = tot;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// (row, first start, end) of candidate tile `tile`
+struct TileSpan {
+  const float* y;
+  const uint16_t* w;
+  int64_t row, t0, end;
+  __device__ TileSpan(const CandParams& p, int64_t tile) {
+    row = tile / p.tiles_per_row;
+    t0 = (tile % p.tiles_per_row) * (int64_t)p.tile;
+    end = (t0 + p.tile < p.nt) ? t0 + p.tile : p.nt;
+    y = p.snr + row * p.ld;
+    w = p.widx + row * p.ld;
+  }
+};
+
+// The warp's SNRs at starts b + u*32 + lane, u < kUnroll (all loads issued
+// before any is used); -inf past the tile.
+constexpr int kUnroll = 16;
+__device__ __forceinline__ void load_block(const TileSpan& ts, int64_t b, int lane, float (&v)[kUnroll]) {
+#pragma unroll
+  for (int u = 0; u < kUnroll; ++u) {
+    const int64_t s = b + u * 32 + lane;
+    v[u] = (s < ts.end) ? __ldcs(ts.y + s) : __int_as_float(0xff800000u);
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) cand_scan_kernel(const CandParams p, int64_t ntiles) {
-  __shared__ int64_t part[kScanThreads];
-  const int64_t per = (ntiles + kScanThreads - 1) / kScanThreads;
-  const int64_t a = threadIdx.x * per;
-  const int64_t b = (a + per < ntiles) ? a + per : ntiles;
-  int64_t s = 0;
-  for (int64_t i = a; i < b; ++i) s += p.counts[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  // inclusive Hillis-Steele scan of the 1024 partial sums (tiny; once per call)
-  for (int o = 1; o < kScanThreads; o <<= 1) {
-    const int64_t v = (threadIdx.x >= o) ? part[threadIdx.x - o] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int64_t run = (threadIdx.x > 0) ? part[threadIdx.x - 1] : 0;
-  for (int64_t i = a; i < b; ++i) {
-    p.offsets[i] = run;
-    run += p.counts[i];
-  }
-  if (threadIdx.x == kScanThreads - 1) *p.d_count = part[kScanThreads - 1];
-}
-
-__global__ void __launch_bounds__(kCandThreads) cand_write_kernel(const CandParams p) {
-  __shared__ int wsum[kCandThreads / 32];
-  const int64_t t = blockIdx.x;
-  if (p.counts[t] == 0) return;
-  const int64_t row = t / p.tiles_per_row;
-  const int64_t t0 = (t % p.tiles_per_row) * (int64_t)p.tile;
-  const float* y = p.snr + row * p.ld;
-  const uint16_t* w = p.widx + row * p.ld;
-  const int64_t end = (t0 + p.tile < p.nt) ? t0 + p.tile : p.nt;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t base = p.offsets[t];
-  for (int64_t s0 = t0; s0 < end; s0 += kCandThreads) {
-    const int64_t s = s0 + threadIdx.x;
-    const bool f = (s < end) && is_cand(y, s, p.nt, p.thr, p.radius);
-    const unsigned bal = __ballot_sync(kFull, f);
-    if (lane == 0) wsum[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0, tot = 0;
-    for (int k = 0; k < kCandThreads / 32; ++k) {
-      before += (k < warp) ? wsum[k] : 0;
-      tot += wsum[k];
+__global__ void __launch_bounds__(kCandThreads) cand_count_kernel(const CandParams p, int64_t ntiles,
+                                                                  int64_t ngroups) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (kCandThreads / 32);
+  for (int64_t g = (int64_t)blockIdx.x * (kCandThreads / 32) + (threadIdx.x >> 5); g < ngroups; g += nwarps) {
+    const int64_t tile = g * kCandGroup + lane;
+    bool live = tile < ntiles;
+    if (live && p.tile_max) live = key_to_float(reinterpret_cast<const int*>(p.tile_max)[tile]) >= p.thr;
+    unsigned todo = __ballot_sync(kFull, live);
+    int mine = 0;
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const TileSpan ts(p, g * kCandGroup + src);
+      int c = 0;
+      for (int64_t b = ts.t0; b < ts.end; b += 32 * kUnroll) {
+        float v[kUnroll];
+        load_block(ts, b, lane, v);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+          if (v[u] >= p.thr) c += is_cand(ts.y, b + u * 32 + lane, p.nt, p.thr, p.radius) ? 1 : 0;
+      }
+      c = warp_sum(c);
+      if (lane == src) mine = c;
     }
-    if (f) {
-      const int64_t pos = base + before + __popc(bal & ((1u << lane) - 1u));
-      if (pos < p.cap) {
-        spd_candidate c;
-        c.row = (int32_t)row;
-        c.width_idx = (int32_t)w[s];
-        c.start = s;
-        c.snr = y[s];
-        c.width = p.width_mode ? p.width_tab[c.width_idx] : c.width_idx + 1;
-        p.out[pos] = c;
+    if (tile < ntiles) p.counts[tile] = mine;
+    const int gs = warp_sum(mine);
+    if (lane == 0) p.gsum[g] = gs;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) cand_scan_kernel(const CandParams p, int64_t ngroups) {
+  __shared__ int64_t wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t carry = 0;
+  for (int64_t base = 0; base < ngroups; base += kScanThreads) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = (i < ngroups) ? p.gsum[i] : 0;
+    int64_t x = v;  // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int64_t w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(kFull, w, o);
+        if (lane >= o) w += u;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    if (i < ngroups) p.goff[i] = carry + (warp ? wsum[warp - 1] : 0) + x - v;
+    carry += wsum[kScanThreads / 32 - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *p.d_count = carry;
+}
+
+__global__ void __launch_bounds__(kCandThreads, 1) cand_write_kernel(const CandParams p, int64_t ntiles,
+                                                                  int64_t ngroups) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t nwarps = (int64_t)gridDim.x * (kCandThreads / 32);
+  for (int64_t g = (int64_t)blockIdx.x * (kCandThreads / 32) + (threadIdx.x >> 5); g < ngroups; g += nwarps) {
+    const int64_t tile = g * kCandGroup + lane;
+    const int c = (tile < ntiles) ? p.counts[tile] : 0;
+    int x = c;  // inclusive warp scan of the tile counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += u;
+    }
+    const int64_t off = p.goff[g] + (x - c);
+    unsigned todo = __ballot_sync(kFull, c > 0);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      int64_t base = __shfl_sync(kFull, off, src);
+      if (base >= p.cap) break;  // later tiles start even later
+      const TileSpan ts(p, g * kCandGroup + src);
+      for (int64_t b = ts.t0; b < ts.end && base < p.cap; b += 32 * kUnroll) {
+        float v[kUnroll];
+        load_block(ts, b, lane, v);
+        static_for<0, kUnroll>([&](auto U) {
+          constexpr int u = decltype(U)::value;
+          const int64_t s = b + u * 32 + lane;
+          const bool f = v[u] >= p.thr && is_cand(ts.y, s, p.nt, p.thr, p.radius);
+          const unsigned bal = __ballot_sync(kFull, f);
+          if (f) {
+            const int64_t pos = base + __popc(bal & below);
+            if (pos < p.cap) {  // the 24-byte record as three 8-byte stores
+              const int wi = (int)ts.w[s];
+              const int wd = p.width_mode ? p.width_tab[wi] : wi + 1;
+              int2* o = reinterpret_cast<int2*>(p.out + pos);
+              o[0] = make_int2((int)ts.row, wi);
+              *reinterpret_cast<long long*>(o + 1) = (long long)s;
+              o[2] = make_int2(__float_as_int(v[u]), wd);
+            }
+          }
+          base += __popc(bal);
+        });
       }
     }
-    base += tot;
-    __syncthreads();
   }
 }
 
@@ -166,21 +236,27 @@ cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaSt
   void* base = nullptr;
   const cudaError_t e = static_cand_scratch(&base);
   if (e != cudaSuccess) return e;
-  p.counts = static_cast<int32_t*>(base);
-  p.offsets = reinterpret_cast<int64_t*>(static_cast<char*>(base) + kStaticCandTiles * sizeof(int32_t));
+  char* b = static_cast<char*>(base);
+  p.counts = reinterpret_cast<int32_t*>(b);
+  p.gsum = reinterpret_cast<int32_t*>(b + kStaticCandTiles * sizeof(int32_t));
+  p.goff = reinterpret_cast<int64_t*>(b + kStaticCandTiles * sizeof(int32_t) +
+                                      (kStaticCandTiles / kCandGroup) * sizeof(int32_t));
   p.tile_max = nullptr;  // no tile maxima without a workspace: every tile is scanned
   return launch_candidates(plan, p, s);
 }
 
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s) {
   const int64_t ntiles = plan.desc.ndm * plan.cand_tiles_per_row;
-  cand_count_kernel<<<(unsigned)ntiles, kCandThreads, 0, s>>>(p);
+  const int64_t ngroups = (ntiles + kCandGroup - 1) / kCandGroup;
+  int64_t ctas = (ngroups + kCandThreads / 32 - 1) / (kCandThreads / 32);
+  if (ctas > kCandCtas) ctas = kCandCtas;
+  cand_count_kernel<<<(unsigned)ctas, kCandThreads, 0, s>>>(p, ntiles, ngroups);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  cand_scan_kernel<<<1, kScanThreads, 0, s>>>(p, ntiles);
+  cand_scan_kernel<<<1, kScanThreads, 0, s>>>(p, ngroups);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  cand_write_kernel<<<(unsigned)ntiles, kCandThreads, 0, s>>>(p);
+  cand_write_kernel<<<(unsigned)ctas, kCandThreads, 0, s>>>(p, ntiles, ngroups);
   return cudaGetLastError();
 }
 

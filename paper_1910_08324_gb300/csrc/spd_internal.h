@@ -37,6 +37,7 @@ constexpr int kMaxLend = 32768;    // largest width a plan may reach
 constexpr int kMaxExhaustive = 4096;
 constexpr int kCandTile = 16384;   // starts per candidate tile (tile maxima granularity)
 constexpr int kMaxPeakRadius = 64;
+constexpr int kCandGroup = 32;     // candidate tiles per warp of the candidate passes
 constexpr int64_t kStaticCandTiles = 262144;  // candidate tiles spd_candidates_static can hold
 
 enum Family { kExhaustive = 0, kBoxdit = 1, kIgrid = 2 };
@@ -68,8 +69,9 @@ struct CandParams {
   const float* snr;
   const uint16_t* widx;
   const float* tile_max;   // ordered-int keys (see fkey) of tile maxima; nullptr: scan every tile
-  int32_t* counts;
-  int64_t* offsets;
+  int32_t* counts;         // [tiles] candidates per tile
+  int32_t* gsum;           // [groups] candidates per group of kCandGroup tiles
+  int64_t* goff;           // [groups] record offset of each group
   spd_candidate* out;
   int64_t* d_count;
   int64_t ndm, nt, ld, cap;
