@@ -102,13 +102,18 @@ typedef struct spd_plan_desc {
 } spd_plan_desc;
 
 /*
- * Noise statistics used for the SNR of Eq. SNRlong.
+ * Noise statistics used for the SNR of Eq. SNRlong, (X_L - mu_L) / sigma_L.
  *   mode 0 (white): mu[ndm], sigma[ndm] are the mean and standard deviation of
- *                   each row's samples; a width-L boxcar uses L*mu and
- *                   sqrt(L)*sigma (Eq. whitenoise).  sigma must be > 0.
- *   mode 1 (table): reserved for per-width statistics; SPD_ERR_UNSUPPORTED in
- *                   this build.
- * Both pointers are device pointers to float32.
+ *                   each row's samples; a width-L boxcar uses mu_L = L*mu and
+ *                   sigma_L = sqrt(L)*sigma (Eq. whitenoise).
+ *   mode 1 (table): mu[ndm][n_widths], sigma[ndm][n_widths] (row-major) give
+ *                   mu_L and sigma_L of every row for every width of the plan,
+ *                   in the order of spd_plan_widths (index 0 is width 1).  For
+ *                   noise that is not white, e.g. red noise or statistics
+ *                   measured at several decimations (Sec. 4.5).
+ * Both pointers are device pointers to float32, 4-byte aligned; every sigma
+ * must be finite and > 0 and every mu finite (not checked: other values give
+ * meaningless SNRs, no error).
  */
 typedef struct spd_noise {
   int32_t mode;
@@ -170,15 +175,15 @@ spd_status spd_workspace_size(const spd_plan *plan, size_t *bytes);
  * padding) are neither read nor written.
  *   d_x         device, [ndm][ld] samples of plan dtype, 4-byte aligned (16-byte
  *               alignment and ld % 4 == 0 enable vector loads)
- *   noise       host struct holding device pointers (mode 0 only)
+ *   noise       host struct holding device pointers (white or table mode)
  *   d_snr       device, [ndm][ld] float32 output
  *   d_width_idx device, [ndm][ld] uint16 output
  *   d_ws        device workspace of at least spd_workspace_size() bytes, or NULL
  *               if that size is 0; 256-byte aligned.  On return it holds the
  *               maximum SNR of every tile of every row (used by spd_search).
  *   stream      stream all work is queued on
- * Errors: SPD_ERR_INVALID_ARG (NULL or misaligned pointers), SPD_ERR_UNSUPPORTED
- * (table noise), SPD_ERR_WORKSPACE_TOO_SMALL, SPD_ERR_CUDA (launch failure).
+ * Errors: SPD_ERR_INVALID_ARG (NULL or misaligned pointers, noise mode not 0
+ * or 1), SPD_ERR_WORKSPACE_TOO_SMALL, SPD_ERR_CUDA (launch failure).
  * Outputs are only valid once the stream has reached this work.
  */
 spd_status spd_execute(const spd_plan *plan, const void *d_x, const spd_noise *noise,

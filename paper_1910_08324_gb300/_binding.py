@@ -211,10 +211,11 @@ def _ptr(t):
     return 0 if t is None else int(t.data_ptr())
 
 
-def execute(plan: Plan, x, mu, sigma, snr, width_idx, ws, stream=None):
-    """Run ``spd_execute`` on torch CUDA tensors (x: float32 [ndm, ld]; snr float32; width_idx int16/uint16)."""
+def execute(plan: Plan, x, mu, sigma, snr, width_idx, ws, stream=None, noise_mode: int = 0):
+    """Run ``spd_execute`` on torch CUDA tensors (x: float32 [ndm, ld]; snr float32;
+    width_idx int16/uint16; mu, sigma float32 [ndm], or [ndm, n_widths] with noise_mode 1)."""
     spd_execute(plan, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(snr), _ptr(width_idx), _ptr(ws),
-                ws.numel() * ws.element_size(), _stream(stream))
+                ws.numel() * ws.element_size(), _stream(stream), noise_mode=noise_mode)
 
 
 def candidates(plan: Plan, snr, width_idx, threshold: float, peak_radius: int, out, count, ws,
@@ -227,12 +228,12 @@ def candidates(plan: Plan, snr, width_idx, threshold: float, peak_radius: int, o
 
 
 def search(plan: Plan, x, mu, sigma, snr, width_idx, threshold: float, peak_radius: int, out, count,
-           ws, stream=None):
+           ws, stream=None, noise_mode: int = 0):
     """Run ``spd_search`` (search + candidates) on torch CUDA tensors."""
     cap = 0 if out is None else out.numel() * out.element_size() // CANDIDATE_DTYPE.itemsize
     spd_search(plan, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(snr), _ptr(width_idx), threshold,
                peak_radius, _ptr(out), cap, _ptr(count), _ptr(ws), ws.numel() * ws.element_size(),
-               _stream(stream))
+               _stream(stream), noise_mode=noise_mode)
 
 
 def records(out_tensor, count: int):

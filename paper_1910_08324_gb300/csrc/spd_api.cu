@@ -116,8 +116,9 @@ spd_status validate_ws(const spd_plan* plan, void* d_ws, size_t ws_bytes) {
 spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* noise, float* d_snr,
                       uint16_t* d_width_idx, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
   if (!plan || !d_x || !noise || !d_snr || !d_width_idx) return SPD_ERR_INVALID_ARG;
-  if (noise->mode != 0) return SPD_ERR_UNSUPPORTED;
-  if (!noise->mu || !noise->sigma) return SPD_ERR_INVALID_ARG;
+  if (noise->mode != 0 && noise->mode != 1) return SPD_ERR_INVALID_ARG;
+  if (!noise->mu || !noise->sigma || ((uintptr_t)noise->mu % 4) || ((uintptr_t)noise->sigma % 4))
+    return SPD_ERR_INVALID_ARG;
   if (((uintptr_t)d_x % 4) || ((uintptr_t)d_snr % 4) || ((uintptr_t)d_width_idx % 2))
     return SPD_ERR_INVALID_ARG;
   const spd_status ws = validate_ws(plan, d_ws, ws_bytes);
@@ -151,6 +152,12 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
     p.lvl_scale[j] = (float)std::pow(2.0, -0.5 * (double)j);
   }
   for (int m = 1; m < 64; ++m) p.rs[m] = (float)(1.0 / std::sqrt((double)m));
+  p.table = noise->mode == 1 ? 1 : 0;
+  p.n_widths = (int32_t)plan->widths.size();
+  p.unit_widths = plan->family == kExhaustive ? 1 : 0;
+  if (!p.unit_widths)
+    for (size_t i = 0; i < plan->widths.size() && i < (size_t)spd::kMaxGridWidths; ++i)
+      p.wtab[i] = plan->widths[i];
   if (plan->family == kBoxdit) {
     for (int j = 0; j <= plan->top; ++j)
       for (int m = 1; m <= plan->k; ++m)
@@ -298,7 +305,8 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
   }
   p->lend = p->widths.back();
   if (p->lend > spd::kMaxLend || p->widths.size() > 65535 ||
-      (p->family != kExhaustive && p->widths.size() > 512) || p->top >= spd::kMaxLevels) {
+      (p->family != kExhaustive && p->widths.size() > (size_t)spd::kMaxGridWidths) ||
+      p->top >= spd::kMaxLevels) {
     delete p;
     return SPD_ERR_INVALID_ARG;
   }
@@ -321,7 +329,7 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
   p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
   p->cand_tiles_per_row = (d.nt + spd::kCandTile - 1) / spd::kCandTile;
   if (p->desc.ndm * p->tiles_per_row > ((int64_t)1 << 31) - 1 ||
-      spd::search_smem_bytes(*p) > 227 * 1024) {
+      spd::search_smem_bytes(*p, true) > 227 * 1024) {
     delete p;
     return SPD_ERR_UNSUPPORTED;
   }

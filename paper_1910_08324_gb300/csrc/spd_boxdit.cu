@@ -82,8 +82,9 @@ __host__ __device__ constexpr int bd_ring_size(int j) {
 // coarse-merge keys (two buffers), the ring table and the coarse scale table.
 template <int K>
 struct BdDyn {
-  int res_y, res_w, bcm, tab, stab, total;
-  __host__ __device__ explicit BdDyn(int top) {
+  int res_y, res_w, bcm, tab, stab, ab, total;
+  // nab: widths of the table-noise constants (0 for white noise)
+  __host__ __device__ BdDyn(int top, int nab) {
     using S = BdS<K>;
     int o = S::RINGS;
     for (int j = kRing0; j <= top; ++j) {
@@ -100,15 +101,18 @@ struct BdDyn {
     o += 3 * kMaxLevels;
     stab = o;
     o += al4(kMaxLevels * (K + 1));
+    ab = o;
+    o += nab ? al4(2 * (nab + kAbPad)) : 0;
     total = o;
   }
 };
 
 // One coarse position: widths c_j + m 2^j, m = 1..K (ranks >= nu masked out).
 // A points at the window's first aligned block (SKIP0: one block earlier, for
-// the level whose base is K - 2 blocks), R at R_j[n].
-template <int K, bool HAS_R, bool SKIP0>
-__device__ __forceinline__ void bd_coarse_eval(const float* A, const float* R, const float* sc,
+// the level whose base is K - 2 blocks), R at R_j[n]; sc[m - 1] is the scale of
+// block count m (a float, or a float2 (a, b) for table noise).
+template <int K, bool HAS_R, bool SKIP0, class SC>
+__device__ __forceinline__ void bd_coarse_eval(const float* A, const float* R, const SC* sc,
                                                int nu, float& bv, int& bq) {
   float S = SKIP0 ? 0.0f : A[0];
   static_for<1, K - 1>([&](auto T) { S += A[decltype(T)::value]; });
@@ -117,7 +121,7 @@ __device__ __forceinline__ void bd_coarse_eval(const float* A, const float* R, c
     constexpr int m = decltype(M)::value;
     S += A[K - 2 + m];
     const float X = HAS_R ? S + R[K - 1 + m] : S;
-    v[m - 1] = (m == 1 || m - 1 < nu) ? X * sc[m] : ninf();
+    v[m - 1] = (m == 1 || m - 1 < nu) ? snr_of(X, sc[m - 1]) : ninf();
   });
   const float best = tree_max<K>(v);
   int q = K - 1;
@@ -129,8 +133,10 @@ __device__ __forceinline__ void bd_coarse_eval(const float* A, const float* R, c
   bq = q;
 }
 
-template <int K, bool COARSE>
-__global__ void __launch_bounds__(kThreads, 2) boxdit_stream_kernel(const SearchParams p) {
+// Table noise with K = 32 keeps 32 (a, b) pairs of level 0 live: one CTA per
+// SM leaves room for them without spilling.
+template <int K, bool COARSE, bool TABLE>
+__global__ void __launch_bounds__(kThreads, (TABLE && K == 32) ? 1 : 2) boxdit_stream_kernel(const SearchParams p) {
   using S = BdS<K>;
   constexpr int KAP = S::KAP;
   constexpr int MIR = S::MIR;
@@ -146,14 +152,15 @@ __global__ void __launch_bounds__(kThreads, 2) boxdit_stream_kernel(const Search
   uint16_t* __restrict__ wseg = p.widx + row * p.ld + t0;
   const int64_t nleft = p.nt - t0;
   const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));
-  const float mu = p.mu[row];
-  const float inv = 1.0f / p.sigma[row];
-  const BdDyn<K> L(top);
+  const BdDyn<K> L(top, TABLE ? p.n_widths : 0);
+  float2* AB = reinterpret_cast<float2*>(smem + L.ab);  // table noise: (a, b) per width index
+  float mu, inv;
+  row_noise<TABLE>(p, row, AB, mu, inv);
   float* RESY = smem + L.res_y;
   uint16_t* RESW = reinterpret_cast<uint16_t*>(smem + L.res_w);
   int* BCM = reinterpret_cast<int*>(smem + L.bcm);
   int* RTAB = reinterpret_cast<int*>(smem + L.tab);  // [3j]: A ring, [3j+1]: R ring, [3j+2]: mask
-  float* STAB = smem + L.stab;                        // [j (K+1) + m] = 1/sqrt(c_j + m 2^j)
+  float* STAB = smem + L.stab;                        // [j (K+1) + m] = 1/sqrt(c_j + m 2^j) (white noise)
 
   for (int i = t; i < L.bcm; i += kThreads) smem[i] = ninf();
   for (int i = t; i < 2 * kBcm; i += kThreads) BCM[i] = INT_MIN;
@@ -296,14 +303,19 @@ __global__ void __launch_bounds__(kThreads, 2) boxdit_stream_kernel(const Search
     const int n = cn - ((k * kC) >> cj);
     float bv;
     int bq;
-    const float* sc = STAB + cj * (K + 1);
-    if (cj > KAP) {
-      bd_coarse_eval<K, true, false>(smem + ca + (n & cmask), smem + cr + (n & cmask), sc, cnu, bv, bq);
-    } else if (K == 32 && cj == 4) {  // c_4 / 16 = K - 2 blocks: window starts one block early
-      bd_coarse_eval<K, false, true>(smem + ca + ((n - 1) & cmask), nullptr, sc, cnu, bv, bq);
-    } else {
-      bd_coarse_eval<K, false, false>(smem + ca + (n & cmask), nullptr, sc, cnu, bv, bq);
-    }
+    auto run = [&](const auto* sc) {
+      if (cj > KAP) {
+        bd_coarse_eval<K, true, false>(smem + ca + (n & cmask), smem + cr + (n & cmask), sc, cnu, bv, bq);
+      } else if (K == 32 && cj == 4) {  // c_4 / 16 = K - 2 blocks: window starts one block early
+        bd_coarse_eval<K, false, true>(smem + ca + ((n - 1) & cmask), nullptr, sc, cnu, bv, bq);
+      } else {
+        bd_coarse_eval<K, false, false>(smem + ca + (n & cmask), nullptr, sc, cnu, bv, bq);
+      }
+    };
+    if constexpr (TABLE)
+      run(static_cast<const float2*>(AB + cfirst));
+    else
+      run(static_cast<const float*>(STAB + cj * (K + 1) + 1));
     RESY[(k & 1) * kResN + t] = bv;
     RESW[(k & 1) * kResN + t] = (uint16_t)(cfirst + bq);
     atomicMax(BCM + (k & 1) * kBcm + cbcm, (fkey(bv) & ~15) | ccode);
@@ -311,10 +323,21 @@ __global__ void __launch_bounds__(kThreads, 2) boxdit_stream_kernel(const Search
 
   // ---- fine levels 0..3, merge and store of chunk k --------------------------
   float tmax = ninf();
-  auto sc0 = [&](auto M) { return p.bscale[0][decltype(M)::value]; };
-  auto sc1 = [&](auto M) { return p.bscale[1][decltype(M)::value]; };
-  auto sc2 = [&](auto M) { return p.bscale[2][decltype(M)::value]; };
-  auto sc3 = [&](auto M) { return p.bscale[3][decltype(M)::value]; };
+  // candidate scale of block count m at fine level I (white: 1/sqrt(c_I + m 2^I);
+  // table: the width's (a, b))
+  auto scl = [&](auto I) {
+    return [&](auto M) {
+      constexpr int i = decltype(I)::value, m = decltype(M)::value;
+      if constexpr (TABLE)
+        return AB[p.lvl_first[i] + m - 1];
+      else
+        return p.bscale[i][m];
+    };
+  };
+  const auto sc0 = scl(std::integral_constant<int, 0>{});
+  const auto sc1 = scl(std::integral_constant<int, 1>{});
+  const auto sc2 = scl(std::integral_constant<int, 2>{});
+  const auto sc3 = scl(std::integral_constant<int, 3>{});
   auto fine = [&](int k) {
     const int ar = a0 - k * kC;
     if (ar >= T) return;
@@ -426,35 +449,36 @@ __global__ void __launch_bounds__(kThreads, 2) boxdit_stream_kernel(const Search
 }
 
 template <int K>
-size_t bd_smem(int top) {
-  return sizeof(float) * (size_t)BdDyn<K>(top).total;
+size_t bd_smem(int top, int nab) {
+  return sizeof(float) * (size_t)BdDyn<K>(top, nab).total;
+}
+
+template <int K, bool TABLE>
+cudaError_t launch_bd(const spd_plan& plan, const SearchParams& p, size_t smem, cudaStream_t s) {
+  const int64_t nblk = plan.desc.ndm * plan.tiles_per_row;
+  return plan.top >= kRing0 ? launch_one(boxdit_stream_kernel<K, true, TABLE>, smem, nblk, p, s)
+                            : launch_one(boxdit_stream_kernel<K, false, TABLE>, smem, nblk, p, s);
 }
 
 }  // namespace
 
-size_t boxdit_smem_bytes(const spd_plan& plan) {
+size_t boxdit_smem_bytes(const spd_plan& plan, bool table) {
+  const int nab = table ? (int)plan.widths.size() : 0;
   switch (plan.k) {
-    case 8: return bd_smem<8>(plan.top);
-    case 16: return bd_smem<16>(plan.top);
-    case 32: return bd_smem<32>(plan.top);
+    case 8: return bd_smem<8>(plan.top, nab);
+    case 16: return bd_smem<16>(plan.top, nab);
+    case 32: return bd_smem<32>(plan.top, nab);
     default: return 0;
   }
 }
 
 cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
-  const size_t smem = boxdit_smem_bytes(plan);
-  const int64_t nblk = plan.desc.ndm * plan.tiles_per_row;
-  const bool coarse = plan.top >= kRing0;
+  const bool table = p.table != 0;
+  const size_t smem = boxdit_smem_bytes(plan, table);
   switch (plan.k) {
-    case 8:
-      return coarse ? launch_one(boxdit_stream_kernel<8, true>, smem, nblk, p, s)
-                    : launch_one(boxdit_stream_kernel<8, false>, smem, nblk, p, s);
-    case 16:
-      return coarse ? launch_one(boxdit_stream_kernel<16, true>, smem, nblk, p, s)
-                    : launch_one(boxdit_stream_kernel<16, false>, smem, nblk, p, s);
-    case 32:
-      return coarse ? launch_one(boxdit_stream_kernel<32, true>, smem, nblk, p, s)
-                    : launch_one(boxdit_stream_kernel<32, false>, smem, nblk, p, s);
+    case 8: return table ? launch_bd<8, true>(plan, p, smem, s) : launch_bd<8, false>(plan, p, smem, s);
+    case 16: return table ? launch_bd<16, true>(plan, p, smem, s) : launch_bd<16, false>(plan, p, smem, s);
+    case 32: return table ? launch_bd<32, true>(plan, p, smem, s) : launch_bd<32, false>(plan, p, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

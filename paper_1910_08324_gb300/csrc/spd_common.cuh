@@ -30,6 +30,46 @@ __host__ __device__ constexpr int next_pow2(int v) {
   return p;
 }
 
+// SNR of a boxcar sum S of normalised samples.  White noise: S times the
+// width's 1/sqrt(L).  Table noise: the width's affine map a S + b (row_noise).
+__device__ __forceinline__ float snr_of(float S, float sc) { return S * sc; }
+__device__ __forceinline__ float snr_of(float S, float2 ab) { return fmaf(S, ab.x, ab.y); }
+
+// Per-row noise constants of a search CTA (Eq. SNRlong).
+//   White noise (Eq. whitenoise): samples are normalised as z = (x - mu_r) / sigma_r
+//   and a width-L sum Z of z-values has SNR Z / sqrt(L).
+//   Table noise (mu_L, sigma_L per row and width index; index 0 is width 1 in
+//   every grid): samples are centred and scaled by the width-1 entry,
+//   z = (x - mu_1) / sigma_1, so that (X_L - mu_L) / sigma_L = a_L Z + b_L with
+//   a_L = sigma_1 / sigma_L and b_L = (L mu_1 - mu_L) / sigma_L, computed in
+//   FP64 and stored as AB[w] = (a, b) in shared memory (caller synchronises).
+//   AB holds kAbPad zero entries past the last width: the masked block counts
+//   of a partial last level (ranks >= n_top) still load their entry.
+constexpr int kAbPad = 32;
+template <bool TABLE>
+__device__ __forceinline__ void row_noise(const SearchParams& p, int64_t row, float2* AB, float& mu,
+                                          float& inv) {
+  if constexpr (!TABLE) {
+    mu = p.mu[row];
+    inv = 1.0f / p.sigma[row];
+  } else {
+    const float* m = p.mu + row * p.n_widths;
+    const float* s = p.sigma + row * p.n_widths;
+    const double c = m[0], d = s[0];
+    mu = m[0];
+    inv = (float)(1.0 / d);
+    for (int w = threadIdx.x; w < p.n_widths + kAbPad; w += blockDim.x) {
+      if (w < p.n_widths) {
+        const double L = p.unit_widths ? (double)(w + 1) : (double)p.wtab[w];
+        const double sg = s[w];
+        AB[w] = make_float2((float)(d / sg), (float)((L * c - (double)m[w]) / sg));
+      } else {
+        AB[w] = make_float2(0.0f, 0.0f);
+      }
+    }
+  }
+}
+
 // Order-preserving int key of a float (signed compare): used for atomic maxima.
 __device__ __forceinline__ int fkey(float f) {
   const int b = __float_as_int(f);
@@ -205,7 +245,7 @@ __device__ __forceinline__ void eval_window(const float* w, int n_used, Scale&& 
       S += w[r + m - 1];
       if constexpr (Pred::in(m)) {
         constexpr int rk = Pred::rank(m);
-        const float v = S * scale(M);
+        const float v = snr_of(S, scale(M));
         if constexpr (rk == 0) {
           best = v;
           q = 0;
@@ -273,7 +313,7 @@ __device__ __forceinline__ void eval_window_mxb(const float* w, const float* bas
     static_for<1, MMAX + 1>([&](auto M) {
       constexpr int m = decltype(M)::value;
       S += w[r + m - 1];
-      if constexpr (Pred::in(m)) v[Pred::rank(m)] = S * scale(M);
+      if constexpr (Pred::in(m)) v[Pred::rank(m)] = snr_of(S, scale(M));
     });
     const float best = tree_max<NC>(v);
     int q = NC - 1;
@@ -307,7 +347,7 @@ __device__ __forceinline__ void eval_one_masked(const float* w, int n_used, Scal
     S += w[m - 1];
     if constexpr (Pred::in(m)) {
       constexpr int rk = Pred::rank(m);
-      const float x = S * scale(M);
+      const float x = snr_of(S, scale(M));
       v[rk] = (rk == 0 || rk < n_used) ? x : ninf();
     }
   });

@@ -92,8 +92,9 @@ constexpr int kResN = kResHi + kMaxLevels;  // slots of one coarse-result buffer
 constexpr int kBcm = kC / 16;               // starts = 0 mod 16 in a chunk
 
 struct IgDyn {
-  int res_y, res_w, bcm, tab, total;
-  __host__ __device__ IgDyn(int rings, int H, int top, int mmax) {
+  int res_y, res_w, bcm, tab, ab, total;
+  // nab: widths of the table-noise constants (0 for white noise)
+  __host__ __device__ IgDyn(int rings, int H, int top, int mmax, int nab) {
     int o = rings;
     for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, H, mmax) + mmax);
     res_y = o;
@@ -104,11 +105,13 @@ struct IgDyn {
     o += 2 * kBcm;
     tab = o;
     o += 2 * kMaxLevels;
+    ab = o;
+    o += nab ? al4(2 * (nab + kAbPad)) : 0;
     total = o;
   }
 };
 
-template <int D, int PL, bool COARSE>
+template <int D, int PL, bool COARSE, bool TABLE>
 __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
     igrid_stream_kernel(const SearchParams p) {
   using S = IgS<D, PL>;
@@ -129,10 +132,23 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   uint16_t* __restrict__ wseg = p.widx + row * p.ld + t0;
   const int64_t nleft = p.nt - t0;
   const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));  // samples that exist
-  const float mu = p.mu[row];
-  const float inv = 1.0f / p.sigma[row];
-  const IgDyn L(FX::RINGS, H, top, MMAX);
-  auto rsM = [&](auto M) { return p.rs[decltype(M)::value]; };
+  const IgDyn L(FX::RINGS, H, top, MMAX, TABLE ? p.n_widths : 0);
+  float2* AB = reinterpret_cast<float2*>(smem + L.ab);  // table noise: (a, b) per width index
+  float mu, inv;
+  row_noise<TABLE>(p, row, AB, mu, inv);
+  // candidate scale of block count m (white noise: 1/sqrt(m), times the level's
+  // 2^(-j/2) after the maximum; table noise: the width's (a, b), first = the
+  // level's first width index)
+  auto scl = [&](const float2* ab, auto Pred) {
+    return [&, ab](auto M) {
+      constexpr int m = decltype(M)::value;
+      if constexpr (TABLE)
+        return ab[decltype(Pred)::rank(m)];
+      else
+        return p.rs[m];
+    };
+  };
+  auto lvl_f = [&](int j) { return TABLE ? 1.0f : p.lvl_scale[j]; };
   float* RESY = smem + L.res_y;
   uint16_t* RESW = reinterpret_cast<uint16_t*>(smem + L.res_w);
   int* BCM = reinterpret_cast<int*>(smem + L.bcm);   // [2][kBcm] keys of the best coarse level
@@ -191,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       cj = j;
       cbase = RTAB[2 * j];
       cmask = RTAB[2 * j + 1];
-      cf = p.lvl_scale[j];
+      cf = lvl_f(j);
       cfirst = p.lvl_first[j];
       cnu = (j == top) ? p.n_top : SM::MM;
       cbcm = cq << (j - 4);   // its start / 16
@@ -288,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
     auto eval_one = [&](const float* w, int nu, float f, int first, int slot, int bcm, int code) {
       float bv;
       int bq;
-      eval_one_masked<MMAX, SM>(w, nu, rsM, bv, bq);
+      eval_one_masked<MMAX, SM>(w, nu, scl(AB + first, SM{}), bv, bq);
       const float y = bv * f;
       RY[slot] = y;
       RW[slot] = (uint16_t)(first + bq);
@@ -299,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       for (int jj = kChunkLog + 1; jj <= top; ++jj)
         if (((t0 + ar) & ((1LL << jj) - 1)) == 0)
           eval_one(smem + RTAB[2 * jj] + ((ar >> jj) & RTAB[2 * jj + 1]), (jj == top) ? p.n_top : SM::MM,
-                   p.lvl_scale[jj], p.lvl_first[jj], kResHi + jj - kChunkLog - 1, 0, 15 - (jj - 4));
+                   lvl_f(jj), p.lvl_first[jj], kResHi + jj - kChunkLog - 1, 0, 15 - (jj - 4));
   };
 
   // ---- fine levels, merge and store of chunk k -----------------------------
@@ -313,22 +329,24 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
     {
       float win[S::NW0 * 4];
       load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
+      const auto sc0 = scl(AB, S0{});
       if (!COARSE && top == 0) {
         float full[8];
-        eval_window<8, MMAX, S0, true, false>(win, p.n_top, rsM, nullptr, y, w, full);
+        eval_window<8, MMAX, S0, true, false>(win, p.n_top, sc0, nullptr, y, w, full);
       } else {
-        eval_window_mx<8, MMAX, S0>(win, rsM, y, w);
+        eval_window_mx<8, MMAX, S0>(win, sc0, y, w);
       }
     }
     if (COARSE || top >= 1) {
       float win[S::NW1 * 4], bv[4], full[4];
       int bq[4];
       load_window4<S::NW1>(smem + FX::f1(buf) + 4 * t, win);
+      const auto scj = scl(AB + p.lvl_first[1], SM{});
       if (!COARSE && top == 1)
-        eval_window<4, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        eval_window<4, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
       else
-        eval_window<4, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-      const float f = p.lvl_scale[1];
+        eval_window<4, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+      const float f = lvl_f(1);
       const int first = p.lvl_first[1];
 #pragma unroll
       for (int r = 0; r < 4; ++r) merge1(y[2 * r], w[2 * r], bv[r] * f, first + bq[r]);
@@ -337,11 +355,12 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       float win[S::NW2 * 2], bv[2], full[2];
       int bq[2];
       load_window2<S::NW2>(smem + FX::f2(buf) + 2 * t, win);
+      const auto scj = scl(AB + p.lvl_first[2], SM{});
       if (!COARSE && top == 2)
-        eval_window<2, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        eval_window<2, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
       else
-        eval_window<2, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-      const float f = p.lvl_scale[2];
+        eval_window<2, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+      const float f = lvl_f(2);
       const int first = p.lvl_first[2];
       merge1(y[0], w[0], bv[0] * f, first + bq[0]);
       merge1(y[4], w[4], bv[1] * f, first + bq[1]);
@@ -350,11 +369,12 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       float win[S::NW3], bv[1], full[1];
       int bq[1];
       load_window1<S::NW3>(smem + FX::f3(buf) + t, win);
+      const auto scj = scl(AB + p.lvl_first[3], SM{});
       if (!COARSE && top == 3)
-        eval_window<1, MMAX, SM, true, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
+        eval_window<1, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
       else
-        eval_window<1, MMAX, SM, false, false>(win, p.n_top, rsM, nullptr, bv, bq, full);
-      merge1(y[0], w[0], bv[0] * p.lvl_scale[3], p.lvl_first[3] + bq[0]);
+        eval_window<1, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+      merge1(y[0], w[0], bv[0] * lvl_f(3), p.lvl_first[3] + bq[0]);
     }
     if (COARSE) {  // best coarse level at start 8t (even t: 8t = 0 mod 16), without branching
       int* kp = BCM + (k & 1) * kBcm + (t >> 1);
@@ -417,11 +437,12 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
 
 }  // namespace
 
-size_t igrid_smem_bytes(const spd_plan& plan) {
+size_t igrid_smem_bytes(const spd_plan& plan, bool table) {
+  const int nab = table ? (int)plan.widths.size() : 0;
   switch (plan.d * 8 + plan.pl) {
 #define SPD_IG_CASE(D, PL) \
   case D * 8 + PL:         \
-    return sizeof(float) * (size_t)IgDyn(IgFix<D, PL>::RINGS, plan.halo, plan.top, IgS<D, PL>::MMAX).total;
+    return sizeof(float) * (size_t)IgDyn(IgFix<D, PL>::RINGS, plan.halo, plan.top, IgS<D, PL>::MMAX, nab).total;
     SPD_IG_CASE(0, 0)
     SPD_IG_CASE(0, 1)
     SPD_IG_CASE(1, 1)
@@ -435,15 +456,22 @@ size_t igrid_smem_bytes(const spd_plan& plan) {
   }
 }
 
-cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
-  const size_t smem = igrid_smem_bytes(plan);
+namespace {
+template <int D, int PL, bool TABLE>
+cudaError_t launch_ig(const spd_plan& plan, const SearchParams& p, size_t smem, cudaStream_t s) {
   const int64_t nblk = plan.desc.ndm * plan.tiles_per_row;
-  const bool coarse = plan.top >= kRing0;
+  return plan.top >= kRing0 ? launch_one(igrid_stream_kernel<D, PL, true, TABLE>, smem, nblk, p, s)
+                            : launch_one(igrid_stream_kernel<D, PL, false, TABLE>, smem, nblk, p, s);
+}
+}  // namespace
+
+cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
+  const bool table = p.table != 0;
+  const size_t smem = igrid_smem_bytes(plan, table);
   switch (plan.d * 8 + plan.pl) {
-#define SPD_IG_LAUNCH(D, PL)                                                              \
-  case D * 8 + PL:                                                                        \
-    return coarse ? launch_one(igrid_stream_kernel<D, PL, true>, smem, nblk, p, s)        \
-                  : launch_one(igrid_stream_kernel<D, PL, false>, smem, nblk, p, s);
+#define SPD_IG_LAUNCH(D, PL)                                                       \
+  case D * 8 + PL:                                                                 \
+    return table ? launch_ig<D, PL, true>(plan, p, smem, s) : launch_ig<D, PL, false>(plan, p, smem, s);
     SPD_IG_LAUNCH(0, 0)
     SPD_IG_LAUNCH(0, 1)
     SPD_IG_LAUNCH(1, 1)

@@ -35,6 +35,7 @@ constexpr int kChunk = 2048;       // starts per sub-chunk of a tile (fine level
 constexpr int kMaxLevels = 24;     // levels a plan may have
 constexpr int kMaxLend = 32768;    // largest width a plan may reach
 constexpr int kMaxExhaustive = 4096;
+constexpr int kMaxGridWidths = 512;  // widths of a BoxDIT / IGRID plan
 constexpr int kCandTile = 16384;   // starts per candidate tile (tile maxima granularity)
 constexpr int kMaxPeakRadius = 64;
 constexpr int kCandGroup = 32;     // candidate tiles per warp of the candidate passes
@@ -48,7 +49,7 @@ struct SearchParams {
   float* snr;
   uint16_t* widx;
   float* tile_max;      // [ndm * cand_tiles_per_row] ordered-int keys of tile maxima (or nullptr)
-  const float* mu;
+  const float* mu;      // white: [ndm]; table: [ndm][n_widths]
   const float* sigma;
   int64_t ndm, nt, ld;
   int32_t tile;         // starts per CTA (multiple of kChunk; streaming kernels: of kCandTile)
@@ -63,6 +64,10 @@ struct SearchParams {
   float lvl_scale[kMaxLevels];    // IGRID: 2^(-j/2), the unit factor of level j
   float rs[64];                   // rs[m] = 1/sqrt(m) (IGRID block-count factor)
   float bscale[kMaxLevels][33];   // BoxDIT: 1/sqrt(c_j + m 2^j), m = 1..K
+  int32_t table;                  // 1: per-row, per-width noise statistics (spd_noise mode 1)
+  int32_t n_widths;               // widths of the plan
+  int32_t unit_widths;            // 1: width index w is width w + 1 (exhaustive grid)
+  int32_t wtab[kMaxGridWidths];   // widths of the plan (table noise, unit_widths == 0)
 };
 
 struct CandParams {
@@ -105,10 +110,10 @@ namespace spd {
 // kernel launchers (spd_search.cu, spd_igrid.cu, spd_boxdit.cu, spd_candidates.cu)
 cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
-size_t igrid_smem_bytes(const spd_plan& plan);
+size_t igrid_smem_bytes(const spd_plan& plan, bool table);
 cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
-size_t boxdit_smem_bytes(const spd_plan& plan);
+size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
 cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s);
-size_t search_smem_bytes(const spd_plan& plan);
+size_t search_smem_bytes(const spd_plan& plan, bool table);
 }  // namespace spd

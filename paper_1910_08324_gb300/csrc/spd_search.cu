@@ -24,20 +24,23 @@ constexpr int kItems0 = kChunk / 4 / kThreads;  // 4-start items per thread per 
 static_assert(kItems0 * 4 * kThreads == kChunk, "tile must split evenly");
 
 // ============================================================================ exhaustive
+// table: the scale table holds (a, b) float2 pairs (table noise) instead of 1/sqrt(L)
+static_assert(kAbPad <= 33, "the exhaustive scale table pads 33 entries");
 struct ExLayout {
   int f0, rs, red, total;
-  __host__ __device__ explicit ExLayout(int lmax) {
+  __host__ __device__ ExLayout(int lmax, bool table) {
     int o = 0;
     f0 = o;
     o += al4(kChunk + ((lmax + 36 + 127) / 128) * 128 + 8);
     rs = o;
-    o += al4(lmax + 33);
+    o += al4((lmax + 33) * (table ? 2 : 1));  // table: lmax widths + kAbPad (<= 33) padding pairs
     red = o;
     o += 32;
     total = o;
   }
 };
 
+template <bool TABLE>
 __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchParams p) {
   extern __shared__ __align__(16) float smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -46,14 +49,17 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
   const int64_t t0 = tile * (int64_t)kChunk;
   const int lmax = p.lmax;
   const float* __restrict__ xrow = p.x + row * p.ld;
-  const float mu = p.mu[row];
-  const float inv = 1.0f / p.sigma[row];
+
   const bool vec = p.vec != 0;
-  const ExLayout L(lmax);
+  const ExLayout L(lmax, TABLE);
   float* F0 = smem + L.f0;
-  float* RS = smem + L.rs;
-  for (int m = tid; m <= lmax + 32; m += kThreads)
-    RS[m] = (m >= 1 && m <= lmax) ? (float)(1.0 / sqrt((double)m)) : 0.0f;
+  float* RS = smem + L.rs;  // white noise: RS[m] = 1/sqrt(m); table noise: AB[m - 1] = (a, b)
+  float2* AB = reinterpret_cast<float2*>(smem + L.rs);
+  float mu, inv;
+  row_noise<TABLE>(p, row, AB, mu, inv);
+  if constexpr (!TABLE)
+    for (int m = tid; m <= lmax + 32; m += kThreads)
+      RS[m] = (m >= 1 && m <= lmax) ? (float)(1.0 / sqrt((double)m)) : 0.0f;
   const int nchunk = (kChunk + ((lmax + 36 + 127) / 128) * 128) / 128;
   for (int c = warp; c < nchunk; c += kThreads / 32) {
     const float4 z = load_z4(xrow, t0 + c * 128 + lane * 4, p.nt, vec, mu, inv);
@@ -89,11 +95,16 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
         constexpr int mi = decltype(MI)::value;
         const int m = mbase + mi + 1;
         if (!tail || m <= lmax) {
-          const float sc = RS[m];
+          const auto sc = [&] {
+            if constexpr (TABLE)
+              return AB[m - 1];
+            else
+              return RS[m];
+          }();
           static_for<0, 4>([&](auto R) {
             constexpr int r = decltype(R)::value;
             S[r] += w[r + mi];
-            const float v = S[r] * sc;
+            const float v = snr_of(S[r], sc);
             if (v > best[r]) {
               best[r] = v;
               q[r] = m - 1;
@@ -113,17 +124,21 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
 
 }  // namespace
 
-size_t search_smem_bytes(const spd_plan& plan) {
+size_t search_smem_bytes(const spd_plan& plan, bool table) {
   switch (plan.family) {
-    case kExhaustive: return sizeof(float) * (size_t)ExLayout(plan.lend).total;
-    case kIgrid: return igrid_smem_bytes(plan);
-    default: return boxdit_smem_bytes(plan);
+    case kExhaustive: return sizeof(float) * (size_t)ExLayout(plan.lend, table).total;
+    case kIgrid: return igrid_smem_bytes(plan, table);
+    default: return boxdit_smem_bytes(plan, table);
   }
 }
 
 cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
-  if (plan.family == kExhaustive)
-    return launch_one(exhaustive_kernel, search_smem_bytes(plan), plan.desc.ndm * plan.tiles_per_row, p, s);
+  if (plan.family == kExhaustive) {
+    const size_t smem = search_smem_bytes(plan, p.table != 0);
+    const int64_t nblk = plan.desc.ndm * plan.tiles_per_row;
+    return p.table ? launch_one(exhaustive_kernel<true>, smem, nblk, p, s)
+                   : launch_one(exhaustive_kernel<false>, smem, nblk, p, s);
+  }
   if (plan.family == kBoxdit) return launch_boxdit(plan, p, s);
   return launch_igrid(plan, p, s);
 }

@@ -38,8 +38,10 @@ def oracle_grid(plan):
     return oracle.Grid(w, s)
 
 
-def run_gpu(plan, x, mu, sigma, ld=None, x_offset=0, return_ws=False):
-    """x: host [ndm, nt] float32.  Returns host (Y float32 [ndm, nt], W uint16 [ndm, nt])."""
+def run_gpu(plan, x, mu, sigma, ld=None, x_offset=0, return_ws=False, noise_mode=0):
+    """x: host [ndm, nt] float32.  Returns host (Y float32 [ndm, nt], W uint16 [ndm, nt]).
+
+    noise_mode 1: mu, sigma are [ndm, n_widths] tables (per row and width index)."""
     t = torch()
     ndm, nt = x.shape
     ld = plan.ld
@@ -51,10 +53,11 @@ def run_gpu(plan, x, mu, sigma, ld=None, x_offset=0, return_ws=False):
     wbuf = t.full((ndm * ld + x_offset + 8,), 54321, dtype=t.int32, device=dev).to(t.int16)
     Y = ybuf[x_offset:x_offset + ndm * ld].view(ndm, ld)
     W = wbuf[x_offset:x_offset + ndm * ld].view(ndm, ld)
-    mu_d = t.as_tensor(np.broadcast_to(np.asarray(mu, np.float32), (ndm,)).copy(), device=dev)
-    sg_d = t.as_tensor(np.broadcast_to(np.asarray(sigma, np.float32), (ndm,)).copy(), device=dev)
+    shape = (ndm,) if noise_mode == 0 else (ndm, len(plan.widths()[0]))
+    mu_d = t.as_tensor(np.broadcast_to(np.asarray(mu, np.float32), shape).copy(), device=dev)
+    sg_d = t.as_tensor(np.broadcast_to(np.asarray(sigma, np.float32), shape).copy(), device=dev)
     ws = t.empty(plan.workspace_size(), dtype=t.uint8, device=dev)
-    spd.execute(plan, xv, mu_d, sg_d, Y, W, ws)
+    spd.execute(plan, xv, mu_d, sg_d, Y, W, ws, noise_mode=noise_mode)
     spd.spd_sync_status(plan, t.cuda.current_stream().cuda_stream)
     Yh = Y.cpu().numpy()
     Wh = W.cpu().numpy().view(np.uint16)

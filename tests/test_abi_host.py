@@ -102,8 +102,11 @@ def test_execute_validates_before_launch():
         spd.spd_candidates(plan, 4096, 4096, 6.0, 65, 0, 0, 4096, 0, 0, 0)
     assert e.value.status == 1  # radius above the maximum
     with pytest.raises(spd.SpdError) as e:
-        spd.spd_execute(plan, 4096, 4096, 4096, 4096, 4096, 4096, 1 << 30, noise_mode=1)
-    assert e.value.status == 2  # table noise not in this build
+        spd.spd_execute(plan, 4096, 4096, 4096, 4096, 4096, 4096, 1 << 30, noise_mode=2)
+    assert e.value.status == 1  # noise modes are 0 (white) and 1 (table)
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_execute(plan, 4096, 4098, 4096, 4096, 4096, 4096, 1 << 30, noise_mode=1)
+    assert e.value.status == 1  # misaligned noise table
 
 
 def test_widths_buffer_too_small():
