@@ -41,7 +41,8 @@ import spd_synth  # noqa: E402
 
 T_SAMP = 64e-6
 SKA_DM = 6000
-BYTES_PER_SAMPLE = 4 + 4 + 2  # f32 in, f32 Y out, u16 W out (algorithmic, once each)
+OUT_BYTES_PER_SAMPLE = 4 + 2  # f32 Y out, u16 W out (algorithmic, once each)
+DTYPES = {"f32": (0, 4), "f16": (1, 2), "bf16": (2, 2), "u8": (3, 1)}  # spd_dtype, bytes per sample
 METRIC = "DM x time samples/s"
 SM_MAX_HZ = 2070e6          # GB300 maximum SM clock
 ALU_BALANCE_CANDIDATES = 10  # above this many candidates per sample a grid is ALU-bound
@@ -76,6 +77,8 @@ def parse():
     ap.add_argument("--threshold", type=float, default=6.0)
     ap.add_argument("--radius", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--dtype", default="f32", choices=sorted(DTYPES),
+                    help="storage type of the input samples")
     ap.add_argument("--cpu-rows", type=int, default=96)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="oracle time the cpu_baseline sample accumulates")
@@ -111,7 +114,8 @@ def source_hash():
 
 def recorded_traffic(algo, ndm, nt):
     """Per-launch DRAM bytes of the search kernel from the committed ncu summary,
-    if it was taken on the current kernel source and this algorithm; else None."""
+    if it was taken on the current kernel source and this algorithm (key: the
+    algorithm, suffixed with the input type when it is not f32); else None."""
     p = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
     if not os.path.exists(p):
         return None
@@ -178,7 +182,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(x_rows, algo, s_end, threads=0):
+def cpu_oracle_rate(x_rows, algo, s_end, mu=0.0, sigma=1.0, threads=0):
     """The oracle (definition form, FP64, OpenMP over rows) on a bounded sample."""
     import oracle
     kw = ALGOS[algo]
@@ -190,7 +194,7 @@ def cpu_oracle_rate(x_rows, algo, s_end, threads=0):
         g = oracle.grid_exhaustive(s_end)
     xs = np.ascontiguousarray(x_rows, np.float64)
     t0 = time.perf_counter()
-    oracle.search(xs, g, 0.0, 1.0, threads=threads)
+    oracle.search(xs, g, mu, sigma, threads=threads)
     dt = time.perf_counter() - t0
     return xs.size / dt, dt
 
@@ -243,7 +247,9 @@ def main():
     dev = torch.device("cuda", local)
     ndm, nt = args.ndm, args.nt
     kw = dict(ALGOS[args.algo])
-    plan = spd.spd_plan_create(ndm=ndm, nt=nt, s_end=args.s_end, **kw)
+    dt_code, esize = DTYPES[args.dtype]
+    bytes_per_sample = esize + OUT_BYTES_PER_SAMPLE
+    plan = spd.spd_plan_create(ndm=ndm, nt=nt, s_end=args.s_end, dtype=dt_code, **kw)
     widths, seps = plan.widths()
     cand_per_sample = float(np.sum(1.0 / seps))
 
@@ -256,8 +262,15 @@ def main():
         tab = spd_synth.ska_mid_pulses(seed=seed, ndm=ndm, nt=nt)
         x = spd_synth.device_noise(ndm, nt, seed, device=dev)
         spd_synth.device_inject(x, tab)
-    mu = torch.zeros(ndm, device=dev)
-    sg = torch.ones(ndm, device=dev)
+    # stored samples of the requested type; noise statistics in stored units
+    if args.dtype == "u8":
+        mu = torch.full((ndm,), spd_synth.U8_OFFSET, device=dev)
+        sg = torch.full((ndm,), spd_synth.U8_SCALE, device=dev)
+    else:
+        mu = torch.zeros(ndm, device=dev)
+        sg = torch.ones(ndm, device=dev)
+    xf = x                                     # float32 samples
+    x = spd_synth.device_quantize(xf, args.dtype)  # the stored input (xf itself for f32)
     Y = torch.empty((ndm, nt), dtype=torch.float32, device=dev)
     W = torch.empty((ndm, nt), dtype=torch.int16, device=dev)
     ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device=dev)
@@ -279,7 +292,7 @@ def main():
     # twice the L2, a 512 MiB buffer is written between steps (outside the events)
     # so that every step starts from a cold L2.
     flush = None
-    if BYTES_PER_SAMPLE * ndm * nt < 2 * L2_BYTES:
+    if bytes_per_sample * ndm * nt < 2 * L2_BYTES:
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
     if world > 1:
@@ -317,9 +330,10 @@ def main():
     # candidates/s (3 lane operations per candidate: add, scale, compare).
     peak, peak_kind = measured_peaks()
     s_avg = statistics.mean(search_ms)
-    traffic = recorded_traffic(args.algo, ndm, nt)
+    traffic = recorded_traffic(args.algo if args.dtype == "f32" else "%s_%s" % (args.algo, args.dtype),
+                               ndm, nt)
     if cand_per_sample <= ALU_BALANCE_CANDIDATES:
-        achieved = BYTES_PER_SAMPLE * ndm * nt / (s_avg / 1e3) / 1e9
+        achieved = bytes_per_sample * ndm * nt / (s_avg / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic,
                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
@@ -332,16 +346,17 @@ def main():
                     "frac": achieved / alu_peak, "traffic": traffic,
                     "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz / 3 ops per candidate"
                                    % (sm_count, SM_MAX_HZ / 1e6),
-                    "hbm_GBps": BYTES_PER_SAMPLE * ndm * nt / (s_avg / 1e3) / 1e9}
+                    "hbm_GBps": bytes_per_sample * ndm * nt / (s_avg / 1e3) / 1e9}
     roofline.update({"kernel": "search (%s)" % args.algo, "kernel_ms": s_avg,
                      "candidates_ms": statistics.mean(cand_ms),
-                     "algorithmic_bytes_per_launch": BYTES_PER_SAMPLE * ndm * nt})
+                     "algorithmic_bytes_per_launch": bytes_per_sample * ndm * nt})
 
     # mean SNR loss on noise-free copies of the workload's pulses (GPU search)
     loss = None
     if not args.no_loss and rank == 0:
-        x.zero_()
-        spd_synth.device_inject(x, tab)
+        xf.zero_()
+        spd_synth.device_inject(xf, tab)
+        x.copy_(spd_synth.device_quantize(xf, args.dtype))
         fused_step()
         torch.cuda.synchronize(dev)
         lend = int(widths[-1])
@@ -349,20 +364,21 @@ def main():
         for p in tab:
             r, s, w = int(p["row"]), int(p["start"]), int(p["width"])
             a = max(0, s - lend)
-            rs.append(float(Y[r, a:s + w].max().item()) / float(p["snr"]))
+            rs.append(float(Y[r, a:s + w].max().item()) / float(p["snr"]))  # SNR in units of sg
         loss = {"mean_snr_loss": float(1.0 - np.mean(rs)), "pulses": len(rs),
                 "max_snr_loss": float(1.0 - np.min(rs)),
                 "definition": "mean over the workload's pulses, noise-free, of 1 - RSNR/SNR"}
         if args.workload == "exhaustive_small":
-            x.copy_(torch.from_numpy(xs).to(dev))
+            xf.copy_(torch.from_numpy(xs).to(dev))
         else:
-            x.copy_(spd_synth.device_noise(ndm, nt, seed, device=dev))
-            spd_synth.device_inject(x, tab)
+            xf.copy_(spd_synth.device_noise(ndm, nt, seed, device=dev))
+            spd_synth.device_inject(xf, tab)
+        x.copy_(spd_synth.device_quantize(xf, args.dtype))
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
-        xh = torch.empty((ndm, nt), dtype=torch.float32, pin_memory=True)
+        xh = torch.empty((ndm, nt), dtype=x.dtype, pin_memory=True)
         xh.copy_(x)
         cnt_h = torch.zeros(1, dtype=torch.int64, pin_memory=True)
         out_h = torch.empty(cap * 24, dtype=torch.uint8, pin_memory=True)
@@ -382,7 +398,7 @@ def main():
             tt = torch.tensor([dt], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             dt = float(tt.item())
-        e2e = {"value": samples_step / dt, "unit": "samples/s", "h2d_bytes_per_step": 4 * ndm * nt,
+        e2e = {"value": samples_step / dt, "unit": "samples/s", "h2d_bytes_per_step": esize * ndm * nt,
                "d2h_bytes_per_step": int(statistics.mean(d2h)), "steps": args.e2e_steps,
                "ms_per_step": 1e3 * dt, "api": "torch pinned H2D + spd_search (C ABI) + D2H of count and records"}
         del xh, out_h
@@ -395,8 +411,8 @@ def main():
         rows = min(args.cpu_rows, ndm)
         done, spent, r0, batches = 0, 0.0, 0, 0
         while batches == 0 or spent < args.cpu_seconds:
-            xs = x[r0:r0 + rows].cpu().numpy()
-            _, dt = cpu_oracle_rate(xs, args.algo, args.s_end)
+            xs = x[r0:r0 + rows].float().cpu().numpy()
+            _, dt = cpu_oracle_rate(xs, args.algo, args.s_end, float(mu[0]), float(sg[0]))
             done += xs.size
             spent += dt
             batches += 1
@@ -417,11 +433,12 @@ def main():
             "config": {"workload": ("ska_mid %d DM x %d samples, 64 us, 500 pulses" % (ndm, nt))
                        if args.workload == "ska_mid" else
                        "exhaustive_small 64 DM x 65536 samples, 8 SNR-10 pulses, widths 1..256",
-                       "algo": args.algo, "s_end": args.s_end, "l_end": int(widths[-1]),
+                       "algo": args.algo, "input_dtype": args.dtype, "s_end": args.s_end,
+                       "l_end": int(widths[-1]),
                        "n_widths": int(len(widths)), "candidates_per_sample": cand_per_sample,
                        "threshold": args.threshold, "peak_radius": args.radius,
                        "candidates_found": n_cand, "parallelism": "dp%d (rows per GPU)" % world,
-                       "l2": ("inputs larger than L2 (%.1f GB per GPU); no flush" % (4 * ndm * nt / 1e9))
+                       "l2": ("inputs larger than L2 (%.1f GB per GPU); no flush" % (esize * ndm * nt / 1e9))
                        if flush is None else "L2 flushed between steps (512 MiB write outside the timed events)",
                        "x_realtime_ska": value * T_SAMP / SKA_DM,
                        "x_realtime_batch": (nt * T_SAMP) / (ms_per_step / 1e3)},

@@ -65,11 +65,14 @@ typedef enum spd_algo {
   SPD_ALGO_IGRID = 2       /* IGRID IG(d) with P layers per step (Sec. 3.2); d = 0, P = 1 is DIT (Alg. 3) */
 } spd_algo;
 
+/* Input sample types.  Every type is converted to float32 on load (exactly:
+ * each value of these types is a float32 value) and summed in float32; mu and
+ * sigma of spd_noise are in the units of the stored values. */
 typedef enum spd_dtype {
   SPD_F32 = 0, /* 32-bit IEEE float samples (the paper's input type, Sec. 4) */
-  SPD_F16 = 1, /* reserved: not implemented in this build (SPD_ERR_UNSUPPORTED) */
-  SPD_BF16 = 2,/* reserved: not implemented in this build */
-  SPD_U8 = 3   /* reserved: not implemented in this build */
+  SPD_F16 = 1, /* 16-bit IEEE half floats */
+  SPD_BF16 = 2,/* bfloat16 (the high 16 bits of a float32) */
+  SPD_U8 = 3   /* unsigned 8-bit integers (e.g. digitised filterbank data) */
 } spd_dtype;
 
 /*
@@ -143,8 +146,9 @@ const char *spd_version(void);
  * chosen algorithm (Sec. 3.1 Alg. 1 width formula; Sec. 3.2 Eq. boxcarsize and
  * Table 1).  Host only: no device work, no device memory.
  * Errors: SPD_ERR_INVALID_ARG for a NULL pointer or any parameter outside the
- * ranges documented in spd_plan_desc; SPD_ERR_UNSUPPORTED for a dtype this
- * build lacks; SPD_ERR_HOST_ALLOC.  *out is NULL on error.
+ * ranges documented in spd_plan_desc; SPD_ERR_UNSUPPORTED for a plan whose
+ * kernel would exceed the device limits (shared memory, grid size);
+ * SPD_ERR_HOST_ALLOC.  *out is NULL on error.
  */
 spd_status spd_plan_create(const spd_plan_desc *desc, spd_plan **out);
 
@@ -173,8 +177,9 @@ spd_status spd_workspace_size(const spd_plan *plan, size_t *bytes);
  * where X_L[s] is the sum of the L samples starting at s.  Width 1 is in every
  * grid, so every s has a value.  Samples at s >= nt of a row (the ld - nt
  * padding) are neither read nor written.
- *   d_x         device, [ndm][ld] samples of plan dtype, 4-byte aligned (16-byte
- *               alignment and ld % 4 == 0 enable vector loads)
+ *   d_x         device, [ndm][ld] samples of plan dtype, aligned to the sample
+ *               size (a 16-byte aligned base with ld * sample size a multiple
+ *               of 16 enables vector loads)
  *   noise       host struct holding device pointers (white or table mode)
  *   d_snr       device, [ndm][ld] float32 output
  *   d_width_idx device, [ndm][ld] uint16 output

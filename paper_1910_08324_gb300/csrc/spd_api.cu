@@ -91,6 +91,15 @@ spd_status build_igrid(spd_plan* p) {
 
 spd_status check_cuda(cudaError_t e) { return e == cudaSuccess ? SPD_OK : SPD_ERR_CUDA; }
 
+int dtype_size(int dtype) {
+  switch (dtype) {
+    case SPD_F32: return 4;
+    case SPD_F16:
+    case SPD_BF16: return 2;
+    default: return 1;
+  }
+}
+
 // Workspace: tile maxima (written by the search, read by the candidate step),
 // per-tile candidate counts, per-group sums and offsets.
 struct WsLayout {
@@ -119,7 +128,8 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   if (noise->mode != 0 && noise->mode != 1) return SPD_ERR_INVALID_ARG;
   if (!noise->mu || !noise->sigma || ((uintptr_t)noise->mu % 4) || ((uintptr_t)noise->sigma % 4))
     return SPD_ERR_INVALID_ARG;
-  if (((uintptr_t)d_x % 4) || ((uintptr_t)d_snr % 4) || ((uintptr_t)d_width_idx % 2))
+  const int esize = dtype_size(plan->desc.dtype);
+  if (((uintptr_t)d_x % esize) || ((uintptr_t)d_snr % 4) || ((uintptr_t)d_width_idx % 2))
     return SPD_ERR_INVALID_ARG;
   const spd_status ws = validate_ws(plan, d_ws, ws_bytes);
   if (ws != SPD_OK) return ws;
@@ -127,7 +137,10 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   spd::SearchParams* sp = new (std::nothrow) spd::SearchParams();
   if (!sp) return SPD_ERR_HOST_ALLOC;
   spd::SearchParams& p = *sp;
-  p.x = static_cast<const float*>(d_x);
+  p.x = d_x;
+  p.dtype = plan->desc.dtype;
+  p.esize = esize;
+  p.vec_x = ((uintptr_t)d_x % 16 == 0 && (plan->desc.ld * esize) % 16 == 0) ? 1 : 0;
   p.snr = d_snr;
   p.widx = d_width_idx;
   p.tile_max = reinterpret_cast<float*>(static_cast<char*>(d_ws) + wl.tile_max);
@@ -142,8 +155,7 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   p.halo = plan->halo;
   p.top = plan->top;
   p.n_top = plan->n_top;
-  p.vec = ((uintptr_t)d_x % 16 == 0 && (uintptr_t)d_snr % 16 == 0 &&
-           (uintptr_t)d_width_idx % 8 == 0 && plan->desc.ld % 4 == 0)
+  p.vec = ((uintptr_t)d_snr % 16 == 0 && (uintptr_t)d_width_idx % 8 == 0 && plan->desc.ld % 4 == 0)
               ? 1
               : 0;
   p.lmax = plan->lend;
@@ -257,7 +269,6 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
   if (d.ndm > (int64_t)1 << 24 || d.nt > (int64_t)1 << 40) return SPD_ERR_INVALID_ARG;
   if (d.dtype < SPD_F32 || d.dtype > SPD_U8) return SPD_ERR_INVALID_ARG;
   if (d.algo < SPD_ALGO_EXHAUSTIVE || d.algo > SPD_ALGO_IGRID) return SPD_ERR_INVALID_ARG;
-  if (d.dtype != SPD_F32) return SPD_ERR_UNSUPPORTED;
   spd_plan* p = new (std::nothrow) spd_plan();
   if (!p) return SPD_ERR_HOST_ALLOC;
   p->desc = d;

@@ -1,6 +1,7 @@
 // spd_common.cuh -- device helpers shared by the search kernels.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -97,47 +98,143 @@ __device__ __forceinline__ void tile_max_atomic(const SearchParams& p, int64_t r
     atomicMax(reinterpret_cast<int*>(p.tile_max) + row * p.cand_tiles_per_row + s / kCandTile, fkey(v));
 }
 
-// z-values of samples [pos, pos + 4) of one row; -inf at and past nt.
-__device__ __forceinline__ float4 load_z4(const float* __restrict__ row, int64_t pos, int64_t nt,
-                                          bool vec, float mu, float inv) {
-  float4 v;
-  if (vec && pos + 4 <= nt) {
-    v = __ldg(reinterpret_cast<const float4*>(row + pos));
-    v.x = (v.x - mu) * inv;
-    v.y = (v.y - mu) * inv;
-    v.z = (v.z - mu) * inv;
-    v.w = (v.w - mu) * inv;
-  } else {
-    v.x = (pos + 0 < nt) ? (__ldg(row + pos + 0) - mu) * inv : ninf();
-    v.y = (pos + 1 < nt) ? (__ldg(row + pos + 1) - mu) * inv : ninf();
-    v.z = (pos + 2 < nt) ? (__ldg(row + pos + 2) - mu) * inv : ninf();
-    v.w = (pos + 3 < nt) ? (__ldg(row + pos + 3) - mu) * inv : ninf();
+// ---------------------------------------------------------------- input samples
+// Input sample types (the spd_dtype values).  Rows are addressed as bytes.
+constexpr int kDtF32 = 0, kDtF16 = 1, kDtBF16 = 2, kDtU8 = 3;
+
+__device__ __forceinline__ float f16_bits(uint32_t h) { return __half2float(__ushort_as_half((unsigned short)h)); }
+
+// Eight consecutive samples of one row as stored: f32 in a and b, f16/bf16 in
+// a (two per word, the earlier sample in the low half), u8 in a.x, a.y (four
+// per word, the earliest in the low byte).
+struct Raw8 {
+  uint4 a, b;
+};
+
+// Raw samples [pos, pos + 8) of the row at byte pointer `row`; n = samples that
+// exist.  One 32/16/8-byte vector load per thread when vec (row and samples
+// 16-byte aligned) and all 8 exist; element loads otherwise (missing ones 0).
+__device__ __forceinline__ Raw8 load_raw8(const unsigned char* __restrict__ row, int pos, int n,
+                                          int dtype, bool vec) {
+  Raw8 r;
+  if (vec && pos + 8 <= n) {
+    if (dtype == kDtF32) {
+      const uint4* q = reinterpret_cast<const uint4*>(row + 4 * pos);
+      r.a = __ldg(q);
+      r.b = __ldg(q + 1);
+    } else if (dtype == kDtU8) {
+      const uint2 v = __ldg(reinterpret_cast<const uint2*>(row + pos));
+      r.a = make_uint4(v.x, v.y, 0u, 0u);
+      r.b = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      r.a = __ldg(reinterpret_cast<const uint4*>(row + 2 * pos));
+      r.b = make_uint4(0u, 0u, 0u, 0u);
+    }
+    return r;
   }
-  return v;
+  uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (pos + i < n) {
+      if (dtype == kDtF32) {
+        w[i] = __ldg(reinterpret_cast<const unsigned int*>(row) + pos + i);
+      } else if (dtype == kDtU8) {
+        w[i >> 2] |= (uint32_t)__ldg(row + pos + i) << (8 * (i & 3));
+      } else {
+        w[i >> 1] |= (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(row) + pos + i) << (16 * (i & 1));
+      }
+    }
+  }
+  r.a = make_uint4(w[0], w[1], w[2], w[3]);
+  r.b = make_uint4(w[4], w[5], w[6], w[7]);
+  return r;
 }
 
-// Raw samples [pos, pos + 4) (no normalisation); -inf marks positions past nt.
-__device__ __forceinline__ float4 load_x4(const float* __restrict__ row, int64_t pos, int64_t nt,
-                                          bool vec) {
-  float4 v;
-  if (vec && pos + 4 <= nt) {
-    v = __ldg(reinterpret_cast<const float4*>(row + pos));
+// The samples of load_raw8 as floats, normalised to (x - mu) * inv; samples at
+// or past n are -inf.
+__device__ __forceinline__ void cvt8(const Raw8& r, int pos, int n, int dtype, float mu, float inv,
+                                     float4& v0, float4& v1) {
+  float f[8];
+  const uint32_t wa[4] = {r.a.x, r.a.y, r.a.z, r.a.w};
+  if (dtype == kDtF32) {
+    const uint32_t wb[4] = {r.b.x, r.b.y, r.b.z, r.b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f[i] = __uint_as_float(wa[i]);
+      f[4 + i] = __uint_as_float(wb[i]);
+    }
+  } else if (dtype == kDtF16) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f[2 * i] = f16_bits(wa[i] & 0xffffu);
+      f[2 * i + 1] = f16_bits(wa[i] >> 16);
+    }
+  } else if (dtype == kDtBF16) {  // bf16 is the high half of an f32
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f[2 * i] = __uint_as_float(wa[i] << 16);
+      f[2 * i + 1] = __uint_as_float(wa[i] & 0xffff0000u);
+    }
   } else {
-    v.x = (pos + 0 < nt) ? __ldg(row + pos + 0) : ninf();
-    v.y = (pos + 1 < nt) ? __ldg(row + pos + 1) : ninf();
-    v.z = (pos + 2 < nt) ? __ldg(row + pos + 2) : ninf();
-    v.w = (pos + 3 < nt) ? __ldg(row + pos + 3) : ninf();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) f[i] = __uint2float_rn((wa[i >> 2] >> (8 * (i & 3))) & 0xffu);
   }
-  return v;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) f[i] = (f[i] - mu) * inv;
+  if (pos + 8 > n) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (pos + i >= n) f[i] = ninf();
+  }
+  v0 = make_float4(f[0], f[1], f[2], f[3]);
+  v1 = make_float4(f[4], f[5], f[6], f[7]);
 }
 
-__device__ __forceinline__ float4 norm4(float4 v, float mu, float inv) {
-  // -inf stays -inf: (-inf - mu) * inv with inv > 0
-  v.x = (v.x - mu) * inv;
-  v.y = (v.y - mu) * inv;
-  v.z = (v.z - mu) * inv;
-  v.w = (v.w - mu) * inv;
-  return v;
+// z-values of samples [pos, pos + 4) of the row at byte pointer `row` (any
+// input type); -inf at and past nt.
+__device__ __forceinline__ float4 load_z4d(const unsigned char* __restrict__ row, int64_t pos, int64_t nt,
+                                           int dtype, bool vec, float mu, float inv) {
+  float f[4];
+  if (vec && pos + 4 <= nt) {
+    if (dtype == kDtF32) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(row + 4 * pos));
+      f[0] = v.x, f[1] = v.y, f[2] = v.z, f[3] = v.w;
+    } else if (dtype == kDtU8) {
+      const uint32_t v = __ldg(reinterpret_cast<const unsigned int*>(row + pos));
+#pragma unroll
+      for (int i = 0; i < 4; ++i) f[i] = __uint2float_rn((v >> (8 * i)) & 0xffu);
+    } else {
+      const uint2 v = __ldg(reinterpret_cast<const uint2*>(row + 2 * pos));
+      const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (dtype == kDtF16) {
+          f[2 * i] = f16_bits(w[i] & 0xffffu);
+          f[2 * i + 1] = f16_bits(w[i] >> 16);
+        } else {
+          f[2 * i] = __uint_as_float(w[i] << 16);
+          f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f[i] = (f[i] - mu) * inv;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (pos + i < nt) {
+        float v;
+        if (dtype == kDtF32) v = __ldg(reinterpret_cast<const float*>(row) + pos + i);
+        else if (dtype == kDtU8) v = __uint2float_rn(__ldg(row + pos + i));
+        else if (dtype == kDtF16) v = f16_bits(__ldg(reinterpret_cast<const unsigned short*>(row) + pos + i));
+        else v = __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(row) + pos + i) << 16);
+        f[i] = (v - mu) * inv;
+      } else {
+        f[i] = ninf();
+      }
+    }
+  }
+  return make_float4(f[0], f[1], f[2], f[3]);
 }
 
 __device__ __forceinline__ void store4(float* __restrict__ yrow, uint16_t* __restrict__ wrow,
@@ -159,7 +256,7 @@ __device__ __forceinline__ void store4(float* __restrict__ yrow, uint16_t* __res
   }
 }
 
-// vec: x/Y bases 16-byte aligned, W base 8-byte aligned, ld % 4 == 0 (so Y rows
+// vec: Y base 16-byte aligned, W base 8-byte aligned, ld % 4 == 0 (so Y rows
 // are 16-byte and W rows 8-byte aligned); s0 % 8 == 0.
 __device__ __forceinline__ void store8(float* __restrict__ yrow, uint16_t* __restrict__ wrow,
                                        int64_t s0, int64_t nt, bool vec, const float (&y)[8],

@@ -127,7 +127,10 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   const int T = p.tile, H = p.halo;
   const bool vec = p.vec != 0;
   // everything below is relative to the segment start t0 (32-bit offsets)
-  const float* __restrict__ xseg = p.x + row * p.ld + t0;
+  const unsigned char* __restrict__ xseg =
+      static_cast<const unsigned char*>(p.x) + (row * p.ld + t0) * p.esize;  // byte address
+  const int dt = p.dtype;
+  const bool vx = p.vec_x != 0;
   float* __restrict__ yseg = p.snr + row * p.ld + t0;
   uint16_t* __restrict__ wseg = p.widx + row * p.ld + t0;
   const int64_t nleft = p.nt - t0;
@@ -223,10 +226,11 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   const bool lbuild = COARSE && warp == kThreads / 32 - 1 && lane < 7 && lj <= top;
 
   // ---- building chunk k: levels 0..3 into buffer k % 4, tails, rings 4..8 ----
-  auto build = [&](int k, float4 x0, float4 x1) {
+  auto build = [&](int k, const Raw8& raw) {
     const int ar = a0 - k * kC;
     const int buf = k % FX::NBUF, nbuf = (k + 1) % FX::NBUF;
-    const float4 v0 = norm4(x0, mu, inv), v1 = norm4(x1, mu, inv);
+    float4 v0, v1;
+    cvt8(raw, ar + 8 * t, nrel, dt, mu, inv, v0, v1);
     float* F0 = smem + FX::f0(buf);
     *reinterpret_cast<float4*>(F0 + 8 * t) = v0;
     *reinterpret_cast<float4*>(F0 + 8 * t + 4) = v1;
@@ -407,27 +411,20 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   };
 
   // ---- pipeline --------------------------------------------------------------
-  float4 n0 = load_x4(xseg, a0 + 8 * t, nrel, vec);
-  float4 n1 = load_x4(xseg, a0 + 8 * t + 4, nrel, vec);
+  Raw8 nx = load_raw8(xseg, a0 + 8 * t, nrel, dt, vx);
   {
-    const float4 c0 = n0, c1 = n1;
-    if (nch > 1) {
-      n0 = load_x4(xseg, a0 - kC + 8 * t, nrel, vec);
-      n1 = load_x4(xseg, a0 - kC + 8 * t + 4, nrel, vec);
-    }
-    build(0, c0, c1);
+    const Raw8 cx = nx;
+    if (nch > 1) nx = load_raw8(xseg, a0 - kC + 8 * t, nrel, dt, vx);
+    build(0, cx);
   }
   __syncthreads();
   if (COARSE) coarse(0);
   for (int k = 0; k < nch; ++k) {
     const bool more = k + 1 < nch;
     if (more) {
-      const float4 c0 = n0, c1 = n1;
-      if (k + 2 < nch) {
-        n0 = load_x4(xseg, a0 - (k + 2) * kC + 8 * t, nrel, vec);
-        n1 = load_x4(xseg, a0 - (k + 2) * kC + 8 * t + 4, nrel, vec);
-      }
-      build(k + 1, c0, c1);
+      const Raw8 cx = nx;
+      if (k + 2 < nch) nx = load_raw8(xseg, a0 - (k + 2) * kC + 8 * t, nrel, dt, vx);
+      build(k + 1, cx);
     }
     __syncthreads();
     if (COARSE && more) coarse(k + 1);

@@ -45,7 +45,7 @@ enum Family { kExhaustive = 0, kBoxdit = 1, kIgrid = 2 };
 
 // Search kernel parameters (passed by value; lives in the constant bank).
 struct SearchParams {
-  const float* x;
+  const void* x;        // [ndm][ld] samples of type dtype
   float* snr;
   uint16_t* widx;
   float* tile_max;      // [ndm * cand_tiles_per_row] ordered-int keys of tile maxima (or nullptr)
@@ -58,7 +58,10 @@ struct SearchParams {
   int32_t halo;         // samples read past the segment (widest boxcar, whole 2048-sample chunks)
   int32_t top;          // index of the last level
   int32_t n_top;        // block counts used on the last level (a prefix of its set)
-  int32_t vec;          // 1: 16-byte vector loads/stores are legal
+  int32_t vec;          // 1: vector stores of Y and W are legal (16-byte Y rows, 8-byte W rows)
+  int32_t vec_x;        // 1: x rows and base are 16-byte aligned (vector loads)
+  int32_t dtype;        // spd_dtype of x
+  int32_t esize;        // bytes per sample of x
   int32_t lmax;         // exhaustive: widest boxcar
   int32_t lvl_first[kMaxLevels];  // width-table index of each level's first width
   float lvl_scale[kMaxLevels];    // IGRID: 2^(-j/2), the unit factor of level j

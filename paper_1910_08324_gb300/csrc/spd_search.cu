@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
   const int64_t tile = blockIdx.x % p.tiles_per_row;
   const int64_t t0 = tile * (int64_t)kChunk;
   const int lmax = p.lmax;
-  const float* __restrict__ xrow = p.x + row * p.ld;
+  const unsigned char* __restrict__ xrow = static_cast<const unsigned char*>(p.x) + row * p.ld * p.esize;
 
   const bool vec = p.vec != 0;
   const ExLayout L(lmax, TABLE);
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
       RS[m] = (m >= 1 && m <= lmax) ? (float)(1.0 / sqrt((double)m)) : 0.0f;
   const int nchunk = (kChunk + ((lmax + 36 + 127) / 128) * 128) / 128;
   for (int c = warp; c < nchunk; c += kThreads / 32) {
-    const float4 z = load_z4(xrow, t0 + c * 128 + lane * 4, p.nt, vec, mu, inv);
+    const float4 z = load_z4d(xrow, t0 + c * 128 + lane * 4, p.nt, p.dtype, p.vec_x != 0, mu, inv);
     *reinterpret_cast<float4*>(F0 + c * 128 + lane * 4) = z;
   }
   __syncthreads();

@@ -161,3 +161,50 @@ def device_inject(x, table, sigma: float = 1.0):
         r, s, w = int(p["row"]), int(p["start"]), int(p["width"])
         x[r, s:s + w] += a
     return x
+
+
+# ---------------------------------------------------------------- reduced-precision inputs
+# Storage types of the input samples (spd_dtype order) and their u8 digitisation.
+U8_OFFSET, U8_SCALE = 128.0, 16.0  # u8 = clip(round_half_even(128 + 16 v), 0, 255) for N(0,1) v
+
+
+def quantize(x: np.ndarray, dtype: str):
+    """Store float samples as ``dtype`` ('f32', 'f16', 'bf16' or 'u8').
+
+    Returns ``(stored, values)``: ``stored`` is the numpy array to upload (bf16
+    as its uint16 bit patterns), ``values`` the float64 value of every stored
+    sample (what a search of the stored data sees).  f16 and bf16 round to
+    nearest even; u8 maps v to clip(round_half_even(128 + 16 v), 0, 255), so its
+    noise statistics are mu = 128 mu_v, sigma = 16 sigma_v in stored units.
+    """
+    x = np.asarray(x)
+    if dtype == "f32":
+        s = x.astype(np.float32)
+        return s, s.astype(np.float64)
+    if dtype == "f16":
+        s = x.astype(np.float16)
+        return s, s.astype(np.float64)
+    if dtype == "bf16":
+        b = np.ascontiguousarray(x.astype(np.float32)).view(np.uint32)
+        r = ((b + np.uint32(0x7FFF) + ((b >> np.uint32(16)) & np.uint32(1))) >> np.uint32(16)).astype(np.uint16)
+        vals = (r.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+        return r, vals
+    if dtype == "u8":
+        v = np.clip(np.rint(U8_OFFSET + U8_SCALE * np.asarray(x, np.float64)), 0, 255).astype(np.uint8)
+        return v, v.astype(np.float64)
+    raise ValueError("unknown dtype %r" % dtype)
+
+
+def device_quantize(x, dtype: str):
+    """Device counterpart of ``quantize`` for torch tensors (float32 in, stored type out;
+    bf16 as torch.bfloat16).  Same rounding rules."""
+    import torch
+    if dtype == "f32":
+        return x.float()
+    if dtype == "f16":
+        return x.half()
+    if dtype == "bf16":
+        return x.bfloat16()
+    if dtype == "u8":
+        return torch.clamp(torch.round(U8_OFFSET + U8_SCALE * x), 0, 255).to(torch.uint8)
+    raise ValueError("unknown dtype %r" % dtype)

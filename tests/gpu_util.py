@@ -39,16 +39,24 @@ def oracle_grid(plan):
 
 
 def run_gpu(plan, x, mu, sigma, ld=None, x_offset=0, return_ws=False, noise_mode=0):
-    """x: host [ndm, nt] float32.  Returns host (Y float32 [ndm, nt], W uint16 [ndm, nt]).
+    """x: host [ndm, nt] float32, or stored float16 / bf16 bits (uint16) / uint8 samples
+    for plans of those dtypes.  Returns host (Y float32 [ndm, nt], W uint16 [ndm, nt]).
 
     noise_mode 1: mu, sigma are [ndm, n_widths] tables (per row and width index)."""
     t = torch()
     ndm, nt = x.shape
     ld = plan.ld
     dev = "cuda"
-    buf = t.full((ndm * ld + x_offset + 8,), float("nan"), dtype=t.float32, device=dev)
-    xv = buf[x_offset:x_offset + ndm * ld].view(ndm, ld)
-    xv[:, :nt] = t.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
+    if x.dtype in (np.float16, np.uint16, np.uint8):  # stored f16 / bf16 bits / u8 samples
+        host = t.from_numpy(np.ascontiguousarray(x).view(np.int16) if x.dtype == np.uint16
+                            else np.ascontiguousarray(x))
+        buf = t.zeros((ndm * ld + x_offset + 16,), dtype=host.dtype, device=dev)
+        xv = buf[x_offset:x_offset + ndm * ld].view(ndm, ld)
+        xv[:, :nt] = host.to(dev)
+    else:
+        buf = t.full((ndm * ld + x_offset + 8,), float("nan"), dtype=t.float32, device=dev)
+        xv = buf[x_offset:x_offset + ndm * ld].view(ndm, ld)
+        xv[:, :nt] = t.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
     ybuf = t.full((ndm * ld + x_offset + 8,), -12345.0, dtype=t.float32, device=dev)
     wbuf = t.full((ndm * ld + x_offset + 8,), 54321, dtype=t.int32, device=dev).to(t.int16)
     Y = ybuf[x_offset:x_offset + ndm * ld].view(ndm, ld)

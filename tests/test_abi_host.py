@@ -83,10 +83,21 @@ def test_bad_shapes_and_dtypes():
     with pytest.raises(spd.SpdError) as e:
         spd.spd_plan_create(spd.SPD_ALGO_IGRID, 64, ndm=0, nt=100, igrid_depth=1, igrid_layers=4)
     assert e.value.status == 1
+    for dt in (spd.SPD_F32, spd.SPD_F16, spd.SPD_BF16, spd.SPD_U8):
+        spd.spd_plan_create(spd.SPD_ALGO_IGRID, 64, ndm=4, nt=100, igrid_depth=1, igrid_layers=4,
+                            dtype=dt)
     with pytest.raises(spd.SpdError) as e:
         spd.spd_plan_create(spd.SPD_ALGO_IGRID, 64, ndm=4, nt=100, igrid_depth=1, igrid_layers=4,
-                            dtype=spd.SPD_F16)
-    assert e.value.status == 2
+                            dtype=4)
+    assert e.value.status == 1
+
+
+def test_execute_rejects_x_misaligned_for_its_dtype():
+    plan = spd.spd_plan_create(spd.SPD_ALGO_IGRID, 64, ndm=4, nt=1000, igrid_depth=1, igrid_layers=4,
+                               dtype=spd.SPD_F16)
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_execute(plan, 4097, 4096, 4096, 4096, 4096, 4096, 1 << 30)
+    assert e.value.status == 1
 
 
 def test_execute_validates_before_launch():
