@@ -80,6 +80,10 @@ def _load():
                                      ctypes.POINTER(f64), ctypes.POINTER(f64),
                                      ctypes.POINTER(f64)]
         lib.spdo_sliding.restype = None
+        lib.spdo_msd_levels.argtypes = [_f64p, i64, i64, i64, i32, f64, i32, _f64p, _f64p, _i64p]
+        lib.spdo_msd_levels.restype = ctypes.c_int
+        lib.spdo_msd_table.argtypes = [_f64p, _f64p, _i64p, i64, i32, _i32p, i32, _f64p, _f64p]
+        lib.spdo_msd_table.restype = ctypes.c_int
         lib.spdo_candidates.argtypes = [_f64p, ctypes.c_void_p, i64, i64, f64, i32,
                                         _i64p, _i64p, _i32p, _f64p, i64]
         lib.spdo_candidates.restype = i64
@@ -270,3 +274,35 @@ def brute_search(x, L, Ls, mu=0.0, sigma=1.0):
         Y.append(best)
         W.append(bi)
     return np.array(Y), np.array(W, np.int32)
+
+
+def msd_levels(x, nlev: int, thr: float = 2.0, max_passes: int = 10):
+    """Mean, deviation and count of every row at decimations 2^0..2^(nlev-1), with
+    iterated outlier rejection at ``thr`` deviations (thr <= 0: none).
+    Returns ``(mu, sigma, n)``, each [ndm, nlev]."""
+    x = _rows(x)
+    ndm, nt = x.shape
+    mu = np.empty((ndm, nlev), np.float64)
+    sg = np.empty((ndm, nlev), np.float64)
+    n = np.empty((ndm, nlev), np.int64)
+    rc = _load().spdo_msd_levels(x.reshape(-1), ndm, nt, nt, int(nlev), float(thr),
+                                 int(max_passes), mu.reshape(-1), sg.reshape(-1), n.reshape(-1))
+    if rc != 0:
+        raise RuntimeError("spdo_msd_levels failed (%d)" % rc)
+    return mu, sg, n
+
+
+def msd_table(mu, sigma, n, widths):
+    """Per-width table (mu_L, sigma_L), each [ndm, len(widths)], from msd_levels."""
+    mu = np.ascontiguousarray(mu, np.float64)
+    sg = np.ascontiguousarray(sigma, np.float64)
+    n = np.ascontiguousarray(n, np.int64)
+    ndm, nlev = mu.shape
+    L = np.ascontiguousarray(widths, np.int32)
+    tm = np.empty((ndm, len(L)), np.float64)
+    ts = np.empty((ndm, len(L)), np.float64)
+    rc = _load().spdo_msd_table(mu.reshape(-1), sg.reshape(-1), n.reshape(-1), ndm, nlev, L,
+                                len(L), tm.reshape(-1), ts.reshape(-1))
+    if rc != 0:
+        raise RuntimeError("spdo_msd_table failed (%d)" % rc)
+    return tm, ts

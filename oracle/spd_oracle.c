@@ -27,6 +27,10 @@
  *   peaks      spdo_candidates: threshold + local-maximum rule (the paper's
  *              peak-finding step of Sec. 4.5 is not defined in the paper; the
  *              rule used here is the one stated in the function's comment)
+ *   noise      spdo_msd_levels / spdo_msd_table: mean and standard deviation
+ *              with iterated outlier rejection at power-of-two decimations,
+ *              interpolated to every width (Sec. 4.5, "Calculation of mean and
+ *              standard deviation"; the interpolation rule is a reading)
  *
  * Conventions shared with the test-suite (readings of the paper):
  *   - A boxcar is indexed by its first sample (Eq. boxcar is forward looking).
@@ -630,4 +634,132 @@ SPDO_EXPORT int64_t spdo_candidates(const double *Y, const int32_t *W, int64_t n
     }
   }
   return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Noise statistics (Sec. 4.5, calculation of mean and standard deviation)   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Mean and standard deviation of the base-level noise of every row, at the
+ * decimations 2^k, k = 0..nlev-1 (Sec. 4.5: the deviation is computed only for
+ * boxcars whose width is a power of two, i.e. for the series decimated in time).
+ *
+ * Level k of a row is the series of sums of its complete, non-overlapping
+ * blocks of 2^k samples.  For each level separately (the paper's point-wise
+ * outlier rejection, repeated until convergence):
+ *   included = every value of the level
+ *   for pass = 0 .. max_passes-1:
+ *     n, mean, sd = count, mean and standard deviation of the included values
+ *                   (population form, sum of squared deviations over n)
+ *     stop if thr <= 0 (no rejection) or pass == max_passes-1
+ *     next = values with |v - mean| <= thr * sd
+ *     stop if |next| == n (the next pass would keep as many values)
+ *     included = next
+ * mu, sigma, cnt: [ndm][nlev] outputs; a level without values gets n = 0 and
+ * mean = sd = 0.  Plain two-pass sums in FP64 (the paper's streaming Chan et al.
+ * update is a faster way to the same two numbers).
+ */
+SPDO_EXPORT int spdo_msd_levels(const double *x, int64_t ndm, int64_t nt, int64_t ld,
+                                int32_t nlev, double thr, int32_t max_passes, double *mu,
+                                double *sigma, int64_t *cnt) {
+  if (ndm < 0 || nt < 0 || ld < nt || nlev < 1 || nlev > 40 || max_passes < 1) return -1;
+  int rc = 0;
+#pragma omp parallel for schedule(dynamic)
+  for (int64_t r = 0; r < ndm; ++r) {
+    const double *xr = x + r * ld;
+    for (int32_t k = 0; k < nlev; ++k) {
+      const int64_t B = (int64_t)1 << k;
+      const int64_t nv = nt / B;
+      double m = 0.0, sd = 0.0;
+      int64_t n = 0;
+      double *v = nv > 0 ? (double *)malloc(sizeof(double) * (size_t)nv) : NULL;
+      char *inc = nv > 0 ? (char *)malloc((size_t)nv) : NULL;
+      if (nv > 0 && (!v || !inc)) {
+        rc = -2;
+        free(v);
+        free(inc);
+        continue;
+      }
+      for (int64_t i = 0; i < nv; ++i) {
+        double a = 0.0;
+        for (int64_t j = 0; j < B; ++j) a += xr[i * B + j];
+        v[i] = a;
+        inc[i] = 1;
+      }
+      for (int32_t pass = 0; pass < max_passes && nv > 0; ++pass) {
+        double s1 = 0.0;
+        n = 0;
+        for (int64_t i = 0; i < nv; ++i)
+          if (inc[i]) {
+            s1 += v[i];
+            ++n;
+          }
+        m = n > 0 ? s1 / (double)n : 0.0;
+        double s2 = 0.0;
+        for (int64_t i = 0; i < nv; ++i)
+          if (inc[i]) s2 += (v[i] - m) * (v[i] - m);
+        sd = n > 0 ? sqrt(s2 / (double)n) : 0.0;
+        if (!(thr > 0.0) || pass == max_passes - 1) break;
+        int64_t nn = 0;
+        for (int64_t i = 0; i < nv; ++i) nn += fabs(v[i] - m) <= thr * sd ? 1 : 0;
+        if (nn == n) break;
+        for (int64_t i = 0; i < nv; ++i) inc[i] = fabs(v[i] - m) <= thr * sd ? 1 : 0;
+      }
+      mu[r * nlev + k] = m;
+      sigma[r * nlev + k] = sd;
+      cnt[r * nlev + k] = n;
+      free(v);
+      free(inc);
+    }
+  }
+  return rc;
+}
+
+/*
+ * Mean and deviation of every width of a grid from the level statistics of
+ * spdo_msd_levels (Sec. 4.5: values for widths between powers of two are
+ * interpolated; the paper does not say how).  Reading used here: the per-sample
+ * mean m_k = mu_k / 2^k and the white-normalised deviation rho_k =
+ * sigma_k / sqrt(2^k) are interpolated linearly in log2(L) between the levels
+ * a = floor(log2 L) and a + 1, then mu_L = L m, sigma_L = sqrt(L) rho.  White
+ * noise (rho constant) therefore follows Eq. whitenoise exactly, and a width
+ * that is a power of two gets its level's values.  A level is usable when it
+ * has at least 2 values; widths beyond the last usable level h keep m_h and
+ * rho_h (white extrapolation).  tmu, tsig: [ndm][nw].
+ */
+SPDO_EXPORT int spdo_msd_table(const double *mu, const double *sigma, const int64_t *cnt,
+                               int64_t ndm, int32_t nlev, const int32_t *L, int32_t nw,
+                               double *tmu, double *tsig) {
+  if (ndm < 0 || nlev < 1 || nw < 0) return -1;
+  for (int64_t r = 0; r < ndm; ++r) {
+    const double *m = mu + r * nlev, *s = sigma + r * nlev;
+    const int64_t *c = cnt + r * nlev;
+    int h = -1;
+    while (h + 1 < nlev && c[h + 1] >= 2) ++h;
+    for (int32_t w = 0; w < nw; ++w) {
+      const double Lw = (double)L[w];
+      double mm, rr;
+      if (h < 0) {
+        mm = 0.0;
+        rr = 0.0;
+      } else {
+        const double lg = log2(Lw);
+        int a = (int)floor(lg);
+        if (a >= h) {
+          mm = m[h] / ldexp(1.0, h);
+          rr = s[h] / sqrt(ldexp(1.0, h));
+        } else {
+          const double f = lg - (double)a;
+          const double ma = m[a] / ldexp(1.0, a), mb = m[a + 1] / ldexp(1.0, a + 1);
+          const double ra = s[a] / sqrt(ldexp(1.0, a)), rb = s[a + 1] / sqrt(ldexp(1.0, a + 1));
+          mm = ma + f * (mb - ma);
+          rr = ra + f * (rb - ra);
+        }
+      }
+      tmu[r * nw + w] = Lw * mm;
+      tsig[r * nw + w] = sqrt(Lw) * rr;
+    }
+  }
+  return 0;
 }
