@@ -164,8 +164,8 @@ spd_status spd_plan_widths(const spd_plan *plan, int32_t *widths, int32_t *seps,
                            int32_t cap, int32_t *n);
 
 /*
- * Bytes of device workspace the plan needs for spd_execute, spd_candidates and
- * spd_search (the largest of the three; 256-byte aligned base required).
+ * Bytes of device workspace the plan needs for spd_execute, spd_candidates,
+ * spd_search and spd_noise_stats (256-byte aligned base required).
  */
 spd_status spd_workspace_size(const spd_plan *plan, size_t *bytes);
 
@@ -258,6 +258,38 @@ spd_status spd_candidates_static(const spd_plan *plan, const float *d_snr,
                                  const uint16_t *d_width_idx, float threshold,
                                  int32_t peak_radius, spd_candidate *d_out, int64_t cap,
                                  int64_t *d_count, spd_stream_t stream);
+
+/*
+ * Noise statistics for table-noise searches (Sec. 4.5, calculation of mean and
+ * standard deviation): the per-row, per-width table that spd_execute takes
+ * with spd_noise mode 1.
+ *
+ * For every row and every decimation level k = 0..K (2^K the smallest power of
+ * two >= the plan's widest boxcar, K <= 15), the series of sums of the row's
+ * complete blocks of 2^k samples gets a mean and a standard deviation
+ * (population form) by point-wise outlier rejection: the first pass keeps every
+ * value; each further pass keeps the values within outlier_sigma deviations of
+ * the previous pass's mean, until a pass keeps as many values as the one before
+ * or max_passes passes have run (outlier_sigma <= 0: one pass, no rejection).
+ * Widths between powers of two are interpolated (the paper does not say how):
+ * the per-sample mean mu_k / 2^k and the deviation per square-root sample
+ * sigma_k / 2^(k/2) are interpolated linearly in log2(L), and
+ * mu_L = L * mean, sigma_L = sqrt(L) * deviation, so white noise follows Eq.
+ * whitenoise.  Levels with fewer than two values are not used: wider widths
+ * extrapolate the last level with two or more values the white way; a row of
+ * one sample gets sigma 0.
+ *   d_x           device, [ndm][ld] samples of the plan dtype (as spd_execute)
+ *   outlier_sigma rejection threshold in deviations (the paper used 2)
+ *   max_passes    1..64
+ *   d_mu, d_sigma device float32 [ndm][n_widths] outputs (n_widths and width
+ *                 order of spd_plan_widths), 4-byte aligned
+ *   d_ws          workspace of spd_workspace_size() bytes (its tile maxima are
+ *                 left alone)
+ * Errors: SPD_ERR_INVALID_ARG, SPD_ERR_WORKSPACE_TOO_SMALL, SPD_ERR_CUDA.
+ */
+spd_status spd_noise_stats(const spd_plan *plan, const void *d_x, float outlier_sigma,
+                           int32_t max_passes, float *d_mu, float *d_sigma, void *d_ws,
+                           size_t ws_bytes, spd_stream_t stream);
 
 /*
  * Wait for the stream and report any asynchronous CUDA error of work queued

@@ -8,9 +8,10 @@ or loaded, importing the binding functions raises.
 
 Entry points (same names as the C ABI): ``spd_plan_create``,
 ``spd_plan_destroy``, ``spd_plan_widths``, ``spd_workspace_size``,
-``spd_execute``, ``spd_candidates``, ``spd_search``, ``spd_sync_status``,
-``spd_status_string``, ``spd_version``.  Convenience wrappers taking torch
-tensors: ``execute``, ``candidates``, ``search``.
+``spd_execute``, ``spd_candidates``, ``spd_candidates_static``, ``spd_search``,
+``spd_noise_stats``, ``spd_sync_status``, ``spd_status_string``,
+``spd_version``.  Convenience wrappers taking torch tensors: ``execute``,
+``candidates``, ``search``, ``noise_stats``.
 """
 from ._binding import (  # noqa: F401
     CANDIDATE_DTYPE,
@@ -27,11 +28,13 @@ from ._binding import (  # noqa: F401
     execute,
     library_path,
     load_library,
+    noise_stats,
     records,
     search,
     spd_candidates,
     spd_candidates_static,
     spd_execute,
+    spd_noise_stats,
     spd_plan_create,
     spd_plan_destroy,
     spd_plan_widths,

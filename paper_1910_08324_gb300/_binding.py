@@ -80,6 +80,7 @@ def load_library():
                                    i64, vp, vp, sz, vp]
         lib.spd_sync_status.argtypes = [vp, vp]
         lib.spd_candidates_static.argtypes = [vp, vp, vp, ctypes.c_float, i32, vp, i64, vp, vp]
+        lib.spd_noise_stats.argtypes = [vp, vp, ctypes.c_float, i32, vp, vp, vp, sz, vp]
         for name in _SYMBOLS[2:]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -194,6 +195,13 @@ def spd_search(plan: Plan, x: int, mu: int, sigma: int, snr: int, width_idx: int
                                      int(cap), count, ws, ws_bytes, stream or None), "spd_search")
 
 
+def spd_noise_stats(plan: Plan, x: int, outlier_sigma: float, max_passes: int, mu: int, sigma: int,
+                    ws: int, ws_bytes: int, stream: int = 0):
+    _check(load_library().spd_noise_stats(ctypes.c_void_p(plan.handle), x, float(outlier_sigma),
+                                          int(max_passes), mu, sigma, ws, ws_bytes, stream or None),
+           "spd_noise_stats")
+
+
 def spd_sync_status(plan: Plan, stream: int = 0):
     _check(load_library().spd_sync_status(ctypes.c_void_p(plan.handle), stream or None),
            "spd_sync_status")
@@ -234,6 +242,14 @@ def search(plan: Plan, x, mu, sigma, snr, width_idx, threshold: float, peak_radi
     spd_search(plan, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(snr), _ptr(width_idx), threshold,
                peak_radius, _ptr(out), cap, _ptr(count), _ptr(ws), ws.numel() * ws.element_size(),
                _stream(stream), noise_mode=noise_mode)
+
+
+def noise_stats(plan: Plan, x, mu_out, sigma_out, ws, outlier_sigma: float = 2.0,
+                max_passes: int = 10, stream=None):
+    """Run ``spd_noise_stats``: fills float32 [ndm, n_widths] mu_out, sigma_out (the
+    table of ``execute(..., noise_mode=1)``)."""
+    spd_noise_stats(plan, _ptr(x), outlier_sigma, max_passes, _ptr(mu_out), _ptr(sigma_out),
+                    _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
 
 
 def records(out_tensor, count: int):

@@ -101,9 +101,10 @@ int dtype_size(int dtype) {
 }
 
 // Workspace: tile maxima (written by the search, read by the candidate step),
-// per-tile candidate counts, per-group sums and offsets.
+// per-tile candidate counts, per-group sums and offsets, and the level
+// statistics of spd_noise_stats.
 struct WsLayout {
-  size_t tile_max, counts, gsum, goff, total;
+  size_t tile_max, counts, gsum, goff, msd, total;
   explicit WsLayout(const spd_plan& p) {
     const size_t nt = (size_t)(p.desc.ndm * p.cand_tiles_per_row);
     const size_t ng = (nt + spd::kCandGroup - 1) / spd::kCandGroup;
@@ -111,7 +112,8 @@ struct WsLayout {
     counts = align_up(tile_max + nt * sizeof(float));
     gsum = align_up(counts + nt * sizeof(int32_t));
     goff = align_up(gsum + ng * sizeof(int32_t));
-    total = align_up(goff + ng * sizeof(int64_t));
+    msd = align_up(goff + ng * sizeof(int64_t));
+    total = align_up(msd + spd::msd_state_bytes(p.desc.ndm));
   }
 };
 
@@ -415,6 +417,44 @@ spd_status spd_search(const spd_plan* plan, const void* d_x, const spd_noise* no
   if (st != SPD_OK) return st;
   return do_candidates(plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count, d_ws,
                        ws_bytes, true, s);
+}
+
+spd_status spd_noise_stats(const spd_plan* plan, const void* d_x, float outlier_sigma,
+                           int32_t max_passes, float* d_mu, float* d_sigma, void* d_ws,
+                           size_t ws_bytes, spd_stream_t stream) {
+  if (!plan || !d_x || !d_mu || !d_sigma) return SPD_ERR_INVALID_ARG;
+  if (max_passes < 1 || max_passes > 64 || std::isnan(outlier_sigma) || std::isinf(outlier_sigma))
+    return SPD_ERR_INVALID_ARG;
+  const int esize = dtype_size(plan->desc.dtype);
+  if (((uintptr_t)d_x % esize) || ((uintptr_t)d_mu % 4) || ((uintptr_t)d_sigma % 4))
+    return SPD_ERR_INVALID_ARG;
+  spd_status st = validate_ws(plan, d_ws, ws_bytes);
+  if (st != SPD_OK) return st;
+  spd::MsdParams* mp = new (std::nothrow) spd::MsdParams();
+  if (!mp) return SPD_ERR_HOST_ALLOC;
+  spd::MsdParams& p = *mp;
+  p.x = d_x;
+  p.ndm = plan->desc.ndm;
+  p.nt = plan->desc.nt;
+  p.ld = plan->desc.ld;
+  p.dtype = plan->desc.dtype;
+  p.esize = esize;
+  p.vec_x = ((uintptr_t)d_x % 16 == 0 && (plan->desc.ld * esize) % 16 == 0) ? 1 : 0;
+  int nlev = 1;
+  while (nlev < spd::kMsdMaxLevels && (1 << (nlev - 1)) < plan->lend) ++nlev;
+  p.nlev = nlev;
+  p.thr = outlier_sigma;
+  p.state = static_cast<char*>(d_ws) + WsLayout(*plan).msd;
+  p.out_mu = d_mu;
+  p.out_sigma = d_sigma;
+  p.n_widths = (int32_t)plan->widths.size();
+  p.unit_widths = plan->family == kExhaustive ? 1 : 0;
+  if (!p.unit_widths)
+    for (size_t i = 0; i < plan->widths.size() && i < (size_t)spd::kMaxGridWidths; ++i)
+      p.wtab[i] = plan->widths[i];
+  const cudaError_t e = spd::launch_msd(*plan, p, max_passes, reinterpret_cast<cudaStream_t>(stream));
+  delete mp;
+  return check_cuda(e);
 }
 
 spd_status spd_sync_status(const spd_plan* plan, spd_stream_t stream) {

@@ -73,6 +73,21 @@ struct SearchParams {
   int32_t wtab[kMaxGridWidths];   // widths of the plan (table noise, unit_widths == 0)
 };
 
+// Noise-statistics kernels (spd_msd.cu).
+constexpr int kMsdMaxLevels = 16;  // decimation levels 2^0 .. 2^15 (kMaxLend = 2^15)
+struct MsdParams {
+  const void* x;
+  int64_t ndm, nt, ld;
+  int32_t dtype, esize, vec_x;
+  int32_t nlev;         // levels computed (2^(nlev-1) >= the widest boxcar)
+  float thr;            // outlier threshold in deviations; <= 0: no rejection
+  void* state;          // workspace: [ndm][kMsdMaxLevels] level statistics
+  float* out_mu;        // [ndm][n_widths]
+  float* out_sigma;
+  int32_t n_widths, unit_widths;
+  int32_t wtab[kMaxGridWidths];
+};
+
 struct CandParams {
   const float* snr;
   const uint16_t* widx;
@@ -110,7 +125,7 @@ struct spd_plan {
 };
 
 namespace spd {
-// kernel launchers (spd_search.cu, spd_igrid.cu, spd_boxdit.cu, spd_candidates.cu)
+// kernel launchers (spd_search.cu, spd_igrid.cu, spd_boxdit.cu, spd_candidates.cu, spd_msd.cu)
 cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 size_t igrid_smem_bytes(const spd_plan& plan, bool table);
@@ -119,4 +134,6 @@ size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
 cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s);
 size_t search_smem_bytes(const spd_plan& plan, bool table);
+size_t msd_state_bytes(int64_t ndm);
+cudaError_t launch_msd(const spd_plan& plan, const MsdParams& p, int max_passes, cudaStream_t s);
 }  // namespace spd
