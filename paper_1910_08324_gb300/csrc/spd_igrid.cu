@@ -15,8 +15,8 @@
 // k (chunks counted in processing order):
 //   build   chunk k+1's 8 samples per thread (prefetched into registers one
 //           iteration earlier) are normalised and reduced in registers and
-//           warp shuffles into levels 0..3 (shared, four buffers, each with a
-//           lookahead tail written by the chunk processed before it) and into
+//           warp shuffles into levels 0..3 (shared, three buffers, each with a
+//           lookahead tail copied from the chunk processed before it) and into
 //           ring buffers for the coarse levels 4.. (unit >= 16); the loads of
 //           chunk k+2 are issued;
 //   barrier
@@ -74,14 +74,15 @@ struct IgFix {
   __host__ __device__ static constexpr int f1(int b) { return b * FB + O1; }
   __host__ __device__ static constexpr int f2(int b) { return b * FB + O2; }
   __host__ __device__ static constexpr int f3(int b) { return b * FB + O3; }
-  static constexpr int NBUF = 4;
+  static constexpr int NBUF = 3;
   static constexpr int RINGS = NBUF * FB;
 };
 
-// A ring holds every block a window of the chunk being evaluated can reach,
-// plus the blocks of the chunk being built meanwhile.
-__host__ __device__ inline int ring_size(int j, int H, int mmax) {
-  return next_pow2(cdiv(2 * kC + H, 1 << j) + mmax + 2);
+// A ring holds every block a window of the chunk being evaluated can reach
+// (the chunk and mmax blocks past it), plus the blocks of the chunk being built
+// meanwhile.
+__host__ __device__ inline int ring_size(int j, int mmax) {
+  return next_pow2(cdiv(2 * kC, 1 << j) + mmax + 2);
 }
 
 // offsets (floats) of the rings' end, the coarse results (two buffers of
@@ -94,9 +95,9 @@ constexpr int kBcm = kC / 16;               // starts = 0 mod 16 in a chunk
 struct IgDyn {
   int res_y, res_w, bcm, tab, ab, total;
   // nab: widths of the table-noise constants (0 for white noise)
-  __host__ __device__ IgDyn(int rings, int H, int top, int mmax, int nab) {
+  __host__ __device__ IgDyn(int rings, int top, int mmax, int nab) {
     int o = rings;
-    for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, H, mmax) + mmax);
+    for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, mmax) + mmax);
     res_y = o;
     o += 2 * kResN;
     res_w = o;
@@ -112,7 +113,7 @@ struct IgDyn {
 };
 
 template <int D, int PL, bool COARSE, bool TABLE>
-__global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
+__global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     igrid_stream_kernel(const SearchParams p) {
   using S = IgS<D, PL>;
   using FX = IgFix<D, PL>;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   uint16_t* __restrict__ wseg = p.widx + row * p.ld + t0;
   const int64_t nleft = p.nt - t0;
   const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));  // samples that exist
-  const IgDyn L(FX::RINGS, H, top, MMAX, TABLE ? p.n_widths : 0);
+  const IgDyn L(FX::RINGS, top, MMAX, TABLE ? p.n_widths : 0);
   float2* AB = reinterpret_cast<float2*>(smem + L.ab);  // table noise: (a, b) per width index
   float mu, inv;
   row_noise<TABLE>(p, row, AB, mu, inv);
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
       RTAB[2 * j + 1] = 0;
     }
     for (int j = kRing0; j <= top; ++j) {
-      const int n = ring_size(j, H, MMAX);
+      const int n = ring_size(j, MMAX);
       RTAB[2 * j] = o;
       RTAB[2 * j + 1] = n - 1;
       o += al4(n + MMAX);
@@ -225,30 +226,33 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 3 : 2))
   const int lw = 1 << (lj - 8);
   const bool lbuild = COARSE && warp == kThreads / 32 - 1 && lane < 7 && lj <= top;
 
-  // ---- building chunk k: levels 0..3 into buffer k % 4, tails, rings 4..8 ----
+  // ---- building chunk k: levels 0..3 into buffer k % 3 (+ tails), rings 4..8 ----
+  // The lookahead tail of chunk k is the head of chunk k-1 (built one iteration
+  // earlier, before the last barrier), copied from its buffer.  Writing it into
+  // the next buffer from registers instead would race with a slow warp still
+  // evaluating the chunk that buffer held three chunks ago.
   auto build = [&](int k, const Raw8& raw) {
     const int ar = a0 - k * kC;
-    const int buf = k % FX::NBUF, nbuf = (k + 1) % FX::NBUF;
+    const int buf = k % FX::NBUF;
+    if (k > 0) {
+      const int pb = (k - 1) % FX::NBUF;
+      if (t < S::TL0) smem[FX::f0(buf) + kC + t] = smem[FX::f0(pb) + t];
+      if (t < S::TL1) smem[FX::f1(buf) + kC / 2 + t] = smem[FX::f1(pb) + t];
+      if (t < S::TL2) smem[FX::f2(buf) + kC / 4 + t] = smem[FX::f2(pb) + t];
+      if (t < S::TL3) smem[FX::f3(buf) + kC / 8 + t] = smem[FX::f3(pb) + t];
+    }
     float4 v0, v1;
     cvt8(raw, ar + 8 * t, nrel, dt, mu, inv, v0, v1);
     float* F0 = smem + FX::f0(buf);
     *reinterpret_cast<float4*>(F0 + 8 * t) = v0;
     *reinterpret_cast<float4*>(F0 + 8 * t + 4) = v1;
-    if (8 * t < S::TL0) {
-      float* T0 = smem + FX::f0(nbuf) + kC + 8 * t;
-      *reinterpret_cast<float4*>(T0) = v0;
-      if (8 * t + 4 < S::TL0) *reinterpret_cast<float4*>(T0 + 4) = v1;
-    }
     const float p0 = v0.x + v0.y, p1 = v0.z + v0.w, p2 = v1.x + v1.y, p3 = v1.z + v1.w;
     const float4 pp = make_float4(p0, p1, p2, p3);
     *reinterpret_cast<float4*>(smem + FX::f1(buf) + 4 * t) = pp;
-    if (4 * t < S::TL1) *reinterpret_cast<float4*>(smem + FX::f1(nbuf) + kC / 2 + 4 * t) = pp;
     const float q0 = p0 + p1, q1 = p2 + p3;
     *reinterpret_cast<float2*>(smem + FX::f2(buf) + 2 * t) = make_float2(q0, q1);
-    if (2 * t < S::TL2) *reinterpret_cast<float2*>(smem + FX::f2(nbuf) + kC / 4 + 2 * t) = make_float2(q0, q1);
     const float o8 = q0 + q1;
     smem[FX::f3(buf) + t] = o8;
-    if (t < S::TL3) smem[FX::f3(nbuf) + kC / 8 + t] = o8;
     if (COARSE) {
       const int d = k * kC;  // rn[] hold chunk-0 block indices
       float s = o8 + __shfl_xor_sync(kFull, o8, 1);
@@ -439,7 +443,7 @@ size_t igrid_smem_bytes(const spd_plan& plan, bool table) {
   switch (plan.d * 8 + plan.pl) {
 #define SPD_IG_CASE(D, PL) \
   case D * 8 + PL:         \
-    return sizeof(float) * (size_t)IgDyn(IgFix<D, PL>::RINGS, plan.halo, plan.top, IgS<D, PL>::MMAX, nab).total;
+    return sizeof(float) * (size_t)IgDyn(IgFix<D, PL>::RINGS, plan.top, IgS<D, PL>::MMAX, nab).total;
     SPD_IG_CASE(0, 0)
     SPD_IG_CASE(0, 1)
     SPD_IG_CASE(1, 1)
