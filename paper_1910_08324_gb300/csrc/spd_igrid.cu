@@ -58,6 +58,8 @@ struct IgS {
   static constexpr int TL1 = 4 * NW1 - 4;
   static constexpr int TL2 = 2 * NW2 - 2;
   static constexpr int TL3 = NW3 - 1;
+  static constexpr int NWQ = cdiv(3 + MMAX, 4);  // float4 window of a coarse quad (4 positions)
+  static constexpr int MIR = 4 * NWQ;            // mirrored ring entries: no window ever wraps
 };
 
 // Shared-memory layout: three buffers of levels 0..3 (compile-time strides),
@@ -97,7 +99,7 @@ struct IgDyn {
   // nab: widths of the table-noise constants (0 for white noise)
   __host__ __device__ IgDyn(int rings, int top, int mmax, int nab) {
     int o = rings;
-    for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, mmax) + mmax);
+    for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, mmax) + 4 * cdiv(3 + mmax, 4));
     res_y = o;
     o += 2 * kResN;
     res_w = o;
@@ -171,52 +173,63 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
       const int n = ring_size(j, MMAX);
       RTAB[2 * j] = o;
       RTAB[2 * j + 1] = n - 1;
-      o += al4(n + MMAX);
+      o += al4(n + S::MIR);
     }
   }
   __syncthreads();
-  // ring write: slot and, for the first MMAX slots, its mirror (a select, no branch)
+  // ring write: slot and, for the first MIR slots, its mirror (a select, no branch)
   auto ring_put = [&](int base, int mask, int n, float v) {
     const int slot = n & mask;
     smem[base + slot] = v;
-    smem[base + (slot < MMAX ? slot + mask + 1 : slot)] = v;
+    smem[base + (slot < S::MIR ? slot + mask + 1 : slot)] = v;
   };
   // chunks at relative starts ar(k) = a0 - k*kC, k = 0..nch-1 (backwards in time)
   int a0 = T + H - kC;
   if (a0 >= nrel) a0 = ((nrel - 1) / kC) * kC;  // chunks at or past nt are all -inf
   const int nch = a0 / kC + 1;
 
-  // rings of levels 4..8 get one value per thread and level per chunk (all lanes
-  // of a block write the same value): block index of this thread at chunk 0
-  int rb[5] = {0, 0, 0, 0, 0}, rm[5] = {0, 0, 0, 0, 0}, rn[5] = {0, 0, 0, 0, 0};
-  // this thread's coarse position per chunk: level cj (0 = none), index cq
+  // Ring writes of levels 4..8: the 31 blocks a warp completes per chunk (16 of
+  // level 4, 8 of 5, 4 of 6, 2 of 7, 1 of 8) are written by one lane each:
+  // lane l writes block wb of level wj, whose sum it fetches from lane wsrc.
+  const int wj = lane < 16 ? 4 : lane < 24 ? 5 : lane < 28 ? 6 : lane < 30 ? 7 : 8;
+  const int wb = lane < 16 ? lane : lane < 24 ? lane - 16 : lane < 28 ? lane - 24 : lane < 30 ? lane - 28 : 0;
+  const bool wput = COARSE && lane < 31 && wj <= top;
+  int wn = 0;
+  // Coarse evaluation: quads of 4 consecutive positions (float4 ring windows) for
+  // levels 4..8 on the 62 first threads (32, 16, 8, 4, 2 quads) and level 9 on
+  // lane 0 of the last warp (after it has built the level); single positions of
+  // levels 10, 11 on its lanes 1..3, levels above 11 on its lane 4.
   const int ctop = top < kChunkLog ? top : kChunkLog;
-  int cj = 0, cbase = 0, cmask = 0, cfirst = 0, cnu = 0, cbcm = 0, ccode = 0, cn = 0;
-  float cf = 0.f;
+  // (ring offsets, masks and level constants are re-read per chunk from the
+  // ring table and the kernel parameters rather than held in registers)
+  int qj = 0, qn = 0, qq = 0;
+  int sj = 0, sn = 0, sq = 0;
   if (COARSE) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const int j = kRing0 + i;
-      rb[i] = RTAB[2 * j];
-      rm[i] = RTAB[2 * j + 1];
-      rn[i] = (a0 >> j) + (t >> (j - 3));
-    }
-    if (t < 256 - (1 << (kChunkLog - ctop))) {  // positions of levels 4..ctop
-      int j = kRing0, off = 0;
-      while (t >= off + (kC >> j)) {
-        off += kC >> j;
+    if (wput) wn = ((a0 + 256 * warp) >> wj) + wb;  // block index at chunk 0 (relative to the segment)
+    int j = 0, u = -1;
+    if (t < 62) {
+      j = kRing0;
+      u = t;
+      while (u >= (512 >> j)) {
+        u -= 512 >> j;
         ++j;
       }
-      const int cq = t - off;
-      cj = j;
-      cbase = RTAB[2 * j];
-      cmask = RTAB[2 * j + 1];
-      cf = lvl_f(j);
-      cfirst = p.lvl_first[j];
-      cnu = (j == top) ? p.n_top : SM::MM;
-      cbcm = cq << (j - 4);   // its start / 16
-      ccode = 15 - (j - 4);   // smaller level wins near-ties of the merge key
-      cn = (a0 >> j) + cq;    // its block index at chunk 0 (decreases by kC >> j per chunk)
+    } else if (warp == kThreads / 32 - 1 && lane == 0) {
+      j = 9;
+      u = 0;
+    }
+    if (u >= 0 && j <= ctop) {
+      qj = j;
+      qq = 4 * u;
+      qn = (a0 >> j) + qq;  // first block of the quad at chunk 0
+    }
+    if (warp == kThreads / 32 - 1 && lane >= 1 && lane <= 3) {
+      const int j1 = lane < 3 ? 10 : 11;
+      if (j1 <= ctop) {
+        sj = j1;
+        sq = lane < 3 ? lane - 1 : 0;
+        sn = (a0 >> j1) + sq;
+      }
     }
   }
   // level-9..11 blocks of a chunk: lane L of the last warp builds block lb of level lj
@@ -254,25 +267,19 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     const float o8 = q0 + q1;
     smem[FX::f3(buf) + t] = o8;
     if (COARSE) {
-      const int d = k * kC;  // rn[] hold chunk-0 block indices
-      float s = o8 + __shfl_xor_sync(kFull, o8, 1);
-      ring_put(rb[0], rm[0], rn[0] - (d >> 4), s);
-      if (top >= 5) {
-        s += __shfl_xor_sync(kFull, s, 2);
-        ring_put(rb[1], rm[1], rn[1] - (d >> 5), s);
-      }
-      if (top >= 6) {
-        s += __shfl_xor_sync(kFull, s, 4);
-        ring_put(rb[2], rm[2], rn[2] - (d >> 6), s);
-      }
-      if (top >= 7) {
-        s += __shfl_xor_sync(kFull, s, 8);
-        ring_put(rb[3], rm[3], rn[3] - (d >> 7), s);
-      }
-      if (top >= 8) {
-        s += __shfl_xor_sync(kFull, s, 16);
-        ring_put(rb[4], rm[4], rn[4] - (d >> 8), s);
-      }
+      // block sums of levels 4..8 (every lane of a block holds its sum), then one
+      // lane per block fetches it and writes the ring
+      const float s4 = o8 + __shfl_xor_sync(kFull, o8, 1);
+      const float s5 = s4 + __shfl_xor_sync(kFull, s4, 2);
+      const float s6 = s5 + __shfl_xor_sync(kFull, s5, 4);
+      const float s7 = s6 + __shfl_xor_sync(kFull, s6, 8);
+      const float s8 = s7 + __shfl_xor_sync(kFull, s7, 16);
+      const float v4 = __shfl_sync(kFull, s4, (2 * lane) & 31);
+      const float v5 = __shfl_sync(kFull, s5, (4 * lane) & 31);
+      const float v6 = __shfl_sync(kFull, s6, (8 * lane) & 31);
+      const float v7 = __shfl_sync(kFull, s7, (16 * lane) & 31);
+      const float v = lane < 16 ? v4 : lane < 24 ? v5 : lane < 28 ? v6 : lane < 30 ? v7 : s8;
+      if (wput) ring_put(RTAB[2 * wj], RTAB[2 * wj + 1], wn - ((k * kC) >> wj), v);
     }
   };
 
@@ -284,12 +291,13 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     const int ar = a0 - k * kC;
     if (warp == kThreads / 32 - 1 && top >= 9) {  // blocks of levels 9.. need every warp's level 8
       if (lbuild) {
-        const float* R8 = smem + rb[4];
+        const float* R8 = smem + RTAB[2 * 8];
+        const int m8 = RTAB[2 * 8 + 1];
         const int n8 = (ar >> 8) + lb * lw;
         float acc = 0.f;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const float v = R8[(n8 + i) & rm[4]];
+          const float v = R8[(n8 + i) & m8];
           acc += (i < lw) ? v : 0.f;
         }
         ring_put(RTAB[2 * lj], RTAB[2 * lj + 1], (ar >> lj) + lb, acc);
@@ -309,21 +317,42 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     float* RY = RESY + (k & 1) * kResN;
     uint16_t* RW = RESW + (k & 1) * kResN;
     int* KB = BCM + (k & 1) * kBcm;
-    auto eval_one = [&](const float* w, int nu, float f, int first, int slot, int bcm, int code) {
+    // result of position q of level j: slot (the position's index among the
+    // chunk's coarse positions), start key for the fine step's merge
+    auto put = [&](int j, int q, float y, int wi) {
+      const int slot = (j <= kChunkLog) ? kThreads - (1 << (kChunkLog + 1 - j)) + q : kResHi + j - kChunkLog - 1;
+      RY[slot] = y;
+      RW[slot] = (uint16_t)wi;
+      atomicMax(KB + (q << (j - 4)), (fkey(y) & ~15) | (15 - (j - 4)));
+    };
+    if (qj) {  // four consecutive positions from one float4 window
+      float win[S::NWQ * 4], bv[4], full[4];
+      int bq[4];
+      const int first = p.lvl_first[qj];
+      load_window4<S::NWQ>(smem + RTAB[2 * qj] + ((qn - ((k * kC) >> qj)) & RTAB[2 * qj + 1]), win);
+      eval_window<4, MMAX, SM, true, false>(win, (qj == top) ? p.n_top : SM::MM, scl(AB + first, SM{}),
+                                            nullptr, bv, bq, full);
+      const float f = lvl_f(qj);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) put(qj, qq + r, bv[r] * f, first + bq[r]);
+    }
+    if (sj) {
       float bv;
       int bq;
-      eval_one_masked<MMAX, SM>(w, nu, scl(AB + first, SM{}), bv, bq);
-      const float y = bv * f;
-      RY[slot] = y;
-      RW[slot] = (uint16_t)(first + bq);
-      atomicMax(KB + bcm, (fkey(y) & ~15) | code);
-    };
-    if (cj) eval_one(smem + cbase + ((cn - ((k * kC) >> cj)) & cmask), cnu, cf, cfirst, t, cbcm, ccode);
-    if (t == kThreads - 1)
+      const int first = p.lvl_first[sj];
+      eval_one_masked<MMAX, SM>(smem + RTAB[2 * sj] + ((sn - ((k * kC) >> sj)) & RTAB[2 * sj + 1]),
+                                (sj == top) ? p.n_top : SM::MM, scl(AB + first, SM{}), bv, bq);
+      put(sj, sq, bv * lvl_f(sj), first + bq);
+    }
+    if (warp == kThreads / 32 - 1 && lane == 4)
       for (int jj = kChunkLog + 1; jj <= top; ++jj)
-        if (((t0 + ar) & ((1LL << jj) - 1)) == 0)
-          eval_one(smem + RTAB[2 * jj] + ((ar >> jj) & RTAB[2 * jj + 1]), (jj == top) ? p.n_top : SM::MM,
-                   lvl_f(jj), p.lvl_first[jj], kResHi + jj - kChunkLog - 1, 0, 15 - (jj - 4));
+        if (((t0 + ar) & ((1LL << jj) - 1)) == 0) {
+          float bv;
+          int bq;
+          eval_one_masked<MMAX, SM>(smem + RTAB[2 * jj] + ((ar >> jj) & RTAB[2 * jj + 1]),
+                                    (jj == top) ? p.n_top : SM::MM, scl(AB + p.lvl_first[jj], SM{}), bv, bq);
+          put(jj, 0, bv * lvl_f(jj), p.lvl_first[jj] + bq);
+        }
   };
 
   // ---- fine levels, merge and store of chunk k -----------------------------

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) msd_pass_kernel(const MsdParams p, i
   for (int k = 0; k < 4; ++k) cw[k] = cw2[k] = 0.0f;
   // levels 0..3 (several values per thread and chunk): chunk-local sums, folded
   // into the compensated sums once per chunk; levels >= 4: one value per chunk
-  float pw[4], pw2[4];
+  float pw[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pw2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   auto keep = [&](auto K, float v, bool valid) {
     constexpr int k = decltype(K)::value;
     const float w = v - cshift[k];
