@@ -177,6 +177,9 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
       for (int m = 1; m <= plan->k; ++m)
         p.bscale[j][m] =
             (float)(1.0 / std::sqrt((double)plan->lvl_base[j] + (double)m * (double)(1 << j)));
+  } else if (plan->family == kIgrid) {  // fine levels 0..3: 1/sqrt(m 2^j) in one constant
+    for (int j = 0; j <= 3 && j <= plan->top; ++j)
+      for (int m = 1; m <= 32; ++m) p.bscale[j][m] = (float)(1.0 / std::sqrt((double)m * (double)(1 << j)));
   }
   // tile maxima start at a key below every float (0x80808080)
   cudaError_t e = cudaMemsetAsync(p.tile_max, 0x80,
@@ -331,6 +334,12 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
     // multiple of the candidate tile); the halo is the widest boxcar, rounded
     // to whole chunks
     if (p->family == kBoxdit && p->top > 11) {  // unreachable below kMaxLend; the kernel stops at 11
+      delete p;
+      return SPD_ERR_UNSUPPORTED;
+    }
+    // IGRID with depth <= 1 and <= 4 layers carries width indices in 5 SNR bits
+    // (at most 31 widths below kMaxLend)
+    if (p->family == kIgrid && p->d <= 1 && p->pl <= 2 && p->widths.size() > 32) {
       delete p;
       return SPD_ERR_UNSUPPORTED;
     }

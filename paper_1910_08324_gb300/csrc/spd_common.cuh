@@ -362,6 +362,27 @@ __device__ __forceinline__ void eval_window(const float* w, int n_used, Scale&& 
   });
 }
 
+// ---------------------------------------------------------------- coded SNRs
+// For grids of at most 2^B widths the width index can travel in the B low
+// mantissa bits of an SNR (code = 2^B - 1 - index): the maximum of coded values
+// is the maximum SNR to within 2^B - 1 ulp and, among values equal to that
+// resolution, the smallest index wins (positive values); maxima and merges are
+// then single max instructions.  A -inf candidate becomes a NaN, which max
+// ignores; a maximum over NaNs only is the canonical (positive) NaN, which
+// callers must treat as "no candidate" before using it as an ordered key.
+template <int B>
+__device__ __forceinline__ float enc_w(float v, int code) {
+  return __int_as_float((__float_as_int(v) & ~((1 << B) - 1)) | code);
+}
+template <int B>
+__device__ __forceinline__ int dec_w(float v) {
+  return ((1 << B) - 1) - (__float_as_int(v) & ((1 << B) - 1));
+}
+template <int B>
+__device__ __forceinline__ float dec_v(float v) {
+  return __int_as_float(__float_as_int(v) & ~((1 << B) - 1));
+}
+
 // Three-input maximum (one instruction on sm_100 and later).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
   float d;
@@ -429,6 +450,33 @@ __device__ __forceinline__ void eval_window_mx(const float* w, Scale&& scale, fl
                                                int (&bq)[NP]) {
   float full[NP];
   eval_window_mxb<NP, MMAX, Pred, false>(w, nullptr, scale, bv, bq, full);
+}
+
+// Coded evaluation of NP consecutive positions (see enc_w): out[r] is the
+// maximum over the set of enc_w(SNR, code(rank)), with code(rank) = code0 -
+// rank; PARTIAL: ranks at or above n_used (rank 0 always counts) are -inf.
+template <int NP, int MMAX, class Pred, int B, bool PARTIAL, class Scale>
+__device__ __forceinline__ void eval_window_enc(const float* w, int n_used, Scale&& scale, int code0,
+                                                float (&out)[NP]) {
+  constexpr int NC = count_in<Pred, MMAX>();
+  static_for<0, NP>([&](auto R) {
+    constexpr int r = decltype(R)::value;
+    float v[NC];
+    float S = 0.0f;
+    static_for<1, MMAX + 1>([&](auto M) {
+      constexpr int m = decltype(M)::value;
+      S += w[r + m - 1];
+      if constexpr (Pred::in(m)) {
+        constexpr int rk = Pred::rank(m);
+        const float x = enc_w<B>(snr_of(S, scale(M)), code0 - rk);
+        if constexpr (PARTIAL && rk > 0)
+          v[rk] = rk < n_used ? x : ninf();
+        else
+          v[rk] = x;
+      }
+    });
+    out[r] = tree_max<NC>(v);
+  });
 }
 
 // Like eval_window_mx for one position, but only ranks below n_used count

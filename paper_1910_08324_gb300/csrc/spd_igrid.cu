@@ -60,6 +60,11 @@ struct IgS {
   static constexpr int TL3 = NW3 - 1;
   static constexpr int NWQ = cdiv(3 + MMAX, 4);  // float4 window of a coarse quad (4 positions)
   static constexpr int MIR = 4 * NWQ;            // mirrored ring entries: no window ever wraps
+  // Grids with at most 32 widths (every plan of these (D, P) up to the widest
+  // boxcar allowed) carry the width index in the SNR's low bits (enc_w).
+  static constexpr bool ENC = D <= 1 && PL <= 2;
+  static constexpr int EB = 5, EMAX = (1 << EB) - 1;
+  static constexpr int NC0 = count_in<S0, MMAX>();  // level-0 widths; level j >= 1 starts at NC0 + (j-1) 2^D
 };
 
 // Shared-memory layout: three buffers of levels 0..3 (compile-time strides),
@@ -96,14 +101,15 @@ constexpr int kBcm = kC / 16;               // starts = 0 mod 16 in a chunk
 
 struct IgDyn {
   int res_y, res_w, bcm, tab, ab, total;
-  // nab: widths of the table-noise constants (0 for white noise)
-  __host__ __device__ IgDyn(int rings, int top, int mmax, int nab) {
+  // nab: widths of the table-noise constants (0 for white noise); enc: coded
+  // SNRs (no result slots)
+  __host__ __device__ IgDyn(int rings, int top, int mmax, int nab, bool enc) {
     int o = rings;
     for (int j = kRing0; j <= top; ++j) o += al4(ring_size(j, mmax) + 4 * cdiv(3 + mmax, 4));
     res_y = o;
-    o += 2 * kResN;
+    o += enc ? 0 : 2 * kResN;
     res_w = o;
-    o += kResN;
+    o += enc ? 0 : kResN;
     bcm = o;
     o += 2 * kBcm;
     tab = o;
@@ -138,7 +144,8 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
   uint16_t* __restrict__ wseg = p.widx + row * p.ld + t0;
   const int64_t nleft = p.nt - t0;
   const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));  // samples that exist
-  const IgDyn L(FX::RINGS, top, MMAX, TABLE ? p.n_widths : 0);
+  constexpr bool ENC = S::ENC;
+  const IgDyn L(FX::RINGS, top, MMAX, TABLE ? p.n_widths : 0, ENC);
   float2* AB = reinterpret_cast<float2*>(smem + L.ab);  // table noise: (a, b) per width index
   float mu, inv;
   row_noise<TABLE>(p, row, AB, mu, inv);
@@ -155,6 +162,16 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     };
   };
   auto lvl_f = [&](int j) { return TABLE ? 1.0f : p.lvl_scale[j]; };
+  // fine level J: white noise scales by bscale[J][m] = 1/sqrt(m 2^J) directly
+  auto scl_fine = [&](auto J, auto Pred) {
+    return [&](auto M) {
+      constexpr int j = decltype(J)::value, m = decltype(M)::value;
+      if constexpr (TABLE)
+        return AB[p.lvl_first[j] + decltype(Pred)::rank(m)];
+      else
+        return p.bscale[j][m];
+    };
+  };
   float* RESY = smem + L.res_y;
   uint16_t* RESW = reinterpret_cast<uint16_t*>(smem + L.res_w);
   int* BCM = reinterpret_cast<int*>(smem + L.bcm);   // [2][kBcm] keys of the best coarse level
@@ -314,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
       __syncwarp();
     }
     if (ar >= T) return;  // halo chunk: nothing to evaluate
-    float* RY = RESY + (k & 1) * kResN;
+    float* RY = RESY + (k & 1) * kResN;  // unused with coded SNRs
     uint16_t* RW = RESW + (k & 1) * kResN;
     int* KB = BCM + (k & 1) * kBcm;
     // result of position q of level j: slot (the position's index among the
@@ -326,15 +343,33 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
       atomicMax(KB + (q << (j - 4)), (fkey(y) & ~15) | (15 - (j - 4)));
     };
     if (qj) {  // four consecutive positions from one float4 window
-      float win[S::NWQ * 4], bv[4], full[4];
-      int bq[4];
+      float win[S::NWQ * 4];
       const int first = p.lvl_first[qj];
-      load_window4<S::NWQ>(smem + RTAB[2 * qj] + ((qn - ((k * kC) >> qj)) & RTAB[2 * qj + 1]), win);
-      eval_window<4, MMAX, SM, true, false>(win, (qj == top) ? p.n_top : SM::MM, scl(AB + first, SM{}),
-                                            nullptr, bv, bq, full);
       const float f = lvl_f(qj);
+      const int nu = (qj == top) ? p.n_top : SM::MM;
+      load_window4<S::NWQ>(smem + RTAB[2 * qj] + ((qn - ((k * kC) >> qj)) & RTAB[2 * qj + 1]), win);
+      if constexpr (ENC) {
+        float out[4];
+        auto scq = [&](auto M) {
+          constexpr int m = decltype(M)::value;
+          if constexpr (TABLE)
+            return AB[first + SM::rank(m)];
+          else
+            return p.rs[m] * f;
+        };
+        eval_window_enc<4, MMAX, SM, S::EB, true>(win, nu, scq, S::EMAX - first, out);
+        // a position without a valid candidate (all -inf, coded as NaNs) yields the
+        // canonical NaN, whose key would beat every SNR: it posts nothing
 #pragma unroll
-      for (int r = 0; r < 4; ++r) put(qj, qq + r, bv[r] * f, first + bq[r]);
+        for (int r = 0; r < 4; ++r)
+          if (out[r] == out[r]) atomicMax(KB + ((qq + r) << (qj - 4)), fkey(out[r]));
+      } else {
+        float bv[4], full[4];
+        int bq[4];
+        eval_window<4, MMAX, SM, true, false>(win, nu, scl(AB + first, SM{}), nullptr, bv, bq, full);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) put(qj, qq + r, bv[r] * f, first + bq[r]);
+      }
     }
     if (sj) {
       float bv;
@@ -342,7 +377,12 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
       const int first = p.lvl_first[sj];
       eval_one_masked<MMAX, SM>(smem + RTAB[2 * sj] + ((sn - ((k * kC) >> sj)) & RTAB[2 * sj + 1]),
                                 (sj == top) ? p.n_top : SM::MM, scl(AB + first, SM{}), bv, bq);
-      put(sj, sq, bv * lvl_f(sj), first + bq);
+      if constexpr (ENC) {
+        const float y = enc_w<S::EB>(bv * lvl_f(sj), S::EMAX - first - bq);
+        if (y == y) atomicMax(KB + (sq << (sj - 4)), fkey(y));
+      }
+      else
+        put(sj, sq, bv * lvl_f(sj), first + bq);
     }
     if (warp == kThreads / 32 - 1 && lane == 4)
       for (int jj = kChunkLog + 1; jj <= top; ++jj)
@@ -351,7 +391,12 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
           int bq;
           eval_one_masked<MMAX, SM>(smem + RTAB[2 * jj] + ((ar >> jj) & RTAB[2 * jj + 1]),
                                     (jj == top) ? p.n_top : SM::MM, scl(AB + p.lvl_first[jj], SM{}), bv, bq);
-          put(jj, 0, bv * lvl_f(jj), p.lvl_first[jj] + bq);
+          if constexpr (ENC) {
+            const float y = enc_w<S::EB>(bv * lvl_f(jj), S::EMAX - p.lvl_first[jj] - bq);
+            if (y == y) atomicMax(KB, fkey(y));
+          }
+          else
+            put(jj, 0, bv * lvl_f(jj), p.lvl_first[jj] + bq);
         }
   };
 
@@ -363,69 +408,127 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     const int buf = k % FX::NBUF;
     float y[8];
     int w[8];
-    {
-      float win[S::NW0 * 4];
-      load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
-      const auto sc0 = scl(AB, S0{});
-      if (!COARSE && top == 0) {
-        float full[8];
-        eval_window<8, MMAX, S0, true, false>(win, p.n_top, sc0, nullptr, y, w, full);
-      } else {
-        eval_window_mx<8, MMAX, S0>(win, sc0, y, w);
+    if constexpr (ENC) {
+      // coded SNRs: every maximum and merge is a max instruction; level j >= 1
+      // starts at width index NC0 + (j-1) MM (compile-time)
+      {
+        float win[S::NW0 * 4];
+        load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
+        const auto sc0 = scl(AB, S0{});
+        if (!COARSE && top == 0)
+          eval_window_enc<8, MMAX, S0, S::EB, true>(win, p.n_top, sc0, S::EMAX, y);
+        else
+          eval_window_enc<8, MMAX, S0, S::EB, false>(win, p.n_top, sc0, S::EMAX, y);
       }
-    }
-    if (COARSE || top >= 1) {
-      float win[S::NW1 * 4], bv[4], full[4];
-      int bq[4];
-      load_window4<S::NW1>(smem + FX::f1(buf) + 4 * t, win);
-      const auto scj = scl(AB + p.lvl_first[1], SM{});
-      if (!COARSE && top == 1)
-        eval_window<4, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
-      else
-        eval_window<4, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
-      const float f = lvl_f(1);
-      const int first = p.lvl_first[1];
+      if (COARSE || top >= 1) {
+        float win[S::NW1 * 4], o[4];
+        load_window4<S::NW1>(smem + FX::f1(buf) + 4 * t, win);
+        const auto scj = scl_fine(std::integral_constant<int, 1>{}, SM{});
+        constexpr int c0 = S::EMAX - S::NC0;
+        if (!COARSE && top == 1)
+          eval_window_enc<4, MMAX, SM, S::EB, true>(win, p.n_top, scj, c0, o);
+        else
+          eval_window_enc<4, MMAX, SM, S::EB, false>(win, p.n_top, scj, c0, o);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) merge1(y[2 * r], w[2 * r], bv[r] * f, first + bq[r]);
-    }
-    if (COARSE || top >= 2) {
-      float win[S::NW2 * 2], bv[2], full[2];
-      int bq[2];
-      load_window2<S::NW2>(smem + FX::f2(buf) + 2 * t, win);
-      const auto scj = scl(AB + p.lvl_first[2], SM{});
-      if (!COARSE && top == 2)
-        eval_window<2, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
-      else
-        eval_window<2, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
-      const float f = lvl_f(2);
-      const int first = p.lvl_first[2];
-      merge1(y[0], w[0], bv[0] * f, first + bq[0]);
-      merge1(y[4], w[4], bv[1] * f, first + bq[1]);
-    }
-    if (COARSE || top >= 3) {
-      float win[S::NW3], bv[1], full[1];
-      int bq[1];
-      load_window1<S::NW3>(smem + FX::f3(buf) + t, win);
-      const auto scj = scl(AB + p.lvl_first[3], SM{});
-      if (!COARSE && top == 3)
-        eval_window<1, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
-      else
-        eval_window<1, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
-      merge1(y[0], w[0], bv[0] * lvl_f(3), p.lvl_first[3] + bq[0]);
-    }
-    if (COARSE) {  // best coarse level at start 8t (even t: 8t = 0 mod 16), without branching
-      int* kp = BCM + (k & 1) * kBcm + (t >> 1);
-      const int key = *kp;
-      *kp = INT_MIN;  // ready for chunk k + 2 (both lanes of a pair write the same value)
-      const int lvl = kRing0 + 15 - (key & 15);
-      const int slot = (lvl <= kChunkLog) ? 256 - (1 << (kChunkLog + 1 - lvl)) + (t >> (lvl - 3))
-                                          : kResHi + lvl - kChunkLog - 1;
-      const bool use = !(t & 1) && key != INT_MIN;
-      const float yv = RESY[(k & 1) * kResN + (use ? slot : 0)];
-      const int wv = RESW[(k & 1) * kResN + (use ? slot : 0)];
-      const bool take = use && yv > y[0];
-      y[0] = take ? yv : y[0];
-      w[0] = take ? wv : w[0];
+        for (int r = 0; r < 4; ++r) y[2 * r] = fmaxf(y[2 * r], o[r]);
+      }
+      if (COARSE || top >= 2) {
+        float win[S::NW2 * 2], o[2];
+        load_window2<S::NW2>(smem + FX::f2(buf) + 2 * t, win);
+        const auto scj = scl_fine(std::integral_constant<int, 2>{}, SM{});
+        constexpr int c0 = S::EMAX - S::NC0 - SM::MM;
+        if (!COARSE && top == 2)
+          eval_window_enc<2, MMAX, SM, S::EB, true>(win, p.n_top, scj, c0, o);
+        else
+          eval_window_enc<2, MMAX, SM, S::EB, false>(win, p.n_top, scj, c0, o);
+        y[0] = fmaxf(y[0], o[0]);
+        y[4] = fmaxf(y[4], o[1]);
+      }
+      if (COARSE || top >= 3) {
+        float win[S::NW3], o[1];
+        load_window1<S::NW3>(smem + FX::f3(buf) + t, win);
+        const auto scj = scl_fine(std::integral_constant<int, 3>{}, SM{});
+        constexpr int c0 = S::EMAX - S::NC0 - 2 * SM::MM;
+        if (!COARSE && top == 3)
+          eval_window_enc<1, MMAX, SM, S::EB, true>(win, p.n_top, scj, c0, o);
+        else
+          eval_window_enc<1, MMAX, SM, S::EB, false>(win, p.n_top, scj, c0, o);
+        y[0] = fmaxf(y[0], o[0]);
+      }
+      if (COARSE) {  // best coarse result at start 8t (even t): one key, NaN when none
+        int* kp = BCM + (k & 1) * kBcm + (t >> 1);
+        const int key = *kp;
+        *kp = INT_MIN;  // ready for chunk k + 2 (both lanes of a pair write the same value)
+        y[0] = fmaxf(y[0], (t & 1) ? ninf() : fkey_inv(key));
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        w[r] = dec_w<S::EB>(y[r]);
+        y[r] = dec_v<S::EB>(y[r]);
+      }
+    } else {
+      {
+        float win[S::NW0 * 4];
+        load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
+        const auto sc0 = scl(AB, S0{});
+        if (!COARSE && top == 0) {
+          float full[8];
+          eval_window<8, MMAX, S0, true, false>(win, p.n_top, sc0, nullptr, y, w, full);
+        } else {
+          eval_window_mx<8, MMAX, S0>(win, sc0, y, w);
+        }
+      }
+      if (COARSE || top >= 1) {
+        float win[S::NW1 * 4], bv[4], full[4];
+        int bq[4];
+        load_window4<S::NW1>(smem + FX::f1(buf) + 4 * t, win);
+        const auto scj = scl_fine(std::integral_constant<int, 1>{}, SM{});
+        if (!COARSE && top == 1)
+          eval_window<4, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+        else
+          eval_window<4, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+        const int first = p.lvl_first[1];
+  #pragma unroll
+        for (int r = 0; r < 4; ++r) merge1(y[2 * r], w[2 * r], bv[r], first + bq[r]);
+      }
+      if (COARSE || top >= 2) {
+        float win[S::NW2 * 2], bv[2], full[2];
+        int bq[2];
+        load_window2<S::NW2>(smem + FX::f2(buf) + 2 * t, win);
+        const auto scj = scl_fine(std::integral_constant<int, 2>{}, SM{});
+        if (!COARSE && top == 2)
+          eval_window<2, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+        else
+          eval_window<2, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+        const int first = p.lvl_first[2];
+        merge1(y[0], w[0], bv[0], first + bq[0]);
+        merge1(y[4], w[4], bv[1], first + bq[1]);
+      }
+      if (COARSE || top >= 3) {
+        float win[S::NW3], bv[1], full[1];
+        int bq[1];
+        load_window1<S::NW3>(smem + FX::f3(buf) + t, win);
+        const auto scj = scl_fine(std::integral_constant<int, 3>{}, SM{});
+        if (!COARSE && top == 3)
+          eval_window<1, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+        else
+          eval_window<1, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+        merge1(y[0], w[0], bv[0], p.lvl_first[3] + bq[0]);
+      }
+      if (COARSE) {  // best coarse level at start 8t (even t: 8t = 0 mod 16), without branching
+        int* kp = BCM + (k & 1) * kBcm + (t >> 1);
+        const int key = *kp;
+        *kp = INT_MIN;  // ready for chunk k + 2 (both lanes of a pair write the same value)
+        const int lvl = kRing0 + 15 - (key & 15);
+        const int slot = (lvl <= kChunkLog) ? 256 - (1 << (kChunkLog + 1 - lvl)) + (t >> (lvl - 3))
+                                            : kResHi + lvl - kChunkLog - 1;
+        const bool use = !(t & 1) && key != INT_MIN;
+        const float yv = RESY[(k & 1) * kResN + (use ? slot : 0)];
+        const int wv = RESW[(k & 1) * kResN + (use ? slot : 0)];
+        const bool take = use && yv > y[0];
+        y[0] = take ? yv : y[0];
+        w[0] = take ? wv : w[0];
+      }
     }
     const int s0 = ar + 8 * t;
     if (s0 + 8 <= nrel) {
@@ -472,7 +575,7 @@ size_t igrid_smem_bytes(const spd_plan& plan, bool table) {
   switch (plan.d * 8 + plan.pl) {
 #define SPD_IG_CASE(D, PL) \
   case D * 8 + PL:         \
-    return sizeof(float) * (size_t)IgDyn(IgFix<D, PL>::RINGS, plan.top, IgS<D, PL>::MMAX, nab).total;
+    return sizeof(float) * (size_t)IgDyn(IgFix<D, PL>::RINGS, plan.top, IgS<D, PL>::MMAX, nab, IgS<D, PL>::ENC).total;
     SPD_IG_CASE(0, 0)
     SPD_IG_CASE(0, 1)
     SPD_IG_CASE(1, 1)

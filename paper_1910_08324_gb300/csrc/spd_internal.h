@@ -66,7 +66,7 @@ struct SearchParams {
   int32_t lvl_first[kMaxLevels];  // width-table index of each level's first width
   float lvl_scale[kMaxLevels];    // IGRID: 2^(-j/2), the unit factor of level j
   float rs[64];                   // rs[m] = 1/sqrt(m) (IGRID block-count factor)
-  float bscale[kMaxLevels][33];   // BoxDIT: 1/sqrt(c_j + m 2^j), m = 1..K
+  float bscale[kMaxLevels][33];   // BoxDIT: 1/sqrt(c_j + m 2^j), m = 1..K; IGRID levels 0..3: 1/sqrt(m 2^j)
   int32_t table;                  // 1: per-row, per-width noise statistics (spd_noise mode 1)
   int32_t n_widths;               // widths of the plan
   int32_t unit_widths;            // 1: width index w is width w + 1 (exhaustive grid)

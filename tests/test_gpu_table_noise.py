@@ -69,4 +69,4 @@ def test_white_table_equals_white_mode(name):
     Yo, Wo, Y2o = oracle.search(x.astype(np.float64), g, mu, sigma)
     assert_parity(Yt, Wt, Yo, Wo, Y2o, nt, ctx="%s white table" % name)
     assert_parity(Yw, Ww, Yo, Wo, Y2o, nt, ctx="%s white" % name)
-    assert np.allclose(Yt, Yw, rtol=2e-6, atol=2e-6)
+    assert np.allclose(Yt, Yw, rtol=1e-5, atol=1e-5)
