@@ -455,20 +455,43 @@ __device__ __forceinline__ void eval_window_mx(const float* w, Scale&& scale, fl
 // Coded evaluation of NP consecutive positions (see enc_w): out[r] is the
 // maximum over the set of enc_w(SNR, code(rank)), with code(rank) = code0 -
 // rank; PARTIAL: ranks at or above n_used (rank 0 always counts) are -inf.
+//
+// With several positions (NP >= 2) the sums are built from pair sums
+// P[i] = w[i] + w[i+1] shared by the positions: the sum of an even number m of
+// blocks extends the one of m - 2 by P[r + m - 2], an odd count adds one block
+// to the even sum below it; odd counts outside the set are never formed.
 template <int NP, int MMAX, class Pred, int B, bool PARTIAL, class Scale>
 __device__ __forceinline__ void eval_window_enc(const float* w, int n_used, Scale&& scale, int code0,
                                                 float (&out)[NP]) {
   constexpr int NC = count_in<Pred, MMAX>();
+  constexpr bool PAIRS = NP >= 2 && MMAX >= 2;
+  constexpr int NPAIR = PAIRS ? NP + MMAX - 2 : 1;
+  float P[NPAIR];
+  if constexpr (PAIRS) static_for<0, NPAIR>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      P[i] = w[i] + w[i + 1];
+    });
   static_for<0, NP>([&](auto R) {
     constexpr int r = decltype(R)::value;
     float v[NC];
-    float S = 0.0f;
+    float S = 0.0f, Se = 0.0f;  // running sum; pairs: the sum of the last even count
     static_for<1, MMAX + 1>([&](auto M) {
       constexpr int m = decltype(M)::value;
-      S += w[r + m - 1];
+      float Sm;
+      if constexpr (!PAIRS) {
+        S += w[r + m - 1];
+        Sm = S;
+      } else if constexpr ((m & 1) == 0) {
+        Se = (m == 2) ? P[r] : Se + P[r + m - 2];
+        Sm = Se;
+      } else if constexpr (Pred::in(m)) {
+        Sm = (m == 1) ? w[r] : Se + w[r + m - 1];
+      } else {
+        Sm = 0.0f;  // not formed
+      }
       if constexpr (Pred::in(m)) {
         constexpr int rk = Pred::rank(m);
-        const float x = enc_w<B>(snr_of(S, scale(M)), code0 - rk);
+        const float x = enc_w<B>(snr_of(Sm, scale(M)), code0 - rk);
         if constexpr (PARTIAL && rk > 0)
           v[rk] = rk < n_used ? x : ninf();
         else

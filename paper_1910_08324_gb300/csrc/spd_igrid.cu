@@ -532,8 +532,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     }
     const int s0 = ar + 8 * t;
     if (s0 + 8 <= nrel) {
-#pragma unroll
-      for (int r = 0; r < 8; ++r) tmax = fmaxf(tmax, y[r]);
+      tmax = fmax3(fmax3(tmax, y[0], y[1]), fmax3(y[2], y[3], y[4]), fmax3(y[5], y[6], y[7]));
     } else {
 #pragma unroll
       for (int r = 0; r < 8; ++r)
