@@ -542,6 +542,20 @@ __device__ __forceinline__ void load_window4(const float* src, float (&w)[NW * 4
   });
 }
 
+// Window of NW float4s from a split layout: float4 k at src + 4 (k / 2), plus
+// ob (the odd array's offset) for odd k.
+template <int NW>
+__device__ __forceinline__ void load_window4_ab(const float* src, int ob, float (&w)[NW * 4]) {
+  static_for<0, NW>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    const float4 t = *reinterpret_cast<const float4*>(src + 4 * (k / 2) + ((k & 1) ? ob : 0));
+    w[4 * k + 0] = t.x;
+    w[4 * k + 1] = t.y;
+    w[4 * k + 2] = t.z;
+    w[4 * k + 3] = t.w;
+  });
+}
+
 template <int NW>
 __device__ __forceinline__ void load_window2(const float* src, float (&w)[NW * 2]) {
   static_for<0, NW>([&](auto K) {

@@ -55,6 +55,10 @@ struct IgS {
   static constexpr int NW2 = cdiv(1 + MMAX, 2);  // float2 window of level 2 (2 positions)
   static constexpr int NW3 = MMAX;               // scalar window of level 3 (1 position)
   static constexpr int TL0 = 4 * NW0 - 8;        // lookahead tails (values past the chunk)
+  // level 0 is stored as two arrays of 4-sample quads, even quads (A) and odd
+  // quads (B), so that a thread's 16-byte accesses are 16 bytes apart (no bank
+  // conflicts); window float4 k of thread t is A[t + k/2] (k even) or B[t + k/2]
+  static constexpr int TLA = 4 * cdiv(NW0, 2) - 4, TLB = 4 * (NW0 / 2) - 4;
   static constexpr int TL1 = 4 * NW1 - 4;
   static constexpr int TL2 = 2 * NW2 - 2;
   static constexpr int TL3 = NW3 - 1;
@@ -73,11 +77,12 @@ struct IgS {
 template <int D, int PL>
 struct IgFix {
   using S = IgS<D, PL>;
-  static constexpr int O1 = al4(kC + S::TL0);
+  static constexpr int OB = al4(kC / 2 + S::TLA);  // B after A
+  static constexpr int O1 = OB + al4(kC / 2 + S::TLB);
   static constexpr int O2 = O1 + al4(kC / 2 + S::TL1);
   static constexpr int O3 = O2 + al4(kC / 4 + S::TL2);
   static constexpr int FB = O3 + al4(kC / 8 + S::TL3);  // one buffer of levels 0..3
-  __host__ __device__ static constexpr int f0(int b) { return b * FB; }
+  __host__ __device__ static constexpr int f0(int b) { return b * FB; }  // A; B at f0 + OB
   __host__ __device__ static constexpr int f1(int b) { return b * FB + O1; }
   __host__ __device__ static constexpr int f2(int b) { return b * FB + O2; }
   __host__ __device__ static constexpr int f3(int b) { return b * FB + O3; }
@@ -266,7 +271,8 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     const int buf = k % FX::NBUF;
     if (k > 0) {
       const int pb = (k - 1) % FX::NBUF;
-      if (t < S::TL0) smem[FX::f0(buf) + kC + t] = smem[FX::f0(pb) + t];
+      if (t < S::TLA) smem[FX::f0(buf) + kC / 2 + t] = smem[FX::f0(pb) + t];
+      if (t < S::TLB) smem[FX::f0(buf) + FX::OB + kC / 2 + t] = smem[FX::f0(pb) + FX::OB + t];
       if (t < S::TL1) smem[FX::f1(buf) + kC / 2 + t] = smem[FX::f1(pb) + t];
       if (t < S::TL2) smem[FX::f2(buf) + kC / 4 + t] = smem[FX::f2(pb) + t];
       if (t < S::TL3) smem[FX::f3(buf) + kC / 8 + t] = smem[FX::f3(pb) + t];
@@ -274,8 +280,8 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     float4 v0, v1;
     cvt8(raw, ar + 8 * t, nrel, dt, mu, inv, v0, v1);
     float* F0 = smem + FX::f0(buf);
-    *reinterpret_cast<float4*>(F0 + 8 * t) = v0;
-    *reinterpret_cast<float4*>(F0 + 8 * t + 4) = v1;
+    *reinterpret_cast<float4*>(F0 + 4 * t) = v0;
+    *reinterpret_cast<float4*>(F0 + FX::OB + 4 * t) = v1;
     const float p0 = v0.x + v0.y, p1 = v0.z + v0.w, p2 = v1.x + v1.y, p3 = v1.z + v1.w;
     const float4 pp = make_float4(p0, p1, p2, p3);
     *reinterpret_cast<float4*>(smem + FX::f1(buf) + 4 * t) = pp;
@@ -413,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
       // starts at width index NC0 + (j-1) MM (compile-time)
       {
         float win[S::NW0 * 4];
-        load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
+        load_window4_ab<S::NW0>(smem + FX::f0(buf) + 4 * t, FX::OB, win);
         const auto sc0 = scl(AB, S0{});
         if (!COARSE && top == 0)
           eval_window_enc<8, MMAX, S0, S::EB, true>(win, p.n_top, sc0, S::EMAX, y);
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     } else {
       {
         float win[S::NW0 * 4];
-        load_window4<S::NW0>(smem + FX::f0(buf) + 8 * t, win);
+        load_window4_ab<S::NW0>(smem + FX::f0(buf) + 4 * t, FX::OB, win);
         const auto sc0 = scl(AB, S0{});
         if (!COARSE && top == 0) {
           float full[8];
