@@ -292,6 +292,71 @@ spd_status spd_noise_stats(const spd_plan *plan, const void *d_x, float outlier_
                            size_t ws_bytes, spd_stream_t stream);
 
 /*
+ * Segment length of a BoxDIT or IGRID plan: one CTA searches `segment` starts of
+ * a row (plus the widest boxcar after them, read again by the next segment).
+ * Longer segments re-read less, shorter ones give more CTAs.  segment must be a
+ * multiple of 16384 and of 2^top (top: the plan's last level), at most 2^24;
+ * the default is 131072.  Host only.  SPD_ERR_INVALID_ARG otherwise (and for
+ * exhaustive plans).
+ */
+spd_status spd_plan_set_segment(spd_plan *plan, int32_t segment);
+
+/*
+ * Batched search of several DM ranges in one launch: ranges of different row
+ * counts and lengths (e.g. the ranges of a dedispersion plan at their own time
+ * decimations) searched with one grid (one BoxDIT or IGRID plan description;
+ * widths, s_end and dtype are shared, in each range's own samples).  One
+ * persistent kernel strides over the work list of (range, row, segment) units;
+ * every launch of the library on the stream is capture-safe (CUDA graphs), but
+ * the first spd_batch_execute on a device queries the device and should run
+ * before a capture begins.
+ *
+ * Each range may name a device flag (d_ready): the units of that range wait
+ * for it to become nonzero (an upstream producer writes it) before reading the
+ * range.  A wait is bounded (spd_batch_set_wait_ns, default 1 s); when it runs
+ * out the range is skipped (its outputs are left unwritten) and
+ * spd_batch_status reports SPD_ERR_TIMEOUT.  Nothing else waits.
+ *
+ * Exhaustive grids and table noise are not batched (SPD_ERR_UNSUPPORTED).
+ */
+typedef struct spd_batch spd_batch;
+
+typedef struct spd_range_io {
+  const void *d_x;          /* [ndm][ld] samples of the grid's dtype */
+  float *d_snr;             /* [ndm][ld] output, as spd_execute */
+  uint16_t *d_width_idx;    /* [ndm][ld] output */
+  const float *d_mu;        /* [ndm] white-noise mean of each row */
+  const float *d_sigma;     /* [ndm] white-noise deviation of each row */
+  const int32_t *d_ready;   /* NULL, or a device int32 flag to wait for */
+} spd_range_io;
+
+/* Creates a batch of n_ranges (1..8) ranges: row counts ndm[r], lengths nt[r],
+ * row strides ld[r] (ld may be NULL: ld = nt).  grid->ndm, nt, ld are ignored.
+ * Host only.  Errors as spd_plan_create. */
+spd_status spd_batch_create(const spd_plan_desc *grid, const int64_t *ndm, const int64_t *nt,
+                            const int64_t *ld, int32_t n_ranges, spd_batch **out);
+spd_status spd_batch_destroy(spd_batch *batch);
+/* Segment length of every range (rules of spd_plan_set_segment). */
+spd_status spd_batch_set_segment(spd_batch *batch, int32_t segment);
+/* Limit of one ready-flag wait, in nanoseconds (0..60 s). */
+spd_status spd_batch_set_wait_ns(spd_batch *batch, int64_t wait_ns);
+/* Device workspace of spd_batch_execute / spd_batch_candidates (256-byte aligned base). */
+spd_status spd_batch_workspace_size(const spd_batch *batch, size_t *bytes);
+/* Searches every range (io: host array of the batch's n_ranges entries), with
+ * the results of spd_execute for each.  Asynchronous on stream. */
+spd_status spd_batch_execute(const spd_batch *batch, const spd_range_io *io, void *d_ws,
+                             size_t ws_bytes, spd_stream_t stream);
+/* Waits for the stream; SPD_ERR_TIMEOUT if a ready-flag wait of the last
+ * spd_batch_execute on this workspace ran out, SPD_ERR_CUDA on a CUDA error. */
+spd_status spd_batch_status(const spd_batch *batch, const void *d_ws, spd_stream_t stream);
+/* spd_candidates for range `range` of the last spd_batch_execute on d_ws
+ * (use_tile_max: its tile maxima, as spd_candidates). */
+spd_status spd_batch_candidates(const spd_batch *batch, int32_t range, const float *d_snr,
+                                const uint16_t *d_width_idx, float threshold, int32_t peak_radius,
+                                spd_candidate *d_out, int64_t cap, int64_t *d_count, void *d_ws,
+                                size_t ws_bytes, int32_t use_tile_max, spd_stream_t stream);
+
+/*
  * Wait for the stream and report any asynchronous CUDA error of work queued
  * on it (SPD_ERR_CUDA), else SPD_OK.
  */

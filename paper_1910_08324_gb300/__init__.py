@@ -9,9 +9,12 @@ or loaded, importing the binding functions raises.
 Entry points (same names as the C ABI): ``spd_plan_create``,
 ``spd_plan_destroy``, ``spd_plan_widths``, ``spd_workspace_size``,
 ``spd_execute``, ``spd_candidates``, ``spd_candidates_static``, ``spd_search``,
-``spd_noise_stats``, ``spd_sync_status``, ``spd_status_string``,
-``spd_version``.  Convenience wrappers taking torch tensors: ``execute``,
-``candidates``, ``search``, ``noise_stats``.
+``spd_noise_stats``, ``spd_plan_set_segment``, the batch calls
+(``spd_batch_create``, ``spd_batch_execute``, ``spd_batch_status``,
+``spd_batch_candidates``; ``Batch`` for the rest), ``spd_sync_status``,
+``spd_status_string``, ``spd_version``.  Convenience wrappers taking torch
+tensors: ``execute``, ``candidates``, ``search``, ``noise_stats``,
+``batch_execute``.
 """
 from ._binding import (  # noqa: F401
     CANDIDATE_DTYPE,
@@ -22,8 +25,10 @@ from ._binding import (  # noqa: F401
     SPD_F16,
     SPD_F32,
     SPD_U8,
+    Batch,
     Plan,
     SpdError,
+    batch_execute,
     candidates,
     execute,
     library_path,
@@ -31,11 +36,16 @@ from ._binding import (  # noqa: F401
     noise_stats,
     records,
     search,
+    spd_batch_candidates,
+    spd_batch_create,
+    spd_batch_execute,
+    spd_batch_status,
     spd_candidates,
     spd_candidates_static,
     spd_execute,
     spd_noise_stats,
     spd_plan_create,
+    spd_plan_set_segment,
     spd_plan_destroy,
     spd_plan_widths,
     spd_search,

@@ -46,11 +46,19 @@ class _Noise(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("mu", ctypes.c_void_p), ("sigma", ctypes.c_void_p)]
 
 
+class _RangeIO(ctypes.Structure):
+    _fields_ = [("d_x", ctypes.c_void_p), ("d_snr", ctypes.c_void_p), ("d_width_idx", ctypes.c_void_p),
+                ("d_mu", ctypes.c_void_p), ("d_sigma", ctypes.c_void_p), ("d_ready", ctypes.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_destroy",
             "spd_plan_widths", "spd_workspace_size", "spd_execute", "spd_candidates",
-            "spd_search", "spd_sync_status", "spd_candidates_static"]
+            "spd_search", "spd_sync_status", "spd_candidates_static", "spd_noise_stats",
+            "spd_plan_set_segment", "spd_batch_create", "spd_batch_destroy", "spd_batch_set_segment",
+            "spd_batch_set_wait_ns", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
+            "spd_batch_candidates"]
 
 
 def library_path() -> str:
@@ -81,6 +89,16 @@ def load_library():
         lib.spd_sync_status.argtypes = [vp, vp]
         lib.spd_candidates_static.argtypes = [vp, vp, vp, ctypes.c_float, i32, vp, i64, vp, vp]
         lib.spd_noise_stats.argtypes = [vp, vp, ctypes.c_float, i32, vp, vp, vp, sz, vp]
+        lib.spd_plan_set_segment.argtypes = [vp, i32]
+        lib.spd_batch_create.argtypes = [ctypes.POINTER(_Desc), vp, vp, vp, i32, ctypes.POINTER(vp)]
+        lib.spd_batch_destroy.argtypes = [vp]
+        lib.spd_batch_set_segment.argtypes = [vp, i32]
+        lib.spd_batch_set_wait_ns.argtypes = [vp, i64]
+        lib.spd_batch_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+        lib.spd_batch_execute.argtypes = [vp, ctypes.POINTER(_RangeIO), vp, sz, vp]
+        lib.spd_batch_status.argtypes = [vp, vp, vp]
+        lib.spd_batch_candidates.argtypes = [vp, i32, vp, vp, ctypes.c_float, i32, vp, i64, vp, vp, sz,
+                                             i32, vp]
         for name in _SYMBOLS[2:]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -202,6 +220,89 @@ def spd_noise_stats(plan: Plan, x: int, outlier_sigma: float, max_passes: int, m
            "spd_noise_stats")
 
 
+def spd_plan_set_segment(plan: Plan, segment: int):
+    _check(load_library().spd_plan_set_segment(ctypes.c_void_p(plan.handle), int(segment)),
+           "spd_plan_set_segment")
+
+
+class Batch:
+    """Owns an ``spd_batch*`` (ranges of one grid searched in one launch)."""
+
+    def __init__(self, handle: int, ndm, nt, ld):
+        self.handle = handle
+        self.ndm, self.nt, self.ld = list(ndm), list(nt), list(ld)
+
+    def close(self):
+        if self.handle:
+            load_library().spd_batch_destroy(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_size(self) -> int:
+        b = ctypes.c_size_t()
+        _check(load_library().spd_batch_workspace_size(ctypes.c_void_p(self.handle), ctypes.byref(b)),
+               "spd_batch_workspace_size")
+        return int(b.value)
+
+    def set_segment(self, segment: int):
+        _check(load_library().spd_batch_set_segment(ctypes.c_void_p(self.handle), int(segment)),
+               "spd_batch_set_segment")
+
+    def set_wait_ns(self, ns: int):
+        _check(load_library().spd_batch_set_wait_ns(ctypes.c_void_p(self.handle), int(ns)),
+               "spd_batch_set_wait_ns")
+
+
+def spd_batch_create(algo: int, s_end: int, ndm, nt, ld=None, boxdit_lmax: int = 0,
+                     igrid_depth: int = 0, igrid_layers: int = 0, dtype: int = SPD_F32) -> Batch:
+    import numpy as np
+    lib = load_library()
+    d = _Desc(int(algo), int(dtype), int(s_end), int(boxdit_lmax), int(igrid_depth), int(igrid_layers), 1, 1, 1)
+    n = len(ndm)
+    a_ndm = np.ascontiguousarray(ndm, np.int64)
+    a_nt = np.ascontiguousarray(nt, np.int64)
+    a_ld = np.ascontiguousarray(nt if ld is None else ld, np.int64)
+    h = ctypes.c_void_p()
+    _check(lib.spd_batch_create(ctypes.byref(d), a_ndm.ctypes.data, a_nt.ctypes.data, a_ld.ctypes.data,
+                                n, ctypes.byref(h)), "spd_batch_create")
+    return Batch(h.value, a_ndm, a_nt, a_ld)
+
+
+def _range_ios(xs, ys, ws_idx, mus, sigmas, readys):
+    n = len(xs)
+    arr = (_RangeIO * n)()
+    for r in range(n):
+        arr[r] = _RangeIO(xs[r], ys[r], ws_idx[r], mus[r], sigmas[r], (readys[r] if readys else 0) or None)
+    return arr
+
+
+def spd_batch_execute(batch: Batch, xs, ys, ws_idx, mus, sigmas, ws: int, ws_bytes: int, stream: int = 0,
+                      readys=None):
+    """xs, ys, ws_idx, mus, sigmas, readys: per-range device addresses (ints)."""
+    arr = _range_ios(xs, ys, ws_idx, mus, sigmas, readys)
+    _check(load_library().spd_batch_execute(ctypes.c_void_p(batch.handle), arr, ws, ws_bytes,
+                                            stream or None), "spd_batch_execute")
+
+
+def spd_batch_status(batch: Batch, ws: int, stream: int = 0):
+    _check(load_library().spd_batch_status(ctypes.c_void_p(batch.handle), ws, stream or None),
+           "spd_batch_status")
+
+
+def spd_batch_candidates(batch: Batch, rng: int, snr: int, width_idx: int, threshold: float,
+                         peak_radius: int, out: int, cap: int, count: int, ws: int, ws_bytes: int,
+                         use_tile_max: int = 1, stream: int = 0):
+    _check(load_library().spd_batch_candidates(ctypes.c_void_p(batch.handle), int(rng), snr, width_idx,
+                                               float(threshold), int(peak_radius), out or None,
+                                               int(cap), count, ws, ws_bytes, int(use_tile_max),
+                                               stream or None), "spd_batch_candidates")
+
+
 def spd_sync_status(plan: Plan, stream: int = 0):
     _check(load_library().spd_sync_status(ctypes.c_void_p(plan.handle), stream or None),
            "spd_sync_status")
@@ -250,6 +351,14 @@ def noise_stats(plan: Plan, x, mu_out, sigma_out, ws, outlier_sigma: float = 2.0
     table of ``execute(..., noise_mode=1)``)."""
     spd_noise_stats(plan, _ptr(x), outlier_sigma, max_passes, _ptr(mu_out), _ptr(sigma_out),
                     _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+
+
+def batch_execute(batch: Batch, xs, ys, widxs, mus, sigmas, ws, readys=None, stream=None):
+    """Run ``spd_batch_execute`` on per-range torch CUDA tensors."""
+    spd_batch_execute(batch, [_ptr(x) for x in xs], [_ptr(y) for y in ys], [_ptr(w) for w in widxs],
+                      [_ptr(m) for m in mus], [_ptr(s) for s in sigmas], _ptr(ws),
+                      ws.numel() * ws.element_size(), _stream(stream),
+                      readys=None if readys is None else [_ptr(r) for r in readys])
 
 
 def records(out_tensor, count: int):

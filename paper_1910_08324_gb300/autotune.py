@@ -1,0 +1,76 @@
+"""Segment-length autotuner for the streaming searches (plans and batches).
+
+A CTA of the BoxDIT/IGRID kernels searches one segment of a row; the segment
+length trades the re-read of the widest boxcar after each segment (shorter
+segments re-read more) against the number of CTAs (longer segments give fewer,
+and a ragged last wave).  ``tune_segment`` times each candidate length with a
+caller-supplied timing function, keeps the fastest, and caches the choice in a
+JSON file keyed by the search's description (grid, dtype, range shapes), so a
+later run with the same key reuses it without timing.
+"""
+from __future__ import annotations
+
+import json
+import os
+import tempfile
+
+DEFAULT_CANDIDATES = (16384, 32768, 65536, 131072, 262144)
+
+
+def key_of(algo: int, s_end: int, dtype: int, shapes, boxdit_lmax: int = 0, igrid_depth: int = 0,
+           igrid_layers: int = 0) -> str:
+    """Cache key: the grid, the input type and every range's (ndm, nt)."""
+    sh = ",".join("%dx%d" % (int(a), int(b)) for a, b in shapes)
+    return "a%d:s%d:k%d:d%d:p%d:t%d:%s" % (algo, s_end, boxdit_lmax, igrid_depth, igrid_layers, dtype, sh)
+
+
+def load_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(path: str, cache: dict):
+    """Atomic write (a temporary file renamed over the cache)."""
+    d = os.path.dirname(os.path.abspath(path))
+    os.makedirs(d, exist_ok=True)
+    fd, tmp = tempfile.mkstemp(dir=d, prefix=".tune", suffix=".json")
+    with os.fdopen(fd, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tune_segment(key: str, set_segment, time_ms, candidates=DEFAULT_CANDIDATES, cache_path=None,
+                 reps: int = 3, force: bool = False):
+    """Returns ``(segment, timings)``.
+
+    set_segment(seg) applies a candidate (it may raise for lengths the grid does
+    not allow: those are skipped); time_ms() runs the search and returns its
+    time in ms.  The minimum over ``reps`` runs is kept per candidate.  With a
+    cache path, a cached choice for ``key`` is returned without timing (and the
+    chosen length is applied) unless ``force``.
+    """
+    cache = load_cache(cache_path) if cache_path else {}
+    if not force and key in cache:
+        seg = int(cache[key]["segment"])
+        set_segment(seg)
+        return seg, cache[key].get("timings", {})
+    timings = {}
+    for seg in candidates:
+        try:
+            set_segment(int(seg))
+        except Exception:
+            continue
+        timings[str(int(seg))] = min(float(time_ms()) for _ in range(max(1, reps)))
+    if not timings:
+        raise RuntimeError("no segment length could be applied")
+    best = min(timings, key=lambda s: timings[s])
+    set_segment(int(best))
+    if cache_path:
+        cache = load_cache(cache_path)
+        cache[key] = {"segment": int(best), "timings": timings}
+        save_cache(cache_path, cache)
+    return int(best), timings

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <new>
 
 #include "spd_internal.h"
@@ -91,6 +92,20 @@ spd_status build_igrid(spd_plan* p) {
 
 spd_status check_cuda(cudaError_t e) { return e == cudaSuccess ? SPD_OK : SPD_ERR_CUDA; }
 
+// Streaming kernels: a CTA searches a segment of `segment` starts of a row (a
+// multiple of the candidate tile), or the whole row rounded up to candidate
+// tiles when that is shorter.
+constexpr int kDefaultSegment = 131072;
+int segment_tile(int64_t nt, int segment) {
+  int64_t T = ((nt + spd::kCandTile - 1) / spd::kCandTile) * spd::kCandTile;
+  if (T > segment) T = segment;
+  return (int)T;
+}
+bool segment_ok(const spd_plan& p, int64_t segment) {
+  const int64_t align = (int64_t)1 << (p.top > 14 ? p.top : 14);  // levels above 11 need aligned segments
+  return segment >= spd::kCandTile && segment <= ((int64_t)1 << 24) && segment % align == 0;
+}
+
 int dtype_size(int dtype) {
   switch (dtype) {
     case SPD_F32: return 4;
@@ -124,6 +139,33 @@ spd_status validate_ws(const spd_plan* plan, void* d_ws, size_t ws_bytes) {
   return SPD_OK;
 }
 
+// Grid constants of the search kernels (levels, widths, scale tables).
+void fill_grid(spd::SearchParams& p, const spd_plan& plan) {
+  p.dtype = plan.desc.dtype;
+  p.esize = dtype_size(plan.desc.dtype);
+  p.halo = plan.halo;
+  p.top = plan.top;
+  p.n_top = plan.n_top;
+  p.lmax = plan.lend;
+  for (size_t j = 0; j < plan.lvl_first.size() && j < (size_t)spd::kMaxLevels; ++j) {
+    p.lvl_first[j] = plan.lvl_first[j];
+    p.lvl_scale[j] = (float)std::pow(2.0, -0.5 * (double)j);
+  }
+  for (int m = 1; m < 64; ++m) p.rs[m] = (float)(1.0 / std::sqrt((double)m));
+  p.n_widths = (int32_t)plan.widths.size();
+  p.unit_widths = plan.family == kExhaustive ? 1 : 0;
+  if (!p.unit_widths)
+    for (size_t i = 0; i < plan.widths.size() && i < (size_t)spd::kMaxGridWidths; ++i) p.wtab[i] = plan.widths[i];
+  if (plan.family == kBoxdit) {
+    for (int j = 0; j <= plan.top; ++j)
+      for (int m = 1; m <= plan.k; ++m)
+        p.bscale[j][m] = (float)(1.0 / std::sqrt((double)plan.lvl_base[j] + (double)m * (double)(1 << j)));
+  } else if (plan.family == kIgrid) {  // fine levels 0..3: 1/sqrt(m 2^j) in one constant
+    for (int j = 0; j <= 3 && j <= plan.top; ++j)
+      for (int m = 1; m <= 32; ++m) p.bscale[j][m] = (float)(1.0 / std::sqrt((double)m * (double)(1 << j)));
+  }
+}
+
 spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* noise, float* d_snr,
                       uint16_t* d_width_idx, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
   if (!plan || !d_x || !noise || !d_snr || !d_width_idx) return SPD_ERR_INVALID_ARG;
@@ -140,8 +182,6 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   if (!sp) return SPD_ERR_HOST_ALLOC;
   spd::SearchParams& p = *sp;
   p.x = d_x;
-  p.dtype = plan->desc.dtype;
-  p.esize = esize;
   p.vec_x = ((uintptr_t)d_x % 16 == 0 && (plan->desc.ld * esize) % 16 == 0) ? 1 : 0;
   p.snr = d_snr;
   p.widx = d_width_idx;
@@ -154,33 +194,11 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   p.tile = plan->tile;
   p.tiles_per_row = (int32_t)plan->tiles_per_row;
   p.cand_tiles_per_row = (int32_t)plan->cand_tiles_per_row;
-  p.halo = plan->halo;
-  p.top = plan->top;
-  p.n_top = plan->n_top;
   p.vec = ((uintptr_t)d_snr % 16 == 0 && (uintptr_t)d_width_idx % 8 == 0 && plan->desc.ld % 4 == 0)
               ? 1
               : 0;
-  p.lmax = plan->lend;
-  for (size_t j = 0; j < plan->lvl_first.size() && j < (size_t)spd::kMaxLevels; ++j) {
-    p.lvl_first[j] = plan->lvl_first[j];
-    p.lvl_scale[j] = (float)std::pow(2.0, -0.5 * (double)j);
-  }
-  for (int m = 1; m < 64; ++m) p.rs[m] = (float)(1.0 / std::sqrt((double)m));
+  fill_grid(p, *plan);
   p.table = noise->mode == 1 ? 1 : 0;
-  p.n_widths = (int32_t)plan->widths.size();
-  p.unit_widths = plan->family == kExhaustive ? 1 : 0;
-  if (!p.unit_widths)
-    for (size_t i = 0; i < plan->widths.size() && i < (size_t)spd::kMaxGridWidths; ++i)
-      p.wtab[i] = plan->widths[i];
-  if (plan->family == kBoxdit) {
-    for (int j = 0; j <= plan->top; ++j)
-      for (int m = 1; m <= plan->k; ++m)
-        p.bscale[j][m] =
-            (float)(1.0 / std::sqrt((double)plan->lvl_base[j] + (double)m * (double)(1 << j)));
-  } else if (plan->family == kIgrid) {  // fine levels 0..3: 1/sqrt(m 2^j) in one constant
-    for (int j = 0; j <= 3 && j <= plan->top; ++j)
-      for (int m = 1; m <= 32; ++m) p.bscale[j][m] = (float)(1.0 / std::sqrt((double)m * (double)(1 << j)));
-  }
   // tile maxima start at a key below every float (0x80808080)
   cudaError_t e = cudaMemsetAsync(p.tile_max, 0x80,
                                   sizeof(float) * (size_t)(plan->desc.ndm * plan->cand_tiles_per_row),
@@ -246,6 +264,88 @@ spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_
 }
 
 }  // namespace
+
+// A batch: ranges of one grid (spd_batch_create).
+struct spd_batch {
+  spd_plan grid;  // the shared grid (desc.ndm 1, desc.nt the longest range)
+  int32_t n;
+  int64_t ndm[spd::kMaxRanges], nt[spd::kMaxRanges], ld[spd::kMaxRanges];
+  int32_t segment;
+  int64_t wait_ns;
+};
+
+namespace {
+
+struct BatchLayout {  // workspace of a batch
+  size_t status, tile_max[spd::kMaxRanges], counts, gsum, goff, total;
+  explicit BatchLayout(const spd_batch& b) {
+    size_t o = 0;
+    status = o;
+    o = align_up(o + sizeof(int32_t));
+    size_t maxt = 0;
+    for (int r = 0; r < b.n; ++r) {
+      const size_t nt = (size_t)(b.ndm[r] * ((b.nt[r] + spd::kCandTile - 1) / spd::kCandTile));
+      tile_max[r] = o;
+      o = align_up(o + nt * sizeof(float));
+      maxt = nt > maxt ? nt : maxt;
+    }
+    const size_t ng = (maxt + spd::kCandGroup - 1) / spd::kCandGroup;
+    counts = o;
+    gsum = align_up(counts + maxt * sizeof(int32_t));
+    goff = align_up(gsum + ng * sizeof(int32_t));
+    total = align_up(goff + ng * sizeof(int64_t));
+  }
+};
+
+// The single-series view of range r (for the candidate step).
+spd_plan range_plan(const spd_batch& b, int r) {
+  spd_plan p = b.grid;
+  p.desc.ndm = b.ndm[r];
+  p.desc.nt = b.nt[r];
+  p.desc.ld = b.ld[r];
+  p.tile = segment_tile(b.nt[r], b.segment);
+  p.tiles_per_row = (b.nt[r] + p.tile - 1) / p.tile;
+  p.cand_tiles_per_row = (b.nt[r] + spd::kCandTile - 1) / spd::kCandTile;
+  return p;
+}
+
+}  // namespace
+
+namespace spd {
+cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int* sms) {
+  struct Entry {
+    const void* k;
+    int dev;
+    size_t smem;
+    int per_sm, sms;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& c : cache)
+      if (c.k == kernel && c.dev == dev && c.smem == smem) {
+        *per_sm = c.per_sm;
+        *sms = c.sms;
+        return cudaSuccess;
+      }
+  }
+  Entry c{kernel, dev, smem, 0, 0};
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, kernel, spd::kThreads, smem)) != cudaSuccess)
+    return e;
+  std::lock_guard<std::mutex> lock(mu);
+  cache.push_back(c);
+  *per_sm = c.per_sm;
+  *sms = c.sms;
+  return cudaSuccess;
+}
+}  // namespace spd
 
 extern "C" {
 
@@ -343,9 +443,7 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
       delete p;
       return SPD_ERR_UNSUPPORTED;
     }
-    int64_t T = ((d.nt + spd::kCandTile - 1) / spd::kCandTile) * spd::kCandTile;
-    if (T > 131072) T = 131072;
-    p->tile = (int)T;
+    p->tile = segment_tile(d.nt, kDefaultSegment);
     p->halo = ((p->lend + spd::kChunk - 1) / spd::kChunk) * spd::kChunk;
   }
   p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
@@ -463,6 +561,172 @@ spd_status spd_noise_stats(const spd_plan* plan, const void* d_x, float outlier_
       p.wtab[i] = plan->widths[i];
   const cudaError_t e = spd::launch_msd(*plan, p, max_passes, reinterpret_cast<cudaStream_t>(stream));
   delete mp;
+  return check_cuda(e);
+}
+
+spd_status spd_plan_set_segment(spd_plan* plan, int32_t segment) {
+  if (!plan || plan->family == kExhaustive || !segment_ok(*plan, segment)) return SPD_ERR_INVALID_ARG;
+  plan->tile = segment_tile(plan->desc.nt, segment);
+  plan->tiles_per_row = (plan->desc.nt + plan->tile - 1) / plan->tile;
+  return SPD_OK;
+}
+
+spd_status spd_batch_create(const spd_plan_desc* grid, const int64_t* ndm, const int64_t* nt,
+                            const int64_t* ld, int32_t n_ranges, spd_batch** out) {
+  if (!out) return SPD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!grid || !ndm || !nt || n_ranges < 1 || n_ranges > spd::kMaxRanges) return SPD_ERR_INVALID_ARG;
+  if (grid->algo == SPD_ALGO_EXHAUSTIVE) return SPD_ERR_UNSUPPORTED;
+  int64_t ntmax = 0, units = 0;
+  for (int r = 0; r < n_ranges; ++r) {
+    const int64_t l = ld ? ld[r] : nt[r];
+    if (ndm[r] < 1 || nt[r] < 1 || l < nt[r] || ndm[r] > ((int64_t)1 << 24) || nt[r] > ((int64_t)1 << 40))
+      return SPD_ERR_INVALID_ARG;
+    ntmax = nt[r] > ntmax ? nt[r] : ntmax;
+  }
+  spd_plan_desc d = *grid;
+  d.ndm = 1;
+  d.nt = ntmax;
+  d.ld = ntmax;
+  spd_plan* g = nullptr;
+  spd_status st = spd_plan_create(&d, &g);
+  if (st != SPD_OK) return st;
+  spd_batch* b = new (std::nothrow) spd_batch();
+  if (!b) {
+    spd_plan_destroy(g);
+    return SPD_ERR_HOST_ALLOC;
+  }
+  b->grid = *g;
+  spd_plan_destroy(g);
+  b->n = n_ranges;
+  b->segment = kDefaultSegment;
+  b->wait_ns = 1000000000LL;
+  for (int r = 0; r < n_ranges; ++r) {
+    b->ndm[r] = ndm[r];
+    b->nt[r] = nt[r];
+    b->ld[r] = ld ? ld[r] : nt[r];
+    units += ndm[r] * ((nt[r] + segment_tile(nt[r], b->segment) - 1) / segment_tile(nt[r], b->segment));
+  }
+  if (units > ((int64_t)1 << 40)) {
+    delete b;
+    return SPD_ERR_INVALID_ARG;
+  }
+  *out = b;
+  return SPD_OK;
+}
+
+spd_status spd_batch_destroy(spd_batch* batch) {
+  delete batch;
+  return SPD_OK;
+}
+
+spd_status spd_batch_set_segment(spd_batch* batch, int32_t segment) {
+  if (!batch || !segment_ok(batch->grid, segment)) return SPD_ERR_INVALID_ARG;
+  batch->segment = segment;
+  return SPD_OK;
+}
+
+spd_status spd_batch_set_wait_ns(spd_batch* batch, int64_t wait_ns) {
+  if (!batch || wait_ns < 0 || wait_ns > 60000000000LL) return SPD_ERR_INVALID_ARG;
+  batch->wait_ns = wait_ns;
+  return SPD_OK;
+}
+
+spd_status spd_batch_workspace_size(const spd_batch* batch, size_t* bytes) {
+  if (!batch || !bytes) return SPD_ERR_INVALID_ARG;
+  *bytes = BatchLayout(*batch).total;
+  return SPD_OK;
+}
+
+spd_status spd_batch_execute(const spd_batch* batch, const spd_range_io* io, void* d_ws, size_t ws_bytes,
+                             spd_stream_t stream) {
+  if (!batch || !io) return SPD_ERR_INVALID_ARG;
+  const BatchLayout bl(*batch);
+  if (ws_bytes < bl.total) return SPD_ERR_WORKSPACE_TOO_SMALL;
+  if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0) return SPD_ERR_INVALID_ARG;
+  const spd_plan& g = batch->grid;
+  const int esize = dtype_size(g.desc.dtype);
+  for (int r = 0; r < batch->n; ++r) {
+    const spd_range_io& a = io[r];
+    if (!a.d_x || !a.d_snr || !a.d_width_idx || !a.d_mu || !a.d_sigma) return SPD_ERR_INVALID_ARG;
+    if (((uintptr_t)a.d_x % esize) || ((uintptr_t)a.d_snr % 4) || ((uintptr_t)a.d_width_idx % 2) ||
+        ((uintptr_t)a.d_mu % 4) || ((uintptr_t)a.d_sigma % 4) || ((uintptr_t)a.d_ready % 4))
+      return SPD_ERR_INVALID_ARG;
+  }
+  spd::SearchParams* sp = new (std::nothrow) spd::SearchParams();
+  if (!sp) return SPD_ERR_HOST_ALLOC;
+  spd::SearchParams& p = *sp;
+  fill_grid(p, g);
+  p.table = 0;
+  p.n_ranges = batch->n;
+  p.wait_ns = batch->wait_ns;
+  char* ws = static_cast<char*>(d_ws);
+  p.status = reinterpret_cast<int32_t*>(ws + bl.status);
+  int64_t units = 0;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(p.status, 0, sizeof(int32_t), s);
+  for (int r = 0; r < batch->n && e == cudaSuccess; ++r) {
+    const spd_range_io& a = io[r];
+    spd::BatchRange& R = p.ranges[r];
+    R.x = a.d_x;
+    R.snr = a.d_snr;
+    R.widx = a.d_width_idx;
+    R.mu = a.d_mu;
+    R.sigma = a.d_sigma;
+    R.ready = a.d_ready;
+    R.ndm = batch->ndm[r];
+    R.nt = batch->nt[r];
+    R.ld = batch->ld[r];
+    R.tile = segment_tile(R.nt, batch->segment);
+    R.tiles_per_row = (int32_t)((R.nt + R.tile - 1) / R.tile);
+    R.cand_tiles_per_row = (int32_t)((R.nt + spd::kCandTile - 1) / spd::kCandTile);
+    R.tile_max = reinterpret_cast<float*>(ws + bl.tile_max[r]);
+    R.vec = ((uintptr_t)a.d_snr % 16 == 0 && (uintptr_t)a.d_width_idx % 8 == 0 && R.ld % 4 == 0) ? 1 : 0;
+    R.vec_x = ((uintptr_t)a.d_x % 16 == 0 && (R.ld * esize) % 16 == 0) ? 1 : 0;
+    R.unit_first = units;
+    units += R.ndm * R.tiles_per_row;
+    e = cudaMemsetAsync(R.tile_max, 0x80, sizeof(float) * (size_t)(R.ndm * R.cand_tiles_per_row), s);
+  }
+  p.n_units = units;
+  if (e == cudaSuccess)
+    e = g.family == kIgrid ? spd::launch_igrid_batch(g, p, s) : spd::launch_boxdit_batch(g, p, s);
+  delete sp;
+  return check_cuda(e);
+}
+
+spd_status spd_batch_status(const spd_batch* batch, const void* d_ws, spd_stream_t stream) {
+  if (!batch || !d_ws) return SPD_ERR_INVALID_ARG;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, static_cast<const char*>(d_ws) + BatchLayout(*batch).status,
+                                  sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return SPD_ERR_CUDA;
+  return h ? SPD_ERR_TIMEOUT : SPD_OK;
+}
+
+spd_status spd_batch_candidates(const spd_batch* batch, int32_t range, const float* d_snr,
+                                const uint16_t* d_width_idx, float threshold, int32_t peak_radius,
+                                spd_candidate* d_out, int64_t cap, int64_t* d_count, void* d_ws,
+                                size_t ws_bytes, int32_t use_tile_max, spd_stream_t stream) {
+  if (!batch || range < 0 || range >= batch->n) return SPD_ERR_INVALID_ARG;
+  const spd_plan rp = range_plan(*batch, range);
+  spd_status st = check_cand_args(&rp, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count);
+  if (st != SPD_OK) return st;
+  const BatchLayout bl(*batch);
+  if (ws_bytes < bl.total) return SPD_ERR_WORKSPACE_TOO_SMALL;
+  if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0) return SPD_ERR_INVALID_ARG;
+  spd::CandParams* cp = new (std::nothrow) spd::CandParams();
+  if (!cp) return SPD_ERR_HOST_ALLOC;
+  fill_cand_params(*cp, &rp, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count);
+  char* ws = static_cast<char*>(d_ws);
+  cp->tile_max = use_tile_max ? reinterpret_cast<const float*>(ws + bl.tile_max[range]) : nullptr;
+  cp->counts = reinterpret_cast<int32_t*>(ws + bl.counts);
+  cp->gsum = reinterpret_cast<int32_t*>(ws + bl.gsum);
+  cp->goff = reinterpret_cast<int64_t*>(ws + bl.goff);
+  const cudaError_t e = spd::launch_candidates(rp, *cp, reinterpret_cast<cudaStream_t>(stream));
+  delete cp;
   return check_cuda(e);
 }
 

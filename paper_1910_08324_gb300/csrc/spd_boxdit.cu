@@ -136,29 +136,26 @@ __device__ __forceinline__ void bd_coarse_eval(const float* A, const float* R, c
 // Table noise with K = 32 keeps 32 (a, b) pairs of level 0 live: one CTA per
 // SM leaves room for them without spilling.
 template <int K, bool COARSE, bool TABLE>
-__global__ void __launch_bounds__(kThreads, (TABLE && K == 32) ? 1 : 2) boxdit_stream_kernel(const SearchParams p) {
+__device__ __forceinline__ void boxdit_unit(const SearchParams& p, const Unit& U, float* smem) {
   using S = BdS<K>;
   constexpr int KAP = S::KAP;
   constexpr int MIR = S::MIR;
-  extern __shared__ __align__(16) float smem[];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t row = blockIdx.x / p.tiles_per_row;
-  const int64_t t0 = (blockIdx.x % p.tiles_per_row) * (int64_t)p.tile;
+  const int64_t row = U.row, t0 = U.t0;
   const int top = p.top;
-  const int T = p.tile, H = p.halo;
-  const bool vec = p.vec != 0;
-  const unsigned char* __restrict__ xseg =
-      static_cast<const unsigned char*>(p.x) + (row * p.ld + t0) * p.esize;  // byte address
+  const int T = U.T, H = p.halo;
+  const bool vec = U.vec;
+  const unsigned char* __restrict__ xseg = U.xrow + t0 * p.esize;  // byte address
   const int dt = p.dtype;
-  const bool vx = p.vec_x != 0;
-  float* __restrict__ yseg = p.snr + row * p.ld + t0;
-  uint16_t* __restrict__ wseg = p.widx + row * p.ld + t0;
-  const int64_t nleft = p.nt - t0;
+  const bool vx = U.vec_x;
+  float* __restrict__ yseg = U.yrow + t0;
+  uint16_t* __restrict__ wseg = U.wrow + t0;
+  const int64_t nleft = U.nt - t0;
   const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));
   const BdDyn<K> L(top, TABLE ? p.n_widths : 0);
   float2* AB = reinterpret_cast<float2*>(smem + L.ab);  // table noise: (a, b) per width index
   float mu, inv;
-  row_noise<TABLE>(p, row, AB, mu, inv);
+  row_noise<TABLE>(p, U.mu, U.sigma, row, AB, mu, inv);
   float* RESY = smem + L.res_y;
   uint16_t* RESW = reinterpret_cast<uint16_t*>(smem + L.res_w);
   int* BCM = reinterpret_cast<int*>(smem + L.bcm);
@@ -418,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, (TABLE && K == 32) ? 1 : 2) boxdit_s
     }
     store8(yseg, wseg, s0, nrel, vec, y, w);
     if ((ar & (kCandTile - 1)) == 0) {
-      tile_max_atomic(p, row, t0 + ar, tmax);
+      tile_max_atomic(U.tm_row, t0 + ar, tmax);
       tmax = ninf();
     }
   };
@@ -445,6 +442,26 @@ __global__ void __launch_bounds__(kThreads, (TABLE && K == 32) ? 1 : 2) boxdit_s
   }
 }
 
+// One CTA per unit of a single-series search.
+template <int K, bool COARSE, bool TABLE>
+__global__ void __launch_bounds__(kThreads, (TABLE && K == 32) ? 1 : 2) boxdit_stream_kernel(const SearchParams p) {
+  extern __shared__ __align__(16) float smem[];
+  boxdit_unit<K, COARSE, TABLE>(p, plan_unit(p, blockIdx.x), smem);
+}
+
+// Batched search: persistent CTAs stride over the units of every range.
+template <int K, bool COARSE>
+__global__ void __launch_bounds__(kThreads, 2) boxdit_batch_kernel(const SearchParams p) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int flag;
+  for (int64_t u = blockIdx.x; u < p.n_units; u += gridDim.x) {
+    Unit U;
+    if (!batch_unit(p, u, U, &flag)) continue;
+    boxdit_unit<K, COARSE, false>(p, U, smem);
+    __syncthreads();
+  }
+}
+
 template <int K>
 size_t bd_smem(int top, int nab) {
   return sizeof(float) * (size_t)BdDyn<K>(top, nab).total;
@@ -466,6 +483,38 @@ size_t boxdit_smem_bytes(const spd_plan& plan, bool table) {
     case 16: return bd_smem<16>(plan.top, nab);
     case 32: return bd_smem<32>(plan.top, nab);
     default: return 0;
+  }
+}
+
+namespace {
+// Persistent launch: as many CTAs as fit on the device at once (at most one per unit).
+template <class KernelT>
+cudaError_t launch_persistent(KernelT kern, size_t smem, int64_t units, const SearchParams& p,
+                              cudaStream_t s) {
+  int per_sm = 0, sms = 0;
+  const cudaError_t e = persistent_config(reinterpret_cast<const void*>(kern), smem, &per_sm, &sms);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > units) grid = units;
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_boxdit_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
+  const size_t smem = boxdit_smem_bytes(plan, false);
+  const bool coarse = plan.top >= kRing0;
+  switch (plan.k) {
+    case 8:
+      return coarse ? launch_persistent(boxdit_batch_kernel<8, true>, smem, p.n_units, p, s)
+                    : launch_persistent(boxdit_batch_kernel<8, false>, smem, p.n_units, p, s);
+    case 16:
+      return coarse ? launch_persistent(boxdit_batch_kernel<16, true>, smem, p.n_units, p, s)
+                    : launch_persistent(boxdit_batch_kernel<16, false>, smem, p.n_units, p, s);
+    case 32:
+      return coarse ? launch_persistent(boxdit_batch_kernel<32, true>, smem, p.n_units, p, s)
+                    : launch_persistent(boxdit_batch_kernel<32, false>, smem, p.n_units, p, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -48,14 +48,15 @@ __device__ __forceinline__ float snr_of(float S, float2 ab) { return fmaf(S, ab.
 //   of a partial last level (ranks >= n_top) still load their entry.
 constexpr int kAbPad = 32;
 template <bool TABLE>
-__device__ __forceinline__ void row_noise(const SearchParams& p, int64_t row, float2* AB, float& mu,
+__device__ __forceinline__ void row_noise(const SearchParams& p, const float* mu_tab,
+                                          const float* sigma_tab, int64_t row, float2* AB, float& mu,
                                           float& inv) {
   if constexpr (!TABLE) {
-    mu = p.mu[row];
-    inv = 1.0f / p.sigma[row];
+    mu = mu_tab[row];
+    inv = 1.0f / sigma_tab[row];
   } else {
-    const float* m = p.mu + row * p.n_widths;
-    const float* s = p.sigma + row * p.n_widths;
+    const float* m = mu_tab + row * p.n_widths;
+    const float* s = sigma_tab + row * p.n_widths;
     const double c = m[0], d = s[0];
     mu = m[0];
     inv = (float)(1.0 / d);
@@ -89,13 +90,94 @@ __host__ __device__ __forceinline__ float fkey_inv(int k) {
 #endif
 }
 
-// Warp-reduced maximum of v folded into the candidate-tile maximum of start s.
-__device__ __forceinline__ void tile_max_atomic(const SearchParams& p, int64_t row, int64_t s,
-                                                float v) {
+// Warp-reduced maximum of v folded into the candidate-tile maximum of start s
+// (tm_row: the row's tile keys, or null).
+__device__ __forceinline__ void tile_max_atomic(int* tm_row, int64_t s, float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  if ((threadIdx.x & 31) == 0 && p.tile_max)
-    atomicMax(reinterpret_cast<int*>(p.tile_max) + row * p.cand_tiles_per_row + s / kCandTile, fkey(v));
+  if ((threadIdx.x & 31) == 0 && tm_row) atomicMax(tm_row + s / kCandTile, fkey(v));
+}
+
+// One unit of a streaming search: segment [t0, t0 + T) of one row (plus the
+// halo after it), with the row's pointers, length and noise.
+struct Unit {
+  const unsigned char* xrow;  // the row's first sample (bytes)
+  float* yrow;
+  uint16_t* wrow;
+  const float* mu;            // noise table base and the row index into it
+  const float* sigma;
+  int* tm_row;                // the row's candidate-tile keys (or null)
+  int64_t row, nt, t0;
+  int32_t T;
+  bool vec, vec_x;
+};
+
+// Unit u of a single-series search: row u / tiles_per_row, segment u % tiles_per_row.
+__device__ __forceinline__ Unit plan_unit(const SearchParams& p, int64_t u) {
+  Unit U;
+  U.row = u / p.tiles_per_row;
+  U.t0 = (u % p.tiles_per_row) * (int64_t)p.tile;
+  U.T = p.tile;
+  U.nt = p.nt;
+  U.xrow = static_cast<const unsigned char*>(p.x) + U.row * p.ld * p.esize;
+  U.yrow = p.snr + U.row * p.ld;
+  U.wrow = p.widx + U.row * p.ld;
+  U.mu = p.mu;
+  U.sigma = p.sigma;
+  U.tm_row = p.tile_max ? reinterpret_cast<int*>(p.tile_max) + U.row * p.cand_tiles_per_row : nullptr;
+  U.vec = p.vec != 0;
+  U.vec_x = p.vec_x != 0;
+  return U;
+}
+
+// Unit u of a batched search (ranges in unit order).  If the range has a ready
+// flag, thread 0 waits for it (nanosleep polling, at most p.wait_ns by the
+// global timer, and at most 2^26 polls); when a wait runs out, the range's bit
+// of *p.status is set and this and every later unit of the range are skipped.
+// Returns false when the unit is skipped (uniform over the CTA).
+__device__ __forceinline__ bool batch_unit(const SearchParams& p, int64_t u, Unit& U, int* flag) {
+  int r = 0;
+  while (r + 1 < p.n_ranges && u >= p.ranges[r + 1].unit_first) ++r;
+  const BatchRange& g = p.ranges[r];
+  if (g.ready) {
+    if (threadIdx.x == 0) {
+      int ok = (atomicOr(p.status, 0) >> r) & 1 ? 0 : 1;
+      if (ok && *reinterpret_cast<const volatile int32_t*>(g.ready) == 0) {
+        unsigned long long t_start, t_now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+        ok = 0;
+        for (int it = 0; it < (1 << 26); ++it) {
+          if (*reinterpret_cast<const volatile int32_t*>(g.ready) != 0) {
+            ok = 1;
+            break;
+          }
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_now));
+          if ((long long)(t_now - t_start) > p.wait_ns) break;
+          __nanosleep(1000);
+        }
+        if (!ok) atomicOr(p.status, 1 << r);
+      }
+      *flag = ok;
+    }
+    __syncthreads();
+    const bool ok = *flag != 0;
+    __syncthreads();  // the flag is reused by the next unit
+    if (!ok) return false;
+  }
+  const int64_t local = u - g.unit_first;
+  U.row = local / g.tiles_per_row;
+  U.t0 = (local % g.tiles_per_row) * (int64_t)g.tile;
+  U.T = g.tile;
+  U.nt = g.nt;
+  U.xrow = static_cast<const unsigned char*>(g.x) + U.row * g.ld * p.esize;
+  U.yrow = g.snr + U.row * g.ld;
+  U.wrow = g.widx + U.row * g.ld;
+  U.mu = g.mu;
+  U.sigma = g.sigma;
+  U.tm_row = reinterpret_cast<int*>(g.tile_max) + U.row * g.cand_tiles_per_row;
+  U.vec = g.vec != 0;
+  U.vec_x = g.vec_x != 0;
+  return true;
 }
 
 // ---------------------------------------------------------------- input samples

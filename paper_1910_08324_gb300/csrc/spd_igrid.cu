@@ -126,34 +126,30 @@ struct IgDyn {
 };
 
 template <int D, int PL, bool COARSE, bool TABLE>
-__global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
-    igrid_stream_kernel(const SearchParams p) {
+__device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U, float* smem) {
   using S = IgS<D, PL>;
   using FX = IgFix<D, PL>;
   using SM = typename S::SM;
   using S0 = typename S::S0;
   constexpr int MMAX = S::MMAX;
-  extern __shared__ __align__(16) float smem[];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t row = blockIdx.x / p.tiles_per_row;
-  const int64_t t0 = (blockIdx.x % p.tiles_per_row) * (int64_t)p.tile;
+  const int64_t row = U.row, t0 = U.t0;
   const int top = p.top;
-  const int T = p.tile, H = p.halo;
-  const bool vec = p.vec != 0;
+  const int T = U.T, H = p.halo;
+  const bool vec = U.vec;
   // everything below is relative to the segment start t0 (32-bit offsets)
-  const unsigned char* __restrict__ xseg =
-      static_cast<const unsigned char*>(p.x) + (row * p.ld + t0) * p.esize;  // byte address
+  const unsigned char* __restrict__ xseg = U.xrow + t0 * p.esize;  // byte address
   const int dt = p.dtype;
-  const bool vx = p.vec_x != 0;
-  float* __restrict__ yseg = p.snr + row * p.ld + t0;
-  uint16_t* __restrict__ wseg = p.widx + row * p.ld + t0;
-  const int64_t nleft = p.nt - t0;
+  const bool vx = U.vec_x;
+  float* __restrict__ yseg = U.yrow + t0;
+  uint16_t* __restrict__ wseg = U.wrow + t0;
+  const int64_t nleft = U.nt - t0;
   const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));  // samples that exist
   constexpr bool ENC = S::ENC;
   const IgDyn L(FX::RINGS, top, MMAX, TABLE ? p.n_widths : 0, ENC);
   float2* AB = reinterpret_cast<float2*>(smem + L.ab);  // table noise: (a, b) per width index
   float mu, inv;
-  row_noise<TABLE>(p, row, AB, mu, inv);
+  row_noise<TABLE>(p, U.mu, U.sigma, row, AB, mu, inv);
   // candidate scale of block count m (white noise: 1/sqrt(m), times the level's
   // 2^(-j/2) after the maximum; table noise: the width's (a, b), first = the
   // level's first width index)
@@ -546,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     }
     store8(yseg, wseg, s0, nrel, vec, y, w);
     if ((ar & (kCandTile - 1)) == 0) {  // last chunk of a candidate tile (we walk backwards)
-      tile_max_atomic(p, row, t0 + ar, tmax);
+      tile_max_atomic(U.tm_row, t0 + ar, tmax);
       tmax = ninf();
     }
   };
@@ -570,6 +566,26 @@ __global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2))
     __syncthreads();
     if (COARSE && more) coarse(k + 1);
     fine(k);
+  }
+}
+
+// One CTA per unit of a single-series search.
+template <int D, int PL, bool COARSE, bool TABLE>
+__global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2)) igrid_stream_kernel(const SearchParams p) {
+  extern __shared__ __align__(16) float smem[];
+  igrid_unit<D, PL, COARSE, TABLE>(p, plan_unit(p, blockIdx.x), smem);
+}
+
+// Batched search: persistent CTAs stride over the units of every range.
+template <int D, int PL, bool COARSE>
+__global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2)) igrid_batch_kernel(const SearchParams p) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int flag;
+  for (int64_t u = blockIdx.x; u < p.n_units; u += gridDim.x) {
+    Unit U;
+    if (!batch_unit(p, u, U, &flag)) continue;
+    igrid_unit<D, PL, COARSE, false>(p, U, smem);
+    __syncthreads();
   }
 }
 
@@ -602,6 +618,42 @@ cudaError_t launch_ig(const spd_plan& plan, const SearchParams& p, size_t smem, 
                             : launch_one(igrid_stream_kernel<D, PL, false, TABLE>, smem, nblk, p, s);
 }
 }  // namespace
+
+namespace {
+// Persistent launch: as many CTAs as fit on the device at once (at most one per unit).
+template <class KernelT>
+cudaError_t launch_persistent(KernelT kern, size_t smem, int64_t units, const SearchParams& p,
+                              cudaStream_t s) {
+  int per_sm = 0, sms = 0;
+  const cudaError_t e = persistent_config(reinterpret_cast<const void*>(kern), smem, &per_sm, &sms);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > units) grid = units;
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_igrid_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
+  const size_t smem = igrid_smem_bytes(plan, false);
+  const bool coarse = plan.top >= kRing0;
+  switch (plan.d * 8 + plan.pl) {
+#define SPD_IG_BATCH(D, PL)                                                                   \
+  case D * 8 + PL:                                                                            \
+    return coarse ? launch_persistent(igrid_batch_kernel<D, PL, true>, smem, p.n_units, p, s) \
+                  : launch_persistent(igrid_batch_kernel<D, PL, false>, smem, p.n_units, p, s);
+    SPD_IG_BATCH(0, 0)
+    SPD_IG_BATCH(0, 1)
+    SPD_IG_BATCH(1, 1)
+    SPD_IG_BATCH(1, 2)
+    SPD_IG_BATCH(2, 2)
+    SPD_IG_BATCH(2, 3)
+    SPD_IG_BATCH(3, 3)
+    SPD_IG_BATCH(3, 4)
+#undef SPD_IG_BATCH
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
   const bool table = p.table != 0;

@@ -36,6 +36,22 @@ constexpr int kMaxLevels = 24;     // levels a plan may have
 constexpr int kMaxLend = 32768;    // largest width a plan may reach
 constexpr int kMaxExhaustive = 4096;
 constexpr int kMaxGridWidths = 512;  // widths of a BoxDIT / IGRID plan
+constexpr int kMaxRanges = 8;        // DM ranges of one batched search
+
+// One range of a batched search (spd_batch_execute): its own series, outputs,
+// white-noise statistics, tile maxima (in the workspace) and optional ready flag.
+struct BatchRange {
+  const void* x;
+  float* snr;
+  uint16_t* widx;
+  const float* mu;
+  const float* sigma;
+  float* tile_max;          // [ndm * cand_tiles_per_row] ordered-int keys
+  const int32_t* ready;     // nullptr, or a flag the units of this range wait for
+  int64_t ndm, nt, ld;
+  int64_t unit_first;       // index of the range's first unit (row-major: row, segment)
+  int32_t tile, tiles_per_row, cand_tiles_per_row, vec, vec_x, pad;
+};
 constexpr int kCandTile = 16384;   // starts per candidate tile (tile maxima granularity)
 constexpr int kMaxPeakRadius = 64;
 constexpr int kCandGroup = 32;     // candidate tiles per warp of the candidate passes
@@ -71,6 +87,12 @@ struct SearchParams {
   int32_t n_widths;               // widths of the plan
   int32_t unit_widths;            // 1: width index w is width w + 1 (exhaustive grid)
   int32_t wtab[kMaxGridWidths];   // widths of the plan (table noise, unit_widths == 0)
+  // batched search: units are (range, row, segment); 0 ranges: the single series above
+  int32_t n_ranges;
+  int64_t n_units;
+  int32_t* status;                // bit r: a wait for range r's ready flag ran out
+  int64_t wait_ns;                // limit of one wait
+  BatchRange ranges[kMaxRanges];
 };
 
 // Noise-statistics kernels (spd_msd.cu).
@@ -131,6 +153,12 @@ cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream
 size_t igrid_smem_bytes(const spd_plan& plan, bool table);
 cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
+// Shared-memory attribute, CTAs per SM and SM count of a persistent kernel,
+// set and queried on the first call per (kernel, device, shared memory) and
+// cached, so that later launches (e.g. during stream capture) make no queries.
+cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int* sms);
+cudaError_t launch_igrid_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
+cudaError_t launch_boxdit_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
 cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s);
 size_t search_smem_bytes(const spd_plan& plan, bool table);

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
   float* RS = smem + L.rs;  // white noise: RS[m] = 1/sqrt(m); table noise: AB[m - 1] = (a, b)
   float2* AB = reinterpret_cast<float2*>(smem + L.rs);
   float mu, inv;
-  row_noise<TABLE>(p, row, AB, mu, inv);
+  row_noise<TABLE>(p, p.mu, p.sigma, row, AB, mu, inv);
   if constexpr (!TABLE)
     for (int m = tid; m <= lmax + 32; m += kThreads)
       RS[m] = (m >= 1 && m <= lmax) ? (float)(1.0 / sqrt((double)m)) : 0.0f;
@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
       if (s0 + r < p.nt) tmax = fmaxf(tmax, best[r]);
     store4(yrow, wrow, s0, p.nt, vec, best, q);
   }
-  tile_max_atomic(p, row, t0, tmax);
+  tile_max_atomic(p.tile_max ? reinterpret_cast<int*>(p.tile_max) + row * p.cand_tiles_per_row : nullptr,
+                  t0, tmax);
 }
 
 }  // namespace

@@ -127,3 +127,43 @@ def test_widths_buffer_too_small():
     buf = np.zeros(10, np.int32)
     st = lib.spd_plan_widths(ctypes.c_void_p(plan.handle), buf.ctypes.data, None, 10, ctypes.byref(n))
     assert st == 5 and n.value == 257
+
+
+def test_batch_validation():
+    A = spd.SPD_ALGO_BOXDIT
+    b = spd.spd_batch_create(A, 4096, [1024, 1024, 768, 512, 256],
+                             [2097152, 1048576, 524288, 262144, 131072], boxdit_lmax=16)
+    assert b.workspace_size() > 0
+    b.set_segment(65536)
+    b.set_wait_ns(10 ** 6)
+    for bad in (1000, 16384 + 8192, 0, 1 << 25):
+        with pytest.raises(spd.SpdError) as e:
+            b.set_segment(bad)
+        assert e.value.status == 1
+    with pytest.raises(spd.SpdError) as e:
+        b.set_wait_ns(-1)
+    assert e.value.status == 1
+    with pytest.raises(spd.SpdError) as e:  # exhaustive grids are not batched
+        spd.spd_batch_create(spd.SPD_ALGO_EXHAUSTIVE, 64, [1], [100])
+    assert e.value.status == 2
+    for ndm, nt, ld in (([1] * 9, [100] * 9, None), ([0], [100], None), ([1], [100], [50])):
+        with pytest.raises(spd.SpdError) as e:
+            spd.spd_batch_create(A, 64, ndm, nt, ld, boxdit_lmax=8)
+        assert e.value.status == 1
+    # execute validates before any launch: NULL range pointers, small workspace
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_batch_execute(b, [0] * 5, [0] * 5, [0] * 5, [0] * 5, [0] * 5, 4096, 1 << 30)
+    assert e.value.status == 1
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_batch_execute(b, [4096] * 5, [4096] * 5, [4096] * 5, [4096] * 5, [4096] * 5, 4096, 16)
+    assert e.value.status == 4
+
+
+def test_plan_segment_rules():
+    plan = spd.spd_plan_create(spd.SPD_ALGO_IGRID, 32768, ndm=1, nt=1 << 20, igrid_depth=0, igrid_layers=1)
+    with pytest.raises(spd.SpdError):
+        spd.spd_plan_set_segment(plan, 16384)  # DIT up to 32768 has a level of 2^15: segments of 2^15
+    spd.spd_plan_set_segment(plan, 32768)
+    ex = spd.spd_plan_create(spd.SPD_ALGO_EXHAUSTIVE, 64, ndm=1, nt=1000)
+    with pytest.raises(spd.SpdError):
+        spd.spd_plan_set_segment(ex, 16384)

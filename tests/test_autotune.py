@@ -1,0 +1,52 @@
+"""Host logic of the segment autotuner: the fastest length wins, lengths the grid
+rejects are skipped, the choice is cached by key and reused without timing."""
+import json
+
+import pytest
+
+from paper_1910_08324_gb300 import autotune
+
+
+def test_picks_fastest_and_caches(tmp_path):
+    path = str(tmp_path / "tune.json")
+    applied = []
+    cost = {16384: 5.0, 32768: 3.0, 65536: 2.5, 131072: 4.0, 262144: 9.0}
+    state = {}
+
+    def set_segment(s):
+        if s == 262144:
+            raise ValueError("too long for this grid")
+        state["s"] = s
+        applied.append(s)
+
+    def time_ms():
+        return cost[state["s"]]
+
+    key = autotune.key_of(1, 4096, 0, [(1024, 2097152), (256, 131072)], boxdit_lmax=16)
+    seg, t = autotune.tune_segment(key, set_segment, time_ms, cache_path=path, reps=2)
+    assert seg == 65536 and state["s"] == 65536
+    assert "262144" not in t and t["65536"] == 2.5
+    d = json.load(open(path))
+    assert d[key]["segment"] == 65536
+    # cached: applied without timing
+    applied.clear()
+    seg2, _ = autotune.tune_segment(key, set_segment, lambda: pytest.fail("timed again"), cache_path=path)
+    assert seg2 == 65536 and applied == [65536]
+    # another key is tuned separately; the file keeps both
+    key2 = autotune.key_of(2, 8192, 0, [(4096, 1048576)], igrid_depth=1, igrid_layers=4)
+    autotune.tune_segment(key2, set_segment, time_ms, cache_path=path, reps=1)
+    assert set(json.load(open(path))) == {key, key2}
+
+
+def test_no_applicable_length_raises():
+    def set_segment(s):
+        raise ValueError("never")
+    with pytest.raises(RuntimeError):
+        autotune.tune_segment("k", set_segment, lambda: 1.0)
+
+
+def test_corrupt_cache_is_ignored(tmp_path):
+    path = tmp_path / "tune.json"
+    path.write_text("{not json")
+    seg, _ = autotune.tune_segment("k", lambda s: None, lambda: 1.0, candidates=(32768,), cache_path=str(path))
+    assert seg == 32768 and json.load(open(path))["k"]["segment"] == 32768
