@@ -58,7 +58,13 @@ ALGOS = {
     "exh": dict(algo=0),
 }
 SEARCH_SOURCES = ["paper_1910_08324_gb300/csrc/spd_igrid.cu", "paper_1910_08324_gb300/csrc/spd_search.cu",
-                  "paper_1910_08324_gb300/csrc/spd_common.cuh", "paper_1910_08324_gb300/csrc/spd_internal.h"]
+                  "paper_1910_08324_gb300/csrc/spd_boxdit.cu", "paper_1910_08324_gb300/csrc/spd_common.cuh",
+                  "paper_1910_08324_gb300/csrc/spd_internal.h"]
+# uneven DM ranges of one batched search: (DM trials, time decimation) of a 2,097,152-sample base
+BATCH_RANGES = [(1024, 1), (1024, 2), (768, 4), (512, 8), (256, 16)]
+BATCH_BASE = 2097152
+BATCH_S_END = 4096
+TUNE_CACHE = os.path.join(ROOT, "paper_1910_08324_gb300", "_tune", "segments.json")
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -68,7 +74,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ska_mid", choices=["ska_mid", "exhaustive_small"],
+    ap.add_argument("--workload", default="ska_mid", choices=["ska_mid", "exhaustive_small", "batched"],
                     help="ska_mid: 4096 x 1M lossy search (default); exhaustive_small: 64 x 65536, widths 1..256")
     ap.add_argument("--algo", default="ig1", choices=sorted(ALGOS))
     ap.add_argument("--ndm", type=int, default=spd_synth.SKA_MID["ndm"])
@@ -229,6 +235,159 @@ def reference_arm(args):
     return 0
 
 
+def run_batched(args, torch, dist, spd, rank, world, local, dev):
+    """Uneven DM ranges at their own decimations searched by one graph-captured
+    persistent launch per step (plus each range's candidate step); the segment
+    length comes from the autotuner."""
+    from paper_1910_08324_gb300 import autotune
+    algo = args.algo if args.algo.startswith("bd") else "bd16"
+    kw = dict(ALGOS[algo])
+    a = kw.pop("algo")
+    dt_code, esize = DTYPES[args.dtype]
+    shapes = [(n, BATCH_BASE // d) for n, d in BATCH_RANGES]
+    b = spd.spd_batch_create(a, BATCH_S_END, [n for n, _ in shapes], [t for _, t in shapes], dtype=dt_code, **kw)
+    xs, ys, wis, mus, sgs, tabs = [], [], [], [], [], []
+    for r, (n, t) in enumerate(shapes):
+        seed = spd_synth.SEED_BASE + 4 + 100 * r + 1000 * rank
+        x = spd_synth.device_noise(n, t, seed, device=dev)
+        tab = spd_synth.pulse_table(100, n, t, seed + 1, width_range=(1, BATCH_S_END), snr_range=(6.0, 20.0),
+                                    min_gap=2 * 4600)
+        spd_synth.device_inject(x, tab)
+        xs.append(spd_synth.device_quantize(x, args.dtype))
+        tabs.append(tab)
+        ys.append(torch.empty((n, t), dtype=torch.float32, device=dev))
+        wis.append(torch.empty((n, t), dtype=torch.int16, device=dev))
+        if args.dtype == "u8":
+            mus.append(torch.full((n,), spd_synth.U8_OFFSET, device=dev))
+            sgs.append(torch.full((n,), spd_synth.U8_SCALE, device=dev))
+        else:
+            mus.append(torch.zeros(n, device=dev))
+            sgs.append(torch.ones(n, device=dev))
+    samples = sum(n * t for n, t in shapes)
+    ws = torch.empty(b.workspace_size(), dtype=torch.uint8, device=dev)
+    cap = 1 << 18
+    outs = [torch.zeros(cap * 24, dtype=torch.uint8, device=dev) for _ in shapes]
+    cnts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in shapes]
+    stream = torch.cuda.Stream(dev)
+
+    def search(st):
+        spd.batch_execute(b, xs, ys, wis, mus, sgs, ws, stream=st)
+
+    def step(st):
+        search(st)
+        for r in range(len(shapes)):
+            spd.spd_batch_candidates(b, r, ys[r].data_ptr(), wis[r].data_ptr(), args.threshold, args.radius,
+                                     outs[r].data_ptr(), cap, cnts[r].data_ptr(), ws.data_ptr(), ws.numel(),
+                                     1, st.cuda_stream)
+
+    def time_ms(fn, reps=1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn(stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with torch.cuda.stream(stream):
+        step(stream)  # first launches outside any capture
+        key = autotune.key_of(a, BATCH_S_END, dt_code, shapes, boxdit_lmax=kw.get("boxdit_lmax", 0))
+        seg, timings = autotune.tune_segment(key, b.set_segment, lambda: time_ms(search), cache_path=TUNE_CACHE,
+                                             reps=2, force=True)
+        step(stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step(stream)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[2 * k].record(stream)
+                graph.replay()
+                ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    total_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = samples * world / (ms_per_step / 1e3)
+    search_ms = min(time_ms(search) for _ in range(3))
+    widths, seps = spd.spd_plan_create(ndm=1, nt=shapes[0][1], s_end=BATCH_S_END, dtype=dt_code,
+                                       algo=a, **kw).widths()
+    cand_per_sample = float(np.sum(1.0 / seps))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sm_count * 128 * SM_MAX_HZ / 3.0
+    achieved = cand_per_sample * samples / (search_ms / 1e3)
+    bps = esize + OUT_BYTES_PER_SAMPLE
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "candidates/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz / 3 ops per candidate" % (sm_count, SM_MAX_HZ / 1e6),
+                "hbm_GBps": bps * samples / (search_ms / 1e3) / 1e9, "kernel": "batched search (%s)" % algo,
+                "kernel_ms": search_ms, "algorithmic_bytes_per_launch": bps * samples}
+    n_cand = sum(int(c.item()) for c in cnts)
+    # end to end: host inputs of every range (pinned), graph replay, counts back
+    e2e = None
+    if not args.no_e2e:
+        hs = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
+        for h, x in zip(hs, xs):
+            h.copy_(x)
+        ch = torch.zeros(len(shapes), dtype=torch.int64, pin_memory=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            with torch.cuda.stream(stream):
+                for h, x in zip(hs, xs):
+                    x.copy_(h, non_blocking=True)
+                graph.replay()
+                for r, c in enumerate(cnts):
+                    ch[r:r + 1].copy_(c, non_blocking=True)
+            stream.synchronize()
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": samples / dt, "unit": "samples/s", "h2d_bytes_per_step": esize * samples,
+               "d2h_bytes_per_step": 8 * len(shapes), "steps": args.e2e_steps, "ms_per_step": 1e3 * dt,
+               "api": "torch pinned H2D + graph replay of spd_batch_execute + spd_batch_candidates + D2H of counts"}
+        del hs
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        done, spent = 0, 0.0
+        while spent < args.cpu_seconds:
+            for r, (n, t) in enumerate(shapes):
+                xr = xs[r][: max(1, 24 >> r)].float().cpu().numpy()
+                _, dtc = cpu_oracle_rate(xr, algo, BATCH_S_END, float(mus[r][0]), float(sgs[r][0]))
+                done += xr.size
+                spent += dtc
+        cpu = {"value": done / spent, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": "%d samples: 24/12/6/3/1 rows of the five ranges per pass, %s grid, FP64, %.1f s"
+                         % (done, algo, spent)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched: 5 DM ranges %s at decimations 1/2/4/8/16 of %d samples, one "
+                                   "graph-captured persistent launch" % ("/".join(str(n) for n, _ in BATCH_RANGES),
+                                                                         BATCH_BASE),
+                       "algo": algo, "input_dtype": args.dtype, "s_end": BATCH_S_END, "samples": samples,
+                       "candidates_per_sample": cand_per_sample, "segment": seg,
+                       "autotune_ms": timings, "candidates_found": n_cand,
+                       "parallelism": "dp%d (ranges per GPU)" % world,
+                       "l2": "inputs larger than L2 (%.1f GB per GPU); no flush" % (esize * samples / 1e9)},
+            "e2e": e2e, "gpu_launches": 1 + 3 * len(shapes), "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "exhaustive_small":
@@ -245,6 +404,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "batched":
+        return run_batched(args, torch, dist, spd, rank, world, local, dev)
     ndm, nt = args.ndm, args.nt
     kw = dict(ALGOS[args.algo])
     dt_code, esize = DTYPES[args.dtype]
