@@ -357,6 +357,37 @@ spd_status spd_batch_candidates(const spd_batch *batch, int32_t range, const flo
                                 size_t ws_bytes, int32_t use_tile_max, spd_stream_t stream);
 
 /*
+ * Block proposal network (no counterpart in the paper): a small 1D-conv net
+ * reads x16-decimated blocks of 256 samples (4096 input samples each) and gives
+ * a logit per block; blocks it flags are searched at full resolution.
+ *   a1 = bf16(relu(b1 + W1 * x)), a2 = bf16(relu(b2 + W2 * a1)), h3 = b3 + W3 * a2,
+ *   g[c] = max_p relu(h3[c][p]), logit = b4 + W4 . g
+ * "*": correlation with kernel 9, zero padding 4; 16 channels (1 input channel
+ * for layer 1); W1..W3 used as bf16, every sum in FP32 (layers 2, 3 on the
+ * tensor cores).  Parameters: float32 vector of spd_net_param_count() (4817)
+ * entries, W1[16][9], b1[16], W2[16][16][9], b2[16], W3[16][16][9], b3[16],
+ * W4[16], b4.  Loss: binary cross-entropy of sigmoid(logit).
+ */
+int32_t spd_net_param_count(void);
+/* Decimated series for the network: d_out[r][j] = (x[r][16j .. 16j+15] summed
+ * - 16 mu_r) / (4 sigma_r), j < nt/16 (device float32 [ndm][nt/16]); d_x as
+ * spd_execute for dtype; d_mu, d_sigma white-noise statistics per row. */
+spd_status spd_net_decimate(const void *d_x, int32_t dtype, int64_t ndm, int64_t nt, int64_t ld,
+                            const float *d_mu, const float *d_sigma, float *d_out, spd_stream_t stream);
+/* Logits of n_blocks blocks (d_blocks: device float32 [n_blocks][256]). */
+spd_status spd_net_forward(const float *d_params, const float *d_blocks, int64_t n_blocks,
+                           float *d_logits, spd_stream_t stream);
+/* Sum over the blocks of the loss gradient (d_grad_sum[4817], overwritten) and
+ * of the loss (*d_loss_sum), labels d_labels[n_blocks] in {0, 1}.  The max pool
+ * passes its gradient to the first maximum; roundings pass it unchanged. */
+spd_status spd_net_gradient(const float *d_params, const float *d_blocks, const float *d_labels,
+                            int64_t n_blocks, float *d_grad_sum, float *d_loss_sum, spd_stream_t stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8, bias-corrected; step counts from 1)
+ * on the mean gradient d_grad_sum / n_blocks; d_m, d_v: moment vectors. */
+spd_status spd_net_adam(float *d_params, float *d_m, float *d_v, const float *d_grad_sum,
+                        int64_t n_blocks, float lr, int32_t step, spd_stream_t stream);
+
+/*
  * Wait for the stream and report any asynchronous CUDA error of work queued
  * on it (SPD_ERR_CUDA), else SPD_OK.
  */

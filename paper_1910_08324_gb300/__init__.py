@@ -33,6 +33,10 @@ from ._binding import (  # noqa: F401
     execute,
     library_path,
     load_library,
+    net_adam,
+    net_decimate,
+    net_forward,
+    net_gradient,
     noise_stats,
     records,
     search,
@@ -43,6 +47,7 @@ from ._binding import (  # noqa: F401
     spd_candidates,
     spd_candidates_static,
     spd_execute,
+    spd_net_param_count,
     spd_noise_stats,
     spd_plan_create,
     spd_plan_set_segment,

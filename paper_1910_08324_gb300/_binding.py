@@ -58,7 +58,8 @@ _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_des
             "spd_search", "spd_sync_status", "spd_candidates_static", "spd_noise_stats",
             "spd_plan_set_segment", "spd_batch_create", "spd_batch_destroy", "spd_batch_set_segment",
             "spd_batch_set_wait_ns", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
-            "spd_batch_candidates"]
+            "spd_batch_candidates", "spd_net_decimate", "spd_net_forward", "spd_net_gradient",
+            "spd_net_adam"]
 
 
 def library_path() -> str:
@@ -90,6 +91,12 @@ def load_library():
         lib.spd_candidates_static.argtypes = [vp, vp, vp, ctypes.c_float, i32, vp, i64, vp, vp]
         lib.spd_noise_stats.argtypes = [vp, vp, ctypes.c_float, i32, vp, vp, vp, sz, vp]
         lib.spd_plan_set_segment.argtypes = [vp, i32]
+        lib.spd_net_param_count.argtypes = []
+        lib.spd_net_param_count.restype = ctypes.c_int32
+        lib.spd_net_decimate.argtypes = [vp, i32, i64, i64, i64, vp, vp, vp, vp]
+        lib.spd_net_forward.argtypes = [vp, vp, i64, vp, vp]
+        lib.spd_net_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        lib.spd_net_adam.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, i32, vp]
         lib.spd_batch_create.argtypes = [ctypes.POINTER(_Desc), vp, vp, vp, i32, ctypes.POINTER(vp)]
         lib.spd_batch_destroy.argtypes = [vp]
         lib.spd_batch_set_segment.argtypes = [vp, i32]
@@ -359,6 +366,35 @@ def batch_execute(batch: Batch, xs, ys, widxs, mus, sigmas, ws, readys=None, str
                       [_ptr(m) for m in mus], [_ptr(s) for s in sigmas], _ptr(ws),
                       ws.numel() * ws.element_size(), _stream(stream),
                       readys=None if readys is None else [_ptr(r) for r in readys])
+
+
+# ----------------------------------------------------------------------------- proposal network
+def spd_net_param_count() -> int:
+    return int(load_library().spd_net_param_count())
+
+
+def net_decimate(x, mu, sigma, out, dtype: int = SPD_F32, stream=None):
+    """x: [ndm, ld] torch tensor of the dtype's storage; out: float32 [ndm, nt // 16] (nt = x's width)."""
+    ndm, ld = x.shape
+    nt = out.shape[1] * 16
+    _check(load_library().spd_net_decimate(_ptr(x), int(dtype), ndm, nt, ld, _ptr(mu), _ptr(sigma), _ptr(out),
+                                           _stream(stream) or None), "spd_net_decimate")
+
+
+def net_forward(params, blocks, logits, stream=None):
+    _check(load_library().spd_net_forward(_ptr(params), _ptr(blocks), blocks.shape[0], _ptr(logits),
+                                          _stream(stream) or None), "spd_net_forward")
+
+
+def net_gradient(params, blocks, labels, grad_sum, loss_sum, stream=None):
+    _check(load_library().spd_net_gradient(_ptr(params), _ptr(blocks), _ptr(labels), blocks.shape[0],
+                                           _ptr(grad_sum), _ptr(loss_sum), _stream(stream) or None),
+           "spd_net_gradient")
+
+
+def net_adam(params, m, v, grad_sum, n_blocks: int, lr: float, step: int, stream=None):
+    _check(load_library().spd_net_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad_sum), int(n_blocks),
+                                       float(lr), int(step), _stream(stream) or None), "spd_net_adam")
 
 
 def records(out_tensor, count: int):

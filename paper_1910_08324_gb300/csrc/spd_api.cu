@@ -730,6 +730,48 @@ spd_status spd_batch_candidates(const spd_batch* batch, int32_t range, const flo
   return check_cuda(e);
 }
 
+int32_t spd_net_param_count(void) { return spd::net_param_count(); }
+
+spd_status spd_net_decimate(const void* d_x, int32_t dtype, int64_t ndm, int64_t nt, int64_t ld,
+                            const float* d_mu, const float* d_sigma, float* d_out, spd_stream_t stream) {
+  if (!d_x || !d_mu || !d_sigma || !d_out || dtype < SPD_F32 || dtype > SPD_U8) return SPD_ERR_INVALID_ARG;
+  if (ndm < 1 || nt < 16 || ld < nt || ndm > ((int64_t)1 << 24) || nt > ((int64_t)1 << 40)) return SPD_ERR_INVALID_ARG;
+  const int esize = dtype_size(dtype);
+  if (((uintptr_t)d_x % esize) || ((uintptr_t)d_out % 4) || ((uintptr_t)d_mu % 4) || ((uintptr_t)d_sigma % 4))
+    return SPD_ERR_INVALID_ARG;
+  const bool vec = (uintptr_t)d_x % 16 == 0 && (ld * esize) % 16 == 0;
+  return check_cuda(spd::launch_net_decimate(d_x, dtype, esize, ndm, nt, ld, vec, d_mu, d_sigma, d_out,
+                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
+spd_status spd_net_forward(const float* d_params, const float* d_blocks, int64_t n_blocks, float* d_logits,
+                           spd_stream_t stream) {
+  if (!d_params || !d_blocks || !d_logits || n_blocks < 0 || ((uintptr_t)d_params % 4) ||
+      ((uintptr_t)d_blocks % 4) || ((uintptr_t)d_logits % 4))
+    return SPD_ERR_INVALID_ARG;
+  if (n_blocks == 0) return SPD_OK;
+  return check_cuda(spd::launch_net_forward(d_params, d_blocks, n_blocks, d_logits,
+                                            reinterpret_cast<cudaStream_t>(stream)));
+}
+
+spd_status spd_net_gradient(const float* d_params, const float* d_blocks, const float* d_labels,
+                            int64_t n_blocks, float* d_grad_sum, float* d_loss_sum, spd_stream_t stream) {
+  if (!d_params || !d_blocks || !d_labels || !d_grad_sum || !d_loss_sum || n_blocks < 1) return SPD_ERR_INVALID_ARG;
+  if (((uintptr_t)d_params % 4) || ((uintptr_t)d_blocks % 4) || ((uintptr_t)d_labels % 4) ||
+      ((uintptr_t)d_grad_sum % 4) || ((uintptr_t)d_loss_sum % 4))
+    return SPD_ERR_INVALID_ARG;
+  return check_cuda(spd::launch_net_grad(d_params, d_blocks, d_labels, n_blocks, d_grad_sum, d_loss_sum,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
+spd_status spd_net_adam(float* d_params, float* d_m, float* d_v, const float* d_grad_sum, int64_t n_blocks,
+                        float lr, int32_t step, spd_stream_t stream) {
+  if (!d_params || !d_m || !d_v || !d_grad_sum || n_blocks < 1 || step < 1 || !(lr >= 0.f) || std::isinf(lr))
+    return SPD_ERR_INVALID_ARG;
+  return check_cuda(spd::launch_net_adam(d_params, d_m, d_v, d_grad_sum, n_blocks, lr, step,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
 spd_status spd_sync_status(const spd_plan* plan, spd_stream_t stream) {
   if (!plan) return SPD_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));

@@ -158,6 +158,15 @@ size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
 // cached, so that later launches (e.g. during stream capture) make no queries.
 cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int* sms);
 cudaError_t launch_igrid_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
+// proposal network (spd_net.cu)
+int net_param_count();
+cudaError_t launch_net_forward(const float* P, const float* X, int64_t nb, float* logits, cudaStream_t s);
+cudaError_t launch_net_grad(const float* P, const float* X, const float* Y, int64_t nb, float* G, float* loss,
+                            cudaStream_t s);
+cudaError_t launch_net_adam(float* P, float* M, float* V, const float* G, int64_t nb, float lr, int step,
+                            cudaStream_t s);
+cudaError_t launch_net_decimate(const void* x, int dtype, int esize, int64_t ndm, int64_t nt, int64_t ld,
+                                bool vec, const float* mu, const float* sigma, float* out, cudaStream_t s);
 cudaError_t launch_boxdit_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
 cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s);

@@ -1,0 +1,411 @@
+// spd_net.cu -- block proposal network (sm_103a): x16 decimation of the series,
+// forward pass with BF16 tensor-core convolutions, gradients and Adam.
+//
+// The network (definition in the oracle's net module, restated here):
+//   a1 = bf16(relu(b1 + W1 * x)),  a2 = bf16(relu(b2 + W2 * a1)),  h3 = b3 + W3 * a2
+//   g[c] = max_p relu(h3[c][p]),    z = b4 + W4 . g
+// over one block of 256 decimated samples; "*" is a 1D correlation with kernel
+// 9 and zero padding 4 over 16 channels (1 input channel for layer 1).  The
+// weights of layers 1..3 enter as bf16 values, every sum accumulates in FP32.
+//
+// Layers 2 and 3 are implicit GEMMs on the tensor cores: per block, M = 256
+// positions, N = 16 output channels, K = 9 taps x 16 input channels, as
+// mma.sync m16n8k16 bf16 -> f32 (one K-step per tap).  Activations live in
+// shared memory as [position + 4][channel] rows of 24 bf16 (48 bytes), which
+// makes the fragment loads conflict-free; weights as [tap][out][in] rows of 24.
+// N = 16 is far below the 64/128-row tiles of tcgen05 MMAs with TMEM
+// accumulators, and the proposal step is bound by the decimation read, so the
+// warp-level MMA is used here.
+//
+// Gradients: the max pool passes one position per channel, so the backward
+// pass is a few dense FP32 loops per block in shared memory (straight-through
+// for the bf16 roundings); each CTA accumulates its blocks' gradients in shared
+// memory and adds them to the global sum once.
+#include <cuda_bf16.h>
+
+#include "spd_common.cuh"
+
+namespace spd {
+namespace {
+
+constexpr int NC = 16, NK = 9, NP = 256, PAD = 4, NPP = NP + 2 * PAD;
+constexpr int kNetThreads = 128;
+constexpr int kNetParams = 4817;
+constexpr int oW1 = 0, ob1 = 144, oW2 = 160, ob2 = 2464, oW3 = 2480, ob3 = 4784, oW4 = 4800, ob4 = 4816;
+constexpr int AS = 24;  // bf16 per activation row
+constexpr int WS = 24;  // bf16 per weight row
+
+struct NetSmem {
+  float w1[NC * NK], b1[NC], b2[NC], b3[NC], w4[NC], b4;
+  __nv_bfloat16 w2[NK][NC][WS], w3[NK][NC][WS];  // [tap][out][in]
+  float x[NPP];
+  __nv_bfloat16 a1[NPP][AS], a2[NPP][AS];
+  float wmax[4][NC];
+  int warg[4][NC];
+  float g[NC];
+  int arg[NC];
+  float z;
+};
+
+struct GradSmem {  // training only
+  float G[kNetParams];
+  float dh2[NP][NC];
+  float dh1[NP][NC];
+  float dh3[NC];
+};
+
+__device__ __forceinline__ float bf(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Weights into shared memory (bf16 copies for the tensor-core layers).
+__device__ void load_weights(const float* __restrict__ P, NetSmem& s) {
+  for (int i = threadIdx.x; i < NC * NK; i += blockDim.x) s.w1[i] = bf(__float2bfloat16_rn(P[oW1 + i]));
+  for (int i = threadIdx.x; i < NC; i += blockDim.x) {
+    s.b1[i] = P[ob1 + i];
+    s.b2[i] = P[ob2 + i];
+    s.b3[i] = P[ob3 + i];
+    s.w4[i] = P[oW4 + i];
+  }
+  if (threadIdx.x == 0) s.b4 = P[ob4];
+  for (int i = threadIdx.x; i < NC * NC * NK; i += blockDim.x) {  // P: W[co][ci][k]
+    const int co = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
+    s.w2[k][co][ci] = __float2bfloat16_rn(P[oW2 + i]);
+    s.w3[k][co][ci] = __float2bfloat16_rn(P[oW3 + i]);
+  }
+  // zero padding rows of the activations and the input
+  for (int i = threadIdx.x; i < 2 * PAD * AS; i += blockDim.x) {
+    const int r = i / AS, c = i % AS, row = r < PAD ? r : NP + r;
+    s.a1[row][c] = __float2bfloat16_rn(0.f);
+    s.a2[row][c] = __float2bfloat16_rn(0.f);
+  }
+  for (int i = threadIdx.x; i < 2 * PAD; i += blockDim.x) s.x[i < PAD ? i : NP + i] = 0.f;
+}
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One tensor-core layer: out[p][co] = sum_{k, ci} w[k][co][ci] in[p + k - 4][ci]
+// for the warp's 4 tiles of 16 positions and both tiles of 8 channels.
+__device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[AS], const __nv_bfloat16 (*w)[NC][WS],
+                                         float (&acc)[4][2][4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    uint32_t b[2][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      b[j][0] = ld32(&w[k][8 * j + gq][2 * tq]);
+      b[j][1] = ld32(&w[k][8 * j + gq][2 * tq + 8]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = 64 * warp + 16 * i + gq;  // row of the tile (stored row p + k: offset -4 + 4)
+      const uint32_t a0 = ld32(&in[p + k][2 * tq]);
+      const uint32_t a1 = ld32(&in[p + 8 + k][2 * tq]);
+      const uint32_t a2 = ld32(&in[p + k][2 * tq + 8]);
+      const uint32_t a3 = ld32(&in[p + 8 + k][2 * tq + 8]);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) mma_bf16(acc[i][j], a0, a1, a2, a3, b[j][0], b[j][1]);
+    }
+  }
+}
+
+// Forward pass of the block already in s.x; leaves a1, a2, g, arg and z in s.
+__device__ void net_block_forward(NetSmem& s) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, gq = lane >> 2, tq = lane & 3;
+  // layer 1 (one input channel): FP32
+  for (int i = t; i < NP * NC; i += kNetThreads) {
+    const int p = i >> 4, c = i & 15;
+    float h = s.b1[c];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) h = fmaf(s.w1[c * NK + k], s.x[p + k], h);
+    s.a1[p + PAD][c] = __float2bfloat16_rn(fmaxf(h, 0.f));
+  }
+  __syncthreads();
+  float acc[4][2][4];
+  conv_mma(s.a1, s.w2, acc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int p = 64 * warp + 16 * i + gq, co = 8 * j + 2 * tq;
+      __nv_bfloat162 lo, hi;
+      lo.x = __float2bfloat16_rn(fmaxf(acc[i][j][0] + s.b2[co], 0.f));
+      lo.y = __float2bfloat16_rn(fmaxf(acc[i][j][1] + s.b2[co + 1], 0.f));
+      hi.x = __float2bfloat16_rn(fmaxf(acc[i][j][2] + s.b2[co], 0.f));
+      hi.y = __float2bfloat16_rn(fmaxf(acc[i][j][3] + s.b2[co + 1], 0.f));
+      *reinterpret_cast<__nv_bfloat162*>(&s.a2[p + PAD][co]) = lo;
+      *reinterpret_cast<__nv_bfloat162*>(&s.a2[p + 8 + PAD][co]) = hi;
+    }
+  __syncthreads();
+  conv_mma(s.a2, s.w3, acc);
+  // max pool: the thread's maximum (first position on ties) of its two channels per tile
+  float mv[2][2];
+  int mp[2][2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      mv[j][e] = -1.f;
+      mp[j][e] = 0;
+    }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int co = 8 * j + 2 * tq + e;
+        const int p = 64 * warp + 16 * i + gq;
+        const float v0 = fmaxf(acc[i][j][e] + s.b3[co], 0.f);      // row p
+        const float v1 = fmaxf(acc[i][j][2 + e] + s.b3[co], 0.f);  // row p + 8
+        if (v0 > mv[j][e]) mv[j][e] = v0, mp[j][e] = p;
+        if (v1 > mv[j][e]) mv[j][e] = v1, mp[j][e] = p + 8;
+      }
+  // across the 8 row groups of the warp (lanes with the same tq)
+#pragma unroll
+  for (int o = 4; o < 32; o <<= 1)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float ov = __shfl_xor_sync(kFull, mv[j][e], o);
+        const int op = __shfl_xor_sync(kFull, mp[j][e], o);
+        if (ov > mv[j][e] || (ov == mv[j][e] && op < mp[j][e])) mv[j][e] = ov, mp[j][e] = op;
+      }
+  if (gq == 0)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        s.wmax[warp][8 * j + 2 * tq + e] = mv[j][e];
+        s.warg[warp][8 * j + 2 * tq + e] = mp[j][e];
+      }
+  __syncthreads();
+  if (t < NC) {  // warps cover increasing positions: the first warp wins ties
+    float v = s.wmax[0][t];
+    int a = s.warg[0][t];
+    for (int w = 1; w < 4; ++w)
+      if (s.wmax[w][t] > v) v = s.wmax[w][t], a = s.warg[w][t];
+    s.g[t] = v;
+    s.arg[t] = a;
+  }
+  __syncthreads();
+  if (t < 32) {
+    float zz = t < NC ? s.w4[t] * s.g[t] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(kFull, zz, o);
+    if (t == 0) s.z = s.b4 + zz;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kNetThreads) net_forward_kernel(const float* __restrict__ P,
+                                                                   const float* __restrict__ X, int64_t nb,
+                                                                   float* __restrict__ logits) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  NetSmem& s = *reinterpret_cast<NetSmem*>(raw);
+  load_weights(P, s);
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < NP; i += kNetThreads) s.x[PAD + i] = X[b * NP + i];
+    __syncthreads();
+    net_block_forward(s);
+    if (threadIdx.x == 0) logits[b] = s.z;
+  }
+}
+
+// Forward + backward of the CTA's blocks; gradients summed into G (global) and
+// the summed loss into *loss.
+__global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* __restrict__ P,
+                                                                const float* __restrict__ X,
+                                                                const float* __restrict__ Y, int64_t nb,
+                                                                float* __restrict__ Gout, float* __restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  NetSmem& s = *reinterpret_cast<NetSmem*>(raw);
+  GradSmem& q = *reinterpret_cast<GradSmem*>(raw + ((sizeof(NetSmem) + 15) / 16) * 16);
+  const int t = threadIdx.x;
+  load_weights(P, s);
+  for (int i = t; i < kNetParams; i += kNetThreads) q.G[i] = 0.f;
+  float lsum = 0.f;
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    __syncthreads();
+    for (int i = t; i < NP; i += kNetThreads) s.x[PAD + i] = X[b * NP + i];
+    __syncthreads();
+    net_block_forward(s);
+    const float z = s.z, y = Y[b];
+    const float dz = 1.f / (1.f + __expf(-z)) - y;
+    if (t == 0) {
+      lsum += fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z))) - y * z;
+      q.G[ob4] += dz;
+    }
+    if (t < NC) {
+      q.G[oW4 + t] += dz * s.g[t];
+      q.dh3[t] = s.g[t] > 0.f ? dz * s.w4[t] : 0.f;
+    }
+    __syncthreads();
+    // layer 3: weights and bias from the pooled positions; d(a2) gathered
+    for (int i = t; i < NC * NC * NK; i += kNetThreads) {
+      const int c = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
+      q.G[oW3 + i] += q.dh3[c] * bf(s.a2[s.arg[c] + k][ci]);
+    }
+    if (t < NC) q.G[ob3 + t] += q.dh3[t];
+    for (int i = t; i < NP * NC; i += kNetThreads) {
+      const int p = i >> 4, ci = i & 15;
+      float d = 0.f;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int k = p - s.arg[c] + PAD;  // a2[p] feeds h3[c][arg] through tap k
+        if (k >= 0 && k < NK) d = fmaf(bf(s.w3[k][c][ci]), q.dh3[c], d);
+      }
+      q.dh2[p][ci] = bf(s.a2[p + PAD][ci]) > 0.f ? d : 0.f;
+    }
+    __syncthreads();
+    // layer 2
+    for (int i = t; i < NC * NC * NK; i += kNetThreads) {
+      const int co = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
+      float acc = 0.f;
+      for (int p = 0; p < NP; ++p) acc = fmaf(q.dh2[p][co], bf(s.a1[p + k][ci]), acc);
+      q.G[oW2 + i] += acc;
+    }
+    if (t < NC) {
+      float acc = 0.f;
+      for (int p = 0; p < NP; ++p) acc += q.dh2[p][t];
+      q.G[ob2 + t] += acc;
+    }
+    for (int i = t; i < NP * NC; i += kNetThreads) {
+      const int p = i >> 4, ci = i & 15;
+      float d = 0.f;
+      for (int k = 0; k < NK; ++k) {
+        const int pp = p - k + PAD;  // output position fed by a1[p] through tap k
+        if (pp >= 0 && pp < NP)
+#pragma unroll
+          for (int co = 0; co < NC; ++co) d = fmaf(bf(s.w2[k][co][ci]), q.dh2[pp][co], d);
+      }
+      q.dh1[p][ci] = bf(s.a1[p + PAD][ci]) > 0.f ? d : 0.f;
+    }
+    __syncthreads();
+    // layer 1
+    for (int i = t; i < NC * NK + NC; i += kNetThreads) {
+      float acc = 0.f;
+      if (i < NC * NK) {
+        const int c = i / NK, k = i % NK;
+        for (int p = 0; p < NP; ++p) acc = fmaf(q.dh1[p][c], s.x[p + k], acc);
+        q.G[oW1 + i] += acc;
+      } else {
+        const int c = i - NC * NK;
+        for (int p = 0; p < NP; ++p) acc += q.dh1[p][c];
+        q.G[ob1 + c] += acc;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = t; i < kNetParams; i += kNetThreads) atomicAdd(Gout + i, q.G[i]);
+  if (t == 0) atomicAdd(loss, lsum);
+}
+
+// Adam on the mean gradient G / nb (bias-corrected, step counts from 1).
+__global__ void net_adam_kernel(float* __restrict__ P, float* __restrict__ M, float* __restrict__ V,
+                                const float* __restrict__ G, float inv_nb, float lr, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNetParams) return;
+  const float g = G[i] * inv_nb;
+  const float m = 0.9f * M[i] + 0.1f * g;
+  const float v = 0.999f * V[i] + 0.001f * g * g;
+  M[i] = m;
+  V[i] = v;
+  P[i] -= lr * (m * c1) / (sqrtf(v * c2) + 1e-8f);
+}
+
+// x16 decimation: out[r][j] = (sum of samples 16 j .. 16 j + 15 - 16 mu_r) / (4 sigma_r).
+__global__ void __launch_bounds__(256) net_decimate_kernel(const void* __restrict__ x, int dtype, int esize,
+                                                            int64_t ndm, int64_t nt, int64_t ld, int vec,
+                                                            const float* __restrict__ mu,
+                                                            const float* __restrict__ sigma,
+                                                            float* __restrict__ out) {
+  const int64_t nd = nt / 16;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ndm * nd) return;
+  const int64_t r = i / nd, j = i % nd;
+  const unsigned char* row = static_cast<const unsigned char*>(x) + (r * ld + 16 * j) * esize;
+  float4 a, b, c, d;
+  cvt8(load_raw8(row, 0, 16, dtype, vec != 0), 0, 16, dtype, 0.f, 1.f, a, b);
+  cvt8(load_raw8(row, 8, 16, dtype, vec != 0), 8, 16, dtype, 0.f, 1.f, c, d);
+  const float s = ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w)) + ((c.x + c.y) + (c.z + c.w)) +
+                  ((d.x + d.y) + (d.z + d.w));
+  out[i] = (s - 16.f * mu[r]) / (4.f * sigma[r]);
+}
+
+size_t net_smem(bool grad) {
+  size_t s = ((sizeof(NetSmem) + 15) / 16) * 16;
+  return grad ? s + sizeof(GradSmem) : s;
+}
+
+template <class KernelT>
+cudaError_t net_grid(KernelT kern, size_t smem, int64_t nb, int* grid) {
+  int per_sm = 0, sms = 0;
+  const cudaError_t e = persistent_config(reinterpret_cast<const void*>(kern), smem, &per_sm, &sms);
+  if (e != cudaSuccess) return e;
+  (void)kNetThreads;
+  int64_t g = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  *grid = (int)(g < nb ? g : nb);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int net_param_count() { return kNetParams; }
+
+cudaError_t launch_net_forward(const float* P, const float* X, int64_t nb, float* logits, cudaStream_t s) {
+  int grid = 0;
+  const size_t smem = net_smem(false);
+  cudaError_t e = net_grid(net_forward_kernel, smem, nb, &grid);
+  if (e != cudaSuccess || grid == 0) return e;
+  net_forward_kernel<<<grid, kNetThreads, smem, s>>>(P, X, nb, logits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_grad(const float* P, const float* X, const float* Y, int64_t nb, float* G, float* loss,
+                            cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * kNetParams, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  int grid = 0;
+  const size_t smem = net_smem(true);
+  e = net_grid(net_grad_kernel, smem, nb, &grid);
+  if (e != cudaSuccess || grid == 0) return e;
+  net_grad_kernel<<<grid, kNetThreads, smem, s>>>(P, X, Y, nb, G, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_adam(float* P, float* M, float* V, const float* G, int64_t nb, float lr, int step,
+                            cudaStream_t s) {
+  const float c1 = 1.f / (1.f - powf(0.9f, (float)step)), c2 = 1.f / (1.f - powf(0.999f, (float)step));
+  net_adam_kernel<<<(kNetParams + 255) / 256, 256, 0, s>>>(P, M, V, G, 1.f / (float)nb, lr, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_decimate(const void* x, int dtype, int esize, int64_t ndm, int64_t nt, int64_t ld,
+                                bool vec, const float* mu, const float* sigma, float* out, cudaStream_t s) {
+  const int64_t n = ndm * (nt / 16);
+  if (n == 0) return cudaSuccess;
+  net_decimate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, dtype, esize, ndm, nt, ld, vec ? 1 : 0, mu,
+                                                                   sigma, out);
+  return cudaGetLastError();
+}
+
+}  // namespace spd
