@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ska_mid", choices=["ska_mid", "exhaustive_small", "batched"],
+    ap.add_argument("--workload", default="ska_mid", choices=["ska_mid", "exhaustive_small", "batched", "proposal"],
                     help="ska_mid: 4096 x 1M lossy search (default); exhaustive_small: 64 x 65536, widths 1..256")
     ap.add_argument("--algo", default="ig1", choices=sorted(ALGOS))
     ap.add_argument("--ndm", type=int, default=spd_synth.SKA_MID["ndm"])
@@ -88,6 +88,9 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=96)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="oracle time the cpu_baseline sample accumulates")
+    ap.add_argument("--train-rows", type=int, default=1024, help="proposal: rows of 1M samples to train on")
+    ap.add_argument("--train-steps", type=int, default=6000, help="proposal: Adam steps of 512 blocks")
+    ap.add_argument("--logit-threshold", type=float, default=0.0, help="proposal: blocks above it are searched")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-loss", action="store_true")
@@ -388,6 +391,236 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
     return 0
 
 
+NET_FLOPS_PER_BLOCK = 2 * 256 * 16 * 9 * (1 + 16 + 16) + 2 * 16  # three k=9 convolutions, 16 channels, head
+PROPOSAL_GRID = dict(algo=1, s_end=4096, boxdit_lmax=16, dtype=1)      # BD-16 on FP16 samples
+
+
+def run_proposal(args, torch, dist, spd, rank, world, local, dev):
+    """Learned block proposals on 4096 x 1M FP16 rows of white + 1/f noise with
+    0.1% zero-DM spikes: the network is trained on the GPU first (untimed; labels
+    from the plain search), then a step decimates and scores every block and
+    searches the flagged ones with BD-16 at full resolution.  The plain BD-16
+    search of every block is timed beside it, and recall and SNR loss of both
+    are judged by the exhaustive search of windows around the injected pulses."""
+    from oracle import net as onet  # initial weights only (a seeded draw)
+    from paper_1910_08324_gb300 import proposal as P
+    ndm, nt = args.ndm, args.nt
+    grid = dict(PROPOSAL_GRID)
+    gx = dict(algo=0, s_end=2048, dtype=1)
+    t_setup = time.perf_counter()
+
+    def series(rows, seed, pulses):
+        x, _ = spd_synth.proposal_series(rows, nt, seed, device=dev)
+        spd_synth.device_inject_many(x, pulses, amp=spd_synth.proposal_amplitudes(pulses, nt, device=dev))
+        return x.half()
+
+    def tables(g, x):
+        plan = spd.spd_plan_create(ndm=x.shape[0], nt=nt, **g)
+        nw = len(plan.widths()[0])
+        mu = torch.empty((x.shape[0], nw), device=dev)
+        sg = torch.empty((x.shape[0], nw), device=dev)
+        ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device=dev)
+        spd.noise_stats(plan, x, mu, sg, ws)
+        return plan, mu, sg, ws
+
+    cap = 1 << 25
+    out = torch.empty(cap * 24, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def plain(plan, x, mu, sg, ws, Y, W):
+        spd.search(plan, x, mu, sg, Y, W, args.threshold, args.radius, out, cnt, ws, noise_mode=1)
+        k = int(cnt.item())
+        if k > cap:
+            raise RuntimeError("plain search: %d candidates exceed the cap" % k)
+        return spd.records(out, k).copy()
+
+    # ---- training (untimed): half the blocks hold one pulse; labels from the plain search
+    seed = spd_synth.SEED_BASE + 50 + 1000 * rank
+    ptr = spd_synth.block_pulses(args.train_rows, nt, P.BLOCK, seed, frac=0.5)
+    xtr = series(args.train_rows, seed + 1, ptr)
+    plan, mu, sg, ws = tables(grid, xtr)
+    Ytr = torch.empty(xtr.shape, device=dev)
+    Wtr = torch.empty(xtr.shape, dtype=torch.int16, device=dev)
+    y = P.label_blocks(plain(plan, xtr, mu, sg, ws, Ytr, Wtr), ptr, args.train_rows, nt)
+    X = P.decimated_blocks(xtr, mu[:, 0].contiguous(), sg[:, 0].contiguous(), dtype=grid["dtype"])
+    del xtr, Ytr, Wtr, plan, ws
+    params = torch.from_numpy(onet.init_params(seed + 2)).to(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    losses, _, _ = P.train(params, X, torch.from_numpy(y).to(dev), steps=args.train_steps, batch=512, lr=3e-3,
+                           seed=seed + 3)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    training = {"blocks": int(X.shape[0]), "positives": int(y.sum()), "steps": args.train_steps, "batch": 512,
+                "seconds": train_s, "blocks_per_s": args.train_steps * 512 / train_s,
+                "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-100:]))}
+    del X
+
+    # ---- evaluation series: 500 pulses, widths log-uniform 1..2048, SNR 5..20 (against the noise at their width)
+    pev = spd_synth.pulse_table(500, ndm, nt, seed + 4, width_range=(1, 2048), snr_range=(5.0, 20.0),
+                                min_gap=2 * 8192)
+    x = series(ndm, seed + 5, pev)
+    plan, mu, sg, ws = tables(grid, x)
+    _, mux, sgx, _ = tables(gx, x)
+    sj = P.pulse_snr(x, pev, mux, sgx, gx)
+    del mux, sgx
+    Y = torch.empty(x.shape, device=dev)
+    W = torch.empty(x.shape, dtype=torch.int16, device=dev)
+    setup_s = time.perf_counter() - t_setup
+
+    def prop_step():
+        return P.propose_and_search(params, x, mu, sg, grid, logit_threshold=args.logit_threshold,
+                                    threshold=args.threshold, radius=args.radius)
+
+    for _ in range(args.warmup):
+        prop_step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rec, nflag = prop_step()
+            torch.cuda.synchronize(dev)
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    if world > 1:
+        tt = torch.tensor([total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    ms_per_step = 1e3 * total / args.steps
+    value = ndm * nt * world / (ms_per_step / 1e3)
+    s_prop = P.score(rec, pev, sj, ndm, nt)
+
+    # the method without the network: plain BD-16 search of every block (same noise tables)
+    pt = []
+    for k in range(max(2, min(args.steps, 5)) + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rp = plain(plan, x, mu, sg, ws, Y, W)
+        torch.cuda.synchronize(dev)
+        if k:
+            pt.append(time.perf_counter() - t0)
+    s_plain = P.score(rp, pev, sj, ndm, nt)
+    plain_ms = 1e3 * statistics.mean(pt)
+
+    # per-kernel breakdown of one proposal step (CUDA events on the launching stream)
+    st = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(st)
+    d = P.decimated_blocks(x, mu[:, 0].contiguous(), sg[:, 0].contiguous(), dtype=grid["dtype"])
+    ev[1].record(st)
+    lg = torch.empty(d.shape[0], device=dev)
+    spd.net_forward(params, d, lg)
+    ev[2].record(st)
+    ids = P.select_blocks(lg, args.logit_threshold)
+    ev[3].record(st)
+    torch.cuda.synchronize(dev)
+    dec_ms, fwd_ms, sel_ms = (ev[i].elapsed_time(ev[i + 1]) for i in range(3))
+    fw = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        spd.net_forward(params, d, lg)
+        e1.record(st)
+        e1.synchronize()
+        fw.append(e0.elapsed_time(e1))
+    fwd_ms = statistics.mean(fw)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    P.search_flagged(x, ids, mu, sg, grid, args.threshold, args.radius, noise_mode=1)
+    torch.cuda.synchronize(dev)
+    flagged_ms = 1e3 * (time.perf_counter() - t0)
+    nblocks = d.shape[0]
+    del d, lg
+
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = NET_FLOPS_PER_BLOCK * nblocks / (fwd_ms / 1e3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "net_forward_kernel (BF16 mma.sync implicit GEMM)", "kernel_ms": fwd_ms,
+                "algorithmic_flops_per_launch": NET_FLOPS_PER_BLOCK * nblocks,
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst, of measured)" if peaks
+                                else "fallback 1900 TFLOP/s"),
+                "decimate_ms": dec_ms, "decimate_GBps": 2 * ndm * nt / (dec_ms / 1e3) / 1e9,
+                "select_ms": sel_ms, "flagged_search_ms": flagged_ms}
+
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        xh.copy_(x)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        nrec = []
+        for _ in range(args.e2e_steps):
+            x.copy_(xh, non_blocking=True)
+            r, _ = prop_step()  # records come back to the host inside the step
+            nrec.append(len(r))
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": ndm * nt / dt, "unit": "samples/s", "h2d_bytes_per_step": 2 * ndm * nt,
+               "d2h_bytes_per_step": int(24 * statistics.mean(nrec) + 16), "steps": args.e2e_steps,
+               "ms_per_step": 1e3 * dt,
+               "api": "torch pinned H2D + proposal.propose_and_search (C ABI calls) + records to the host"}
+        del xh
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        import oracle
+        g = oracle.grid_boxdit(16, 4096)
+        lend, sep = P.plan_geometry(grid)
+        done, spent, r = 0, 0.0, 0
+        while done == 0 or spent < args.cpu_seconds:
+            xr = x[r].float().cpu().numpy().astype(np.float64)
+            m0, s0 = float(mu[r, 0]), float(sg[r, 0])
+            t0 = time.perf_counter()
+            dec = (xr.reshape(-1, 16).sum(axis=1) - 16 * m0) / (4 * s0)
+            lgs = np.array([onet.forward(params.cpu().numpy().astype(np.float64), b)[0]
+                            for b in dec.reshape(-1, 256)])
+            flag = np.nonzero(lgs > args.logit_threshold)[0]
+            if len(flag):
+                rows = np.full((len(flag), sep + P.BLOCK + lend), -np.inf)
+                for i, b in enumerate(flag):
+                    a = b * P.BLOCK - sep
+                    lo, hi = max(a, 0), min(a + rows.shape[1], nt)
+                    rows[i, lo - a:hi - a] = xr[lo:hi]
+                oracle.search(rows, g, np.repeat(mu[r:r + 1].cpu().numpy(), len(flag), 0),
+                              np.repeat(sg[r:r + 1].cpu().numpy(), len(flag), 0), noise_mode=1)
+            spent += time.perf_counter() - t0
+            done += nt
+            r += 1
+        cpu = {"value": done / spent, "unit": "samples/s", "cores": 1, "kind": "oracle",
+               "sample": "%d rows x %d samples: FP64 decimation, network forward per block (oracle.net) and "
+                         "definition-form BD-16 search of the flagged blocks, %.1f s" % (r, nt, spent)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "proposal %d DM x %d FP16 samples, white + 1/f noise, 0.1%% zero-DM spikes, "
+                                   "500 pulses (widths 1..2048, SNR 5..20)" % (ndm, nt),
+                       "algo": "network proposals + bd16 (table noise)", "s_end": 4096,
+                       "logit_threshold": args.logit_threshold, "threshold": args.threshold,
+                       "peak_radius": args.radius, "blocks": nblocks, "blocks_searched": int(nflag),
+                       "searched_fraction": nflag / nblocks,
+                       "parallelism": "dp%d (rows per GPU)" % world,
+                       "l2": "inputs larger than L2 (%.1f GB per GPU); no flush" % (2 * ndm * nt / 1e9),
+                       "x_realtime_ska": value * T_SAMP / SKA_DM, "setup_s": setup_s},
+            "proposal": s_prop, "plain": dict(s_plain, ms_per_step=plain_ms,
+                                              value=ndm * nt / (plain_ms / 1e3)),
+            "speedup_vs_plain": plain_ms / ms_per_step, "training": training,
+            "e2e": e2e, "gpu_launches": 8 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "exhaustive_small":
@@ -406,6 +639,8 @@ def main():
     dev = torch.device("cuda", local)
     if args.workload == "batched":
         return run_batched(args, torch, dist, spd, rank, world, local, dev)
+    if args.workload == "proposal":
+        return run_proposal(args, torch, dist, spd, rank, world, local, dev)
     ndm, nt = args.ndm, args.nt
     kw = dict(ALGOS[args.algo])
     dt_code, esize = DTYPES[args.dtype]

@@ -387,6 +387,24 @@ spd_status spd_net_gradient(const float *d_params, const float *d_blocks, const 
 spd_status spd_net_adam(float *d_params, float *d_m, float *d_v, const float *d_grad_sum,
                         int64_t n_blocks, float lr, int32_t step, spd_stream_t stream);
 
+/* Flagged blocks: appends to d_list (device int64[cap]) the ids i < n with
+ * d_logits[i] > threshold, in no fixed order, and writes their number to
+ * *d_count (device int64; the full number, also when it exceeds cap, in which
+ * case only cap ids are written). */
+spd_status spd_net_select(const float *d_logits, int64_t n, float threshold, int64_t *d_list, int64_t cap,
+                          int64_t *d_count, spd_stream_t stream);
+/* Compact copy of blocks of a series for a restricted search: row k of d_out
+ * (device [n][ld_out] of dtype; 16-byte aligned, ld_out * sample size a
+ * multiple of 16) holds samples b * block - left .. b * block - left + width - 1
+ * of row r of d_x, where (r, b) = (d_list[k] / bpr, d_list[k] % bpr) and
+ * bpr = ceil(nt / block).  Positions outside [0, nt), the padding columns
+ * width .. ld_out - 1 and rows of ids outside [0, ndm * bpr) are -inf, the value
+ * the search treats as past the end of a row.  d_x as spd_execute.  F32, F16
+ * and BF16 (u8 has no -inf: SPD_ERR_UNSUPPORTED). */
+spd_status spd_net_gather(const void *d_x, int32_t dtype, int64_t ndm, int64_t nt, int64_t ld,
+                          const int64_t *d_list, int64_t n, int32_t block, int32_t left, int32_t width,
+                          void *d_out, int64_t ld_out, spd_stream_t stream);
+
 /*
  * Wait for the stream and report any asynchronous CUDA error of work queued
  * on it (SPD_ERR_CUDA), else SPD_OK.

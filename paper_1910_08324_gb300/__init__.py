@@ -35,6 +35,8 @@ from ._binding import (  # noqa: F401
     load_library,
     net_adam,
     net_decimate,
+    net_gather,
+    net_select,
     net_forward,
     net_gradient,
     noise_stats,

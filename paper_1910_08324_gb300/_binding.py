@@ -59,7 +59,7 @@ _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_des
             "spd_plan_set_segment", "spd_batch_create", "spd_batch_destroy", "spd_batch_set_segment",
             "spd_batch_set_wait_ns", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
             "spd_batch_candidates", "spd_net_decimate", "spd_net_forward", "spd_net_gradient",
-            "spd_net_adam"]
+            "spd_net_adam", "spd_net_select", "spd_net_gather"]
 
 
 def library_path() -> str:
@@ -97,6 +97,8 @@ def load_library():
         lib.spd_net_forward.argtypes = [vp, vp, i64, vp, vp]
         lib.spd_net_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         lib.spd_net_adam.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, i32, vp]
+        lib.spd_net_select.argtypes = [vp, i64, ctypes.c_float, vp, i64, vp, vp]
+        lib.spd_net_gather.argtypes = [vp, i32, i64, i64, i64, vp, i64, i32, i32, i32, vp, i64, vp]
         lib.spd_batch_create.argtypes = [ctypes.POINTER(_Desc), vp, vp, vp, i32, ctypes.POINTER(vp)]
         lib.spd_batch_destroy.argtypes = [vp]
         lib.spd_batch_set_segment.argtypes = [vp, i32]
@@ -327,9 +329,24 @@ def _ptr(t):
     return 0 if t is None else int(t.data_ptr())
 
 
+def _need(where: str, plan: Plan, **tensors):
+    """Raise SPD_ERR_BUFFER_TOO_SMALL unless every given tensor is contiguous and
+    holds the plan's ndm * ld elements (the C calls take bare pointers and
+    cannot check this themselves)."""
+    n = plan.ndm * plan.ld
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        if not t.is_contiguous() or t.numel() < n:
+            raise SpdError(5, "%s: %s needs %d contiguous elements ([ndm][ld] = [%d][%d]), got %s %s"
+                           % (where, name, n, plan.ndm, plan.ld, tuple(t.shape),
+                              "contiguous" if t.is_contiguous() else "strided"))
+
+
 def execute(plan: Plan, x, mu, sigma, snr, width_idx, ws, stream=None, noise_mode: int = 0):
     """Run ``spd_execute`` on torch CUDA tensors (x: float32 [ndm, ld]; snr float32;
     width_idx int16/uint16; mu, sigma float32 [ndm], or [ndm, n_widths] with noise_mode 1)."""
+    _need("execute", plan, x=x, snr=snr, width_idx=width_idx)
     spd_execute(plan, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(snr), _ptr(width_idx), _ptr(ws),
                 ws.numel() * ws.element_size(), _stream(stream), noise_mode=noise_mode)
 
@@ -337,6 +354,7 @@ def execute(plan: Plan, x, mu, sigma, snr, width_idx, ws, stream=None, noise_mod
 def candidates(plan: Plan, snr, width_idx, threshold: float, peak_radius: int, out, count, ws,
                use_tile_max: bool = False, stream=None):
     """Run ``spd_candidates``; ``out`` is a uint8 CUDA tensor of cap*24 bytes, ``count`` int64[1]."""
+    _need("candidates", plan, snr=snr, width_idx=width_idx)
     cap = 0 if out is None else out.numel() * out.element_size() // CANDIDATE_DTYPE.itemsize
     spd_candidates(plan, _ptr(snr), _ptr(width_idx), threshold, peak_radius, _ptr(out), cap,
                    _ptr(count), _ptr(ws), ws.numel() * ws.element_size(), int(bool(use_tile_max)),
@@ -346,6 +364,7 @@ def candidates(plan: Plan, snr, width_idx, threshold: float, peak_radius: int, o
 def search(plan: Plan, x, mu, sigma, snr, width_idx, threshold: float, peak_radius: int, out, count,
            ws, stream=None, noise_mode: int = 0):
     """Run ``spd_search`` (search + candidates) on torch CUDA tensors."""
+    _need("search", plan, x=x, snr=snr, width_idx=width_idx)
     cap = 0 if out is None else out.numel() * out.element_size() // CANDIDATE_DTYPE.itemsize
     spd_search(plan, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(snr), _ptr(width_idx), threshold,
                peak_radius, _ptr(out), cap, _ptr(count), _ptr(ws), ws.numel() * ws.element_size(),
@@ -356,6 +375,7 @@ def noise_stats(plan: Plan, x, mu_out, sigma_out, ws, outlier_sigma: float = 2.0
                 max_passes: int = 10, stream=None):
     """Run ``spd_noise_stats``: fills float32 [ndm, n_widths] mu_out, sigma_out (the
     table of ``execute(..., noise_mode=1)``)."""
+    _need("noise_stats", plan, x=x)
     spd_noise_stats(plan, _ptr(x), outlier_sigma, max_passes, _ptr(mu_out), _ptr(sigma_out),
                     _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
 
@@ -395,6 +415,29 @@ def net_gradient(params, blocks, labels, grad_sum, loss_sum, stream=None):
 def net_adam(params, m, v, grad_sum, n_blocks: int, lr: float, step: int, stream=None):
     _check(load_library().spd_net_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad_sum), int(n_blocks),
                                        float(lr), int(step), _stream(stream) or None), "spd_net_adam")
+
+
+def net_select(logits, threshold: float, out_list, count, stream=None):
+    """Ids of the logits above ``threshold`` into the int64 tensor ``out_list`` (in no
+    fixed order); their number into the int64[1] tensor ``count``."""
+    _check(load_library().spd_net_select(_ptr(logits), logits.numel(), float(threshold), _ptr(out_list),
+                                         out_list.numel(), _ptr(count), _stream(stream) or None),
+           "spd_net_select")
+
+
+def net_gather(x, block_ids, n: int, block: int, left: int, width: int, out, dtype: int = SPD_F32, nt=None,
+               stream=None):
+    """Rows of ``out`` ([n, ld_out] of the dtype's storage) = samples
+    b * block - left .. + width - 1 of the rows of ``x`` ([ndm, ld]) named by the
+    first ``n`` ids r * ceil(nt / block) + b of ``block_ids``; -inf elsewhere."""
+    ndm, ld = x.shape
+    nt = ld if nt is None else int(nt)
+    if n > block_ids.numel() or out.shape[0] < n:
+        raise SpdError(5, "net_gather: %d ids for a list of %d and %d output rows" % (n, block_ids.numel(),
+                                                                                      out.shape[0]))
+    _check(load_library().spd_net_gather(_ptr(x), int(dtype), ndm, nt, ld, _ptr(block_ids), int(n), int(block),
+                                         int(left), int(width), _ptr(out), out.shape[1],
+                                         _stream(stream) or None), "spd_net_gather")
 
 
 def records(out_tensor, count: int):

@@ -772,6 +772,32 @@ spd_status spd_net_adam(float* d_params, float* d_m, float* d_v, const float* d_
                                          reinterpret_cast<cudaStream_t>(stream)));
 }
 
+spd_status spd_net_select(const float* d_logits, int64_t n, float threshold, int64_t* d_list, int64_t cap,
+                          int64_t* d_count, spd_stream_t stream) {
+  if (!d_logits || !d_count || n < 0 || cap < 0 || (cap > 0 && !d_list) || std::isnan(threshold) ||
+      ((uintptr_t)d_logits % 4) || ((uintptr_t)d_list % 8) || ((uintptr_t)d_count % 8))
+    return SPD_ERR_INVALID_ARG;
+  return check_cuda(spd::launch_net_select(d_logits, n, threshold, d_list, cap, d_count,
+                                           reinterpret_cast<cudaStream_t>(stream)));
+}
+
+spd_status spd_net_gather(const void* d_x, int32_t dtype, int64_t ndm, int64_t nt, int64_t ld,
+                          const int64_t* d_list, int64_t n, int32_t block, int32_t left, int32_t width,
+                          void* d_out, int64_t ld_out, spd_stream_t stream) {
+  if (dtype == SPD_U8) return SPD_ERR_UNSUPPORTED;  // no -inf code
+  if (!d_x || !d_out || dtype < SPD_F32 || dtype > SPD_BF16 || n < 0 || (n > 0 && !d_list))
+    return SPD_ERR_INVALID_ARG;
+  if (ndm < 1 || nt < 1 || ld < nt || block < 1 || left < 0 || width < 1 || ld_out < width ||
+      n > (int64_t)INT32_MAX || ld_out > ((int64_t)1 << 25))
+    return SPD_ERR_INVALID_ARG;
+  const int esize = dtype_size(dtype);
+  if (((uintptr_t)d_x % esize) || ((uintptr_t)d_list % 8) || ((uintptr_t)d_out % 16) || ((ld_out * esize) % 16))
+    return SPD_ERR_INVALID_ARG;
+  const bool vec = (uintptr_t)d_x % 16 == 0 && (ld * esize) % 16 == 0;
+  return check_cuda(spd::launch_net_gather(d_x, dtype, esize, ndm, nt, ld, d_list, n, block, left, width, d_out,
+                                           ld_out, vec, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 spd_status spd_sync_status(const spd_plan* plan, spd_stream_t stream) {
   if (!plan) return SPD_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));

@@ -167,6 +167,11 @@ cudaError_t launch_net_adam(float* P, float* M, float* V, const float* G, int64_
                             cudaStream_t s);
 cudaError_t launch_net_decimate(const void* x, int dtype, int esize, int64_t ndm, int64_t nt, int64_t ld,
                                 bool vec, const float* mu, const float* sigma, float* out, cudaStream_t s);
+cudaError_t launch_net_select(const float* logits, int64_t n, float thr, int64_t* list, int64_t cap,
+                              int64_t* count, cudaStream_t s);
+cudaError_t launch_net_gather(const void* x, int dtype, int esize, int64_t ndm, int64_t nt, int64_t ld,
+                              const int64_t* list, int64_t n, int block, int left, int width, void* out,
+                              int64_t ld_out, bool vec, cudaStream_t s);
 cudaError_t launch_boxdit_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
 cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s);

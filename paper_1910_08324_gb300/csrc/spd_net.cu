@@ -350,6 +350,68 @@ __global__ void __launch_bounds__(256) net_decimate_kernel(const void* __restric
   out[i] = (s - 16.f * mu[r]) / (4.f * sigma[r]);
 }
 
+// Flagged blocks: the ids i < n with logits[i] > thr, appended to list (one
+// atomic per warp; the order of the ids is not fixed) and counted in *count.
+// At most cap ids are written; *count holds the full number.
+__global__ void __launch_bounds__(256) net_select_kernel(const float* __restrict__ logits, int64_t n, float thr,
+                                                          int64_t* __restrict__ list, int64_t cap,
+                                                          unsigned long long* __restrict__ count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool f = i < n && logits[i] > thr;
+  const unsigned m = __ballot_sync(0xffffffffu, f);
+  if (m == 0u) return;  // uniform across the warp
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  unsigned long long base = 0ull;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (f) {
+    const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+    if (slot < (unsigned long long)cap) list[slot] = i;
+  }
+}
+
+// Gather of flagged blocks: out[k][c] = x[r][b * block - left + c] for c < width,
+// with (r, b) = (list[k] / bpr, list[k] % bpr), and -inf where that position lies
+// outside [0, nt) or c >= width (the row padding up to ld_out).  One thread
+// writes 16 bytes; ids outside [0, ndm * bpr) give rows of -inf.
+template <int ES>
+__global__ void __launch_bounds__(256) net_gather_kernel(const unsigned char* __restrict__ x, int64_t ndm,
+                                                          int64_t nt, int64_t ld, int64_t bpr, int block,
+                                                          int left, int width, const int64_t* __restrict__ list,
+                                                          unsigned char* __restrict__ out, int64_t ld_out, int vec,
+                                                          uint32_t neg_inf) {
+  constexpr int kPer = 16 / ES;  // samples per thread
+  const int64_t k = blockIdx.x;
+  const int64_t c0 = ((int64_t)blockIdx.y * blockDim.x + threadIdx.x) * kPer;
+  if (c0 >= ld_out) return;
+  const int64_t id = list[k];
+  const bool ok_id = id >= 0 && id < ndm * bpr;
+  const int64_t r = ok_id ? id / bpr : 0;
+  const int64_t p0 = (ok_id ? (id % bpr) * (int64_t)block : 0) - left + c0;  // source position of c0
+  unsigned char* dst = out + (k * ld_out + c0) * ES;
+  const unsigned char* src = x + (r * ld) * ES;
+  if (ok_id && vec && c0 + kPer <= width && p0 >= 0 && p0 + kPer <= nt && ((p0 * ES) & 15) == 0) {
+    *reinterpret_cast<uint4*>(dst) = __ldg(reinterpret_cast<const uint4*>(src + p0 * ES));
+    return;
+  }
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int e = 0; e < kPer; ++e) {
+    const int64_t q = p0 + e;
+    const bool in = ok_id && c0 + e < width && q >= 0 && q < nt;
+    uint32_t v;
+    if (ES == 4)
+      v = in ? __ldg(reinterpret_cast<const uint32_t*>(src) + q) : neg_inf;
+    else
+      v = in ? (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(src) + q) : neg_inf;
+    if (ES == 4)
+      w[e] = v;
+    else
+      w[e >> 1] |= (v & 0xffffu) << (16 * (e & 1));
+  }
+  *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 size_t net_smem(bool grad) {
   size_t s = ((sizeof(NetSmem) + 15) / 16) * 16;
   return grad ? s + sizeof(GradSmem) : s;
@@ -396,6 +458,35 @@ cudaError_t launch_net_adam(float* P, float* M, float* V, const float* G, int64_
                             cudaStream_t s) {
   const float c1 = 1.f / (1.f - powf(0.9f, (float)step)), c2 = 1.f / (1.f - powf(0.999f, (float)step));
   net_adam_kernel<<<(kNetParams + 255) / 256, 256, 0, s>>>(P, M, V, G, 1.f / (float)nb, lr, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_select(const float* logits, int64_t n, float thr, int64_t* list, int64_t cap,
+                              int64_t* count, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess || n == 0) return e;
+  net_select_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(logits, n, thr, list, cap,
+                                                                reinterpret_cast<unsigned long long*>(count));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_gather(const void* x, int dtype, int esize, int64_t ndm, int64_t nt, int64_t ld,
+                              const int64_t* list, int64_t n, int block, int left, int width, void* out,
+                              int64_t ld_out, bool vec, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t per_row = ld_out * esize / 16;  // threads per output row
+  const dim3 grid((unsigned)n, (unsigned)((per_row + 255) / 256));
+  const int64_t bpr = (nt + block - 1) / block;
+  const auto* xs = static_cast<const unsigned char*>(x);
+  auto* o = static_cast<unsigned char*>(out);
+  if (esize == 4) {
+    net_gather_kernel<4><<<grid, 256, 0, s>>>(xs, ndm, nt, ld, bpr, block, left, width, list, o, ld_out,
+                                              vec ? 1 : 0, 0xff800000u);
+  } else {
+    const uint32_t ninf = dtype == SPD_BF16 ? 0xff80u : 0xfc00u;  // -inf of bf16 / f16
+    net_gather_kernel<2><<<grid, 256, 0, s>>>(xs, ndm, nt, ld, bpr, block, left, width, list, o, ld_out,
+                                              vec ? 1 : 0, ninf);
+  }
   return cudaGetLastError();
 }
 

@@ -1,0 +1,306 @@
+"""Block proposals: a full-resolution search restricted to the blocks that a
+trained network flags.
+
+A block is 4096 input samples of one row; the network reads it as 256
+samples after an x16 decimation.  ``flag_blocks`` decimates the series and
+scores every block (``spd_net_decimate``, ``spd_net_forward``).
+``search_flagged`` then searches the flagged blocks at full resolution.  Each
+flagged block is copied into one compact series, together with
+
+* the ``radius`` samples before it, so that the peak test of its first start
+  sees its left neighbours;
+* the samples that a boxcar starting in the block can reach (up to the plan's
+  widest width).
+
+Samples past the row's ends are -inf, the same value the kernels use past a
+row's end, so boxcars that would need them never count.  The compact series
+is searched with one plan and the row's noise statistics.  Candidates that
+start inside a block are then mapped back to (row, start).
+
+``train`` fits the network with the gradient and Adam kernels, and
+``label_blocks`` makes its labels.  A block is positive iff it holds the
+start of an injected pulse that the plain search recovers.  ``match_pulses``
+is the shared yardstick: it pairs candidates with injected pulses.
+
+All arithmetic on samples runs in the library's kernels.  This module only
+orders the calls, moves blocks with torch indexing and does host bookkeeping
+on candidate lists.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+
+BLOCK = 4096      # input samples per block
+DECIMATION = 16   # the network reads BLOCK / DECIMATION = 256 samples per block
+
+
+def flag_blocks(params, x, mu, sigma, dtype: int = B.SPD_F32, threshold: float = 0.0, stream=None):
+    """Logits [ndm, nt // 4096] of the blocks of ``x`` ([ndm, nt], nt a multiple of
+    4096, stored as ``dtype``; ``mu``/``sigma`` float32 [ndm]) and the mask
+    logit > threshold."""
+    import torch
+    ndm, nt = x.shape
+    if nt % BLOCK:
+        raise ValueError("the series length must be a multiple of %d" % BLOCK)
+    d = torch.empty((ndm, nt // DECIMATION), dtype=torch.float32, device=x.device)
+    B.net_decimate(x, mu, sigma, d, dtype=dtype, stream=stream)
+    logits = torch.empty(ndm * (nt // BLOCK), dtype=torch.float32, device=x.device)
+    B.net_forward(params, d.view(-1, BLOCK // DECIMATION), logits, stream=stream)
+    logits = logits.view(ndm, nt // BLOCK)
+    return logits, logits > threshold
+
+
+def decimated_blocks(x, mu, sigma, dtype: int = B.SPD_F32, stream=None):
+    """The network's input: float32 [ndm * nt / 4096, 256] decimated blocks of ``x``."""
+    import torch
+    ndm, nt = x.shape
+    d = torch.empty((ndm, nt // DECIMATION), dtype=torch.float32, device=x.device)
+    B.net_decimate(x, mu, sigma, d, dtype=dtype, stream=stream)
+    return d.view(-1, BLOCK // DECIMATION)
+
+
+def plan_geometry(grid: dict):
+    """(widest width, largest start separation) of a plan grid (``spd_plan_create``
+    keywords without the shape)."""
+    p = B.spd_plan_create(ndm=1, nt=1 << 16, **grid)
+    try:
+        w, sep = p.widths()
+        return int(w[-1]), int(sep.max())
+    finally:
+        p.close()
+
+
+def select_blocks(logits, threshold: float = 0.0, stream=None):
+    """Device list (int64, sorted) of the ids row * blocks_per_row + block of the
+    blocks whose logit exceeds ``threshold`` (``spd_net_select``)."""
+    import torch
+    flat = logits.reshape(-1)
+    ids = torch.empty(flat.numel(), dtype=torch.int64, device=flat.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=flat.device)
+    B.net_select(flat, threshold, ids, cnt, stream=stream)
+    n = int(cnt.item())
+    return torch.sort(ids[:n]).values
+
+
+def gather_blocks(x, ids, left: int, right: int, dtype: int, ld_align: int = 64, stream=None):
+    """Compact copy of the blocks ``ids`` (``spd_net_gather``): [n, ld] rows holding
+    ``left`` samples before each block, the block and ``right`` samples after it
+    (-inf outside the series); ``ld`` rounds the row length up to ``ld_align``
+    samples so that rows stay 16-byte aligned.  Returns (rows, row length)."""
+    import torch
+    width = left + BLOCK + right
+    ld = -(-width // ld_align) * ld_align
+    out = torch.empty((ids.numel(), ld), dtype=x.dtype, device=x.device)
+    B.net_gather(x, ids, ids.numel(), BLOCK, left, width, out, dtype=dtype, stream=stream)
+    return out, width
+
+
+def search_flagged(x, ids, mu, sigma, grid: dict, threshold: float = 6.0, radius: int = 1,
+                   cap: int = 1 << 22, noise_mode: int = 0, stream=None):
+    """Search the blocks ``ids`` (``select_blocks``) of ``x`` ([ndm, nt]) with the
+    plan grid ``grid`` (``spd_plan_create`` keywords: algo, s_end, boxdit_lmax,
+    ..., dtype).  ``mu``/``sigma`` are the full series' statistics: [ndm] (white)
+    or [ndm, n_widths] of the same grid (``noise_mode`` 1).  The context before a
+    block is a whole number of the grid's largest start separation, so every
+    level's starts fall where they fall in a search of the whole row and each
+    block gets the outputs the plain search gives it.  Returns the candidate
+    records (numpy, rows and starts of ``x``, sorted by row and start)."""
+    import torch
+    ndm, nt = x.shape
+    n = ids.numel()
+    if n == 0:
+        return np.zeros(0, B.CANDIDATE_DTYPE)
+    lend, sep = plan_geometry(grid)
+    if BLOCK % sep:
+        raise ValueError("grid start separation %d does not divide the %d-sample block" % (sep, BLOCK))
+    left = -(-max(radius, 1) // sep) * sep
+    xs, width = gather_blocks(x, ids, left, lend, grid.get("dtype", B.SPD_F32), stream=stream)
+    plan = B.spd_plan_create(ndm=n, nt=width, ld=xs.shape[1], **grid)
+    try:
+        Y = torch.empty(xs.shape, dtype=torch.float32, device=x.device)  # outputs share the row stride
+        W = torch.empty(xs.shape, dtype=torch.int16, device=x.device)
+        ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device=x.device)
+        bpr = nt // BLOCK
+        rows = ids // bpr
+        mu_r = mu[rows].contiguous()
+        sg_r = sigma[rows].contiguous()
+        out = torch.empty(cap * B.CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device=x.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=x.device)
+        B.search(plan, xs, mu_r, sg_r, Y, W, threshold, radius, out, cnt, ws, stream=stream,
+                 noise_mode=noise_mode)
+        k = int(cnt.item())
+        if k > cap:
+            raise B.SpdError(5, "search_flagged: %d candidates exceed cap %d" % (k, cap))
+        rec = B.records(out, k).copy()
+    finally:
+        plan.close()
+    rec = rec[(rec["start"] >= left) & (rec["start"] < left + BLOCK)]
+    ids_h = ids.cpu().numpy()
+    blk = ids_h[rec["row"]]
+    rec["start"] = rec["start"] - left + (blk % bpr) * BLOCK
+    rec["row"] = blk // bpr
+    return rec[np.lexsort((rec["start"], rec["row"]))]
+
+
+def propose_and_search(params, x, mu_tab, sigma_tab, grid: dict, logit_threshold: float = 0.0,
+                       threshold: float = 6.0, radius: int = 1, cap: int = 1 << 22, stream=None):
+    """The proposal path: decimate and score every block, select those above
+    ``logit_threshold`` and search them with per-width noise tables ``mu_tab``,
+    ``sigma_tab`` ([ndm, n_widths] of ``grid``; the network reads the width-1
+    entries).  Returns (records, number of searched blocks)."""
+    dtype = grid.get("dtype", B.SPD_F32)
+    logits, _ = flag_blocks(params, x, mu_tab[:, 0].contiguous(), sigma_tab[:, 0].contiguous(), dtype=dtype,
+                            stream=stream)
+    ids = select_blocks(logits, logit_threshold, stream=stream)
+    rec = search_flagged(x, ids, mu_tab, sigma_tab, grid, threshold, radius, cap, noise_mode=1, stream=stream)
+    return rec, ids.numel()
+
+
+def score(rec, pulses, snr_judge, ndm: int, nt: int, judge_threshold: float = 6.0):
+    """Detection figures of candidate records against injected pulses whose SNR
+    under the ideal search is ``snr_judge`` (``pulse_snr`` with the exhaustive
+    grid): recall of the pulses the ideal search finds (SNR >= judge_threshold),
+    overall and by width class; the mean SNR loss 1 - SNR / ideal SNR of the
+    recalled ones; and the false alarms, candidates starting in quiet blocks
+    (neither the block nor the next one holds a pulse, so no boxcar starting
+    there reaches a pulse)."""
+    best, _ = match_pulses(rec, pulses)
+    found = snr_judge >= judge_threshold
+    det = found & (best > 0)
+    bpr = nt // BLOCK
+    busy = np.zeros(ndm * bpr + 1, bool)
+    b = pulses["row"].astype(np.int64) * bpr + pulses["start"] // BLOCK
+    busy[b] = True
+    busy[(b - 1)[pulses["start"] // BLOCK > 0]] = True  # the block before, in the same row
+    cb = rec["row"].astype(np.int64) * bpr + rec["start"] // BLOCK
+    out = {"pulses": int(len(pulses)), "judge_found": int(found.sum()),
+           "recall": float(det.sum() / max(found.sum(), 1)),
+           "snr_loss": float(np.mean(1.0 - best[det] / snr_judge[det])) if det.any() else float("nan"),
+           "false_alarms": int((~busy[cb]).sum()), "candidates": int(len(rec))}
+    for lo, hi in ((1, 16), (16, 256), (256, 1 << 30)):
+        s = found & (pulses["width"] >= lo) & (pulses["width"] < hi)
+        out["recall_w%d_%d" % (lo, min(hi, 4096))] = float(det[s].sum() / max(s.sum(), 1))
+    return out
+
+
+def match_pulses(rec, pulses, width_ratio: float = 4.0):
+    """Pair candidate records with injected pulses.  A candidate matches a pulse
+    (row, start s0, width w) when it lies in the same row, starts in
+    [s0 - w, s0 + w] and its width lies within a factor ``width_ratio`` of w.
+    Returns (best matched SNR per pulse, 0 where none; bool per candidate: it
+    matches some pulse)."""
+    best = np.zeros(len(pulses), np.float64)
+    hit = np.zeros(len(rec), bool)
+    if len(rec) == 0 or len(pulses) == 0:
+        return best, hit
+    span = np.int64(1) << 40
+    key = rec["row"].astype(np.int64) * span + rec["start"].astype(np.int64)
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    pr = pulses["row"].astype(np.int64)
+    ps = pulses["start"].astype(np.int64)
+    pw = pulses["width"].astype(np.int64)
+    lo = np.searchsorted(ks, pr * span + np.maximum(ps - pw, 0), side="left")
+    hi = np.searchsorted(ks, pr * span + ps + pw, side="right")
+    cnt = hi - lo
+    tot = int(cnt.sum())
+    if tot == 0:
+        return best, hit
+    pid = np.repeat(np.arange(len(pulses)), cnt)
+    first = np.repeat(lo - np.concatenate(([0], np.cumsum(cnt)[:-1])), cnt)
+    cid = order[first + np.arange(tot)]
+    cw = rec["width"][cid].astype(np.float64)
+    ok = (cw <= width_ratio * pw[pid]) & (cw * width_ratio >= pw[pid])
+    np.maximum.at(best, pid[ok], rec["snr"][cid[ok]].astype(np.float64))
+    hit[cid[ok]] = True
+    return best, hit
+
+
+def label_blocks(rec, pulses, ndm: int, nt: int):
+    """Block labels [ndm * nt / 4096] (float32): 1 iff the block holds the start of
+    a pulse that some candidate of ``rec`` recovers (``match_pulses``)."""
+    y = np.zeros(ndm * (nt // BLOCK), np.float32)
+    best, _ = match_pulses(rec, pulses)
+    found = best > 0
+    y[pulses["row"][found] * (nt // BLOCK) + pulses["start"][found] // BLOCK] = 1.0
+    return y
+
+
+def train(params, X, y, steps: int, batch: int = 512, lr: float = 3e-3, seed: int = 0, m=None, v=None,
+          step0: int = 0, stream=None):
+    """``steps`` Adam steps of the network on shuffled mini-batches of the decimated
+    blocks ``X`` (float32 [n, 256]) with labels ``y`` (float32 [n]); updates
+    ``params`` (and the moments ``m``, ``v``) in place.  Returns the mean loss of
+    each step (host list)."""
+    import torch
+    dev = params.device
+    m = torch.zeros_like(params) if m is None else m
+    v = torch.zeros_like(params) if v is None else v
+    G = torch.empty_like(params)
+    L = torch.empty(1, dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    n = X.shape[0]
+    losses = torch.empty(steps, dtype=torch.float32, device=dev)
+    perm = torch.randperm(n, generator=g, device=dev)
+    pos = 0
+    for i in range(steps):
+        if pos + batch > n:
+            perm = torch.randperm(n, generator=g, device=dev)
+            pos = 0
+        idx = perm[pos:pos + batch]
+        pos += batch
+        xb = X[idx].contiguous()
+        yb = y[idx].contiguous()
+        B.net_gradient(params, xb, yb, G, L, stream=stream)
+        B.net_adam(params, m, v, G, batch, lr, step0 + i + 1, stream=stream)
+        losses[i] = L[0] / batch
+    return losses.cpu().tolist(), m, v
+
+
+def pulse_snr(x, pulses, mu, sigma, grid: dict, noise_mode: int = 1, width_ratio: float = 4.0, stream=None):
+    """SNR that a search with the plan grid ``grid`` measures for each injected
+    pulse of ``x``: the largest output SNR over starts in [s0 - w, s0 + w] whose
+    best width lies within a factor ``width_ratio`` of w (0 where none).  A
+    window from s0 - w, rounded down to the grid's largest start separation, to
+    past s0 + w, with the samples its boxcars reach, is gathered for each pulse
+    (``spd_net_gather``) and all windows are searched with one plan; ``mu`` and
+    ``sigma`` are the full series' statistics as in ``search_flagged``.  With the
+    exhaustive grid this is the ideal search's SNR of the pulse."""
+    import torch
+    if len(pulses) == 0:
+        return np.zeros(0)
+    ndm, nt = x.shape
+    dev = x.device
+    dtype = grid.get("dtype", B.SPD_F32)
+    lend, sep = plan_geometry(grid)
+    wmax = int(pulses["width"].max())
+    nst = 2 * wmax + 1 + sep
+    width = nst + lend
+    ld = -(-width // 64) * 64
+    a0 = (np.maximum(pulses["start"] - pulses["width"], 0) // sep).astype(np.int64)  # window start / sep
+    bpr = -(-nt // sep)
+    ids = torch.as_tensor(pulses["row"].astype(np.int64) * bpr + a0, device=dev)
+    xs = torch.empty((len(pulses), ld), dtype=x.dtype, device=dev)
+    B.net_gather(x, ids, len(pulses), sep, 0, width, xs, dtype=dtype, stream=stream)
+    rows = torch.as_tensor(pulses["row"].astype(np.int64), device=dev)
+    plan = B.spd_plan_create(ndm=len(pulses), nt=width, ld=ld, **grid)
+    try:
+        Y = torch.empty(xs.shape, dtype=torch.float32, device=dev)  # outputs share the row stride
+        W = torch.empty(xs.shape, dtype=torch.int16, device=dev)
+        ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device=dev)
+        B.execute(plan, xs, mu[rows].contiguous(), sigma[rows].contiguous(), Y, W, ws, stream=stream,
+                  noise_mode=noise_mode)
+        wt = torch.as_tensor(plan.widths()[0].astype(np.float64), device=dev)
+    finally:
+        plan.close()
+    off = torch.as_tensor(pulses["start"] - pulses["width"] - a0 * sep, device=dev)  # window index of s0 - w
+    pw = torch.as_tensor(pulses["width"].astype(np.float64), device=dev)
+    j = torch.arange(nst, device=dev)[None, :]
+    cw = wt[torch.clamp(W[:, :nst].long() & 0xFFFF, max=len(wt) - 1)]
+    sel = ((j >= off[:, None]) & (j <= off[:, None] + 2 * pw[:, None]) & (cw <= width_ratio * pw[:, None])
+           & (cw * width_ratio >= pw[:, None]))
+    y = torch.where(sel, Y[:, :nst].double(), torch.zeros_like(cw))
+    return torch.clamp(y.max(dim=1).values, min=0.0).cpu().numpy()

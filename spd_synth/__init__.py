@@ -208,3 +208,129 @@ def device_quantize(x, dtype: str):
     if dtype == "u8":
         return torch.clamp(torch.round(U8_OFFSET + U8_SCALE * x), 0, 255).to(torch.uint8)
     raise ValueError("unknown dtype %r" % dtype)
+
+
+# ---------------------------------------------------------------- non-white inputs (proposal workload)
+def device_red_noise(ndm: int, nt: int, seed: int, device="cuda", alpha: float = 1.0):
+    """1/f^alpha noise (power spectrum proportional to f^-alpha) per row, shaped in the
+    Fourier domain from seeded white noise and scaled to unit variance per row."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = torch.empty((ndm, nt), dtype=torch.float32, device=device)
+    f = torch.fft.rfftfreq(nt, device=device)
+    shape = torch.zeros_like(f)
+    shape[1:] = f[1:] ** (-alpha / 2.0)
+    step = max(1, (1 << 25) // max(nt, 1))
+    for r0 in range(0, ndm, step):
+        n = min(step, ndm - r0)
+        w = torch.randn((n, nt), generator=g, device=device, dtype=torch.float32)
+        v = torch.fft.irfft(torch.fft.rfft(w, dim=1) * shape, n=nt, dim=1)
+        out[r0:r0 + n] = v / v.std(dim=1, keepdim=True)
+    return out
+
+
+def zero_dm_spikes(nt: int, frac: float, seed: int) -> np.ndarray:
+    """Time indices of impulsive zero-DM interference: the same samples in every row."""
+    n = int(round(frac * nt))
+    return np.sort(rng(seed).choice(nt, n, replace=False)) if n > 0 else np.zeros(0, np.int64)
+
+
+def proposal_series(ndm: int, nt: int, seed: int, device="cuda", red: bool = True, spike_frac: float = 1e-3,
+                    spike_amp: float = 10.0):
+    """Float32 rows of white N(0,1) + (red) unit-variance 1/f noise + zero-DM spikes of spike_amp
+    noise deviations at spike_frac of the time samples.  Returns (x, sigma): the noise deviation
+    (sqrt(2) with red noise) in which pulse amplitudes and SNRs are stated."""
+    x = device_noise(ndm, nt, seed, device=device)
+    sigma = 1.0
+    if red:
+        x += device_red_noise(ndm, nt, seed + 7919, device=device)
+        sigma = math.sqrt(2.0)
+    idx = zero_dm_spikes(nt, spike_frac, seed + 104729)
+    if len(idx):
+        import torch
+        x[:, torch.as_tensor(idx, device=device)] += spike_amp * sigma
+    return x, sigma
+
+
+def device_inject_many(x, table, sigma: float = 1.0, amp=None, rows_per_chunk: int = 64):
+    """Add many rectangular pulses to a float32 device tensor ``x`` [ndm, nt] in place:
+    +a at each start and -a one past each end in an FP64 difference array, prefix-summed
+    along time (row chunks bound the temporary memory).  ``amp``: per-pulse
+    amplitudes; default the white-noise amplitude snr * sigma / sqrt(width)."""
+    import torch
+    if len(table) == 0:
+        return x
+    ndm, nt = x.shape
+    dev = x.device
+    r = torch.as_tensor(table["row"].astype(np.int64), device=dev)
+    s = torch.as_tensor(table["start"].astype(np.int64), device=dev)
+    w = torch.as_tensor(table["width"].astype(np.int64), device=dev)
+    if amp is None:
+        amp = table["snr"] * sigma / np.sqrt(table["width"].astype(np.float64))
+    a = torch.as_tensor(np.asarray(amp, np.float64), device=dev)
+    order = np.argsort(table["row"], kind="stable")
+    rows_sorted = table["row"][order].astype(np.int64)
+    order_d = torch.as_tensor(order, device=dev)
+    for r0 in range(0, ndm, rows_per_chunk):
+        n = min(rows_per_chunk, ndm - r0)
+        i0, i1 = np.searchsorted(rows_sorted, [r0, r0 + n])
+        if i1 == i0:
+            continue
+        sel = order_d[i0:i1]
+        d = torch.zeros(n * (nt + 1), dtype=torch.float64, device=dev)
+        rr = r[sel] - r0
+        d.index_add_(0, rr * (nt + 1) + s[sel], a[sel])
+        d.index_add_(0, rr * (nt + 1) + s[sel] + w[sel], -a[sel])
+        x[r0:r0 + n] += torch.cumsum(d.view(n, nt + 1), dim=1)[:, :nt].to(x.dtype)
+    return x
+
+
+def block_pulses(ndm: int, nt: int, block: int, seed: int, frac: float = 0.5,
+                 width_range=(1, 2048), snr_range=(5.0, 20.0)) -> np.ndarray:
+    """Pulse table with one pulse, in a random ``frac`` of the ``block``-sample blocks,
+    lying wholly inside its block: widths log-uniform in ``width_range``, SNRs uniform
+    in ``snr_range``.  Sorted by (row, start)."""
+    g = rng(seed)
+    nb = nt // block
+    hit = np.nonzero(g.random(ndm * nb) < frac)[0]
+    n = len(hit)
+    lo, hi = math.log(width_range[0]), math.log(width_range[1] + 1)
+    w = np.clip(np.floor(np.exp(g.uniform(lo, hi, n))), width_range[0], width_range[1]).astype(np.int64)
+    off = np.floor(g.random(n) * (block - w + 1)).astype(np.int64)
+    out = np.zeros(n, PULSE_DTYPE)
+    out["row"] = hit // nb
+    out["start"] = (hit % nb) * block + off
+    out["width"] = w
+    out["snr"] = g.uniform(snr_range[0], snr_range[1], n)
+    return out
+
+
+def red_boxcar_var(widths, nt: int, alpha: float = 1.0, device="cuda") -> np.ndarray:
+    """Expected variance of an L-sample sum of the unit-variance 1/f^alpha noise of
+    ``device_red_noise``, for each L in ``widths``: the power p_k of frequency bin k
+    (proportional to k^-alpha over k = 1..nt/2, summing to one) times the boxcar's
+    power gain (sin(pi k L / nt) / sin(pi k / nt))^2, summed over k."""
+    import torch
+    u = np.unique(np.asarray(widths, np.int64))
+    k = torch.arange(1, nt // 2 + 1, device=device, dtype=torch.float64)
+    p = k ** (-alpha)
+    p /= p.sum()
+    th = math.pi * k / nt
+    s2 = torch.sin(th) ** 2
+    out = torch.empty(len(u), dtype=torch.float64, device=device)
+    for i in range(0, len(u), 32):
+        L = torch.as_tensor(u[i:i + 32], device=device, dtype=torch.float64)
+        g = torch.sin(th[None, :] * L[:, None]) ** 2 / s2[None, :]
+        out[i:i + 32] = (g * p[None, :]).sum(dim=1)
+    return out.cpu().numpy()[np.searchsorted(u, np.asarray(widths, np.int64))]
+
+
+def proposal_amplitudes(table, nt: int, red: bool = True, device="cuda") -> np.ndarray:
+    """Per-sample amplitudes that give each pulse of ``table`` its SNR against the
+    noise of ``proposal_series`` at the pulse's own width: unit white noise plus,
+    with ``red``, unit-variance 1/f noise, so a w-sample sum has variance
+    w + red_boxcar_var(w)."""
+    w = table["width"].astype(np.float64)
+    var = w + (red_boxcar_var(table["width"], nt, device=device) if red and len(table) else 0.0)
+    return table["snr"] * np.sqrt(var) / w

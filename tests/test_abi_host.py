@@ -167,3 +167,34 @@ def test_plan_segment_rules():
     ex = spd.spd_plan_create(spd.SPD_ALGO_EXHAUSTIVE, 64, ndm=1, nt=1000)
     with pytest.raises(spd.SpdError):
         spd.spd_plan_set_segment(ex, 16384)
+
+
+def test_net_select_and_gather_validate_before_launch():
+    lib = spd.load_library()
+    # u8 has no -inf code to pad with
+    assert lib.spd_net_gather(4096, spd.SPD_U8, 1, 4096, 4096, 4096, 1, 4096, 0, 4096, 4096, 4096, None) == 2
+    # output row shorter than the copied width; misaligned output; bad dtype
+    assert lib.spd_net_gather(4096, spd.SPD_F16, 1, 4096, 4096, 4096, 1, 4096, 0, 4096, 4096, 4000, None) == 1
+    assert lib.spd_net_gather(4096, spd.SPD_F16, 1, 4096, 4096, 4096, 1, 4096, 0, 4096, 4104, 4096, None) == 1
+    assert lib.spd_net_gather(4096, 7, 1, 4096, 4096, 4096, 1, 4096, 0, 4096, 4096, 4096, None) == 1
+    # f16 rows of 4100 samples are not 16-byte multiples
+    assert lib.spd_net_gather(4096, spd.SPD_F16, 1, 4096, 4096, 4096, 1, 4096, 0, 4096, 4096, 4100, None) == 1
+    assert lib.spd_net_gather(4096, spd.SPD_F16, 1, 4096, 4096, 4096, 1, 4096, -1, 4096, 4096, 4096, None) == 1
+    assert lib.spd_net_select(4096, 16, ctypes.c_float(float("nan")), 4096, 16, 4096, None) == 1
+    assert lib.spd_net_select(4096, 16, ctypes.c_float(0.0), None, 16, 4096, None) == 1
+    assert lib.spd_net_select(4096, -1, ctypes.c_float(0.0), 4096, 16, 4096, None) == 1
+
+
+def test_torch_helpers_refuse_short_outputs():
+    """The torch-level helpers check every [ndm][ld] buffer before the C call
+    (the C calls take bare pointers)."""
+    torch = pytest.importorskip("torch")
+    plan = spd.spd_plan_create(algo=spd.SPD_ALGO_BOXDIT, s_end=64, boxdit_lmax=8, ndm=2, nt=1000, ld=1024)
+    x = torch.zeros((2, 1024))
+    ws = torch.zeros(16, dtype=torch.uint8)
+    with pytest.raises(spd.SpdError) as e:
+        spd.execute(plan, x, torch.zeros(2), torch.ones(2), torch.zeros((2, 1000)), torch.zeros((2, 1024), dtype=torch.int16), ws)
+    assert e.value.status == 5
+    with pytest.raises(spd.SpdError):
+        spd.search(plan, x[:, :1000], torch.zeros(2), torch.ones(2), torch.zeros((2, 1024)),
+                   torch.zeros((2, 1024), dtype=torch.int16), 6.0, 1, None, torch.zeros(1, dtype=torch.int64), ws)
