@@ -35,6 +35,11 @@ __host__ __device__ constexpr int next_pow2(int v) {
 // width's 1/sqrt(L).  Table noise: the width's affine map a S + b (row_noise).
 __device__ __forceinline__ float snr_of(float S, float sc) { return S * sc; }
 __device__ __forceinline__ float snr_of(float S, float2 ab) { return fmaf(S, ab.x, ab.y); }
+// The same for two sums at once (packed f32x2: identical roundings).
+__device__ __forceinline__ float2 snr_of2(float2 S, float sc) { return __fmul2_rn(S, make_float2(sc, sc)); }
+__device__ __forceinline__ float2 snr_of2(float2 S, float2 ab) {
+  return __ffma2_rn(S, make_float2(ab.x, ab.x), make_float2(ab.y, ab.y));
+}
 
 // Per-row noise constants of a search CTA (Eq. SNRlong).
 //   White noise (Eq. whitenoise): samples are normalised as z = (x - mu_r) / sigma_r
@@ -542,6 +547,16 @@ __device__ __forceinline__ void eval_window_mx(const float* w, Scale&& scale, fl
 // P[i] = w[i] + w[i+1] shared by the positions: the sum of an even number m of
 // blocks extends the one of m - 2 by P[r + m - 2], an odd count adds one block
 // to the even sum below it; odd counts outside the set are never formed.
+// Coded candidate of rank RK into v[RK] (-inf when PARTIAL and RK >= n_used, RK > 0).
+template <int B, bool PARTIAL, int RK, int NC>
+__device__ __forceinline__ void enc_post(float x, int code0, int n_used, float (&v)[NC]) {
+  const float c = enc_w<B>(x, code0 - RK);
+  if constexpr (PARTIAL && RK > 0)
+    v[RK] = RK < n_used ? c : ninf();
+  else
+    v[RK] = c;
+}
+
 template <int NP, int MMAX, class Pred, int B, bool PARTIAL, class Scale>
 __device__ __forceinline__ void eval_window_enc(const float* w, int n_used, Scale&& scale, int code0,
                                                 float (&out)[NP]) {
@@ -553,35 +568,57 @@ __device__ __forceinline__ void eval_window_enc(const float* w, int n_used, Scal
       constexpr int i = decltype(I)::value;
       P[i] = w[i] + w[i + 1];
     });
-  static_for<0, NP>([&](auto R) {
-    constexpr int r = decltype(R)::value;
-    float v[NC];
-    float S = 0.0f, Se = 0.0f;  // running sum; pairs: the sum of the last even count
-    static_for<1, MMAX + 1>([&](auto M) {
-      constexpr int m = decltype(M)::value;
-      float Sm;
-      if constexpr (!PAIRS) {
-        S += w[r + m - 1];
-        Sm = S;
-      } else if constexpr ((m & 1) == 0) {
-        Se = (m == 2) ? P[r] : Se + P[r + m - 2];
-        Sm = Se;
-      } else if constexpr (Pred::in(m)) {
-        Sm = (m == 1) ? w[r] : Se + w[r + m - 1];
-      } else {
-        Sm = 0.0f;  // not formed
-      }
-      if constexpr (Pred::in(m)) {
-        constexpr int rk = Pred::rank(m);
-        const float x = enc_w<B>(snr_of(Sm, scale(M)), code0 - rk);
-        if constexpr (PARTIAL && rk > 0)
-          v[rk] = rk < n_used ? x : ninf();
-        else
-          v[rk] = x;
-      }
+  if constexpr (PAIRS && (NP % 2) == 0) {
+    // two positions (r, r + 1) at a time in packed f32x2 arithmetic: the same
+    // roundings as the scalar form, half the add and scale instructions.  Their
+    // operands are aligned pairs: (P[r + m - 2], P[r + m - 1]) and
+    // (w[r + m - 1], w[r + m]) with r even and m even resp. odd.
+    static_for<0, NP / 2>([&](auto R2) {
+      constexpr int r = 2 * decltype(R2)::value;
+      float v0[NC], v1[NC];
+      float2 Se = make_float2(0.0f, 0.0f);
+      static_for<1, MMAX + 1>([&](auto M) {
+        constexpr int m = decltype(M)::value;
+        float2 Sm = make_float2(0.0f, 0.0f);
+        if constexpr ((m & 1) == 0) {
+          Se = (m == 2) ? make_float2(P[r], P[r + 1]) : __fadd2_rn(Se, make_float2(P[r + m - 2], P[r + m - 1]));
+          Sm = Se;
+        } else if constexpr (Pred::in(m)) {
+          Sm = (m == 1) ? make_float2(w[r], w[r + 1]) : __fadd2_rn(Se, make_float2(w[r + m - 1], w[r + m]));
+        }
+        if constexpr (Pred::in(m)) {
+          const float2 x = snr_of2(Sm, scale(M));
+          enc_post<B, PARTIAL, Pred::rank(m)>(x.x, code0, n_used, v0);
+          enc_post<B, PARTIAL, Pred::rank(m)>(x.y, code0, n_used, v1);
+        }
+      });
+      out[r] = tree_max<NC>(v0);
+      out[r + 1] = tree_max<NC>(v1);
     });
-    out[r] = tree_max<NC>(v);
-  });
+  } else {
+    static_for<0, NP>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      float v[NC];
+      float S = 0.0f, Se = 0.0f;  // running sum; pairs: the sum of the last even count
+      static_for<1, MMAX + 1>([&](auto M) {
+        constexpr int m = decltype(M)::value;
+        float Sm;
+        if constexpr (!PAIRS) {
+          S += w[r + m - 1];
+          Sm = S;
+        } else if constexpr ((m & 1) == 0) {
+          Se = (m == 2) ? P[r] : Se + P[r + m - 2];
+          Sm = Se;
+        } else if constexpr (Pred::in(m)) {
+          Sm = (m == 1) ? w[r] : Se + w[r + m - 1];
+        } else {
+          Sm = 0.0f;  // not formed
+        }
+        if constexpr (Pred::in(m)) enc_post<B, PARTIAL, Pred::rank(m)>(snr_of(Sm, scale(M)), code0, n_used, v);
+      });
+      out[r] = tree_max<NC>(v);
+    });
+  }
 }
 
 // Like eval_window_mx for one position, but only ranks below n_used count
