@@ -44,6 +44,7 @@ constexpr int kRing0 = 4;             // first coarse (ring) level
 constexpr int kChunkLog = 11;         // log2(kC): levels above it span several chunks
 static_assert((1 << kChunkLog) == kC, "chunk must be 2^11");
 constexpr int kResHi = 256;           // RES slots of levels > kChunkLog start here
+constexpr int kTailWarp = 2;          // the warp that copies the lookahead tails
 
 template <int D, int PL>
 struct IgS {
@@ -62,6 +63,7 @@ struct IgS {
   static constexpr int TL1 = 4 * NW1 - 4;
   static constexpr int TL2 = 2 * NW2 - 2;
   static constexpr int TL3 = NW3 - 1;
+  static constexpr int TLALL = TLA + TLB + TL1 + TL2 + TL3;  // tail values per chunk
   static constexpr int NWQ = cdiv(3 + MMAX, 4);  // float4 window of a coarse quad (4 positions)
   static constexpr int MIR = 4 * NWQ;            // mirrored ring entries: no window ever wraps
   // Grids with at most 32 widths (every plan of these (D, P) up to the widest
@@ -124,6 +126,30 @@ struct IgDyn {
     total = o;
   }
 };
+
+// Tail value i of a chunk (levels 0A, 0B, 1, 2, 3 in turn): its offset src in
+// the buffer of the previous chunk (that chunk's head) and dst in the chunk's
+// own buffer (past the chunk's values).
+template <class S, class FX>
+__device__ __forceinline__ void tail_offsets(int i, int& src, int& dst) {
+  if (i < S::TLA) {
+    src = i;
+    dst = kC / 2 + i;
+  } else if ((i -= S::TLA) < S::TLB) {
+    src = FX::OB + i;
+    dst = FX::OB + kC / 2 + i;
+  } else if ((i -= S::TLB) < S::TL1) {
+    src = FX::O1 + i;
+    dst = FX::O1 + kC / 2 + i;
+  } else if ((i -= S::TL1) < S::TL2) {
+    src = FX::O2 + i;
+    dst = FX::O2 + kC / 4 + i;
+  } else {
+    i -= S::TL2;
+    src = FX::O3 + i;
+    dst = FX::O3 + kC / 8 + i;
+  }
+}
 
 template <int D, int PL, bool COARSE, bool TABLE>
 __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U, float* smem) {
@@ -265,13 +291,13 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
   auto build = [&](int k, const Raw8& raw) {
     const int ar = a0 - k * kC;
     const int buf = k % FX::NBUF;
-    if (k > 0) {
+    if (k > 0 && warp == kTailWarp) {  // lookahead tails, one value per lane of one warp
       const int pb = (k - 1) % FX::NBUF;
-      if (t < S::TLA) smem[FX::f0(buf) + kC / 2 + t] = smem[FX::f0(pb) + t];
-      if (t < S::TLB) smem[FX::f0(buf) + FX::OB + kC / 2 + t] = smem[FX::f0(pb) + FX::OB + t];
-      if (t < S::TL1) smem[FX::f1(buf) + kC / 2 + t] = smem[FX::f1(pb) + t];
-      if (t < S::TL2) smem[FX::f2(buf) + kC / 4 + t] = smem[FX::f2(pb) + t];
-      if (t < S::TL3) smem[FX::f3(buf) + kC / 8 + t] = smem[FX::f3(pb) + t];
+      for (int i = lane; i < S::TLALL; i += 32) {
+        int src, dst;
+        tail_offsets<S, FX>(i, src, dst);
+        smem[buf * FX::FB + dst] = smem[pb * FX::FB + src];
+      }
     }
     float4 v0, v1;
     cvt8(raw, ar + 8 * t, nrel, dt, mu, inv, v0, v1);
