@@ -387,10 +387,10 @@ spd_status spd_net_gradient(const float *d_params, const float *d_blocks, const 
 spd_status spd_net_adam(float *d_params, float *d_m, float *d_v, const float *d_grad_sum,
                         int64_t n_blocks, float lr, int32_t step, spd_stream_t stream);
 
-/* Flagged blocks: appends to d_list (device int64[cap]) the ids i < n with
- * d_logits[i] > threshold, in no fixed order, and writes their number to
- * *d_count (device int64; the full number, also when it exceeds cap, in which
- * case only cap ids are written). */
+/* Flagged blocks: writes to d_list (device int64[cap]) the ids i < n with
+ * d_logits[i] > threshold in increasing order, and their number to *d_count
+ * (device int64; the full number, also when it exceeds cap, in which case only
+ * the first cap ids are written). */
 spd_status spd_net_select(const float *d_logits, int64_t n, float threshold, int64_t *d_list, int64_t cap,
                           int64_t *d_count, spd_stream_t stream);
 /* Compact copy of blocks of a series for a restricted search: row k of d_out

@@ -312,12 +312,12 @@ spd_plan range_plan(const spd_batch& b, int r) {
 }  // namespace
 
 namespace spd {
-cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int* sms) {
+cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int* sms, int threads) {
   struct Entry {
     const void* k;
     int dev;
     size_t smem;
-    int per_sm, sms;
+    int threads, per_sm, sms;
   };
   static std::mutex mu;
   static std::vector<Entry> cache;
@@ -327,17 +327,17 @@ cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int*
   {
     std::lock_guard<std::mutex> lock(mu);
     for (const Entry& c : cache)
-      if (c.k == kernel && c.dev == dev && c.smem == smem) {
+      if (c.k == kernel && c.dev == dev && c.smem == smem && c.threads == threads) {
         *per_sm = c.per_sm;
         *sms = c.sms;
         return cudaSuccess;
       }
   }
-  Entry c{kernel, dev, smem, 0, 0};
+  Entry c{kernel, dev, smem, threads, 0, 0};
   if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   if ((e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, kernel, spd::kThreads, smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, kernel, threads, smem)) != cudaSuccess)
     return e;
   std::lock_guard<std::mutex> lock(mu);
   cache.push_back(c);

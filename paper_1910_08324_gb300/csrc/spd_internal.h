@@ -153,10 +153,11 @@ cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream
 size_t igrid_smem_bytes(const spd_plan& plan, bool table);
 cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
-// Shared-memory attribute, CTAs per SM and SM count of a persistent kernel,
-// set and queried on the first call per (kernel, device, shared memory) and
+// Shared-memory attribute, CTAs per SM (of `threads` threads each) and SM count
+// of a persistent kernel, set and queried on the first call per (kernel, device,
+// shared memory, threads) and
 // cached, so that later launches (e.g. during stream capture) make no queries.
-cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int* sms);
+cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int* sms, int threads = kThreads);
 cudaError_t launch_igrid_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 // proposal network (spd_net.cu)
 int net_param_count();

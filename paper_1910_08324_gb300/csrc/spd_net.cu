@@ -37,9 +37,11 @@ constexpr int WS = 24;  // bf16 per weight row
 
 struct NetSmem {
   float w1[NC * NK], b1[NC], b2[NC], b3[NC], w4[NC], b4;
-  __nv_bfloat16 w2[NK][NC][WS], w3[NK][NC][WS];  // [tap][out][in]
-  float x[NPP];
-  __nv_bfloat16 a1[NPP][AS], a2[NPP][AS];
+  alignas(16) __nv_bfloat16 w2[NK][NC][WS];  // [tap][out][in]; 16-byte rows for ldmatrix
+  alignas(16) __nv_bfloat16 w3[NK][NC][WS];
+  alignas(16) float x[NPP];
+  alignas(16) __nv_bfloat16 a1[NPP][AS];
+  alignas(16) __nv_bfloat16 a2[NPP][AS];
   float wmax[4][NC];
   int warg[4][NC];
   float g[NC];
@@ -80,7 +82,15 @@ __device__ void load_weights(const float* __restrict__ P, NetSmem& s) {
   for (int i = threadIdx.x; i < 2 * PAD; i += blockDim.x) s.x[i < PAD ? i : NP + i] = 0.f;
 }
 
-__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// Four 8x8 bf16 matrices from shared memory (lanes 8m .. 8m + 7 give the row
+// addresses of matrix m; 16-byte aligned rows): thread (g, q) = (lane / 4,
+// lane % 4) receives row g, columns 2q and 2q + 1 of each matrix.
+__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const __nv_bfloat16* p) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
@@ -96,7 +106,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 __device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[AS], const __nv_bfloat16 (*w)[NC][WS],
                                          float (&acc)[4][2][4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gq = lane >> 2, tq = lane & 3;
+  const int lr = lane & 7, lm = lane >> 3;  // row within, and index of, the 8x8 matrix this lane addresses
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -105,21 +115,17 @@ __device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[AS], const __
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
 #pragma unroll
   for (int k = 0; k < NK; ++k) {
-    uint32_t b[2][2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      b[j][0] = ld32(&w[k][8 * j + gq][2 * tq]);
-      b[j][1] = ld32(&w[k][8 * j + gq][2 * tq + 8]);
-    }
+    // B of both channel tiles: matrices (tile 0, in 0-7), (tile 0, in 8-15), (tile 1, ...), (tile 1, ...)
+    uint32_t b[4];
+    ldsm4(b, &w[k][8 * (lm >> 1) + lr][8 * (lm & 1)]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int p = 64 * warp + 16 * i + gq;  // row of the tile (stored row p + k: offset -4 + 4)
-      const uint32_t a0 = ld32(&in[p + k][2 * tq]);
-      const uint32_t a1 = ld32(&in[p + 8 + k][2 * tq]);
-      const uint32_t a2 = ld32(&in[p + k][2 * tq + 8]);
-      const uint32_t a3 = ld32(&in[p + 8 + k][2 * tq + 8]);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) mma_bf16(acc[i][j], a0, a1, a2, a3, b[j][0], b[j][1]);
+      // A of positions 64 warp + 16 i .. + 15 (stored row p + k: offset -4 + 4): matrices
+      // (rows 0-7, in 0-7), (rows 8-15, in 0-7), (rows 0-7, in 8-15), (rows 8-15, in 8-15)
+      uint32_t a[4];
+      ldsm4(a, &in[64 * warp + 16 * i + k + lr + 8 * (lm & 1)][8 * (lm >> 1)]);
+      mma_bf16(acc[i][0], a[0], a[1], a[2], a[3], b[0], b[1]);
+      mma_bf16(acc[i][1], a[0], a[1], a[2], a[3], b[2], b[3]);
     }
   }
 }
@@ -127,13 +133,31 @@ __device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[AS], const __
 // Forward pass of the block already in s.x; leaves a1, a2, g, arg and z in s.
 __device__ void net_block_forward(NetSmem& s) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, gq = lane >> 2, tq = lane & 3;
-  // layer 1 (one input channel): FP32
-  for (int i = t; i < NP * NC; i += kNetThreads) {
-    const int p = i >> 4, c = i & 15;
-    float h = s.b1[c];
+  // layer 1 (one input channel): FP32; thread (c, g) = (t % 16, t / 16) computes
+  // channel c at positions 32 g .. 32 g + 31 from a register window of the input
+  {
+    static_assert(kNetThreads == NC * NP / 32, "layer 1 assigns 32 positions of one channel per thread");
+    const int c = t & 15, g = t >> 4;
+    float wk[NK];
 #pragma unroll
-    for (int k = 0; k < NK; ++k) h = fmaf(s.w1[c * NK + k], s.x[p + k], h);
-    s.a1[p + PAD][c] = __float2bfloat16_rn(fmaxf(h, 0.f));
+    for (int k = 0; k < NK; ++k) wk[k] = s.w1[c * NK + k];
+    const float bc = s.b1[c];
+    float xw[40];  // x[32 g + i], i < 40 (padded input: 32 g + 39 <= NPP - 1)
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(&s.x[32 * g + 4 * q]);
+      xw[4 * q] = v.x;
+      xw[4 * q + 1] = v.y;
+      xw[4 * q + 2] = v.z;
+      xw[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      float h = bc;
+#pragma unroll
+      for (int k = 0; k < NK; ++k) h = fmaf(wk[k], xw[i + k], h);
+      s.a1[32 * g + i + PAD][c] = __float2bfloat16_rn(fmaxf(h, 0.f));
+    }
   }
   __syncthreads();
   float acc[4][2][4];
@@ -220,12 +244,26 @@ __global__ void __launch_bounds__(kNetThreads) net_forward_kernel(const float* _
   extern __shared__ __align__(16) unsigned char raw[];
   NetSmem& s = *reinterpret_cast<NetSmem*>(raw);
   load_weights(P, s);
+  static_assert(NP == 2 * kNetThreads, "two input samples per thread");
+  const int t = threadIdx.x;
+  // the next block's input is loaded into registers while the current one is evaluated
+  float x0 = 0.f, x1 = 0.f;
+  if (blockIdx.x < nb) {
+    x0 = X[(int64_t)blockIdx.x * NP + t];
+    x1 = X[(int64_t)blockIdx.x * NP + kNetThreads + t];
+  }
   for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
     __syncthreads();
-    for (int i = threadIdx.x; i < NP; i += kNetThreads) s.x[PAD + i] = X[b * NP + i];
+    s.x[PAD + t] = x0;
+    s.x[PAD + kNetThreads + t] = x1;
+    const int64_t bn = b + gridDim.x;
+    if (bn < nb) {
+      x0 = X[bn * NP + t];
+      x1 = X[bn * NP + kNetThreads + t];
+    }
     __syncthreads();
     net_block_forward(s);
-    if (threadIdx.x == 0) logits[b] = s.z;
+    if (t == 0) logits[b] = s.z;
   }
 }
 
@@ -350,24 +388,55 @@ __global__ void __launch_bounds__(256) net_decimate_kernel(const void* __restric
   out[i] = (s - 16.f * mu[r]) / (4.f * sigma[r]);
 }
 
-// Flagged blocks: the ids i < n with logits[i] > thr, appended to list (one
-// atomic per warp; the order of the ids is not fixed) and counted in *count.
-// At most cap ids are written; *count holds the full number.
-__global__ void __launch_bounds__(256) net_select_kernel(const float* __restrict__ logits, int64_t n, float thr,
-                                                          int64_t* __restrict__ list, int64_t cap,
-                                                          unsigned long long* __restrict__ count) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool f = i < n && logits[i] > thr;
-  const unsigned m = __ballot_sync(0xffffffffu, f);
-  if (m == 0u) return;  // uniform across the warp
-  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-  unsigned long long base = 0ull;
-  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (f) {
-    const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
-    if (slot < (unsigned long long)cap) list[slot] = i;
+// Flagged blocks: the ids i < n with logits[i] > thr, written to list in
+// increasing order (at most cap of them); *count receives their full number.
+// CTA c takes the ids of tile c (tile ids in a row of kSelThreads-wide rounds):
+// it first counts the flagged ids of every earlier tile (the logits stay in L2,
+// and n / tile CTAs read n^2 / (2 tile) values in all), then writes its own in
+// order with warp ballots and a scan over the warps.  No scratch memory, one
+// launch, deterministic output.
+constexpr int kSelThreads = 1024;
+__global__ void __launch_bounds__(kSelThreads) net_select_kernel(const float* __restrict__ logits, int64_t n,
+                                                                  float thr, int64_t tile,
+                                                                  int64_t* __restrict__ list, int64_t cap,
+                                                                  int64_t* __restrict__ count) {
+  __shared__ int wsum[kSelThreads / 32];
+  __shared__ long long red[kSelThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t first = (int64_t)blockIdx.x * tile;
+  // flagged ids before this tile
+  long long c = 0;
+  for (int64_t i = t; i < first; i += kSelThreads) c += logits[i] > thr ? 1 : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  if (lane == 0) red[warp] = c;
+  __syncthreads();
+  long long base = 0;
+#pragma unroll 1
+  for (int w = 0; w < kSelThreads / 32; ++w) base += red[w];
+  // this tile, kSelThreads ids per round
+  const int64_t last = first + tile < n ? first + tile : n;
+  for (int64_t r0 = first; r0 < last; r0 += kSelThreads) {
+    const int64_t i = r0 + t;
+    const bool f = i < last && logits[i] > thr;
+    const unsigned m = __ballot_sync(kFull, f);
+    __syncthreads();  // wsum of the previous round has been read
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll 1
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+      const int v = wsum[w];
+      before += w < warp ? v : 0;
+      total += v;
+    }
+    if (f) {
+      const long long slot = base + before + __popc(m & ((1u << lane) - 1u));
+      if (slot < cap) list[slot] = i;
+    }
+    base += total;
   }
+  if (blockIdx.x == gridDim.x - 1 && t == 0) *count = base;
 }
 
 // Gather of flagged blocks: out[k][c] = x[r][b * block - left + c] for c < width,
@@ -420,9 +489,8 @@ size_t net_smem(bool grad) {
 template <class KernelT>
 cudaError_t net_grid(KernelT kern, size_t smem, int64_t nb, int* grid) {
   int per_sm = 0, sms = 0;
-  const cudaError_t e = persistent_config(reinterpret_cast<const void*>(kern), smem, &per_sm, &sms);
+  const cudaError_t e = persistent_config(reinterpret_cast<const void*>(kern), smem, &per_sm, &sms, kNetThreads);
   if (e != cudaSuccess) return e;
-  (void)kNetThreads;
   int64_t g = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   *grid = (int)(g < nb ? g : nb);
   return cudaSuccess;
@@ -463,10 +531,11 @@ cudaError_t launch_net_adam(float* P, float* M, float* V, const float* G, int64_
 
 cudaError_t launch_net_select(const float* logits, int64_t n, float thr, int64_t* list, int64_t cap,
                               int64_t* count, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int64_t), s);
-  if (e != cudaSuccess || n == 0) return e;
-  net_select_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(logits, n, thr, list, cap,
-                                                                reinterpret_cast<unsigned long long*>(count));
+  if (n == 0) return cudaMemsetAsync(count, 0, sizeof(int64_t), s);
+  // tiles of at least 8 rounds, at most 256 CTAs (the prefix counts read n^2 / (2 tile) logits)
+  int64_t tile = 8 * kSelThreads;
+  while (n > 256 * tile) tile *= 2;
+  net_select_kernel<<<(unsigned)((n + tile - 1) / tile), kSelThreads, 0, s>>>(logits, n, thr, tile, list, cap, count);
   return cudaGetLastError();
 }
 

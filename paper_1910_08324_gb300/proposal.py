@@ -28,6 +28,8 @@ on candidate lists.
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 from . import _binding as B
@@ -64,7 +66,12 @@ def decimated_blocks(x, mu, sigma, dtype: int = B.SPD_F32, stream=None):
 def plan_geometry(grid: dict):
     """(widest width, largest start separation) of a plan grid (``spd_plan_create``
     keywords without the shape)."""
-    p = B.spd_plan_create(ndm=1, nt=1 << 16, **grid)
+    return _geometry(tuple(sorted(grid.items())))
+
+
+@functools.lru_cache(maxsize=64)
+def _geometry(key):
+    p = B.spd_plan_create(ndm=1, nt=1 << 16, **dict(key))
     try:
         w, sep = p.widths()
         return int(w[-1]), int(sep.max())
@@ -73,15 +80,14 @@ def plan_geometry(grid: dict):
 
 
 def select_blocks(logits, threshold: float = 0.0, stream=None):
-    """Device list (int64, sorted) of the ids row * blocks_per_row + block of the
-    blocks whose logit exceeds ``threshold`` (``spd_net_select``)."""
+    """Device list (int64, increasing) of the ids row * blocks_per_row + block of
+    the blocks whose logit exceeds ``threshold`` (``spd_net_select``)."""
     import torch
     flat = logits.reshape(-1)
     ids = torch.empty(flat.numel(), dtype=torch.int64, device=flat.device)
     cnt = torch.zeros(1, dtype=torch.int64, device=flat.device)
     B.net_select(flat, threshold, ids, cnt, stream=stream)
-    n = int(cnt.item())
-    return torch.sort(ids[:n]).values
+    return ids[:int(cnt.item())]
 
 
 def gather_blocks(x, ids, left: int, right: int, dtype: int, ld_align: int = 64, stream=None):
@@ -136,12 +142,14 @@ def search_flagged(x, ids, mu, sigma, grid: dict, threshold: float = 6.0, radius
         rec = B.records(out, k).copy()
     finally:
         plan.close()
-    rec = rec[(rec["start"] >= left) & (rec["start"] < left + BLOCK)]
-    ids_h = ids.cpu().numpy()
-    blk = ids_h[rec["row"]]
-    rec["start"] = rec["start"] - left + (blk % bpr) * BLOCK
+    # starts inside the blocks; the ids increase, so the records (in compact row,
+    # start order) come out in (row, start) order of the series
+    st = rec["start"]
+    rec = rec[(st >= left) & (st < left + BLOCK)]
+    blk = ids.cpu().numpy()[rec["row"]]
+    rec["start"] += (blk % bpr) * BLOCK - left
     rec["row"] = blk // bpr
-    return rec[np.lexsort((rec["start"], rec["row"]))]
+    return rec
 
 
 def propose_and_search(params, x, mu_tab, sigma_tab, grid: dict, logit_threshold: float = 0.0,

@@ -25,6 +25,15 @@ def test_select_matches_threshold():
         assert np.array_equal(ids.cpu().numpy(), np.nonzero(lg > 0.5)[0])
     ids = P.select_blocks(t.full((100,), -1.0, device="cuda"), 0.0)
     assert ids.numel() == 0
+    # more than 256 tiles of 8192 (larger tiles), and a list shorter than the count
+    lg = rng.normal(size=3_000_001).astype(np.float32)
+    ref = np.nonzero(lg > 1.0)[0]
+    d = t.from_numpy(lg).cuda()
+    assert np.array_equal(P.select_blocks(d, 1.0).cpu().numpy(), ref)
+    out = t.full((1000,), -7, dtype=t.int64, device="cuda")
+    cnt = t.zeros(1, dtype=t.int64, device="cuda")
+    spd.net_select(d, 1.0, out, cnt)
+    assert int(cnt.item()) == len(ref) and np.array_equal(out.cpu().numpy(), ref[:1000])
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
