@@ -191,6 +191,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    """Host CPU model name (lscpu), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_rate(x_rows, algo, s_end, mu=0.0, sigma=1.0, threads=0):
     """The oracle (definition form, FP64, OpenMP over rows) on a bounded sample."""
     import oracle
@@ -318,9 +331,7 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
         torch.cuda.synchronize(dev)
     total_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
     if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        total_ms = shard.max_over_ranks(total_ms, dist)
     ms_per_step = total_ms / args.steps
     value = samples * world / (ms_per_step / 1e3)
     search_ms = min(time_ms(search) for _ in range(3))
@@ -487,9 +498,7 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
             times.append(time.perf_counter() - t0)
     total = sum(times)
     if world > 1:
-        tt = torch.tensor([total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
+        total = shard.max_over_ranks(total, dist)
     ms_per_step = 1e3 * total / args.steps
     value = ndm * nt * world / (ms_per_step / 1e3)
     s_prop = P.score(rec, pev, sj, ndm, nt)
@@ -712,9 +721,7 @@ def main():
     cand_ms = [ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(args.steps)]
     total_ms = sum(ev[3 * k].elapsed_time(ev[3 * k + 2]) for k in range(args.steps))
     if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        total_ms = shard.max_over_ranks(total_ms, dist)
     ms_per_step = total_ms / args.steps
     samples_step = ndm * nt * world
     value = samples_step / (ms_per_step / 1e3)
@@ -731,7 +738,7 @@ def main():
     if cand_per_sample <= ALU_BALANCE_CANDIDATES:
         achieved = bytes_per_sample * ndm * nt / (s_avg / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic,
+                    "frac": achieved / peak, "traffic": traffic, "frac_of_nominal_7900": achieved / 7900.0,
                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                     if peak_kind == "measured" else "fallback 6800 GB/s"}
     else:
@@ -791,9 +798,7 @@ def main():
             d2h.append(8 + 24 * k)
         dt = (time.perf_counter() - t0) / args.e2e_steps
         if world > 1:
-            tt = torch.tensor([dt], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+            dt = shard.max_over_ranks(dt, dist)
         e2e = {"value": samples_step / dt, "unit": "samples/s", "h2d_bytes_per_step": esize * ndm * nt,
                "d2h_bytes_per_step": int(statistics.mean(d2h)), "steps": args.e2e_steps,
                "ms_per_step": 1e3 * dt, "api": "torch pinned H2D + spd_search (C ABI) + D2H of count and records"}
@@ -815,9 +820,12 @@ def main():
             r0 = (r0 + rows) % ndm
             if r0 + rows > ndm:
                 r0 = 0
+        x1 = x[:4].float().cpu().numpy()
+        rate1, _ = cpu_oracle_rate(x1, args.algo, args.s_end, float(mu[0]), float(sg[0]), threads=1)
         cpu = {"value": done / spent, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "cpu_model": cpu_model(), "value_1thread": rate1,
                "sample": "%d batches of %d of %d rows x %d samples (%d row passes), %s grid, "
-                         "definition form FP64, %.1f s of oracle time"
+                         "definition form FP64, %.1f s of oracle time; 1-thread figure on 4 rows"
                          % (batches, rows, ndm, nt, batches * rows, args.algo, spent)}
 
     if rank == 0:
