@@ -55,3 +55,34 @@ def test_dtype_scalar_path(dtype, name):
     Yg, Wg = run_gpu(plan, stored, mu, sigma, x_offset=1)
     Yo, Wo, Y2o = oracle.search(vals, oracle_grid(plan), mu, sigma)
     assert_parity(Yg, Wg, Yo, Wo, Y2o, nt, ctx="%s %s scalar" % (dtype, name))
+
+
+# error of each stored type against the FP64 oracle on the original (unquantised)
+# series: quantisation error, reported (pytest -s) and bounded by the type's step
+ERR_BOUNDS = {"f32": (1e-5, 1e-6, 0.999), "f16": (5e-3, 5e-4, 0.99), "bf16": (4e-2, 4e-3, 0.95),
+              "u8": (0.2, 0.03, 0.9)}
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16", "u8"])
+def test_dtype_error_against_fp64_original(dtype):
+    ndm, nt = 4, 131072
+    x = spd_synth.gaussian_noise(ndm, nt, 77, dtype=np.float64)
+    tab = spd_synth.pulse_table(8, ndm, nt, 78, width_range=(1, 2000), snr_range=(6.0, 15.0), min_gap=9000)
+    spd_synth.inject(x, tab, 1.0)
+    if dtype == "f32":
+        stored, mu, sigma, code = x.astype(np.float32), 0.0, 1.0, spd.SPD_F32
+    else:
+        stored, _ = spd_synth.quantize(x, dtype)
+        mu, sigma = (spd_synth.U8_OFFSET, spd_synth.U8_SCALE) if dtype == "u8" else (0.0, 1.0)
+        code = DT[dtype]
+    plan = spd.spd_plan_create(ndm=ndm, nt=nt, dtype=code, **ALGOS["ig1"](8192))
+    Yg, Wg = run_gpu(plan, stored, mu, sigma)
+    Yo, Wo, Y2o = oracle.search(x, oracle_grid(plan), 0.0, 1.0)
+    rel = np.abs(Yg.astype(np.float64) - Yo) / np.maximum(np.abs(Yo), 1.0)
+    clear = (Yo - Y2o) > 0.05
+    agree = float(np.mean(Wg[clear] == Wo[clear]))
+    print("\n%s vs FP64 original: max %.3g, p99.9 %.3g, mean %.3g relative SNR error; width agreement %.5f "
+          "(%d starts with a clear winner)" % (dtype, rel.max(), np.quantile(rel, 0.999), rel.mean(), agree,
+                                               int(clear.sum())))
+    mx, mean, ag = ERR_BOUNDS[dtype]
+    assert np.quantile(rel, 0.999) <= mx and rel.mean() <= mean and agree >= ag
