@@ -240,9 +240,9 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
   const bool wput = COARSE && lane < 31 && wj <= top;
   int wn = 0;
   // Coarse evaluation: quads of 4 consecutive positions (float4 ring windows) for
-  // levels 4..8 on the 62 first threads (32, 16, 8, 4, 2 quads) and level 9 on
-  // lane 0 of the last warp (after it has built the level); single positions of
-  // levels 10, 11 on its lanes 1..3, levels above 11 on its lane 4.
+  // levels 4..8 on the 62 first threads (32, 16, 8, 4, 2 quads); single positions
+  // of levels 9, 10, 11 on lanes 0..6 of the last warp (after it has built those
+  // levels; one code path for all seven), levels above 11 on its lane 7.
   const int ctop = top < kChunkLog ? top : kChunkLog;
   // (ring offsets, masks and level constants are re-read per chunk from the
   // ring table and the kernel parameters rather than held in registers)
@@ -258,20 +258,17 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
         u -= 512 >> j;
         ++j;
       }
-    } else if (warp == kThreads / 32 - 1 && lane == 0) {
-      j = 9;
-      u = 0;
     }
     if (u >= 0 && j <= ctop) {
       qj = j;
       qq = 4 * u;
       qn = (a0 >> j) + qq;  // first block of the quad at chunk 0
     }
-    if (warp == kThreads / 32 - 1 && lane >= 1 && lane <= 3) {
-      const int j1 = lane < 3 ? 10 : 11;
+    if (warp == kThreads / 32 - 1 && lane < 7) {
+      const int j1 = lane < 4 ? 9 : (lane < 6 ? 10 : 11);
       if (j1 <= ctop) {
         sj = j1;
-        sq = lane < 3 ? lane - 1 : 0;
+        sq = lane < 4 ? lane : (lane < 6 ? lane - 4 : 0);
         sn = (a0 >> j1) + sq;
       }
     }
@@ -390,7 +387,7 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
         // canonical NaN, whose key would beat every SNR: it posts nothing
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-          if (out[r] == out[r]) atomicMax(KB + ((qq + r) << (qj - 4)), fkey(out[r]));
+          atomicMax(KB + ((qq + r) << (qj - 4)), out[r] == out[r] ? fkey(out[r]) : INT_MIN);
       } else {
         float bv[4], full[4];
         int bq[4];
@@ -407,12 +404,12 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
                                 (sj == top) ? p.n_top : SM::MM, scl(AB + first, SM{}), bv, bq);
       if constexpr (ENC) {
         const float y = enc_w<S::EB>(bv * lvl_f(sj), S::EMAX - first - bq);
-        if (y == y) atomicMax(KB + (sq << (sj - 4)), fkey(y));
+        atomicMax(KB + (sq << (sj - 4)), y == y ? fkey(y) : INT_MIN);
       }
       else
         put(sj, sq, bv * lvl_f(sj), first + bq);
     }
-    if (warp == kThreads / 32 - 1 && lane == 4)
+    if (warp == kThreads / 32 - 1 && lane == 7)
       for (int jj = kChunkLog + 1; jj <= top; ++jj)
         if (((t0 + ar) & ((1LL << jj) - 1)) == 0) {
           float bv;
