@@ -10,12 +10,13 @@
 //
 // Layers 2 and 3 are implicit GEMMs on the tensor cores: per block, M = 256
 // positions, N = 16 output channels, K = 9 taps x 16 input channels, as
-// mma.sync m16n8k16 bf16 -> f32 (one K-step per tap).  Activations live in
-// shared memory as [position + 4][channel] rows of 24 bf16 (48 bytes), which
-// makes the fragment loads conflict-free; weights as [tap][out][in] rows of 24.
-// N = 16 is far below the 64/128-row tiles of tcgen05 MMAs with TMEM
-// accumulators, and the proposal step is bound by the decimation read, so the
-// warp-level MMA is used here.
+// mma.sync m16n8k16 bf16 -> f32 (one K-step per tap), fragments loaded with
+// ldmatrix.  Activations live in shared memory as [position + 4][channel] rows of
+// 16 bf16 and weights as [tap][out][in] rows of 16, each row's 16-byte halves
+// swizzled by bit 2 of its index (conflict-free fragment loads without padding).
+// The contraction per block is small (N = 16 output channels) and each layer's
+// input is the previous layer's output in shared memory, so the warp-level MMA
+// keeps a block's three layers inside one CTA without TMEM round trips.
 //
 // Gradients: the max pool passes one position per channel, so the backward
 // pass is a few dense FP32 loops per block in shared memory (straight-through
@@ -32,16 +33,19 @@ constexpr int NC = 16, NK = 9, NP = 256, PAD = 4, NPP = NP + 2 * PAD;
 constexpr int kNetThreads = 128;
 constexpr int kNetParams = 4817;
 constexpr int oW1 = 0, ob1 = 144, oW2 = 160, ob2 = 2464, oW3 = 2480, ob3 = 4784, oW4 = 4800, ob4 = 4816;
-constexpr int AS = 24;  // bf16 per activation row
-constexpr int WS = 24;  // bf16 per weight row
+// Activation rows [position][16 channels] and weight rows [tap][out][16 in] are 32
+// bytes of bf16 with the two 16-byte halves of a row swapped when bit 2 of the row
+// index is set: every 8-row ldmatrix phase is then conflict-free at any row offset
+// (rows r and r + 4 fall in different banks), without padding.
+__device__ __forceinline__ int swz(int row, int col) { return col ^ (((row >> 2) & 1) << 3); }
 
 struct NetSmem {
   float w1[NC * NK], b1[NC], b2[NC], b3[NC], w4[NC], b4;
-  alignas(16) __nv_bfloat16 w2[NK][NC][WS];  // [tap][out][in]; 16-byte rows for ldmatrix
-  alignas(16) __nv_bfloat16 w3[NK][NC][WS];
+  alignas(16) __nv_bfloat16 w2[NK][NC][NC];  // [tap][out][in, swizzled by out]
+  alignas(16) __nv_bfloat16 w3[NK][NC][NC];
   alignas(16) float x[NPP];
-  alignas(16) __nv_bfloat16 a1[NPP][AS];
-  alignas(16) __nv_bfloat16 a2[NPP][AS];
+  alignas(16) __nv_bfloat16 a1[NPP][NC];  // [padded position][channel, swizzled by position]
+  alignas(16) __nv_bfloat16 a2[NPP][NC];
   float wmax[4][NC];
   int warg[4][NC];
   float g[NC];
@@ -70,12 +74,12 @@ __device__ void load_weights(const float* __restrict__ P, NetSmem& s) {
   if (threadIdx.x == 0) s.b4 = P[ob4];
   for (int i = threadIdx.x; i < NC * NC * NK; i += blockDim.x) {  // P: W[co][ci][k]
     const int co = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
-    s.w2[k][co][ci] = __float2bfloat16_rn(P[oW2 + i]);
-    s.w3[k][co][ci] = __float2bfloat16_rn(P[oW3 + i]);
+    s.w2[k][co][swz(co, ci)] = __float2bfloat16_rn(P[oW2 + i]);
+    s.w3[k][co][swz(co, ci)] = __float2bfloat16_rn(P[oW3 + i]);
   }
   // zero padding rows of the activations and the input
-  for (int i = threadIdx.x; i < 2 * PAD * AS; i += blockDim.x) {
-    const int r = i / AS, c = i % AS, row = r < PAD ? r : NP + r;
+  for (int i = threadIdx.x; i < 2 * PAD * NC; i += blockDim.x) {
+    const int r = i / NC, c = i % NC, row = r < PAD ? r : NP + r;
     s.a1[row][c] = __float2bfloat16_rn(0.f);
     s.a2[row][c] = __float2bfloat16_rn(0.f);
   }
@@ -103,7 +107,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 
 // One tensor-core layer: out[p][co] = sum_{k, ci} w[k][co][ci] in[p + k - 4][ci]
 // for the warp's 4 tiles of 16 positions and both tiles of 8 channels.
-__device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[AS], const __nv_bfloat16 (*w)[NC][WS],
+__device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[NC], const __nv_bfloat16 (*w)[NC][NC],
                                          float (&acc)[4][2][4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lr = lane & 7, lm = lane >> 3;  // row within, and index of, the 8x8 matrix this lane addresses
@@ -117,13 +121,15 @@ __device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[AS], const __
   for (int k = 0; k < NK; ++k) {
     // B of both channel tiles: matrices (tile 0, in 0-7), (tile 0, in 8-15), (tile 1, ...), (tile 1, ...)
     uint32_t b[4];
-    ldsm4(b, &w[k][8 * (lm >> 1) + lr][8 * (lm & 1)]);
+    const int brow = 8 * (lm >> 1) + lr;
+    ldsm4(b, &w[k][brow][swz(brow, 8 * (lm & 1))]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       // A of positions 64 warp + 16 i .. + 15 (stored row p + k: offset -4 + 4): matrices
       // (rows 0-7, in 0-7), (rows 8-15, in 0-7), (rows 0-7, in 8-15), (rows 8-15, in 8-15)
       uint32_t a[4];
-      ldsm4(a, &in[64 * warp + 16 * i + k + lr + 8 * (lm & 1)][8 * (lm >> 1)]);
+      const int arow = 64 * warp + 16 * i + k + lr + 8 * (lm & 1);
+      ldsm4(a, &in[arow][swz(arow, 8 * (lm >> 1))]);
       mma_bf16(acc[i][0], a[0], a[1], a[2], a[3], b[0], b[1]);
       mma_bf16(acc[i][1], a[0], a[1], a[2], a[3], b[2], b[3]);
     }
@@ -156,7 +162,8 @@ __device__ void net_block_forward(NetSmem& s) {
       float h = bc;
 #pragma unroll
       for (int k = 0; k < NK; ++k) h = fmaf(wk[k], xw[i + k], h);
-      s.a1[32 * g + i + PAD][c] = __float2bfloat16_rn(fmaxf(h, 0.f));
+      const int row = 32 * g + i + PAD;
+      s.a1[row][swz(row, c)] = __float2bfloat16_rn(fmaxf(h, 0.f));
     }
   }
   __syncthreads();
@@ -172,8 +179,8 @@ __device__ void net_block_forward(NetSmem& s) {
       lo.y = __float2bfloat16_rn(fmaxf(acc[i][j][1] + s.b2[co + 1], 0.f));
       hi.x = __float2bfloat16_rn(fmaxf(acc[i][j][2] + s.b2[co], 0.f));
       hi.y = __float2bfloat16_rn(fmaxf(acc[i][j][3] + s.b2[co + 1], 0.f));
-      *reinterpret_cast<__nv_bfloat162*>(&s.a2[p + PAD][co]) = lo;
-      *reinterpret_cast<__nv_bfloat162*>(&s.a2[p + 8 + PAD][co]) = hi;
+      *reinterpret_cast<__nv_bfloat162*>(&s.a2[p + PAD][swz(p + PAD, co)]) = lo;
+      *reinterpret_cast<__nv_bfloat162*>(&s.a2[p + 8 + PAD][swz(p + 8 + PAD, co)]) = hi;
     }
   __syncthreads();
   conv_mma(s.a2, s.w3, acc);
@@ -238,7 +245,7 @@ __device__ void net_block_forward(NetSmem& s) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kNetThreads) net_forward_kernel(const float* __restrict__ P,
+__global__ void __launch_bounds__(kNetThreads, 7) net_forward_kernel(const float* __restrict__ P,
                                                                    const float* __restrict__ X, int64_t nb,
                                                                    float* __restrict__ logits) {
   extern __shared__ __align__(16) unsigned char raw[];
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* _
     // layer 3: weights and bias from the pooled positions; d(a2) gathered
     for (int i = t; i < NC * NC * NK; i += kNetThreads) {
       const int c = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
-      q.G[oW3 + i] += q.dh3[c] * bf(s.a2[s.arg[c] + k][ci]);
+      q.G[oW3 + i] += q.dh3[c] * bf(s.a2[s.arg[c] + k][swz(s.arg[c] + k, ci)]);
     }
     if (t < NC) q.G[ob3 + t] += q.dh3[t];
     for (int i = t; i < NP * NC; i += kNetThreads) {
@@ -308,16 +315,16 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* _
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int k = p - s.arg[c] + PAD;  // a2[p] feeds h3[c][arg] through tap k
-        if (k >= 0 && k < NK) d = fmaf(bf(s.w3[k][c][ci]), q.dh3[c], d);
+        if (k >= 0 && k < NK) d = fmaf(bf(s.w3[k][c][swz(c, ci)]), q.dh3[c], d);
       }
-      q.dh2[p][ci] = bf(s.a2[p + PAD][ci]) > 0.f ? d : 0.f;
+      q.dh2[p][ci] = bf(s.a2[p + PAD][swz(p + PAD, ci)]) > 0.f ? d : 0.f;
     }
     __syncthreads();
     // layer 2
     for (int i = t; i < NC * NC * NK; i += kNetThreads) {
       const int co = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
       float acc = 0.f;
-      for (int p = 0; p < NP; ++p) acc = fmaf(q.dh2[p][co], bf(s.a1[p + k][ci]), acc);
+      for (int p = 0; p < NP; ++p) acc = fmaf(q.dh2[p][co], bf(s.a1[p + k][swz(p + k, ci)]), acc);
       q.G[oW2 + i] += acc;
     }
     if (t < NC) {
@@ -332,9 +339,9 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* _
         const int pp = p - k + PAD;  // output position fed by a1[p] through tap k
         if (pp >= 0 && pp < NP)
 #pragma unroll
-          for (int co = 0; co < NC; ++co) d = fmaf(bf(s.w2[k][co][ci]), q.dh2[pp][co], d);
+          for (int co = 0; co < NC; ++co) d = fmaf(bf(s.w2[k][co][swz(co, ci)]), q.dh2[pp][co], d);
       }
-      q.dh1[p][ci] = bf(s.a1[p + PAD][ci]) > 0.f ? d : 0.f;
+      q.dh1[p][ci] = bf(s.a1[p + PAD][swz(p + PAD, ci)]) > 0.f ? d : 0.f;
     }
     __syncthreads();
     // layer 1
