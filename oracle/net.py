@@ -6,7 +6,7 @@ file is its definition, written plainly in numpy:
 
   input   x[256]: one block of the x16-decimated, normalised series
   conv l  a_l[c][p] = bf16(relu(b_l[c] + sum_{ci,k} bf16(W_l[c][ci][k]) a_{l-1}[ci][p + k - 4]))
-          (l = 1, 2, 3; 16 channels; kernel 9, zero padding of 4; a_0 = x, one channel;
+          (l = 1, 2, 3; 16 channels; kernel 9, zero padding of 4; a_0 = bf16(x), one channel;
           the layer-3 activations are kept unrounded: they only feed the pool)
   pool    g[c] = max_p a_3[c][p]
   head    z = b_4 + sum_c W_4[c] g[c],  p = sigmoid(z)
@@ -71,7 +71,7 @@ def forward(theta, x, rounding=True):
     q = unpack(theta)
     rd = bf16 if rounding else (lambda v: np.asarray(v, np.float64))
     W1, W2, W3 = rd(q["W1"]), rd(q["W2"]), rd(q["W3"])
-    a0 = np.asarray(x, np.float64).reshape(1, P)
+    a0 = rd(np.asarray(x, np.float64).reshape(1, P))
     h1 = _conv(a0, W1, q["b1"])
     a1 = rd(np.maximum(h1, 0.0))
     h2 = _conv(a1, W2, q["b2"])
