@@ -2,16 +2,18 @@
 // forward pass with BF16 tensor-core convolutions, gradients and Adam.
 //
 // The network (definition in the oracle's net module, restated here):
-//   a1 = bf16(relu(b1 + W1 * x)),  a2 = bf16(relu(b2 + W2 * a1)),  h3 = b3 + W3 * a2
+//   a1 = bf16(relu(b1 + W1 * bf16(x))),  a2 = bf16(relu(b2 + W2 * a1)),  h3 = b3 + W3 * a2
 //   g[c] = max_p relu(h3[c][p]),    z = b4 + W4 . g
 // over one block of 256 decimated samples; "*" is a 1D correlation with kernel
 // 9 and zero padding 4 over 16 channels (1 input channel for layer 1).  The
 // weights of layers 1..3 enter as bf16 values, every sum accumulates in FP32.
 //
-// Layers 2 and 3 are implicit GEMMs on the tensor cores: per block, M = 256
-// positions, N = 16 output channels, K = 9 taps x 16 input channels, as
-// mma.sync m16n8k16 bf16 -> f32 (one K-step per tap), fragments loaded with
-// ldmatrix.  Activations live in shared memory as [position + 4][channel] rows of
+// All three layers are implicit GEMMs on the tensor cores: per block, M = 256
+// positions, N = 16 output channels and, for layers 2 and 3, K = 9 taps x 16
+// input channels as mma.sync m16n8k16 bf16 -> f32 (one K-step per tap, the tap
+// a row offset of the activation operand); layer 1 (one input channel) is one
+// K-step over an im2col of the block's 9 taps (padded to 16), built in shared
+// memory.  Fragments are loaded with ldmatrix.  Activations live in shared memory as [position + 4][channel] rows of
 // 16 bf16 and weights as [tap][out][in] rows of 16, each row's 16-byte halves
 // swizzled by bit 2 of its index (conflict-free fragment loads without padding).
 // The contraction per block is small (N = 16 output channels) and each layer's
@@ -40,7 +42,8 @@ constexpr int oW1 = 0, ob1 = 144, oW2 = 160, ob2 = 2464, oW3 = 2480, ob3 = 4784,
 __device__ __forceinline__ int swz(int row, int col) { return col ^ (((row >> 2) & 1) << 3); }
 
 struct NetSmem {
-  float w1[NC * NK], b1[NC], b2[NC], b3[NC], w4[NC], b4;
+  float b1[NC], b2[NC], b3[NC], w4[NC], b4;
+  alignas(16) __nv_bfloat16 w1b[NC][NC];     // [out][tap, 9..15 zero; swizzled by out]
   alignas(16) __nv_bfloat16 w2[NK][NC][NC];  // [tap][out][in, swizzled by out]
   alignas(16) __nv_bfloat16 w3[NK][NC][NC];
   alignas(16) float x[NPP];
@@ -64,7 +67,10 @@ __device__ __forceinline__ float bf(__nv_bfloat16 v) { return __bfloat162float(v
 
 // Weights into shared memory (bf16 copies for the tensor-core layers).
 __device__ void load_weights(const float* __restrict__ P, NetSmem& s) {
-  for (int i = threadIdx.x; i < NC * NK; i += blockDim.x) s.w1[i] = bf(__float2bfloat16_rn(P[oW1 + i]));
+  for (int i = threadIdx.x; i < NC * NC; i += blockDim.x) {  // P: W1[co][k]
+    const int co = i / NC, k = i % NC;
+    s.w1b[co][swz(co, k)] = __float2bfloat16_rn(k < NK ? P[oW1 + co * NK + k] : 0.f);
+  }
   for (int i = threadIdx.x; i < NC; i += blockDim.x) {
     s.b1[i] = P[ob1 + i];
     s.b2[i] = P[ob2 + i];
@@ -136,52 +142,70 @@ __device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[NC], const __
   }
 }
 
-// Forward pass of the block already in s.x; leaves a1, a2, g, arg and z in s.
-__device__ void net_block_forward(NetSmem& s) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, gq = lane >> 2, tq = lane & 3;
-  // layer 1 (one input channel): FP32; thread (c, g) = (t % 16, t / 16) computes
-  // channel c at positions 32 g .. 32 g + 31 from a register window of the input
-  {
-    static_assert(kNetThreads == NC * NP / 32, "layer 1 assigns 32 positions of one channel per thread");
-    const int c = t & 15, g = t >> 4;
-    float wk[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) wk[k] = s.w1[c * NK + k];
-    const float bc = s.b1[c];
-    float xw[40];  // x[32 g + i], i < 40 (padded input: 32 g + 39 <= NPP - 1)
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-      const float4 v = *reinterpret_cast<const float4*>(&s.x[32 * g + 4 * q]);
-      xw[4 * q] = v.x;
-      xw[4 * q + 1] = v.y;
-      xw[4 * q + 2] = v.z;
-      xw[4 * q + 3] = v.w;
-    }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      float h = bc;
-#pragma unroll
-      for (int k = 0; k < NK; ++k) h = fmaf(wk[k], xw[i + k], h);
-      const int row = 32 * g + i + PAD;
-      s.a1[row][swz(row, c)] = __float2bfloat16_rn(fmaxf(h, 0.f));
-    }
-  }
-  __syncthreads();
-  float acc[4][2][4];
-  conv_mma(s.a1, s.w2, acc);
+// Epilogue of a tensor-core layer: out[p + PAD][co] = bf16(relu(acc + bias[co]))
+// for the warp's four 16-position tiles (fragment layout of mma m16n8k16).
+__device__ __forceinline__ void store_act(const float (&acc)[4][2][4], const float* bias,
+                                          __nv_bfloat16 (*out)[NC]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gq = lane >> 2, tq = lane & 3;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int p = 64 * warp + 16 * i + gq, co = 8 * j + 2 * tq;
       __nv_bfloat162 lo, hi;
-      lo.x = __float2bfloat16_rn(fmaxf(acc[i][j][0] + s.b2[co], 0.f));
-      lo.y = __float2bfloat16_rn(fmaxf(acc[i][j][1] + s.b2[co + 1], 0.f));
-      hi.x = __float2bfloat16_rn(fmaxf(acc[i][j][2] + s.b2[co], 0.f));
-      hi.y = __float2bfloat16_rn(fmaxf(acc[i][j][3] + s.b2[co + 1], 0.f));
-      *reinterpret_cast<__nv_bfloat162*>(&s.a2[p + PAD][swz(p + PAD, co)]) = lo;
-      *reinterpret_cast<__nv_bfloat162*>(&s.a2[p + 8 + PAD][swz(p + 8 + PAD, co)]) = hi;
+      lo.x = __float2bfloat16_rn(fmaxf(acc[i][j][0] + bias[co], 0.f));
+      lo.y = __float2bfloat16_rn(fmaxf(acc[i][j][1] + bias[co + 1], 0.f));
+      hi.x = __float2bfloat16_rn(fmaxf(acc[i][j][2] + bias[co], 0.f));
+      hi.y = __float2bfloat16_rn(fmaxf(acc[i][j][3] + bias[co + 1], 0.f));
+      *reinterpret_cast<__nv_bfloat162*>(&out[p + PAD][swz(p + PAD, co)]) = lo;
+      *reinterpret_cast<__nv_bfloat162*>(&out[p + 8 + PAD][swz(p + 8 + PAD, co)]) = hi;
     }
+}
+
+// Forward pass of the block already in s.x; leaves a1, a2, g, arg and z in s.
+__device__ void net_block_forward(NetSmem& s) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, gq = lane >> 2, tq = lane & 3;
+  // layer 1: im2col of the bf16 input into the rows of a2 (free until layer 2's
+  // epilogue; its zero padding rows are not touched): row p + PAD holds
+  // bf16(x[p + tap - 4]), taps 0..8, and zeros for taps 9..15
+  for (int r = t; r < NP; r += kNetThreads) {
+    uint32_t v[8];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const float x0 = 2 * h < NK ? s.x[r + 2 * h] : 0.f;
+      const float x1 = 2 * h + 1 < NK ? s.x[r + 2 * h + 1] : 0.f;
+      const __nv_bfloat162 pr = __floats2bfloat162_rn(x0, x1);
+      v[h] = *reinterpret_cast<const uint32_t*>(&pr);
+    }
+    const int row = r + PAD, sw = (row >> 2) & 1;
+    uint4* dst = reinterpret_cast<uint4*>(&s.a2[row][0]);
+    dst[sw] = make_uint4(v[0], v[1], v[2], v[3]);      // taps 0..7
+    dst[sw ^ 1] = make_uint4(v[4], v[5], v[6], v[7]);  // taps 8..15
+  }
+  __syncthreads();
+  float acc[4][2][4];
+  {
+    const int lr = lane & 7, lm = lane >> 3;
+    uint32_t b[4];
+    const int brow = 8 * (lm >> 1) + lr;
+    ldsm4(b, &s.w1b[brow][swz(brow, 8 * (lm & 1))]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint32_t a[4];
+      const int arow = PAD + 64 * warp + 16 * i + lr + 8 * (lm & 1);
+      ldsm4(a, &s.a2[arow][swz(arow, 8 * (lm >> 1))]);
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+      mma_bf16(acc[i][0], a[0], a[1], a[2], a[3], b[0], b[1]);
+      mma_bf16(acc[i][1], a[0], a[1], a[2], a[3], b[2], b[3]);
+    }
+  }
+  store_act(acc, s.b1, s.a1);
+  __syncthreads();
+  conv_mma(s.a1, s.w2, acc);
+  store_act(acc, s.b2, s.a2);
   __syncthreads();
   conv_mma(s.a2, s.w3, acc);
   // max pool: the thread's maximum (first position on ties) of its two channels per tile
@@ -349,7 +373,7 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* _
       float acc = 0.f;
       if (i < NC * NK) {
         const int c = i / NK, k = i % NK;
-        for (int p = 0; p < NP; ++p) acc = fmaf(q.dh1[p][c], s.x[p + k], acc);
+        for (int p = 0; p < NP; ++p) acc = fmaf(q.dh1[p][c], bf(__float2bfloat16_rn(s.x[p + k])), acc);
         q.G[oW1 + i] += acc;
       } else {
         const int c = i - NC * NK;
