@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--s-end", type=int, default=spd_synth.SKA_MID["s_end"])
     ap.add_argument("--threshold", type=float, default=6.0)
     ap.add_argument("--radius", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-chunks", type=int, default=4, help="row chunks of the end-to-end pipeline")
     ap.add_argument("--dtype", default="f32", choices=sorted(DTYPES),
                     help="storage type of the input samples")
@@ -818,11 +818,13 @@ def main():
 
         e2e_step()  # first use of the chunk plans outside the timed region
         torch.cuda.synchronize(dev)
-        d2h = []
-        t0 = time.perf_counter()
+        d2h, per_step = [], []
         for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
             d2h.append(e2e_step())
-        dt = (time.perf_counter() - t0) / args.e2e_steps
+            per_step.append(time.perf_counter() - t0)
+        # the host link is shared with the machine's other work: the median step
+        dt = statistics.median(per_step)
         if world > 1:
             dt = shard.max_over_ranks(dt, dist)
         torch.cuda.synchronize(dev)
@@ -832,7 +834,8 @@ def main():
         h2d_gbps = esize * ndm * nt / (time.perf_counter() - t1) / 1e9
         e2e = {"value": samples_step / dt, "unit": "samples/s", "h2d_bytes_per_step": esize * ndm * nt,
                "d2h_bytes_per_step": int(statistics.mean(d2h)), "steps": args.e2e_steps,
-               "ms_per_step": 1e3 * dt, "chunks": nck, "h2d_GBps_one_copy": h2d_gbps,
+               "ms_per_step": 1e3 * dt, "ms_steps": [round(1e3 * v, 2) for v in per_step], "chunks": nck,
+               "h2d_GBps_one_copy": h2d_gbps,
                "api": "torch pinned H2D per row chunk (copy stream) + spd_search per chunk (C ABI, compute "
                       "stream, after its copy) + D2H of counts and records"}
         del xh, out_h, outs

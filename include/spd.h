@@ -296,7 +296,8 @@ spd_status spd_noise_stats(const spd_plan *plan, const void *d_x, float outlier_
  * a row (plus the widest boxcar after them, read again by the next segment).
  * Longer segments re-read less, shorter ones give more CTAs.  segment must be a
  * multiple of 16384 and of 2^top (top: the plan's last level), at most 2^24;
- * the default is 131072.  Host only.  SPD_ERR_INVALID_ARG otherwise (and for
+ * the default is the longest of 524288, 262144 and 131072 that gives at least
+ * 2432 segments (ndm x segments per row).  Host only.  SPD_ERR_INVALID_ARG otherwise (and for
  * exhaustive plans).
  */
 spd_status spd_plan_set_segment(spd_plan *plan, int32_t segment);
