@@ -303,6 +303,18 @@ spd_status spd_noise_stats(const spd_plan *plan, const void *d_x, float outlier_
 spd_status spd_plan_set_segment(spd_plan *plan, int32_t segment);
 
 /*
+ * Starts evaluated per row: only starts s < n_starts get outputs (and
+ * candidates), while every sample below nt still feeds their boxcars (the rule
+ * s + L <= nt of Eq. boxcar is unchanged).  For overlapping blocks of a longer
+ * series, a block of n_starts + L_end - 1 samples yields exactly the outputs of
+ * its n_starts starts (overlap-save).  snr / width_idx at starts >= n_starts are
+ * not written; the candidate step treats n_starts as the row's end (the peak
+ * test of start n_starts - 1 sees no right-hand neighbour).  1 <= n_starts <= nt;
+ * the default is nt.  Host only.  SPD_ERR_INVALID_ARG otherwise.
+ */
+spd_status spd_plan_set_starts(spd_plan *plan, int64_t n_starts);
+
+/*
  * Batched search of several DM ranges in one launch: ranges of different row
  * counts and lengths (e.g. the ranges of a dedispersion plan at their own time
  * decimations) searched with one grid (one BoxDIT or IGRID plan description;

@@ -53,6 +53,7 @@ from ._binding import (  # noqa: F401
     spd_noise_stats,
     spd_plan_create,
     spd_plan_set_segment,
+    spd_plan_set_starts,
     spd_plan_destroy,
     spd_plan_widths,
     spd_search,

@@ -59,7 +59,7 @@ _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_des
             "spd_plan_set_segment", "spd_batch_create", "spd_batch_destroy", "spd_batch_set_segment",
             "spd_batch_set_wait_ns", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
             "spd_batch_candidates", "spd_net_decimate", "spd_net_forward", "spd_net_gradient",
-            "spd_net_adam", "spd_net_select", "spd_net_gather"]
+            "spd_net_adam", "spd_net_select", "spd_net_gather", "spd_plan_set_starts"]
 
 
 def library_path() -> str:
@@ -91,6 +91,7 @@ def load_library():
         lib.spd_candidates_static.argtypes = [vp, vp, vp, ctypes.c_float, i32, vp, i64, vp, vp]
         lib.spd_noise_stats.argtypes = [vp, vp, ctypes.c_float, i32, vp, vp, vp, sz, vp]
         lib.spd_plan_set_segment.argtypes = [vp, i32]
+        lib.spd_plan_set_starts.argtypes = [vp, i64]
         lib.spd_net_param_count.argtypes = []
         lib.spd_net_param_count.restype = ctypes.c_int32
         lib.spd_net_decimate.argtypes = [vp, i32, i64, i64, i64, vp, vp, vp, vp]
@@ -227,6 +228,10 @@ def spd_noise_stats(plan: Plan, x: int, outlier_sigma: float, max_passes: int, m
     _check(load_library().spd_noise_stats(ctypes.c_void_p(plan.handle), x, float(outlier_sigma),
                                           int(max_passes), mu, sigma, ws, ws_bytes, stream or None),
            "spd_noise_stats")
+
+
+def spd_plan_set_starts(plan: Plan, n_starts: int):
+    _check(load_library().spd_plan_set_starts(ctypes.c_void_p(plan.handle), int(n_starts)), "spd_plan_set_starts")
 
 
 def spd_plan_set_segment(plan: Plan, segment: int):

@@ -200,6 +200,7 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   p.sigma = noise->sigma;
   p.ndm = plan->desc.ndm;
   p.nt = plan->desc.nt;
+  p.n_starts = plan->n_starts;
   p.ld = plan->desc.ld;
   p.tile = plan->tile;
   p.tiles_per_row = (int32_t)plan->tiles_per_row;
@@ -238,7 +239,7 @@ void fill_cand_params(spd::CandParams& p, const spd_plan* plan, const float* d_s
   p.out = d_out;
   p.d_count = d_count;
   p.ndm = plan->desc.ndm;
-  p.nt = plan->desc.nt;
+  p.nt = plan->n_starts;  // the candidate step's extent: the evaluated starts
   p.ld = plan->desc.ld;
   p.cap = cap;
   p.tile = spd::kCandTile;
@@ -314,6 +315,7 @@ spd_plan range_plan(const spd_batch& b, int r) {
   p.desc.nt = b.nt[r];
   p.desc.ld = b.ld[r];
   p.tile = segment_tile(b.nt[r], b.segment);
+  p.n_starts = b.nt[r];
   p.tiles_per_row = (b.nt[r] + p.tile - 1) / p.tile;
   p.cand_tiles_per_row = (b.nt[r] + spd::kCandTile - 1) / spd::kCandTile;
   return p;
@@ -456,6 +458,7 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
     p->tile = segment_tile(d.nt, default_segment(d.ndm, d.nt));
     p->halo = ((p->lend + spd::kChunk - 1) / spd::kChunk) * spd::kChunk;
   }
+  p->n_starts = d.nt;
   p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
   p->cand_tiles_per_row = (d.nt + spd::kCandTile - 1) / spd::kCandTile;
   if (p->desc.ndm * p->tiles_per_row > ((int64_t)1 << 31) - 1 ||
@@ -577,7 +580,14 @@ spd_status spd_noise_stats(const spd_plan* plan, const void* d_x, float outlier_
 spd_status spd_plan_set_segment(spd_plan* plan, int32_t segment) {
   if (!plan || plan->family == kExhaustive || !segment_ok(*plan, segment)) return SPD_ERR_INVALID_ARG;
   plan->tile = segment_tile(plan->desc.nt, segment);
-  plan->tiles_per_row = (plan->desc.nt + plan->tile - 1) / plan->tile;
+  plan->tiles_per_row = (plan->n_starts + plan->tile - 1) / plan->tile;
+  return SPD_OK;
+}
+
+spd_status spd_plan_set_starts(spd_plan* plan, int64_t n_starts) {
+  if (!plan || n_starts < 1 || n_starts > plan->desc.nt) return SPD_ERR_INVALID_ARG;
+  plan->n_starts = n_starts;
+  plan->tiles_per_row = (n_starts + plan->tile - 1) / plan->tile;  // CTAs of the search per row
   return SPD_OK;
 }
 

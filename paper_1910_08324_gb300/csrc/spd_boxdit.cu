@@ -152,6 +152,8 @@ __device__ __forceinline__ void boxdit_unit(const SearchParams& p, const Unit& U
   uint16_t* __restrict__ wseg = U.wrow + t0;
   const int64_t nleft = U.nt - t0;
   const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));
+  const int64_t sleft = U.ns - t0;
+  const int srel = (int)(sleft < (int64_t)T ? sleft : (int64_t)T);  // starts evaluated and stored
   const BdDyn<K> L(top, TABLE ? p.n_widths : 0);
   float2* AB = reinterpret_cast<float2*>(smem + L.ab);  // table noise: (a, b) per width index
   float mu, inv;
@@ -300,7 +302,7 @@ __device__ __forceinline__ void boxdit_unit(const SearchParams& p, const Unit& U
       }
       __syncwarp();
     }
-    if (ar >= T || !cj) return;
+    if (ar >= srel || !cj) return;
     const int n = cn - ((k * kC) >> cj);
     float bv;
     int bq;
@@ -341,7 +343,7 @@ __device__ __forceinline__ void boxdit_unit(const SearchParams& p, const Unit& U
   const auto sc3 = scl(std::integral_constant<int, 3>{});
   auto fine = [&](int k) {
     const int ar = a0 - k * kC;
-    if (ar >= T) return;
+    if (ar >= srel) return;
     const int buf = k % S::NBUF;
     float y[8], f0[8];
     int w[8];
@@ -405,15 +407,15 @@ __device__ __forceinline__ void boxdit_unit(const SearchParams& p, const Unit& U
       w[0] = take ? wv : w[0];
     }
     const int s0 = ar + 8 * t;
-    if (s0 + 8 <= nrel) {
+    if (s0 + 8 <= srel) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) tmax = fmaxf(tmax, y[r]);
     } else {
 #pragma unroll
       for (int r = 0; r < 8; ++r)
-        if (s0 + r < nrel) tmax = fmaxf(tmax, y[r]);
+        if (s0 + r < srel) tmax = fmaxf(tmax, y[r]);
     }
-    store8(yseg, wseg, s0, nrel, vec, y, w);
+    store8(yseg, wseg, s0, srel, vec, y, w);
     if ((ar & (kCandTile - 1)) == 0) {
       tile_max_atomic(U.tm_row, t0 + ar, tmax);
       tmax = ninf();

@@ -113,6 +113,7 @@ struct Unit {
   const float* sigma;
   int* tm_row;                // the row's candidate-tile keys (or null)
   int64_t row, nt, t0;
+  int64_t ns;                 // starts of the row that are evaluated (<= nt)
   int32_t T;
   bool vec, vec_x;
 };
@@ -124,6 +125,7 @@ __device__ __forceinline__ Unit plan_unit(const SearchParams& p, int64_t u) {
   U.t0 = (u % p.tiles_per_row) * (int64_t)p.tile;
   U.T = p.tile;
   U.nt = p.nt;
+  U.ns = p.n_starts;
   U.xrow = static_cast<const unsigned char*>(p.x) + U.row * p.ld * p.esize;
   U.yrow = p.snr + U.row * p.ld;
   U.wrow = p.widx + U.row * p.ld;
@@ -174,6 +176,7 @@ __device__ __forceinline__ bool batch_unit(const SearchParams& p, int64_t u, Uni
   U.t0 = (local % g.tiles_per_row) * (int64_t)g.tile;
   U.T = g.tile;
   U.nt = g.nt;
+  U.ns = g.nt;
   U.xrow = static_cast<const unsigned char*>(g.x) + U.row * g.ld * p.esize;
   U.yrow = g.snr + U.row * g.ld;
   U.wrow = g.widx + U.row * g.ld;

@@ -171,6 +171,8 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
   uint16_t* __restrict__ wseg = U.wrow + t0;
   const int64_t nleft = U.nt - t0;
   const int nrel = (int)(nleft < (int64_t)(T + H) ? nleft : (int64_t)(T + H));  // samples that exist
+  const int64_t sleft = U.ns - t0;
+  const int srel = (int)(sleft < (int64_t)T ? sleft : (int64_t)T);  // starts evaluated and stored
   constexpr bool ENC = S::ENC;
   const IgDyn L(FX::RINGS, top, MMAX, TABLE ? p.n_widths : 0, ENC);
   float2* AB = reinterpret_cast<float2*>(smem + L.ab);  // table noise: (a, b) per width index
@@ -355,7 +357,7 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
       }
       __syncwarp();
     }
-    if (ar >= T) return;  // halo chunk: nothing to evaluate
+    if (ar >= srel) return;  // halo chunk (or past the evaluated starts): nothing to evaluate
     float* RY = RESY + (k & 1) * kResN;  // unused with coded SNRs
     uint16_t* RW = RESW + (k & 1) * kResN;
     int* KB = BCM + (k & 1) * kBcm;
@@ -429,7 +431,7 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
   float tmax = ninf();
   auto fine = [&](int k) {
     const int ar = a0 - k * kC;
-    if (ar >= T) return;
+    if (ar >= srel) return;
     const int buf = k % FX::NBUF;
     float y[8];
     int w[8];
@@ -556,14 +558,14 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
       }
     }
     const int s0 = ar + 8 * t;
-    if (s0 + 8 <= nrel) {
+    if (s0 + 8 <= srel) {
       tmax = fmax3(fmax3(tmax, y[0], y[1]), fmax3(y[2], y[3], y[4]), fmax3(y[5], y[6], y[7]));
     } else {
 #pragma unroll
       for (int r = 0; r < 8; ++r)
-        if (s0 + r < nrel) tmax = fmaxf(tmax, y[r]);
+        if (s0 + r < srel) tmax = fmaxf(tmax, y[r]);
     }
-    store8(yseg, wseg, s0, nrel, vec, y, w);
+    store8(yseg, wseg, s0, srel, vec, y, w);
     if ((ar & (kCandTile - 1)) == 0) {  // last chunk of a candidate tile (we walk backwards)
       tile_max_atomic(U.tm_row, t0 + ar, tmax);
       tmax = ninf();

@@ -68,6 +68,7 @@ struct SearchParams {
   const float* mu;      // white: [ndm]; table: [ndm][n_widths]
   const float* sigma;
   int64_t ndm, nt, ld;
+  int64_t n_starts;     // starts evaluated per row (<= nt; samples up to nt feed them)
   int32_t tile;         // starts per CTA (multiple of kChunk; streaming kernels: of kCandTile)
   int32_t tiles_per_row;
   int32_t cand_tiles_per_row;  // ceil(nt / kCandTile)
@@ -137,6 +138,7 @@ struct spd_plan {
   int top;        // last level index
   int n_top;      // block counts used on the last level
   int lend;       // largest width
+  int64_t n_starts;  // starts evaluated per row (spd_plan_set_starts; default nt)
   int tile;       // starts per search CTA
   int halo;
   int64_t tiles_per_row;       // search CTAs per row

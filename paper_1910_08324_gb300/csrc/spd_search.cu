@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
     const int64_t s0 = t0 + p0;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (s0 + r < p.nt) tmax = fmaxf(tmax, best[r]);
-    store4(yrow, wrow, s0, p.nt, vec, best, q);
+      if (s0 + r < p.n_starts) tmax = fmaxf(tmax, best[r]);
+    store4(yrow, wrow, s0, p.n_starts, vec, best, q);  // samples to nt feed starts below n_starts
   }
   tile_max_atomic(p.tile_max ? reinterpret_cast<int*>(p.tile_max) + row * p.cand_tiles_per_row : nullptr,
                   t0, tmax);

@@ -124,6 +124,9 @@ def search_flagged(x, ids, mu, sigma, grid: dict, threshold: float = 6.0, radius
     left = -(-max(radius, 1) // sep) * sep
     xs, width = gather_blocks(x, ids, left, lend, grid.get("dtype", B.SPD_F32), stream=stream)
     plan = B.spd_plan_create(ndm=n, nt=width, ld=xs.shape[1], **grid)
+    # evaluate only the block's starts (and the right-hand neighbours its peak test
+    # needs): the context after them only supplies samples
+    B.spd_plan_set_starts(plan, left + BLOCK + radius)
     try:
         Y = torch.empty(xs.shape, dtype=torch.float32, device=x.device)  # outputs share the row stride
         W = torch.empty(xs.shape, dtype=torch.int16, device=x.device)

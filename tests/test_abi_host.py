@@ -198,3 +198,15 @@ def test_torch_helpers_refuse_short_outputs():
     with pytest.raises(spd.SpdError):
         spd.search(plan, x[:, :1000], torch.zeros(2), torch.ones(2), torch.zeros((2, 1024)),
                    torch.zeros((2, 1024), dtype=torch.int16), 6.0, 1, None, torch.zeros(1, dtype=torch.int64), ws)
+
+
+def test_plan_set_starts_rules():
+    plan = spd.spd_plan_create(algo=spd.SPD_ALGO_IGRID, s_end=4096, igrid_depth=1, igrid_layers=4, ndm=2, nt=50000)
+    spd.spd_plan_set_starts(plan, 1)
+    spd.spd_plan_set_starts(plan, 50000)
+    for bad in (0, -5, 50001):
+        with pytest.raises(spd.SpdError) as e:
+            spd.spd_plan_set_starts(plan, bad)
+        assert e.value.status == 1
+    exh = spd.spd_plan_create(algo=spd.SPD_ALGO_EXHAUSTIVE, s_end=64, ndm=1, nt=9000)
+    spd.spd_plan_set_starts(exh, 4097)

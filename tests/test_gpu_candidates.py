@@ -84,3 +84,49 @@ def test_no_candidates_when_threshold_above_everything():
     plan, x, Yh, Wh, (Y, W, ws, *_), _ = _setup()
     n, rec = _gpu_cands(plan, Y, W, 1e9, 1, ws, cap=16)
     assert n == 0 and len(rec) == 0
+
+
+@pytest.mark.parametrize("name,s_end,table", [("exh", 256, False), ("bd16", 4096, True), ("ig1", 4096, False),
+                                              ("dit", 4096, False), ("ig3", 2048, False), ("bd8", 2048, False)])
+def test_fewer_starts_than_samples(name, s_end, table):
+    """spd_plan_set_starts: the first n_starts starts get exactly the outputs of a
+    plan over every start, later starts are not written, and the candidates equal
+    the full plan's away from the new row end."""
+    t = torch()
+    ndm, nt, ns, R = 3, 50000, 30001, 2
+    x = spd_synth.gaussian_noise(ndm, nt, 31, dtype=np.float64)
+    tab = spd_synth.pulse_table(6, ndm, nt, 32, width_range=(1, 300), snr_range=(7.0, 20.0))
+    spd_synth.inject(x, tab, 1.0)
+    xd = t.from_numpy(x.astype(np.float32)).cuda()
+    full = spd.spd_plan_create(ndm=ndm, nt=nt, **ALGOS[name](s_end))
+    part = spd.spd_plan_create(ndm=ndm, nt=nt, **ALGOS[name](s_end))
+    if name != "exh":
+        for pl in (full, part):
+            spd.spd_plan_set_segment(pl, 16384)  # several segments per row
+    spd.spd_plan_set_starts(part, ns)
+    if table:
+        nw = len(full.widths()[0])
+        mu, sg = t.empty((ndm, nw), device="cuda"), t.empty((ndm, nw), device="cuda")
+        ws0 = t.empty(full.workspace_size(), dtype=t.uint8, device="cuda")
+        spd.noise_stats(full, xd, mu, sg, ws0)
+    else:
+        mu, sg = t.zeros(ndm, device="cuda"), t.ones(ndm, device="cuda")
+    mode = 1 if table else 0
+    res = []
+    for pl in (full, part):
+        Y = t.full((ndm, nt), -12345.0, device="cuda")
+        W = t.full((ndm, nt), 777, dtype=t.int16, device="cuda")
+        ws = t.empty(pl.workspace_size(), dtype=t.uint8, device="cuda")
+        out = t.empty(8192 * 24, dtype=t.uint8, device="cuda")
+        cnt = t.zeros(1, dtype=t.int64, device="cuda")
+        spd.search(pl, xd, mu, sg, Y, W, 5.0, R, out, cnt, ws, noise_mode=mode)
+        k = int(cnt.item())
+        assert k <= 8192
+        res.append((Y.cpu().numpy(), W.cpu().numpy(), spd.records(out, k).copy()))
+    (Yf, Wf, rf), (Yp, Wp, rp) = res
+    assert np.array_equal(Yp[:, :ns], Yf[:, :ns]) and np.array_equal(Wp[:, :ns], Wf[:, :ns])
+    assert np.all(Yp[:, ns:] == -12345.0) and np.all(Wp[:, ns:] == 777)
+    near_end = lambda r: r["start"] >= ns - R
+    assert not np.any(rp["start"] >= ns)
+    assert np.array_equal(rp[~near_end(rp)], rf[(rf["start"] < ns) & ~near_end(rf)])
+    assert len(rp) >= 1 and len(rf) >= len(rp)
