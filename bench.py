@@ -446,7 +446,6 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
     searches the flagged ones with BD-16 at full resolution.  The plain BD-16
     search of every block is timed beside it, and recall and SNR loss of both
     are judged by the exhaustive search of windows around the injected pulses."""
-    from oracle import net as onet  # initial weights only (a seeded draw)
     from paper_1910_08324_gb300 import proposal as P
     ndm, nt = args.ndm, args.nt
     grid = dict(PROPOSAL_GRID)
@@ -488,7 +487,7 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
     y = P.label_blocks(plain(plan, xtr, mu, sg, ws, Ytr, Wtr), ptr, args.train_rows, nt)
     X = P.decimated_blocks(xtr, mu[:, 0].contiguous(), sg[:, 0].contiguous(), dtype=grid["dtype"])
     del xtr, Ytr, Wtr, plan, ws
-    params = torch.from_numpy(onet.init_params(seed + 2)).to(dev)
+    params = torch.from_numpy(spd_synth.net_init_params(seed + 2)).to(dev)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     losses, _, _ = P.train(params, X, torch.from_numpy(y).to(dev), steps=args.train_steps, batch=512, lr=3e-3,
@@ -611,6 +610,7 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
     cpu = None
     if not args.no_cpu and rank == 0:
         import oracle
+        from oracle import net as onet
         g = oracle.grid_boxdit(16, 4096)
         lend, sep = P.plan_geometry(grid)
         done, spent, r = 0, 0.0, 0

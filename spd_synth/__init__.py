@@ -334,3 +334,24 @@ def proposal_amplitudes(table, nt: int, red: bool = True, device="cuda") -> np.n
     w = table["width"].astype(np.float64)
     var = w + (red_boxcar_var(table["width"], nt, device=device) if red and len(table) else 0.0)
     return table["snr"] * np.sqrt(var) / w
+
+
+# ---------------------------------------------------------------- proposal network weights
+# Parameter layout of the proposal network (float32 vector): W1[16][9], b1[16],
+# W2[16][16][9], b2[16], W3[16][16][9], b3[16], W4[16], b4.
+NET_SHAPES = [("W1", (16, 1, 9)), ("b1", (16,)), ("W2", (16, 16, 9)), ("b2", (16,)), ("W3", (16, 16, 9)),
+              ("b3", (16,)), ("W4", (16,)), ("b4", (1,))]
+
+
+def net_init_params(seed: int) -> np.ndarray:
+    """Seeded He-style initial weights of the proposal network (normal, deviation
+    sqrt(2 / fan-in) for the weights; zero biases), float32 in the layout above."""
+    g = np.random.default_rng(int(seed))
+    parts = []
+    for name, shp in NET_SHAPES:
+        if name.startswith("W"):
+            fan_in = shp[1] * shp[2] if len(shp) == 3 else shp[0]
+            parts.append(g.normal(0.0, math.sqrt(2.0 / fan_in), shp).reshape(-1))
+        else:
+            parts.append(np.zeros(int(np.prod(shp))))
+    return np.concatenate(parts).astype(np.float32)

@@ -145,3 +145,36 @@ def test_batch_ready_flags_and_bounded_wait():
     spd.batch_execute(b, dx, ys, wis, mus, sgs, ws, readys=ready)
     spd.spd_batch_status(b, ws.data_ptr(), st)
     assert np.array_equal(ys[2].cpu().numpy(), ref[2])
+
+
+def test_batch_flags_set_while_the_search_waits():
+    """Ranges copied in after the persistent search was launched: a copy stream
+    uploads each range and then sets its ready flag with a 4-byte copy; the
+    units of each range start when they see the flag, and the outputs equal the
+    search of data already in place."""
+    t = torch()
+    xs = _ranges(950)
+    b = _batch("bd16", 4096)
+    dx, ys, wis, mus, sgs = _alloc(t, xs)
+    ws = t.empty(b.workspace_size(), dtype=t.uint8, device="cuda")
+    spd.batch_execute(b, dx, ys, wis, mus, sgs, ws)
+    ref = [y.cpu().numpy().copy() for y in ys]
+    hs = [t.from_numpy(x).pin_memory() for x in xs]
+    for d in dx:
+        d.zero_()
+    for y in ys:
+        y.fill_(-7.0)
+    flags = t.zeros(len(xs), dtype=t.int32, device="cuda")
+    one = t.ones(1, dtype=t.int32).pin_memory()
+    b.set_wait_ns(5 * 10 ** 9)
+    main, cs = t.cuda.current_stream(), t.cuda.Stream()
+    t.cuda.synchronize()
+    spd.batch_execute(b, dx, ys, wis, mus, sgs, ws, readys=[flags[r:r + 1] for r in range(len(xs))], stream=main)
+    with t.cuda.stream(cs):
+        for r, (h, d) in enumerate(zip(hs, dx)):
+            d.copy_(h, non_blocking=True)
+            flags[r:r + 1].copy_(one, non_blocking=True)
+    cs.synchronize()
+    spd.spd_batch_status(b, ws.data_ptr(), main.cuda_stream)
+    for r, y in enumerate(ys):
+        assert np.array_equal(y.cpu().numpy(), ref[r]), r
