@@ -27,7 +27,8 @@
 //     Alg. 1's, added in another order (fp32 rounding differs, exactness of the
 //     grid does not).
 // Coarse results reach the fine step of their chunk through a per-start atomic
-// key, as in the IGRID kernel.  Samples past the end of a row are -inf.
+// key, as in the IGRID kernel.  Samples past the end of a row are -inf; starts at
+// or past the plan's n_starts are neither evaluated nor stored.
 #include <climits>
 
 #include "spd_common.cuh"

@@ -20,16 +20,22 @@
 //           ring buffers for the coarse levels 4.. (unit >= 16); the loads of
 //           chunk k+2 are issued;
 //   barrier
-//   coarse  one thread per coarse position of chunk k+1 evaluates it from its
-//           ring (scalar loads); results go to one of two result buffers;
+//   coarse  chunk k+1's coarse positions: quads of 4 consecutive positions of
+//           levels 4..8 (one float4 ring window each) on the first 62 threads,
+//           single positions of levels 9..11 on the last warp (after it has
+//           built those levels' blocks); each result is posted to a per-start
+//           key with a shared atomic maximum;
 //   fine    each thread owns 8 consecutive starts of chunk k and evaluates
 //           levels 0..3 from register windows (8 + 4 + 2 + 1 positions),
-//           merges them and chunk k's coarse results (computed one iteration
-//           earlier) in registers (strict '>' in increasing width order), and
-//           writes 8 SNRs (2 x float4) and 8 widths.
-// The coarse evaluation of one chunk thus overlaps the fine evaluation of the
-// next instead of sitting between two barriers.  Samples past the end of the
-// row are -inf, so a boxcar needing them never wins (the s + L <= nt rule).
+//           merges them with the start's coarse key (computed one iteration
+//           earlier) and writes 8 SNRs (2 x float4) and 8 widths.
+// Grids of at most 32 widths carry the width index in the SNRs' low mantissa
+// bits, so every maximum and merge is one max instruction; two starts share
+// each add and scale instruction (packed f32x2).  The coarse evaluation of one
+// chunk overlaps the fine evaluation of the previous one instead of sitting
+// between two barriers.  Samples past the end of the row are -inf, so a boxcar
+// needing them never wins (the s + L <= nt rule); starts at or past the plan's
+// n_starts are neither evaluated nor stored.
 #include <climits>
 
 #include "spd_common.cuh"

@@ -13,7 +13,8 @@
 // staged once in shared memory, each thread owns 4 starts and extends their
 // running sums width by width in register windows (32 widths per window),
 // with 1/sqrt(L) from a shared table.  The tile maximum goes to the workspace
-// for the candidate step.  BoxDIT and IGRID have streaming kernels of their
+// for the candidate step.  Only starts below the plan's n_starts are stored;
+// samples up to nt feed them.  BoxDIT and IGRID have streaming kernels of their
 // own (spd_boxdit.cu, spd_igrid.cu).
 #include "spd_common.cuh"
 
