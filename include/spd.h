@@ -152,6 +152,19 @@ const char *spd_version(void);
  */
 spd_status spd_plan_create(const spd_plan_desc *desc, spd_plan **out);
 
+/*
+ * Build a plan over an explicit grid: Sec. 2.2 characterises a search by its
+ * set of boxcar widths and the boxcar separation L_s of each width; here both
+ * are given as lists, widths[i] searched at the starts that are multiples of
+ * seps[i].  widths strictly increasing, 1 <= widths[i] <= 4096,
+ * widths[0] == 1 with seps[0] == 1 (every start has a value); seps powers of
+ * two <= 4096; 1 <= n_widths <= 512.  desc supplies dtype, ndm, nt and ld (its
+ * algorithm fields are ignored).  Searched like the exhaustive grid, widths
+ * outside the set skipped: width index i of snr / width_idx is widths[i].  Host
+ * only.  SPD_ERR_INVALID_ARG for a set or shape that breaks these rules.
+ */
+spd_status spd_plan_create_grid(const spd_plan_desc *desc, const int32_t *widths, const int32_t *seps,
+                                int32_t n_widths, spd_plan **out);
 /* Release a plan (NULL is accepted).  No device synchronisation. */
 spd_status spd_plan_destroy(spd_plan *plan);
 

@@ -54,6 +54,7 @@ from ._binding import (  # noqa: F401
     spd_plan_create,
     spd_plan_set_segment,
     spd_plan_set_starts,
+    spd_plan_create_grid,
     spd_plan_destroy,
     spd_plan_widths,
     spd_search,

@@ -59,7 +59,7 @@ _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_des
             "spd_plan_set_segment", "spd_batch_create", "spd_batch_destroy", "spd_batch_set_segment",
             "spd_batch_set_wait_ns", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
             "spd_batch_candidates", "spd_net_decimate", "spd_net_forward", "spd_net_gradient",
-            "spd_net_adam", "spd_net_select", "spd_net_gather", "spd_plan_set_starts"]
+            "spd_net_adam", "spd_net_select", "spd_net_gather", "spd_plan_set_starts", "spd_plan_create_grid"]
 
 
 def library_path() -> str:
@@ -92,6 +92,7 @@ def load_library():
         lib.spd_noise_stats.argtypes = [vp, vp, ctypes.c_float, i32, vp, vp, vp, sz, vp]
         lib.spd_plan_set_segment.argtypes = [vp, i32]
         lib.spd_plan_set_starts.argtypes = [vp, i64]
+        lib.spd_plan_create_grid.argtypes = [ctypes.POINTER(_Desc), vp, vp, i32, ctypes.POINTER(vp)]
         lib.spd_net_param_count.argtypes = []
         lib.spd_net_param_count.restype = ctypes.c_int32
         lib.spd_net_decimate.argtypes = [vp, i32, i64, i64, i64, vp, vp, vp, vp]
@@ -162,6 +163,22 @@ def spd_plan_create(algo: int, s_end: int, ndm: int, nt: int, ld: int | None = N
               int(igrid_layers), int(ndm), int(nt), int(nt if ld is None else ld))
     h = ctypes.c_void_p()
     _check(lib.spd_plan_create(ctypes.byref(d), ctypes.byref(h)), "spd_plan_create")
+    return Plan(h.value, d)
+
+
+def spd_plan_create_grid(widths, seps, ndm: int, nt: int, ld: int | None = None, dtype: int = SPD_F32) -> Plan:
+    """Plan over an explicit width set: widths[i] searched at the starts that are
+    multiples of seps[i] (width 1 at every start first; separations powers of two)."""
+    lib = load_library()
+    w = np.ascontiguousarray(np.asarray(widths, np.int32))
+    s = np.ascontiguousarray(np.asarray(seps, np.int32))
+    if w.shape != s.shape or w.ndim != 1:
+        raise SpdError(1, "spd_plan_create_grid: widths and seps differ in shape")
+    d = _Desc(SPD_ALGO_EXHAUSTIVE, int(dtype), int(w[-1]) if len(w) else 1, 0, 0, 0, int(ndm), int(nt),
+              int(nt if ld is None else ld))
+    h = ctypes.c_void_p()
+    _check(lib.spd_plan_create_grid(ctypes.byref(d), w.ctypes.data, s.ctypes.data, len(w), ctypes.byref(h)),
+           "spd_plan_create_grid")
     return Plan(h.value, d)
 
 

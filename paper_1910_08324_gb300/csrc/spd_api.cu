@@ -163,9 +163,12 @@ void fill_grid(spd::SearchParams& p, const spd_plan& plan) {
   }
   for (int m = 1; m < 64; ++m) p.rs[m] = (float)(1.0 / std::sqrt((double)m));
   p.n_widths = (int32_t)plan.widths.size();
-  p.unit_widths = plan.family == kExhaustive ? 1 : 0;
+  p.unit_widths = (plan.family == kExhaustive && !plan.explicit_grid) ? 1 : 0;
   if (!p.unit_widths)
     for (size_t i = 0; i < plan.widths.size() && i < (size_t)spd::kMaxGridWidths; ++i) p.wtab[i] = plan.widths[i];
+  p.grid = plan.explicit_grid ? 1 : 0;
+  if (plan.explicit_grid)
+    for (size_t i = 0; i < plan.seps.size() && i < (size_t)spd::kMaxGridWidths; ++i) p.wsep[i] = plan.seps[i];
   if (plan.family == kBoxdit) {
     for (int j = 0; j <= plan.top; ++j)
       for (int m = 1; m <= plan.k; ++m)
@@ -246,7 +249,7 @@ void fill_cand_params(spd::CandParams& p, const spd_plan* plan, const float* d_s
   p.tiles_per_row = (int32_t)plan->cand_tiles_per_row;
   p.radius = peak_radius;
   p.thr = threshold;
-  p.width_mode = plan->family == kExhaustive ? 0 : 1;
+  p.width_mode = (plan->family == kExhaustive && !plan->explicit_grid) ? 0 : 1;
   if (p.width_mode)
     for (size_t i = 0; i < plan->widths.size() && i < 512; ++i) p.width_tab[i] = plan->widths[i];
 }
@@ -359,6 +362,51 @@ cudaError_t persistent_config(const void* kernel, size_t smem, int* per_sm, int*
 }
 }  // namespace spd
 
+namespace {
+// Geometry common to every plan (widest width, tiles, halo, limits); takes
+// ownership of p.
+spd_status finish_plan(spd_plan* p, spd_plan** out) {
+  const spd_plan_desc& d = p->desc;
+  p->lend = p->widths.back();
+  if (p->lend > spd::kMaxLend || p->widths.size() > 65535 ||
+      (p->family != kExhaustive && p->widths.size() > (size_t)spd::kMaxGridWidths) ||
+      p->top >= spd::kMaxLevels) {
+    delete p;
+    return SPD_ERR_INVALID_ARG;
+  }
+  if (p->family == kExhaustive) {
+    p->tile = spd::kChunk;
+    p->halo = 0;
+  } else {
+    // BoxDIT and IGRID: one CTA streams a segment of 131072 to 524288 starts (a
+    // multiple of the candidate tile; default_segment); the halo is the widest
+    // boxcar, rounded to whole chunks
+    if (p->family == kBoxdit && p->top > 11) {  // unreachable below kMaxLend; the kernel stops at 11
+      delete p;
+      return SPD_ERR_UNSUPPORTED;
+    }
+    // IGRID with depth <= 1 and <= 4 layers carries width indices in 5 SNR bits
+    // (at most 31 widths below kMaxLend)
+    if (p->family == kIgrid && p->d <= 1 && p->pl <= 2 && p->widths.size() > 32) {
+      delete p;
+      return SPD_ERR_UNSUPPORTED;
+    }
+    p->tile = segment_tile(d.nt, default_segment(d.ndm, d.nt));
+    p->halo = ((p->lend + spd::kChunk - 1) / spd::kChunk) * spd::kChunk;
+  }
+  p->n_starts = d.nt;
+  p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
+  p->cand_tiles_per_row = (d.nt + spd::kCandTile - 1) / spd::kCandTile;
+  if (p->desc.ndm * p->tiles_per_row > ((int64_t)1 << 31) - 1 ||
+      spd::search_smem_bytes(*p, true) > 227 * 1024) {
+    delete p;
+    return SPD_ERR_UNSUPPORTED;
+  }
+  *out = p;
+  return SPD_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* spd_status_string(spd_status s) {
@@ -431,43 +479,43 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
     delete p;
     return st;
   }
-  p->lend = p->widths.back();
-  if (p->lend > spd::kMaxLend || p->widths.size() > 65535 ||
-      (p->family != kExhaustive && p->widths.size() > (size_t)spd::kMaxGridWidths) ||
-      p->top >= spd::kMaxLevels) {
-    delete p;
+  return finish_plan(p, out);
+}
+
+spd_status spd_plan_create_grid(const spd_plan_desc* desc, const int32_t* widths, const int32_t* seps,
+                                int32_t n_widths, spd_plan** out) {
+  if (!out) return SPD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc || !widths || !seps || n_widths < 1 || n_widths > spd::kMaxGridWidths) return SPD_ERR_INVALID_ARG;
+  const spd_plan_desc& d = *desc;
+  if (d.ndm < 1 || d.nt < 1 || d.ld < d.nt || d.ndm > (int64_t)1 << 24 || d.nt > (int64_t)1 << 40)
     return SPD_ERR_INVALID_ARG;
+  if (d.dtype < SPD_F32 || d.dtype > SPD_U8) return SPD_ERR_INVALID_ARG;
+  if (widths[0] != 1 || seps[0] != 1) return SPD_ERR_INVALID_ARG;  // width 1 at every start
+  for (int32_t i = 0; i < n_widths; ++i) {
+    if (widths[i] < 1 || widths[i] > spd::kMaxExhaustive || (i > 0 && widths[i] <= widths[i - 1]))
+      return SPD_ERR_INVALID_ARG;
+    if (seps[i] < 1 || seps[i] > spd::kMaxExhaustive || !is_pow2(seps[i])) return SPD_ERR_INVALID_ARG;
   }
-  if (p->family == kExhaustive) {
-    p->tile = spd::kChunk;
-    p->halo = 0;
-  } else {
-    // BoxDIT and IGRID: one CTA streams a segment of 131072 to 524288 starts (a
-    // multiple of the candidate tile; default_segment); the halo is the widest
-    // boxcar, rounded to whole chunks
-    if (p->family == kBoxdit && p->top > 11) {  // unreachable below kMaxLend; the kernel stops at 11
-      delete p;
-      return SPD_ERR_UNSUPPORTED;
-    }
-    // IGRID with depth <= 1 and <= 4 layers carries width indices in 5 SNR bits
-    // (at most 31 widths below kMaxLend)
-    if (p->family == kIgrid && p->d <= 1 && p->pl <= 2 && p->widths.size() > 32) {
-      delete p;
-      return SPD_ERR_UNSUPPORTED;
-    }
-    p->tile = segment_tile(d.nt, default_segment(d.ndm, d.nt));
-    p->halo = ((p->lend + spd::kChunk - 1) / spd::kChunk) * spd::kChunk;
-  }
-  p->n_starts = d.nt;
-  p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
-  p->cand_tiles_per_row = (d.nt + spd::kCandTile - 1) / spd::kCandTile;
-  if (p->desc.ndm * p->tiles_per_row > ((int64_t)1 << 31) - 1 ||
-      spd::search_smem_bytes(*p, true) > 227 * 1024) {
+  spd_plan* p = new (std::nothrow) spd_plan();
+  if (!p) return SPD_ERR_HOST_ALLOC;
+  p->desc = d;
+  p->desc.algo = SPD_ALGO_EXHAUSTIVE;
+  p->desc.s_end = widths[n_widths - 1];
+  try {
+    p->family = kExhaustive;
+    p->explicit_grid = true;
+    p->widths.assign(widths, widths + n_widths);
+    p->seps.assign(seps, seps + n_widths);
+    p->lvl_first.push_back(0);
+    p->lvl_base.push_back(0);
+  } catch (const std::bad_alloc&) {
     delete p;
-    return SPD_ERR_UNSUPPORTED;
+    return SPD_ERR_HOST_ALLOC;
   }
-  *out = p;
-  return SPD_OK;
+  p->top = 0;
+  p->n_top = n_widths;
+  return finish_plan(p, out);
 }
 
 spd_status spd_plan_destroy(spd_plan* plan) {
@@ -568,7 +616,7 @@ spd_status spd_noise_stats(const spd_plan* plan, const void* d_x, float outlier_
   p.out_mu = d_mu;
   p.out_sigma = d_sigma;
   p.n_widths = (int32_t)plan->widths.size();
-  p.unit_widths = plan->family == kExhaustive ? 1 : 0;
+  p.unit_widths = (plan->family == kExhaustive && !plan->explicit_grid) ? 1 : 0;
   if (!p.unit_widths)
     for (size_t i = 0; i < plan->widths.size() && i < (size_t)spd::kMaxGridWidths; ++i)
       p.wtab[i] = plan->widths[i];

@@ -88,6 +88,8 @@ struct SearchParams {
   int32_t n_widths;               // widths of the plan
   int32_t unit_widths;            // 1: width index w is width w + 1 (exhaustive grid)
   int32_t wtab[kMaxGridWidths];   // widths of the plan (table noise, unit_widths == 0)
+  int32_t grid;                   // 1: explicit width set (spd_plan_create_grid), exhaustive kernel
+  int32_t wsep[kMaxGridWidths];   // explicit set: start separation of each width (a power of two)
   // batched search: units are (range, row, segment); 0 ranges: the single series above
   int32_t n_ranges;
   int64_t n_units;
@@ -139,6 +141,7 @@ struct spd_plan {
   int n_top;      // block counts used on the last level
   int lend;       // largest width
   int64_t n_starts;  // starts evaluated per row (spd_plan_set_starts; default nt)
+  bool explicit_grid = false;  // widths and separations given by the caller (spd_plan_create_grid)
   int tile;       // starts per search CTA
   int halo;
   int64_t tiles_per_row;       // search CTAs per row

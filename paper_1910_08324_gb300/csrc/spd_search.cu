@@ -27,9 +27,11 @@ static_assert(kItems0 * 4 * kThreads == kChunk, "tile must split evenly");
 // ============================================================================ exhaustive
 // table: the scale table holds (a, b) float2 pairs (table noise) instead of 1/sqrt(L)
 static_assert(kAbPad <= 33, "the exhaustive scale table pads 33 entries");
+// grid: an explicit width set, with per-block-count tables of the width index
+// (-1 outside the set) and of the start mask (separation - 1)
 struct ExLayout {
-  int f0, rs, red, total;
-  __host__ __device__ ExLayout(int lmax, bool table) {
+  int f0, rs, red, ix, ms, total;
+  __host__ __device__ ExLayout(int lmax, bool table, bool grid) {
     int o = 0;
     f0 = o;
     o += al4(kChunk + ((lmax + 36 + 127) / 128) * 128 + 8);
@@ -37,11 +39,19 @@ struct ExLayout {
     o += al4((lmax + 33) * (table ? 2 : 1));  // table: lmax widths + kAbPad (<= 33) padding pairs
     red = o;
     o += 32;
+    ix = o;
+    o += grid ? al4(lmax + 33) : 0;
+    ms = o;
+    o += grid ? al4(lmax + 33) : 0;
     total = o;
   }
 };
 
-template <bool TABLE>
+// GRID: the widths of an explicit set only (p.wtab, p.wsep; width 1 at every
+// start): the running sums still advance one sample per block count m, and
+// width m is a candidate at start s iff it is in the set and s is a multiple of
+// its separation; the stored width index is its index in the set.
+template <bool TABLE, bool GRID>
 __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchParams p) {
   extern __shared__ __align__(16) float smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -52,7 +62,7 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
   const unsigned char* __restrict__ xrow = static_cast<const unsigned char*>(p.x) + row * p.ld * p.esize;
 
   const bool vec = p.vec != 0;
-  const ExLayout L(lmax, TABLE);
+  const ExLayout L(lmax, TABLE, GRID);
   float* F0 = smem + L.f0;
   float* RS = smem + L.rs;  // white noise: RS[m] = 1/sqrt(m); table noise: AB[m - 1] = (a, b)
   float2* AB = reinterpret_cast<float2*>(smem + L.rs);
@@ -61,6 +71,19 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
   if constexpr (!TABLE)
     for (int m = tid; m <= lmax + 32; m += kThreads)
       RS[m] = (m >= 1 && m <= lmax) ? (float)(1.0 / sqrt((double)m)) : 0.0f;
+  int* IX = reinterpret_cast<int*>(smem + L.ix);
+  int* MS = reinterpret_cast<int*>(smem + L.ms);
+  if constexpr (GRID) {
+    for (int m = tid; m <= lmax + 32; m += kThreads) {
+      IX[m] = -1;
+      MS[m] = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < p.n_widths; i += kThreads) {
+      IX[p.wtab[i]] = i;
+      MS[p.wtab[i]] = p.wsep[i] - 1;
+    }
+  }
   const int nchunk = (kChunk + ((lmax + 36 + 127) / 128) * 128) / 128;
   for (int c = warp; c < nchunk; c += kThreads / 32) {
     const float4 z = load_z4d(xrow, t0 + c * 128 + lane * 4, p.nt, p.dtype, p.vec_x != 0, mu, inv);
@@ -95,7 +118,31 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
       static_for<0, 32>([&](auto MI) {
         constexpr int mi = decltype(MI)::value;
         const int m = mbase + mi + 1;
-        if (!tail || m <= lmax) {
+        if constexpr (GRID) {
+          if (!tail || m <= lmax) {
+            const int ix = IX[m], ms = MS[m];
+            static_for<0, 4>([&](auto R) {
+              constexpr int r = decltype(R)::value;
+              S[r] += w[r + mi];
+            });
+            if (ix >= 0) {
+              const auto sc = [&] {
+                if constexpr (TABLE)
+                  return AB[ix];
+                else
+                  return RS[m];
+              }();
+              static_for<0, 4>([&](auto R) {
+                constexpr int r = decltype(R)::value;
+                const float v = snr_of(S[r], sc);
+                if (((t0 + p0 + r) & ms) == 0 && v > best[r]) {
+                  best[r] = v;
+                  q[r] = ix;
+                }
+              });
+            }
+          }
+        } else if (!tail || m <= lmax) {
           const auto sc = [&] {
             if constexpr (TABLE)
               return AB[m - 1];
@@ -128,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
 
 size_t search_smem_bytes(const spd_plan& plan, bool table) {
   switch (plan.family) {
-    case kExhaustive: return sizeof(float) * (size_t)ExLayout(plan.lend, table).total;
+    case kExhaustive: return sizeof(float) * (size_t)ExLayout(plan.lend, table, plan.explicit_grid).total;
     case kIgrid: return igrid_smem_bytes(plan, table);
     default: return boxdit_smem_bytes(plan, table);
   }
@@ -138,8 +185,11 @@ cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStrea
   if (plan.family == kExhaustive) {
     const size_t smem = search_smem_bytes(plan, p.table != 0);
     const int64_t nblk = plan.desc.ndm * plan.tiles_per_row;
-    return p.table ? launch_one(exhaustive_kernel<true>, smem, nblk, p, s)
-                   : launch_one(exhaustive_kernel<false>, smem, nblk, p, s);
+    if (plan.explicit_grid)
+      return p.table ? launch_one(exhaustive_kernel<true, true>, smem, nblk, p, s)
+                     : launch_one(exhaustive_kernel<false, true>, smem, nblk, p, s);
+    return p.table ? launch_one(exhaustive_kernel<true, false>, smem, nblk, p, s)
+                   : launch_one(exhaustive_kernel<false, false>, smem, nblk, p, s);
   }
   if (plan.family == kBoxdit) return launch_boxdit(plan, p, s);
   return launch_igrid(plan, p, s);

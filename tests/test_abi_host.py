@@ -210,3 +210,24 @@ def test_plan_set_starts_rules():
         assert e.value.status == 1
     exh = spd.spd_plan_create(algo=spd.SPD_ALGO_EXHAUSTIVE, s_end=64, ndm=1, nt=9000)
     spd.spd_plan_set_starts(exh, 4097)
+
+
+def test_explicit_grid_rules():
+    ok = spd.spd_plan_create_grid([1, 3, 5, 10, 50, 200], [1, 1, 2, 4, 8, 32], ndm=2, nt=5000)
+    w, s = ok.widths()
+    assert w.tolist() == [1, 3, 5, 10, 50, 200] and s.tolist() == [1, 1, 2, 4, 8, 32]
+    bad = [([2, 3], [1, 1]),            # width 1 must come first
+           ([1, 3], [2, 1]),            # width 1 at every start
+           ([1, 5, 5], [1, 1, 1]),      # strictly increasing
+           ([1, 5, 4], [1, 1, 1]),
+           ([1, 6], [1, 3]),            # separations are powers of two
+           ([1, 5000], [1, 1]),         # at most 4096
+           (list(range(1, 514)), [1] * 513)]  # at most 512 widths
+    for widths, seps in bad:
+        with pytest.raises(spd.SpdError) as e:
+            spd.spd_plan_create_grid(widths, seps, ndm=2, nt=5000)
+        assert e.value.status == 1, (widths[:4], seps[:4])
+    # an explicit grid equal to a built-in one has the same table
+    g = oracle.grid_boxdit(8, 512)
+    pl = spd.spd_plan_create_grid(g.L, g.Ls, ndm=1, nt=4096)
+    assert np.array_equal(pl.widths()[0], g.L) and np.array_equal(pl.widths()[1], g.Ls)

@@ -160,3 +160,34 @@ def test_sliding_pulse_within_appendix_bounds(name):
         bmax, bmin = oracle.rsnr_bounds(g, S, 1.0)
         assert abs(best.max() - bmax) < 1e-5, (name, S, best.max(), bmax)
         assert best.min() >= bmin - 1e-5, (name, S, best.min(), bmin)
+
+
+EXPLICIT = {
+    "bd8": lambda: oracle.grid_boxdit(8, 512),
+    "ig2": lambda: oracle.grid_igrid(2, 8, 1024),
+    "sparse": lambda: oracle.Grid([1, 3, 5, 10, 50, 200, 999], [1, 1, 2, 4, 8, 32, 64]),
+}
+
+
+@pytest.mark.parametrize("name", list(EXPLICIT))
+@pytest.mark.parametrize("table", [False, True])
+def test_explicit_grid_parity(name, table):
+    """spd_plan_create_grid: a caller-given width set with per-width separations
+    against the oracle's search of the same grid (several tiles, ragged tail)."""
+    g = EXPLICIT[name]()
+    ndm, nt = 3, 20011
+    x = spd_synth.gaussian_noise(ndm, nt, 71, dtype=np.float64)
+    tab = spd_synth.pulse_table(6, ndm, nt, 72, width_range=(1, 400), snr_range=(7.0, 25.0))
+    spd_synth.inject(x, tab, 1.0)
+    plan = spd.spd_plan_create_grid(g.L, g.Ls, ndm=ndm, nt=nt)
+    if table:
+        rng = np.random.default_rng(73)
+        L = g.L.astype(np.float64)
+        mu = 0.1 * L[None, :] + rng.normal(0, 0.05, (ndm, 1)) * L[None, :]
+        sg = np.sqrt(L)[None, :] * rng.uniform(0.9, 1.3, (ndm, 1))
+        Yg, Wg = run_gpu(plan, x.astype(np.float32), mu, sg, noise_mode=1)
+        Yo, Wo, Y2o = oracle.search(x, g, mu, sg, noise_mode=1)
+    else:
+        Yg, Wg = run_gpu(plan, x.astype(np.float32), 0.0, 1.0)
+        Yo, Wo, Y2o = oracle.search(x, g)
+    assert_parity(Yg, Wg, Yo, Wo, Y2o, nt, ctx="explicit %s" % name)
