@@ -239,36 +239,90 @@ def label_blocks(rec, pulses, ndm: int, nt: int):
     return y
 
 
+_PERM_CACHE: dict = {}  # the permutation of the epoch last used (key, tensor)
+
+
+def batch_indices(n: int, batch: int, seed: int, step: int, device=None):
+    """Block indices of training step ``step`` (counting from 0): the steps of an
+    epoch take consecutive slices of a permutation of the n blocks drawn from a
+    generator seeded with (seed, epoch), so the schedule is a function of the
+    step alone and a resumed run sees the batches an uninterrupted one would."""
+    import torch
+    per_epoch = max(n // batch, 1)
+    epoch, k = divmod(step, per_epoch)
+    key = (n, int(seed), epoch, str(device))
+    perm = _PERM_CACHE.get("perm") if _PERM_CACHE.get("key") == key else None
+    if perm is None:
+        g = torch.Generator(device=device)
+        g.manual_seed(int(seed) * 1000003 + epoch)
+        perm = torch.randperm(n, generator=g, device=device)
+        _PERM_CACHE["key"], _PERM_CACHE["perm"] = key, perm
+    return perm[k * batch:(k + 1) * batch]
+
+
 def train(params, X, y, steps: int, batch: int = 512, lr: float = 3e-3, seed: int = 0, m=None, v=None,
           step0: int = 0, stream=None):
-    """``steps`` Adam steps of the network on shuffled mini-batches of the decimated
-    blocks ``X`` (float32 [n, 256]) with labels ``y`` (float32 [n]); updates
-    ``params`` (and the moments ``m``, ``v``) in place.  Returns the mean loss of
-    each step (host list)."""
+    """Steps step0 .. step0 + steps - 1 of Adam on mini-batches of the decimated
+    blocks ``X`` (float32 [n, 256]) with labels ``y`` (float32 [n])
+    (``batch_indices``); updates ``params`` (and the moments ``m``, ``v``) in
+    place.  Returns (mean loss of each step as a host list, m, v)."""
     import torch
     dev = params.device
     m = torch.zeros_like(params) if m is None else m
     v = torch.zeros_like(params) if v is None else v
     G = torch.empty_like(params)
     L = torch.empty(1, dtype=torch.float32, device=dev)
-    g = torch.Generator(device=dev)
-    g.manual_seed(int(seed))
     n = X.shape[0]
     losses = torch.empty(steps, dtype=torch.float32, device=dev)
-    perm = torch.randperm(n, generator=g, device=dev)
-    pos = 0
     for i in range(steps):
-        if pos + batch > n:
-            perm = torch.randperm(n, generator=g, device=dev)
-            pos = 0
-        idx = perm[pos:pos + batch]
-        pos += batch
+        idx = batch_indices(n, batch, seed, step0 + i, device=dev)
         xb = X[idx].contiguous()
         yb = y[idx].contiguous()
         B.net_gradient(params, xb, yb, G, L, stream=stream)
-        B.net_adam(params, m, v, G, batch, lr, step0 + i + 1, stream=stream)
-        losses[i] = L[0] / batch
+        B.net_adam(params, m, v, G, idx.numel(), lr, step0 + i + 1, stream=stream)
+        losses[i] = L[0] / idx.numel()
     return losses.cpu().tolist(), m, v
+
+
+# checkpoints of training: magic, version, parameter count, step, seed, then the
+# parameters and the two Adam moments as float32 (little-endian throughout)
+_CKPT_MAGIC = b"SPDNETCK"
+_CKPT_VERSION = 1
+
+
+def save_checkpoint(path, params, m, v, step: int, seed: int):
+    """Write the training state (weights, Adam moments, next step, schedule
+    seed) to ``path`` as one flat binary file (atomically: a temporary file
+    renamed over it)."""
+    import os
+    import struct
+    arrs = [np.ascontiguousarray(t.detach().float().cpu().numpy(), dtype="<f4") for t in (params, m, v)]
+    if not (arrs[0].size == arrs[1].size == arrs[2].size):
+        raise ValueError("parameter and moment vectors differ in size")
+    tmp = str(path) + ".tmp"
+    with open(tmp, "wb") as f:
+        f.write(_CKPT_MAGIC + struct.pack("<IIqq", _CKPT_VERSION, arrs[0].size, int(step), int(seed)))
+        for a in arrs:
+            f.write(a.tobytes())
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path, device="cuda"):
+    """(params, m, v, step, seed) from ``save_checkpoint``'s file, the vectors as
+    float32 tensors on ``device``; ValueError for a file of another format."""
+    import struct
+    import torch
+    with open(path, "rb") as f:
+        raw = f.read()
+    head = len(_CKPT_MAGIC) + struct.calcsize("<IIqq")
+    if len(raw) < head or raw[:len(_CKPT_MAGIC)] != _CKPT_MAGIC:
+        raise ValueError("not a proposal-network checkpoint: %s" % path)
+    version, n, step, seed = struct.unpack("<IIqq", raw[len(_CKPT_MAGIC):head])
+    if version != _CKPT_VERSION or len(raw) != head + 12 * n:
+        raise ValueError("checkpoint %s: version %d, %d bytes for %d parameters" % (path, version, len(raw), n))
+    vecs = [torch.from_numpy(np.frombuffer(raw, dtype="<f4", count=n, offset=head + 4 * n * i).copy()).to(device)
+            for i in range(3)]
+    return vecs[0], vecs[1], vecs[2], int(step), int(seed)
 
 
 def pulse_snr(x, pulses, mu, sigma, grid: dict, noise_mode: int = 1, width_ratio: float = 4.0, stream=None):

@@ -175,3 +175,24 @@ def test_trained_network_gain_on_red_noise_with_spikes():
     assert s_prop["recall_w16_256"] >= 0.95 and s_prop["recall_w256_4096"] >= 0.95
     assert s_prop["snr_loss"] <= 0.07
     assert s_prop["false_alarms"] <= 0.1 * s_plain["false_alarms"]
+
+
+def test_training_resumes_from_a_checkpoint(tmp_path):
+    """30 Adam steps straight equal 15 steps, a checkpoint written and read back,
+    and 15 more (the batch schedule is a function of the step; the gradient sums
+    over CTAs in any order, so the comparison allows FP32 reordering)."""
+    t = torch()
+    rng = np.random.default_rng(11)
+    X = t.from_numpy(rng.normal(size=(2048, 256)).astype(np.float32)).cuda()
+    y = t.from_numpy((rng.random(2048) < 0.5).astype(np.float32)).cuda()
+    X[y > 0.5, 100:120] += 2.0
+    p0 = t.from_numpy(spd_synth.net_init_params(5)).cuda()
+    pa = p0.clone()
+    la, ma, va = P.train(pa, X, y, steps=30, batch=256, lr=3e-3, seed=4)
+    pb = p0.clone()
+    lb, mb, vb = P.train(pb, X, y, steps=15, batch=256, lr=3e-3, seed=4)
+    P.save_checkpoint(tmp_path / "c.ckpt", pb, mb, vb, step=15, seed=4)
+    pc, mc, vc, step, seed = P.load_checkpoint(tmp_path / "c.ckpt")
+    lc, _, _ = P.train(pc, X, y, steps=30 - step, batch=256, lr=3e-3, seed=seed, m=mc, v=vc, step0=step)
+    assert np.allclose(la[:15], lb, rtol=1e-4) and np.allclose(la[15:], lc, rtol=1e-3, atol=1e-4)
+    assert t.allclose(pa, pc, rtol=1e-4, atol=1e-5), (pa - pc).abs().max().item()

@@ -79,3 +79,31 @@ def test_match_label_and_score():
     assert abs(s["snr_loss"] - np.mean([1 - 7 / 8, 1 - 8 / 16])) < 1e-12
     # quiet blocks: row 1 block 7 (30000) holds no pulse and precedes none; row 0's blocks 0, 1, 2 are busy
     assert s["false_alarms"] == 1
+
+
+def test_batch_schedule_is_a_function_of_the_step():
+    n, b = 1000, 128
+    per_epoch = n // b
+    seen = np.concatenate([P.batch_indices(n, b, 7, k, device="cpu").numpy() for k in range(per_epoch)])
+    assert len(np.unique(seen)) == per_epoch * b  # an epoch never repeats a block
+    late = P.batch_indices(n, b, 7, 3 * per_epoch + 2, device="cpu").numpy()
+    P.batch_indices(n, b, 7, 0, device="cpu")  # another epoch in between
+    assert np.array_equal(P.batch_indices(n, b, 7, 3 * per_epoch + 2, device="cpu").numpy(), late)
+    assert not np.array_equal(P.batch_indices(n, b, 8, 2, device="cpu").numpy(),
+                              P.batch_indices(n, b, 7, 2, device="cpu").numpy())
+
+
+def test_checkpoint_round_trip(tmp_path):
+    rng = np.random.default_rng(3)
+    vec = [torch.from_numpy(rng.normal(size=4817).astype(np.float32)) for _ in range(3)]
+    path = tmp_path / "net.ckpt"
+    P.save_checkpoint(path, *vec, step=1234, seed=99)
+    p2, m2, v2, step, seed = P.load_checkpoint(path, device="cpu")
+    assert step == 1234 and seed == 99
+    for a, b in zip(vec, (p2, m2, v2)):
+        assert torch.equal(a, b)
+    assert path.stat().st_size == 8 + 24 + 3 * 4 * 4817
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"NOTACKPT" + bytes(100))
+    with pytest.raises(ValueError):
+        P.load_checkpoint(bad, device="cpu")
