@@ -48,7 +48,7 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   s = t;
 }
 
-__global__ void __launch_bounds__(kThreads) msd_pass_kernel(const MsdParams p, int pass) {
+__global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p, int pass) {
   __shared__ float cshift[kMsdMaxLevels], clim[kMsdMaxLevels];
   __shared__ float s8[2][kThreads / 32];
   __shared__ double red[kThreads / 32][kMsdMaxLevels][2];
