@@ -408,6 +408,16 @@ spd_status spd_net_forward(const float *d_params, const float *d_blocks, int64_t
  * passes its gradient to the first maximum; roundings pass it unchanged. */
 spd_status spd_net_gradient(const float *d_params, const float *d_blocks, const float *d_labels,
                             int64_t n_blocks, float *d_grad_sum, float *d_loss_sum, spd_stream_t stream);
+/* spd_net_gradient with a deterministic sum: each CTA writes its partial sums
+ * to its row of d_ws (device, at least spd_net_gradient_workspace_size()
+ * bytes, 4-byte aligned) and a second launch adds the rows in a fixed order, so
+ * equal inputs give bit-identical results (training runs are reproducible and
+ * resume exactly from a checkpoint).  SPD_ERR_WORKSPACE_TOO_SMALL when ws_bytes
+ * is short. */
+size_t spd_net_gradient_workspace_size(void);
+spd_status spd_net_gradient_ordered(const float *d_params, const float *d_blocks, const float *d_labels,
+                                    int64_t n_blocks, float *d_grad_sum, float *d_loss_sum, void *d_ws,
+                                    size_t ws_bytes, spd_stream_t stream);
 /* One Adam step (beta 0.9, 0.999, eps 1e-8, bias-corrected; step counts from 1)
  * on the mean gradient d_grad_sum / n_blocks; d_m, d_v: moment vectors. */
 spd_status spd_net_adam(float *d_params, float *d_m, float *d_v, const float *d_grad_sum,

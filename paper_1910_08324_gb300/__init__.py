@@ -39,6 +39,8 @@ from ._binding import (  # noqa: F401
     net_select,
     net_forward,
     net_gradient,
+    net_gradient_ordered,
+    spd_net_gradient_workspace_size,
     noise_stats,
     records,
     search,

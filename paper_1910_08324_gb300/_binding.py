@@ -59,7 +59,8 @@ _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_des
             "spd_plan_set_segment", "spd_batch_create", "spd_batch_destroy", "spd_batch_set_segment",
             "spd_batch_set_wait_ns", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
             "spd_batch_candidates", "spd_net_decimate", "spd_net_forward", "spd_net_gradient",
-            "spd_net_adam", "spd_net_select", "spd_net_gather", "spd_plan_set_starts", "spd_plan_create_grid"]
+            "spd_net_adam", "spd_net_select", "spd_net_gather", "spd_plan_set_starts", "spd_plan_create_grid",
+            "spd_net_gradient_ordered"]
 
 
 def library_path() -> str:
@@ -99,6 +100,9 @@ def load_library():
         lib.spd_net_forward.argtypes = [vp, vp, i64, vp, vp]
         lib.spd_net_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         lib.spd_net_adam.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, i32, vp]
+        lib.spd_net_gradient_workspace_size.argtypes = []
+        lib.spd_net_gradient_workspace_size.restype = sz
+        lib.spd_net_gradient_ordered.argtypes = [vp, vp, vp, i64, vp, vp, vp, sz, vp]
         lib.spd_net_select.argtypes = [vp, i64, ctypes.c_float, vp, i64, vp, vp]
         lib.spd_net_gather.argtypes = [vp, i32, i64, i64, i64, vp, i64, i32, i32, i32, vp, i64, vp]
         lib.spd_batch_create.argtypes = [ctypes.POINTER(_Desc), vp, vp, vp, i32, ctypes.POINTER(vp)]
@@ -432,6 +436,19 @@ def net_gradient(params, blocks, labels, grad_sum, loss_sum, stream=None):
     _check(load_library().spd_net_gradient(_ptr(params), _ptr(blocks), _ptr(labels), blocks.shape[0],
                                            _ptr(grad_sum), _ptr(loss_sum), _stream(stream) or None),
            "spd_net_gradient")
+
+
+def spd_net_gradient_workspace_size() -> int:
+    return int(load_library().spd_net_gradient_workspace_size())
+
+
+def net_gradient_ordered(params, blocks, labels, grad_sum, loss_sum, ws, stream=None):
+    """net_gradient with a deterministic sum over the CTAs (``ws``: uint8 CUDA
+    tensor of spd_net_gradient_workspace_size() bytes)."""
+    _check(load_library().spd_net_gradient_ordered(_ptr(params), _ptr(blocks), _ptr(labels), blocks.shape[0],
+                                                   _ptr(grad_sum), _ptr(loss_sum), _ptr(ws),
+                                                   ws.numel() * ws.element_size(), _stream(stream) or None),
+           "spd_net_gradient_ordered")
 
 
 def net_adam(params, m, v, grad_sum, n_blocks: int, lr: float, step: int, stream=None):

@@ -828,8 +828,23 @@ spd_status spd_net_gradient(const float* d_params, const float* d_blocks, const 
   if (((uintptr_t)d_params % 4) || ((uintptr_t)d_blocks % 4) || ((uintptr_t)d_labels % 4) ||
       ((uintptr_t)d_grad_sum % 4) || ((uintptr_t)d_loss_sum % 4))
     return SPD_ERR_INVALID_ARG;
-  return check_cuda(spd::launch_net_grad(d_params, d_blocks, d_labels, n_blocks, d_grad_sum, d_loss_sum,
+  return check_cuda(spd::launch_net_grad(d_params, d_blocks, d_labels, n_blocks, d_grad_sum, d_loss_sum, nullptr,
                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t spd_net_gradient_workspace_size(void) { return spd::net_grad_workspace_bytes(); }
+
+spd_status spd_net_gradient_ordered(const float* d_params, const float* d_blocks, const float* d_labels,
+                                    int64_t n_blocks, float* d_grad_sum, float* d_loss_sum, void* d_ws,
+                                    size_t ws_bytes, spd_stream_t stream) {
+  if (!d_params || !d_blocks || !d_labels || !d_grad_sum || !d_loss_sum || !d_ws || n_blocks < 1)
+    return SPD_ERR_INVALID_ARG;
+  if (((uintptr_t)d_params % 4) || ((uintptr_t)d_blocks % 4) || ((uintptr_t)d_labels % 4) ||
+      ((uintptr_t)d_grad_sum % 4) || ((uintptr_t)d_loss_sum % 4) || ((uintptr_t)d_ws % 4))
+    return SPD_ERR_INVALID_ARG;
+  if (ws_bytes < spd::net_grad_workspace_bytes()) return SPD_ERR_WORKSPACE_TOO_SMALL;
+  return check_cuda(spd::launch_net_grad(d_params, d_blocks, d_labels, n_blocks, d_grad_sum, d_loss_sum,
+                                         static_cast<float*>(d_ws), reinterpret_cast<cudaStream_t>(stream)));
 }
 
 spd_status spd_net_adam(float* d_params, float* d_m, float* d_v, const float* d_grad_sum, int64_t n_blocks,

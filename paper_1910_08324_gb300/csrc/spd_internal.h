@@ -168,7 +168,8 @@ cudaError_t launch_igrid_batch(const spd_plan& plan, const SearchParams& p, cuda
 int net_param_count();
 cudaError_t launch_net_forward(const float* P, const float* X, int64_t nb, float* logits, cudaStream_t s);
 cudaError_t launch_net_grad(const float* P, const float* X, const float* Y, int64_t nb, float* G, float* loss,
-                            cudaStream_t s);
+                            float* partials, cudaStream_t s);
+size_t net_grad_workspace_bytes();
 cudaError_t launch_net_adam(float* P, float* M, float* V, const float* G, int64_t nb, float lr, int step,
                             cudaStream_t s);
 cudaError_t launch_net_decimate(const void* x, int dtype, int esize, int64_t ndm, int64_t nt, int64_t ld,

@@ -34,6 +34,7 @@ namespace {
 constexpr int NC = 16, NK = 9, NP = 256, PAD = 4, NPP = NP + 2 * PAD;
 constexpr int kNetThreads = 128;
 constexpr int kNetParams = 4817;
+constexpr int kNetMaxGradCtas = 1024;  // CTAs of a gradient launch (rows of the ordered workspace)
 constexpr int oW1 = 0, ob1 = 144, oW2 = 160, ob2 = 2464, oW3 = 2480, ob3 = 4784, oW4 = 4800, ob4 = 4816;
 // Activation rows [position][16 channels] and weight rows [tap][out][16 in] are 32
 // bytes of bf16 with the two 16-byte halves of a row swapped when bit 2 of the row
@@ -303,7 +304,8 @@ __global__ void __launch_bounds__(kNetThreads, 7) net_forward_kernel(const float
 __global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* __restrict__ P,
                                                                 const float* __restrict__ X,
                                                                 const float* __restrict__ Y, int64_t nb,
-                                                                float* __restrict__ Gout, float* __restrict__ loss) {
+                                                                float* __restrict__ Gout, float* __restrict__ loss,
+                                                                float* __restrict__ partials) {
   extern __shared__ __align__(16) unsigned char raw[];
   NetSmem& s = *reinterpret_cast<NetSmem*>(raw);
   GradSmem& q = *reinterpret_cast<GradSmem*>(raw + ((sizeof(NetSmem) + 15) / 16) * 16);
@@ -383,8 +385,28 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* _
     }
   }
   __syncthreads();
-  for (int i = t; i < kNetParams; i += kNetThreads) atomicAdd(Gout + i, q.G[i]);
-  if (t == 0) atomicAdd(loss, lsum);
+  if (partials) {  // ordered: this CTA's row of partial sums (gradient, then loss)
+    float* row = partials + (int64_t)blockIdx.x * (kNetParams + 1);
+    for (int i = t; i < kNetParams; i += kNetThreads) row[i] = q.G[i];
+    if (t == 0) row[kNetParams] = lsum;
+  } else {
+    for (int i = t; i < kNetParams; i += kNetThreads) atomicAdd(Gout + i, q.G[i]);
+    if (t == 0) atomicAdd(loss, lsum);
+  }
+}
+
+// Sum of the CTAs' partial rows in CTA order (deterministic): gradient entries,
+// then the loss.
+__global__ void net_reduce_kernel(const float* __restrict__ partials, int rows, float* __restrict__ Gout,
+                                  float* __restrict__ loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > kNetParams) return;
+  float acc = 0.f;
+  for (int r = 0; r < rows; ++r) acc += partials[(int64_t)r * (kNetParams + 1) + i];
+  if (i < kNetParams)
+    Gout[i] = acc;
+  else
+    *loss = acc;
 }
 
 // Adam on the mean gradient G / nb (bias-corrected, step counts from 1).
@@ -540,16 +562,24 @@ cudaError_t launch_net_forward(const float* P, const float* X, int64_t nb, float
   return cudaGetLastError();
 }
 
+size_t net_grad_workspace_bytes() { return sizeof(float) * (size_t)kNetMaxGradCtas * (kNetParams + 1); }
+
 cudaError_t launch_net_grad(const float* P, const float* X, const float* Y, int64_t nb, float* G, float* loss,
-                            cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * kNetParams, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), s);
-  if (e != cudaSuccess) return e;
+                            float* partials, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (!partials) {
+    e = cudaMemsetAsync(G, 0, sizeof(float) * kNetParams, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+  }
   int grid = 0;
   const size_t smem = net_smem(true);
   e = net_grid(net_grad_kernel, smem, nb, &grid);
   if (e != cudaSuccess || grid == 0) return e;
-  net_grad_kernel<<<grid, kNetThreads, smem, s>>>(P, X, Y, nb, G, loss);
+  if (grid > kNetMaxGradCtas) grid = kNetMaxGradCtas;
+  net_grad_kernel<<<grid, kNetThreads, smem, s>>>(P, X, Y, nb, G, loss, partials);
+  if (partials && (e = cudaGetLastError()) == cudaSuccess)
+    net_reduce_kernel<<<(kNetParams + 1 + 255) / 256, 256, 0, s>>>(partials, grid, G, loss);
   return cudaGetLastError();
 }
 

@@ -272,13 +272,14 @@ def train(params, X, y, steps: int, batch: int = 512, lr: float = 3e-3, seed: in
     v = torch.zeros_like(params) if v is None else v
     G = torch.empty_like(params)
     L = torch.empty(1, dtype=torch.float32, device=dev)
+    ws = torch.empty(B.spd_net_gradient_workspace_size(), dtype=torch.uint8, device=dev)
     n = X.shape[0]
     losses = torch.empty(steps, dtype=torch.float32, device=dev)
     for i in range(steps):
         idx = batch_indices(n, batch, seed, step0 + i, device=dev)
         xb = X[idx].contiguous()
         yb = y[idx].contiguous()
-        B.net_gradient(params, xb, yb, G, L, stream=stream)
+        B.net_gradient_ordered(params, xb, yb, G, L, ws, stream=stream)  # deterministic: runs repeat exactly
         B.net_adam(params, m, v, G, idx.numel(), lr, step0 + i + 1, stream=stream)
         losses[i] = L[0] / idx.numel()
     return losses.cpu().tolist(), m, v

@@ -231,3 +231,12 @@ def test_explicit_grid_rules():
     g = oracle.grid_boxdit(8, 512)
     pl = spd.spd_plan_create_grid(g.L, g.Ls, ndm=1, nt=4096)
     assert np.array_equal(pl.widths()[0], g.L) and np.array_equal(pl.widths()[1], g.Ls)
+
+
+def test_ordered_gradient_workspace_rules():
+    lib = spd.load_library()
+    need = spd.spd_net_gradient_workspace_size()
+    assert need == 4 * 1024 * (4817 + 1)
+    assert lib.spd_net_gradient_ordered(4096, 4096, 4096, 8, 4096, 4096, 4096, need - 4, None) == 4
+    assert lib.spd_net_gradient_ordered(4096, 4096, 4096, 8, 4096, 4096, None, need, None) == 1
+    assert lib.spd_net_gradient_ordered(4096, 4096, 4096, 0, 4096, 4096, 4096, need, None) == 1

@@ -109,3 +109,19 @@ def test_training_separates_pulse_blocks():
     acc = np.mean((lg.cpu().numpy() > 0) == (yv > 0.5))
     assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:20]), (losses[:5], losses[-5:])
     assert acc > 0.9, acc
+
+
+def test_ordered_gradient_equals_atomic_sum_and_repeats():
+    t = torch()
+    X, y = _blocks(3000, 13)
+    th = _params(14)
+    P_, Xd, yd = t.from_numpy(th).cuda(), t.from_numpy(X).cuda(), t.from_numpy(y).cuda()
+    G1, L1 = t.empty(net.N_PARAMS, device="cuda"), t.empty(1, device="cuda")
+    spd.net_gradient(P_, Xd, yd, G1, L1)
+    ws = t.empty(spd.spd_net_gradient_workspace_size(), dtype=t.uint8, device="cuda")
+    G2, L2 = t.empty_like(G1), t.empty_like(L1)
+    G3, L3 = t.empty_like(G1), t.empty_like(L1)
+    spd.net_gradient_ordered(P_, Xd, yd, G2, L2, ws)
+    spd.net_gradient_ordered(P_, Xd, yd, G3, L3, ws)
+    assert t.equal(G2, G3) and t.equal(L2, L3)  # the ordered sum repeats exactly
+    assert t.allclose(G1, G2, rtol=1e-4, atol=1e-6) and t.allclose(L1, L2, rtol=1e-5)
