@@ -8,12 +8,17 @@
 // Level k of a row is the series of sums of its complete blocks of 2^k samples,
 // k = 0..nlev-1 (nlev covers the plan's widest boxcar).  Every pass streams the
 // row once and updates all levels together:
-//   * one CTA per row, 2048-sample chunks, 8 samples per thread; levels 0..3 in
-//     registers, 4..8 by warp shuffles, 9..11 from the warps' level-8 sums,
-//     12.. accumulated over chunks;
+//   * one CTA per row; each of its 8 warps streams its own contiguous share of
+//     the row in steps of 256 samples (8 per lane), the samples of 16-byte
+//     aligned rows arriving by bulk copies (cp.async.bulk) into a per-warp ring
+//     of shared-memory stages completed on mbarriers; no barrier of the CTA
+//     until the final reduction;
+//   * levels 0..3 from each lane's samples, 4..8 from the warp's shuffle tree,
+//     9..11 from a tree over the level-8 sums of the 8 steps of a 2048-sample
+//     chunk, 12.. accumulated over chunks; one lane keeps each block;
 //   * a value of level k is kept when |v - mu_k| <= thr sigma_k of the previous
 //     pass (the first pass keeps every value);
-//   * each thread sums the kept values shifted by the previous mean (w = v - c_k,
+//   * each lane sums the kept values shifted by the previous mean (w = v - c_k,
 //     so the sums stay small: a numerically stable form, Chan et al.), w and w^2,
 //     per chunk in registers and across chunks with compensated (Kahan) adds;
 //   * at the end, an FP64 reduction over the CTA gives n, mean and deviation
@@ -48,13 +53,95 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   s = t;
 }
 
+// ---- staged copies: cp.async.bulk into per-warp shared rings, completion on mbarriers
+constexpr int kSub = 256;                       // samples of one warp step (8 per lane)
+constexpr int kWarpRing = 4096;                 // bytes of one warp's ring (4 f32 / 8 f16 / 16 u8 steps)
+constexpr int kMaxStages = kWarpRing / kSub;    // stages of u8 steps
+constexpr int kWarps = kThreads / 32;
+constexpr long long kMsdWaitNs = 2000000000LL;  // limit of one wait for a step's samples (they arrive in microseconds)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* q) { return (uint32_t)__cvta_generic_to_shared(q); }
+
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// One thread: announce `bytes` on `bar` and copy them from global `src` to shared `dst`
+// (both 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Wait until the phase of parity `par` of `bar` has completed; false when that
+// takes longer than kMsdWaitNs.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t par) {
+  const uint32_t a = smem_addr(bar);
+  uint32_t ok;
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(par)
+        : "memory");
+    if (ok) return true;
+    uint64_t now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (it == 0) t0 = now;
+    else if ((long long)(now - t0) > kMsdWaitNs) return false;
+  }
+}
+
+// The 8 raw samples of lane l from a staged step (the layout of load_raw8).
+__device__ __forceinline__ Raw8 read_stage(const unsigned char* s, int l, int dtype) {
+  Raw8 r;
+  if (dtype == kDtF32) {
+    const uint4* q = reinterpret_cast<const uint4*>(s + 32 * l);
+    r.a = q[0];
+    r.b = q[1];
+  } else if (dtype == kDtU8) {
+    const uint2 v = *reinterpret_cast<const uint2*>(s + 8 * l);
+    r.a = make_uint4(v.x, v.y, 0u, 0u);
+    r.b = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    r.a = *reinterpret_cast<const uint4*>(s + 16 * l);
+    r.b = make_uint4(0u, 0u, 0u, 0u);
+  }
+  return r;
+}
+
+// One pass over a row (one CTA of 8 warps).  Each warp streams its own
+// contiguous share of the row, whole groups of max(2048, 2^(nlev-1)) samples,
+// so that no block of any level straddles two warps, in steps of 256 samples (8
+// per lane) and needs no barrier until the final reduction.  BULK (16-byte
+// aligned rows): the whole steps of a warp arrive through its shared ring, lane 0
+// refilling a stage once the warp has used it; otherwise each lane loads its
+// samples one step ahead into registers.
+//   * levels 0..3: each lane's 8 samples;
+//   * levels 4..8: after the warp's shuffle tree lane l (l > 0) holds the block of
+//     level 4 + ctz(l) that no other lane keeps (level 4: odd lanes, 5: lanes 2
+//     mod 4, 6: 4 mod 8, 7: 8 and 24, 8: 16);
+//   * levels 9..11: lane i (i < 8) holds the level-8 sum of step i of the
+//     current 2048-sample chunk; the same tree over lanes 0..7 leaves level
+//     9 + ctz(l) in lane l = 1..7;
+//   * levels 12..15: lane 4 + k accumulates chunk sums into blocks of 2^(k-11)
+//     chunks.
+// So each lane keeps at most one value of one level per step and one per chunk.
+// A row whose staged copy did not arrive gets NaN statistics.
+template <bool BULK>
 __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p, int pass) {
+  __shared__ alignas(128) unsigned char ring[BULK ? kWarps * kWarpRing : 16];
+  __shared__ alignas(8) uint64_t full[kWarps][kMaxStages];
   __shared__ float cshift[kMsdMaxLevels], clim[kMsdMaxLevels];
-  __shared__ float s8[2][kThreads / 32];
+  __shared__ float s8[kThreads / 32];
   __shared__ double red[kThreads / 32][kMsdMaxLevels][2];
   __shared__ long long redn[kThreads / 32][kMsdMaxLevels];
-  __shared__ int done;
-  __shared__ float blk[kMsdMaxLevels];  // partial blocks of levels >= 12 (one thread)
+  __shared__ int done, failed;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t row = blockIdx.x;
   const int nlev = p.nlev;
@@ -76,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
       clim[t] = (float)(p.thr * st[t].sd);
     }
   } else {
-    // pilot shift: the mean of the row's first chunk, times 2^k
+    // pilot shift: the mean of the row's first 2048 samples, times 2^k
     const int n0 = nt < kC ? (int)nt : kC;
     float v0, v1;
     {
@@ -89,129 +176,209 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v0 += __shfl_xor_sync(kFull, v0, o);
-    if (lane == 0) s8[0][warp] = v0;
+    if (lane == 0) s8[warp] = v0;
     __syncthreads();
     v1 = 0.0f;
-    for (int w = 0; w < kThreads / 32; ++w) v1 += s8[0][w];
+    for (int w = 0; w < kThreads / 32; ++w) v1 += s8[w];
     const float c0 = v1 / (float)n0;
     if (t < nlev) {
       cshift[t] = c0 * (float)(1 << t);
       clim[t] = FLT_MAX;
     }
   }
-  __syncthreads();
+  if (t == 0) failed = 0;
 
-  float sw[kMsdMaxLevels], sw2[kMsdMaxLevels], cw[4], cw2[4];  // compensation: levels 0..3
-  int cn[kMsdMaxLevels];
-#pragma unroll
-  for (int k = 0; k < kMsdMaxLevels; ++k) sw[k] = sw2[k] = 0.0f, cn[k] = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) cw[k] = cw2[k] = 0.0f;
-  // levels 0..3 (several values per thread and chunk): chunk-local sums, folded
-  // into the compensated sums once per chunk; levels >= 4: one value per chunk
-  float pw[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pw2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  auto keep = [&](auto K, float v, bool valid) {
-    constexpr int k = decltype(K)::value;
-    const float w = v - cshift[k];
-    const bool in = valid && fabsf(w) <= clim[k];
-    if constexpr (k < 4) {
-      pw[k] += in ? w : 0.0f;
-      pw2[k] += in ? w * w : 0.0f;
-    } else {  // at most one value per chunk: plain sums (<= 512 adds per row and lane)
-      sw[k] += in ? w : 0.0f;
-      sw2[k] += in ? w * w : 0.0f;
+  // this warp's steps [u0, u1): whole groups of gs steps
+  const int64_t nsub = (nt + kSub - 1) / kSub, nfs = nt / kSub;  // steps; whole steps
+  const int gs = (1 << (nlev - 1)) > kC ? (1 << (nlev - 1)) / kSub : kC / kSub;
+  const int64_t ng = (nsub + gs - 1) / gs;
+  const int64_t u0 = (ng * warp / kWarps) * gs;
+  const int64_t u1 = min((ng * (warp + 1) / kWarps) * gs, nsub);
+  const int sbytes = kSub * p.esize;
+  const int lgs = p.esize == 4 ? 2 : (p.esize == 2 ? 3 : 4);  // stages: kWarpRing / sbytes
+  const int64_t ub = BULK ? min(u1, nfs) : u0;                 // steps [u0, ub) arrive staged
+  unsigned char* wring = ring + (BULK ? warp * kWarpRing : 0);
+  if (BULK) {
+    if (lane == 0) {
+      for (int i = 0; i < (1 << lgs); ++i) bar_init(&full[warp][i]);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      for (int64_t u = u0; u < ub && u < u0 + (1 << lgs); ++u)
+        bulk_load(wring + (u - u0) * sbytes, xrow + u * sbytes, (uint32_t)sbytes, &full[warp][u - u0]);
     }
-    cn[k] += in ? 1 : 0;
-  };
-  if (t < kMsdMaxLevels) blk[t] = 0.0f;
+  }
   __syncthreads();
 
-  const int64_t nch = (nt + kC - 1) / kC;
-  auto chunk_n = [&](int64_t c) {  // samples of chunk c that exist
-    const int64_t left = nt - c * kC;
-    return left < kC ? (int)left : kC;
-  };
-  Raw8 nx = load_raw8(xrow, 8 * t, chunk_n(0), p.dtype, vx);  // one chunk ahead
-  for (int64_t c = 0; c < nch; ++c) {
+  // levels this lane keeps; an unused level gets limit -1 (nothing passes |w| <= -1)
+  float sh[4], lim[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) pw[k] = pw2[k] = 0.0f;
-    const int64_t base = c * kC + 8 * t;  // first sample of this thread
+  for (int k = 0; k < 4; ++k) {
+    sh[k] = k < nlev ? cshift[k] : 0.0f;
+    lim[k] = k < nlev ? clim[k] : -1.0f;
+  }
+  const int jl = lane ? __ffs(lane) - 1 : 5;  // set A: level 4 + jl (lane 0: none)
+  const int ka = 4 + jl;
+  const float sha = (jl < 5 && ka < nlev) ? cshift[ka] : 0.0f;
+  const float lima = (jl < 5 && ka < nlev) ? clim[ka] : -1.0f;
+  // set B: lanes 1..7 level 9 + ctz(lane), block lane >> (ctz + 1); lanes 8..11 level lane + 4
+  const int kb = (lane >= 1 && lane < 8) ? 9 + jl : ((lane >= 8 && lane < 12) ? lane + 4 : 0);
+  const float shb = (kb && kb < nlev) ? cshift[kb] : 0.0f;
+  const float limb = (kb && kb < nlev) ? clim[kb] : -1.0f;
+  const int endb = (lane >= 1 && lane < 8) ? ((lane >> (jl + 1)) + 1) << kb : kC;  // block end in its chunk
+
+  float sw[4], sw2[4], cw[4], cw2[4];  // levels 0..3: compensated sums over chunks
+  float pw[4], pw2[4];                 // ... and over the steps of the current chunk
+  int cn[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sw[k] = sw2[k] = cw[k] = cw2[k] = pw[k] = pw2[k] = 0.0f, cn[k] = 0;
+  float sa = 0.0f, sa2 = 0.0f, sb = 0.0f, sb2 = 0.0f, blk = 0.0f, q = 0.0f;
+  int na = 0, nb = 0, bad = 0;
+
+  auto step = [&](auto WHOLE, const Raw8& cx, int64_t u) {
+    constexpr bool whole = decltype(WHOLE)::value;
+    const int rem = whole ? kSub : (int)(nt - u * kSub);  // samples of the step
+    const int o = 8 * lane;
     float f[8];
     {
-      const Raw8 cx = nx;
-      if (c + 1 < nch) nx = load_raw8(xrow + (c + 1) * kC * p.esize, 8 * t, chunk_n(c + 1), p.dtype, vx);
-      const int nrel = chunk_n(c);
       float4 a, b;
-      cvt8(cx, 8 * t, nrel, p.dtype, 0.0f, 1.0f, a, b);
+      cvt8(cx, o, rem, p.dtype, 0.0f, 1.0f, a, b);
       f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w, f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
+      if (!whole) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) f[i] = (base + i < nt) ? f[i] : 0.0f;  // sums stay finite
-    }
-    // levels 0..3 from this thread's samples; a block counts when it ends by nt
-    static_for<0, 8>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      keep(std::integral_constant<int, 0>{}, f[i], base + i + 1 <= nt);
-    });
-    float p1[4], p2[2];
-    static_for<0, 4>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      p1[i] = f[2 * i] + f[2 * i + 1];
-      if (nlev > 1) keep(std::integral_constant<int, 1>{}, p1[i], base + 2 * i + 2 <= nt);
-    });
-    static_for<0, 2>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      p2[i] = p1[2 * i] + p1[2 * i + 1];
-      if (nlev > 2) keep(std::integral_constant<int, 2>{}, p2[i], base + 4 * i + 4 <= nt);
-    });
-    float s = p2[0] + p2[1];
-    if (nlev > 3) keep(std::integral_constant<int, 3>{}, s, base + 8 <= nt);
-    // levels 4..8: lanes of a block share its sum; its first lane keeps it
-    static_for<4, 9>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      s += __shfl_xor_sync(kFull, s, 1 << (k - 4));
-      if (nlev > k && (lane & ((1 << (k - 3)) - 1)) == 0) keep(K, s, base + (1 << k) <= nt);
-    });
-    // levels 9..11 from the warps' level-8 sums (lanes 0..3, 4..5 and 6 of warp 0)
-    if (lane == 0) s8[c & 1][warp] = s;
-    __syncthreads();
-    if (warp == 0 && lane < 7 && nlev > 9) {
-      const int lj = lane < 4 ? 9 : (lane < 6 ? 10 : 11);
-      const int lb = lane < 4 ? lane : (lane < 6 ? lane - 4 : 0);
-      const int nw = 1 << (lj - 8);
-      float v = 0.0f;
-      for (int i = 0; i < nw; ++i) v += s8[c & 1][lb * nw + i];
-      const bool valid = c * kC + (int64_t)(lb + 1) * (1 << lj) <= nt;
-      if (lj == 9) keep(std::integral_constant<int, 9>{}, v, valid);
-      else if (lj == 10) {
-        if (nlev > 10) keep(std::integral_constant<int, 10>{}, v, valid);
-      } else {
-        if (nlev > 11) keep(std::integral_constant<int, 11>{}, v, valid);
-        // levels >= 12: blocks of 2^(k-11) chunks
-        static_for<12, kMsdMaxLevels>([&](auto K) {
-          constexpr int k = decltype(K)::value;
-          if (nlev > k) {
-            blk[k] += v;
-            if (((c + 1) & ((1 << (k - 11)) - 1)) == 0) {
-              keep(K, blk[k], (c + 1) * kC <= nt);
-              blk[k] = 0.0f;
-            }
-          }
-        });
+        for (int i = 0; i < 8; ++i) f[i] = (o + i < rem) ? f[i] : 0.0f;  // sums stay finite
       }
     }
+    // a block counts when it ends inside the row
+    auto keep = [&](int k, float v, int end) {
+      const float w = v - sh[k];
+      const bool in = (whole || end <= rem) && fabsf(w) <= lim[k];
+      const float wm = in ? w : 0.0f;
+      pw[k] += wm;
+      pw2[k] = fmaf(wm, wm, pw2[k]);
+      cn[k] += in ? 1 : 0;
+    };
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      kahan_add(sw[k], cw[k], pw[k]);
-      kahan_add(sw2[k], cw2[k], pw2[k]);
+    for (int i = 0; i < 8; ++i) keep(0, f[i], o + i + 1);
+    float p1[4], p2[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      p1[i] = f[2 * i] + f[2 * i + 1];
+      keep(1, p1[i], o + 2 * i + 2);
     }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      p2[i] = p1[2 * i] + p1[2 * i + 1];
+      keep(2, p2[i], o + 4 * i + 4);
+    }
+    float s = p2[0] + p2[1];
+    keep(3, s, o + 8);
+    float v = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      s += __shfl_xor_sync(kFull, s, 1 << j);
+      if (jl == j) v = s;
+    }
+    const float w = v - sha;
+    const int end = 8 * (lane & ~((2 << jl) - 1)) + (16 << jl);
+    const bool in = (whole || end <= rem) && fabsf(w) <= lima;
+    const float wa = in ? w : 0.0f;
+    sa += wa;
+    sa2 = fmaf(wa, wa, sa2);
+    na += in ? 1 : 0;
+    return s;  // the step's sum (level 8)
+  };
+
+  Raw8 nx;
+  if (!BULK && u0 < u1) {
+    const int64_t left = nt - u0 * kSub;
+    nx = load_raw8(xrow + u0 * sbytes, 8 * lane, left < kSub ? (int)left : kSub, p.dtype, vx);
+  }
+  for (int64_t u = u0; u < u1; ++u) {
+    Raw8 cx;
+    const int stg = (int)((u - u0) & ((1 << lgs) - 1));
+    if (BULK && u < ub) {
+      bad |= bar_wait(&full[warp][stg], (uint32_t)((u - u0) >> lgs) & 1u) ? 0 : 1;
+      cx = read_stage(wring + stg * sbytes, lane, p.dtype);
+    } else if (BULK) {
+      cx = load_raw8(xrow + u * sbytes, 8 * lane, (int)(nt - u * kSub), p.dtype, vx);
+    } else {
+      cx = nx;
+      if (u + 1 < u1) {
+        const int64_t left = nt - (u + 1) * kSub;
+        nx = load_raw8(xrow + (u + 1) * sbytes, 8 * lane, left < kSub ? (int)left : kSub, p.dtype, vx);
+      }
+    }
+    const float s = u < nfs ? step(std::true_type{}, cx, u) : step(std::false_type{}, cx, u);
+    if (lane == (int)(u & 7)) q = s;
+    if (BULK) {
+      if (__any_sync(kFull, bad)) {  // a step did not arrive: wait (bounded) for this warp's copies in flight
+        if (lane == 0)
+          for (int64_t r = u; r < ub && r < u + (1 << lgs); ++r)
+            bar_wait(&full[warp][(r - u0) & ((1 << lgs) - 1)], (uint32_t)((r - u0) >> lgs) & 1u);
+        if (lane == 0) failed = 1;
+        break;
+      }
+      __syncwarp();  // every lane has used the stage: refill it
+      if (lane == 0 && u + (1 << lgs) < ub)
+        bulk_load(wring + stg * sbytes, xrow + (u + (1 << lgs)) * sbytes, (uint32_t)sbytes, &full[warp][stg]);
+    }
+    if ((u & 7) == 7 || u + 1 == u1) {  // end of a 2048-sample chunk (or of the warp's share)
+      const int64_t ch = u >> 3;
+      float z = lane < 8 ? q : 0.0f, vb = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        z += __shfl_xor_sync(kFull, z, 1 << j);
+        if (jl == j) vb = z;
+      }
+      const float v11 = __shfl_sync(kFull, z, 0);
+      bool valid = ch * kC + endb <= nt;
+      if (lane >= 8 && lane < 12) {
+        blk += v11;
+        vb = blk;
+        const bool complete = ((ch + 1) & ((1 << (kb - 11)) - 1)) == 0;
+        valid = complete && valid;
+        if (complete) blk = 0.0f;
+      }
+      const float wb = vb - shb;
+      const bool inb = valid && fabsf(wb) <= limb;
+      sb += inb ? wb : 0.0f;
+      sb2 += inb ? wb * wb : 0.0f;
+      nb += inb ? 1 : 0;
+      q = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        kahan_add(sw[k], cw[k], pw[k]);
+        kahan_add(sw2[k], cw2[k], pw2[k]);
+        pw[k] = pw2[k] = 0.0f;
+      }
+    }
+  }
+  __syncthreads();
+  if (failed) {
+    if (t < kMsdMaxLevels) {
+      MsdLevel L;
+      L.mu = L.sd = __longlong_as_double(0x7ff8000000000000LL);
+      L.n = -2;
+      L.conv = 1;
+      L.pad = 0;
+      st[t] = L;
+    }
+    return;
   }
 
   // FP64 reduction over the CTA, then the new statistics of every level
 #pragma unroll
   for (int k = 0; k < kMsdMaxLevels; ++k) {
-    double a = sw[k], b = sw2[k];
-    if (k < 4) a -= (double)cw[k < 4 ? k : 0], b -= (double)cw2[k < 4 ? k : 0];
-    long long n = cn[k];
+    double a, b;
+    long long n;
+    if (k < 4) {
+      a = (double)sw[k] - (double)cw[k];
+      b = (double)sw2[k] - (double)cw2[k];
+      n = cn[k];
+    } else if (k < 9) {
+      a = ka == k ? sa : 0.0, b = ka == k ? sa2 : 0.0, n = ka == k ? na : 0;
+    } else {
+      a = kb == k ? sb : 0.0, b = kb == k ? sb2 : 0.0, n = kb == k ? nb : 0;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(kFull, a, o);
@@ -250,6 +417,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
 __global__ void __launch_bounds__(kThreads) msd_table_kernel(const MsdParams p) {
   const int64_t row = blockIdx.x;
   const MsdLevel* st = reinterpret_cast<const MsdLevel*>(p.state) + row * kMsdMaxLevels;
+  const bool failed = st[0].n == -2;  // a chunk of the row did not arrive
   int h = -1;
   while (h + 1 < p.nlev && st[h + 1].n >= 2) ++h;
   for (int w = threadIdx.x; w < p.n_widths; w += kThreads) {
@@ -269,8 +437,8 @@ __global__ void __launch_bounds__(kThreads) msd_table_kernel(const MsdParams p) 
         r = ra + fr * (rb - ra);
       }
     }
-    p.out_mu[row * p.n_widths + w] = (float)((double)L * m);
-    p.out_sigma[row * p.n_widths + w] = (float)(sqrt((double)L) * r);
+    p.out_mu[row * p.n_widths + w] = failed ? __int_as_float(0x7fc00000) : (float)((double)L * m);
+    p.out_sigma[row * p.n_widths + w] = failed ? __int_as_float(0x7fc00000) : (float)(sqrt((double)L) * r);
   }
 }
 
@@ -292,7 +460,8 @@ cudaError_t launch_msd(const spd_plan& plan, const MsdParams& p, int max_passes,
   msd_reset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
   cudaError_t e = cudaGetLastError();
   for (int pass = 0; pass < max_passes && e == cudaSuccess; ++pass) {
-    msd_pass_kernel<<<(unsigned)plan.desc.ndm, kThreads, 0, s>>>(p, pass);
+    if (p.vec_x) msd_pass_kernel<true><<<(unsigned)plan.desc.ndm, kThreads, 0, s>>>(p, pass);
+    else msd_pass_kernel<false><<<(unsigned)plan.desc.ndm, kThreads, 0, s>>>(p, pass);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
