@@ -38,6 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import spd_synth  # noqa: E402
+from paper_1910_08324_gb300 import shard  # noqa: E402  (host-only helpers, no library load)
 
 T_SAMP = 64e-6
 SKA_DM = 6000
@@ -74,7 +75,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ska_mid", choices=["ska_mid", "exhaustive_small", "batched", "proposal"],
+    ap.add_argument("--workload", default="ska_mid", choices=["ska_mid", "exhaustive_small", "batched", "proposal", "noise_stats"],
                     help="ska_mid: 4096 x 1M lossy search (default); exhaustive_small: 64 x 65536, widths 1..256")
     ap.add_argument("--algo", default="ig1", choices=sorted(ALGOS))
     ap.add_argument("--ndm", type=int, default=spd_synth.SKA_MID["ndm"])
@@ -435,6 +436,135 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
     return 0
 
 
+def run_noise_stats(args, torch, dist, spd, rank, world, local, dev):
+    """Noise statistics (Sec. 4.5) of the search's input: one step = one
+    ``spd_noise_stats`` call of one pass (every decimation level of every row,
+    then the per-width table) over the workload's rows (default 4096 x 1M samples
+    of N(0,1) noise with the SKA-MID-shaped pulses).  Each rank computes the
+    statistics of its own rows (weak scaling).  A 3-pass call with 2-sigma
+    rejection is timed beside it."""
+    import oracle  # the CPU leg only
+    ndm, nt = args.ndm, args.nt
+    dt_code, esize = DTYPES[args.dtype]
+    kw = dict(ALGOS[args.algo])
+    plan = spd.spd_plan_create(ndm=ndm, nt=nt, s_end=args.s_end, dtype=dt_code, **kw)
+    widths = plan.widths()[0]
+    nw = len(widths)
+    seed = spd_synth.SEED_BASE + 7 + 1000 * rank
+    x = spd_synth.device_noise(ndm, nt, seed, device=dev)
+    spd_synth.device_inject(x, spd_synth.ska_mid_pulses(seed=seed, ndm=ndm, nt=nt))
+    xf = x
+    x = spd_synth.device_quantize(xf, args.dtype)
+    if x is not xf:
+        del xf
+    mu = torch.empty((ndm, nw), dtype=torch.float32, device=dev)
+    sg = torch.empty((ndm, nw), dtype=torch.float32, device=dev)
+    ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def step(passes=1):
+        spd.noise_stats(plan, x, mu, sg, ws, outlier_sigma=2.0, max_passes=passes, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[2 * k].record(stream)
+                step()
+                ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    total_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
+    if world > 1:
+        total_ms = shard.max_over_ranks(total_ms, dist)
+    ms_per_step = total_ms / args.steps
+    samples = ndm * nt
+    value = samples * world / (ms_per_step / 1e3)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(3)
+        e1.record(stream)
+    e1.synchronize()
+    ms_3 = e0.elapsed_time(e1)
+    # roofline: the pass kernel reads every sample once; the per-step time also
+    # holds the (small) reset and table kernels, so the achieved rate is a lower bound
+    peak, peak_src = measured_peaks()
+    alg_bytes = esize * samples
+    achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
+                if peak_src == "measured" else "fallback 6.8 TB/s",
+                "kernel": "msd_pass_kernel (+ reset and table kernels in the timed call)",
+                "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": ms_per_step}
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        hx.copy_(x)
+        hm = torch.empty((ndm, nw), dtype=torch.float32, pin_memory=True)
+        hs = torch.empty((ndm, nw), dtype=torch.float32, pin_memory=True)
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                x.copy_(hx, non_blocking=True)
+                step()
+                hm.copy_(mu, non_blocking=True)
+                hs.copy_(sg, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        per = []
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            e2e_step()
+            per.append(time.perf_counter() - t0)
+        dt = statistics.median(per)
+        e2e = {"value": samples / dt, "unit": "samples/s", "h2d_bytes_per_step": esize * samples,
+               "d2h_bytes_per_step": 8 * ndm * nw, "steps": args.e2e_steps, "ms_per_step": 1e3 * dt,
+               "api": "pinned H2D of the rows, spd_noise_stats (one pass), D2H of the mu and sigma tables"}
+        del hx
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        nlev = 1
+        while nlev < 16 and (1 << (nlev - 1)) < int(widths[-1]):
+            nlev += 1
+        done, spent, rows = 0, 0.0, 0
+        while spent < args.cpu_seconds and rows < ndm:
+            r = min(16, ndm - rows)
+            xr = x[rows:rows + r].float().cpu().numpy().astype(np.float64)
+            t0 = time.perf_counter()
+            m, sd, n = oracle.msd_levels(xr, nlev, thr=2.0, max_passes=1)
+            oracle.msd_table(m, sd, n, widths)
+            spent += time.perf_counter() - t0
+            done += xr.size
+            rows += r
+        cpu = {"value": done / spent, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": "%d rows x %d samples, one pass, FP64 (oracle msd_levels + msd_table), %.1f s"
+                         % (rows, nt, spent)}
+    if rank == 0:
+        line = {
+            "metric": "noise-statistics samples/s (one pass)", "value": value, "unit": "samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "noise statistics %d DM x %d samples" % (ndm, nt), "input_dtype": args.dtype,
+                       "algo": args.algo, "s_end": args.s_end, "widths": nw, "ms_3_passes_2sigma": ms_3,
+                       "parallelism": "dp%d (rows per GPU)" % world,
+                       "l2": "input larger than L2 (%.1f GB per GPU); no flush" % (esize * samples / 1e9)},
+            "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 NET_FLOPS_PER_BLOCK = 2 * 256 * 16 * 9 * (1 + 16 + 16) + 2 * 16  # three k=9 convolutions, 16 channels, head
 PROPOSAL_GRID = dict(algo=1, s_end=4096, boxdit_lmax=16, dtype=1)      # BD-16 on FP16 samples
 
@@ -683,6 +813,8 @@ def main():
         return run_batched(args, torch, dist, spd, rank, world, local, dev)
     if args.workload == "proposal":
         return run_proposal(args, torch, dist, spd, rank, world, local, dev)
+    if args.workload == "noise_stats":
+        return run_noise_stats(args, torch, dist, spd, rank, world, local, dev)
     ndm, nt = args.ndm, args.nt
     kw = dict(ALGOS[args.algo])
     dt_code, esize = DTYPES[args.dtype]

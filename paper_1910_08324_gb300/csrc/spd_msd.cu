@@ -133,8 +133,9 @@ __device__ __forceinline__ Raw8 read_stage(const unsigned char* s, int l, int dt
 //     chunks.
 // So each lane keeps at most one value of one level per step and one per chunk.
 // A row whose staged copy did not arrive gets NaN statistics.
-template <bool BULK>
+template <bool BULK, int DT>
 __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p, int pass) {
+  constexpr int ES = DT == kDtF32 ? 4 : (DT == kDtU8 ? 1 : 2);  // bytes per sample
   __shared__ alignas(128) unsigned char ring[BULK ? kWarps * kWarpRing : 16];
   __shared__ alignas(8) uint64_t full[kWarps][kMaxStages];
   __shared__ float cshift[kMsdMaxLevels], clim[kMsdMaxLevels];
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
   const int64_t row = blockIdx.x;
   const int nlev = p.nlev;
   MsdLevel* st = reinterpret_cast<MsdLevel*>(p.state) + row * kMsdMaxLevels;
-  const unsigned char* __restrict__ xrow = static_cast<const unsigned char*>(p.x) + row * p.ld * p.esize;
+  const unsigned char* __restrict__ xrow = static_cast<const unsigned char*>(p.x) + row * p.ld * ES;
   const int64_t nt = p.nt;
   const bool vx = p.vec_x != 0;
 
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
     float v0, v1;
     {
       float4 a, b;
-      cvt8(load_raw8(xrow, 8 * t, n0, p.dtype, vx), 8 * t, n0, p.dtype, 0.0f, 1.0f, a, b);
+      cvt8(load_raw8(xrow, 8 * t, n0, DT, vx), 8 * t, n0, DT, 0.0f, 1.0f, a, b);
       float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
       v0 = 0.0f;
 #pragma unroll
@@ -194,8 +195,8 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
   const int64_t ng = (nsub + gs - 1) / gs;
   const int64_t u0 = (ng * warp / kWarps) * gs;
   const int64_t u1 = min((ng * (warp + 1) / kWarps) * gs, nsub);
-  const int sbytes = kSub * p.esize;
-  const int lgs = p.esize == 4 ? 2 : (p.esize == 2 ? 3 : 4);  // stages: kWarpRing / sbytes
+  constexpr int sbytes = kSub * ES;
+  constexpr int lgs = ES == 4 ? 2 : (ES == 2 ? 3 : 4);  // stages: kWarpRing / sbytes
   const int64_t ub = BULK ? min(u1, nfs) : u0;                 // steps [u0, ub) arrive staged
   unsigned char* wring = ring + (BULK ? warp * kWarpRing : 0);
   if (BULK) {
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
     float f[8];
     {
       float4 a, b;
-      cvt8(cx, o, rem, p.dtype, 0.0f, 1.0f, a, b);
+      cvt8(cx, o, rem, DT, 0.0f, 1.0f, a, b);
       f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w, f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
       if (!whole) {
 #pragma unroll
@@ -290,30 +291,31 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
   Raw8 nx;
   if (!BULK && u0 < u1) {
     const int64_t left = nt - u0 * kSub;
-    nx = load_raw8(xrow + u0 * sbytes, 8 * lane, left < kSub ? (int)left : kSub, p.dtype, vx);
+    nx = load_raw8(xrow + u0 * sbytes, 8 * lane, left < kSub ? (int)left : kSub, DT, vx);
   }
-  for (int64_t u = u0; u < u1; ++u) {
+  uint32_t kk = 0;  // steps done by this warp (mod 2^32: ring stage, phase parity, step within its chunk)
+  for (int64_t u = u0; u < u1; ++u, ++kk) {
     Raw8 cx;
-    const int stg = (int)((u - u0) & ((1 << lgs) - 1));
+    const int stg = (int)(kk & ((1u << lgs) - 1));
     if (BULK && u < ub) {
-      bad |= bar_wait(&full[warp][stg], (uint32_t)((u - u0) >> lgs) & 1u) ? 0 : 1;
-      cx = read_stage(wring + stg * sbytes, lane, p.dtype);
+      bad |= bar_wait(&full[warp][stg], (kk >> lgs) & 1u) ? 0 : 1;
+      cx = read_stage(wring + stg * sbytes, lane, DT);
     } else if (BULK) {
-      cx = load_raw8(xrow + u * sbytes, 8 * lane, (int)(nt - u * kSub), p.dtype, vx);
+      cx = load_raw8(xrow + u * sbytes, 8 * lane, (int)(nt - u * kSub), DT, vx);
     } else {
       cx = nx;
       if (u + 1 < u1) {
         const int64_t left = nt - (u + 1) * kSub;
-        nx = load_raw8(xrow + (u + 1) * sbytes, 8 * lane, left < kSub ? (int)left : kSub, p.dtype, vx);
+        nx = load_raw8(xrow + (u + 1) * sbytes, 8 * lane, left < kSub ? (int)left : kSub, DT, vx);
       }
     }
     const float s = u < nfs ? step(std::true_type{}, cx, u) : step(std::false_type{}, cx, u);
-    if (lane == (int)(u & 7)) q = s;
+    if (lane == (int)(kk & 7u)) q = s;
     if (BULK) {
       if (__any_sync(kFull, bad)) {  // a step did not arrive: wait (bounded) for this warp's copies in flight
         if (lane == 0)
-          for (int64_t r = u; r < ub && r < u + (1 << lgs); ++r)
-            bar_wait(&full[warp][(r - u0) & ((1 << lgs) - 1)], (uint32_t)((r - u0) >> lgs) & 1u);
+          for (uint32_t r = 0; r < (1u << lgs) && u + r < ub; ++r)
+            bar_wait(&full[warp][(kk + r) & ((1u << lgs) - 1)], ((kk + r) >> lgs) & 1u);
         if (lane == 0) failed = 1;
         break;
       }
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
       if (lane == 0 && u + (1 << lgs) < ub)
         bulk_load(wring + stg * sbytes, xrow + (u + (1 << lgs)) * sbytes, (uint32_t)sbytes, &full[warp][stg]);
     }
-    if ((u & 7) == 7 || u + 1 == u1) {  // end of a 2048-sample chunk (or of the warp's share)
+    if ((kk & 7u) == 7u || u + 1 == u1) {  // end of a 2048-sample chunk (or of the warp's share)
       const int64_t ch = u >> 3;
       float z = lane < 8 ? q : 0.0f, vb = 0.0f;
 #pragma unroll
@@ -460,8 +462,17 @@ cudaError_t launch_msd(const spd_plan& plan, const MsdParams& p, int max_passes,
   msd_reset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
   cudaError_t e = cudaGetLastError();
   for (int pass = 0; pass < max_passes && e == cudaSuccess; ++pass) {
-    if (p.vec_x) msd_pass_kernel<true><<<(unsigned)plan.desc.ndm, kThreads, 0, s>>>(p, pass);
-    else msd_pass_kernel<false><<<(unsigned)plan.desc.ndm, kThreads, 0, s>>>(p, pass);
+    const unsigned g = (unsigned)plan.desc.ndm;
+    switch (p.dtype * 2 + (p.vec_x ? 1 : 0)) {
+      case kDtF32 * 2 + 1: msd_pass_kernel<true, kDtF32><<<g, kThreads, 0, s>>>(p, pass); break;
+      case kDtF32 * 2: msd_pass_kernel<false, kDtF32><<<g, kThreads, 0, s>>>(p, pass); break;
+      case kDtF16 * 2 + 1: msd_pass_kernel<true, kDtF16><<<g, kThreads, 0, s>>>(p, pass); break;
+      case kDtF16 * 2: msd_pass_kernel<false, kDtF16><<<g, kThreads, 0, s>>>(p, pass); break;
+      case kDtBF16 * 2 + 1: msd_pass_kernel<true, kDtBF16><<<g, kThreads, 0, s>>>(p, pass); break;
+      case kDtBF16 * 2: msd_pass_kernel<false, kDtBF16><<<g, kThreads, 0, s>>>(p, pass); break;
+      case kDtU8 * 2 + 1: msd_pass_kernel<true, kDtU8><<<g, kThreads, 0, s>>>(p, pass); break;
+      default: msd_pass_kernel<false, kDtU8><<<g, kThreads, 0, s>>>(p, pass); break;
+    }
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
