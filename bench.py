@@ -138,6 +138,27 @@ def recorded_traffic(algo, ndm, nt):
     return float(e["bytes_per_sample"]) * ndm * nt
 
 
+MSD_SOURCES = ["paper_1910_08324_gb300/csrc/spd_msd.cu", "paper_1910_08324_gb300/csrc/spd_common.cuh",
+               "paper_1910_08324_gb300/csrc/spd_internal.h"]
+
+
+def recorded_msd_traffic(dtype, ndm, nt):
+    """Per-launch DRAM bytes of the noise-statistics pass kernel from the committed
+    ncu summary, if it was taken on the current sources and input type; else None."""
+    p = os.path.join(ROOT, "profiles", "msd_pass_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        e = json.load(f).get("msd_pass_" + dtype)
+    h = hashlib.sha256()
+    for s in MSD_SOURCES:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    if not e or e.get("source_hash") != h.hexdigest()[:16]:
+        return None
+    return float(e["bytes_per_sample"]) * ndm * nt
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -499,7 +520,7 @@ def run_noise_stats(args, torch, dist, spd, rank, world, local, dev):
     alg_bytes = esize * samples
     achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
+                "traffic": recorded_msd_traffic(args.dtype, ndm, nt), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
                 if peak_src == "measured" else "fallback 6.8 TB/s",
                 "kernel": "msd_pass_kernel (+ reset and table kernels in the timed call)",
                 "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": ms_per_step}
