@@ -129,8 +129,8 @@ __device__ __forceinline__ Raw8 read_stage(const unsigned char* s, int l, int dt
 //   * levels 9..11: lane i (i < 8) holds the level-8 sum of step i of the
 //     current 2048-sample chunk; the same tree over lanes 0..7 leaves level
 //     9 + ctz(l) in lane l = 1..7;
-//   * levels 12..15: lane 4 + k accumulates chunk sums into blocks of 2^(k-11)
-//     chunks.
+//   * levels 12..15: lane k - 4 (lanes 8..11) accumulates chunk sums into blocks
+//     of 2^(k-11) chunks.
 // So each lane keeps at most one value of one level per step and one per chunk.
 // A row whose staged copy did not arrive gets NaN statistics.
 template <bool BULK, int DT>
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
   const int64_t u1 = min((ng * (warp + 1) / kWarps) * gs, nsub);
   constexpr int sbytes = kSub * ES;
   constexpr int lgs = ES == 4 ? 2 : (ES == 2 ? 3 : 4);  // stages: kWarpRing / sbytes
-  const int64_t ub = BULK ? min(u1, nfs) : u0;                 // steps [u0, ub) arrive staged
+  const int64_t ub = BULK ? min(u1, nfs) : u0;  // steps [u0, ub) arrive staged
   unsigned char* wring = ring + (BULK ? warp * kWarpRing : 0);
   if (BULK) {
     if (lane == 0) {
