@@ -79,6 +79,19 @@ def test_noise_stats_dtypes(dtype, code, nt):
     _close(_gpu_table(plan, stored, 2.0, 10), _oracle_table(plan, vals, 2.0, 10), dtype)
 
 
+# short rows: a single sample, fewer samples than one 256-sample warp step, and the
+# step and 2048-sample chunk boundaries; ld = nt loads into registers, ld a multiple
+# of 4 (16-byte rows) takes bulk copies for the whole steps and plain loads for the rest
+@pytest.mark.parametrize("aligned", [False, True], ids=["ld=nt", "ld16B"])
+@pytest.mark.parametrize("nt", [1, 3, 255, 256, 257, 2047, 2049, 4097])
+def test_noise_stats_short_rows(nt, aligned):
+    ndm, ld = 3, ((nt + 3) // 4) * 4 if aligned else nt
+    xf = _rows(ndm, ld, 900 + nt).astype(np.float32)
+    plan = spd.spd_plan_create(ndm=ndm, nt=nt, ld=ld, **ALGOS["exh"](16))
+    _close(_gpu_table(plan, xf, 2.0, 10), _oracle_table(plan, xf[:, :nt].astype(np.float64), 2.0, 10),
+           "nt %d ld %d" % (nt, ld))
+
+
 def test_noise_stats_table_drives_table_search():
     # spikes inflate a plain deviation; the rejected estimate gives the search its noise table
     ndm, nt = 2, 80000
