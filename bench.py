@@ -943,9 +943,11 @@ def main():
     n_cand = int(cnt.item())
 
     # roofline of the dominant kernel (the search): algorithmic work / event time.
-    # A grid is HBM-bound when its candidates per sample fit the ALU budget of
-    # 10 bytes; dense grids are reported against the ALU peak in
-    # candidates/s (3 lane operations per candidate: add, scale, compare).
+    # A grid is HBM-bound when the ALU work of its candidates fits in the time of
+    # its 10 bytes per sample (machine balance: about 55 lane operations per sample
+    # at the measured HBM rate, i.e. about 10 candidates at 3 operations each);
+    # dense grids are reported against the ALU peak in candidates/s (3 lane
+    # operations per candidate: add, scale, compare).
     peak, peak_kind = measured_peaks()
     s_avg = statistics.mean(search_ms)
     traffic = recorded_traffic(args.algo if args.dtype == "f32" else "%s_%s" % (args.algo, args.dtype),
