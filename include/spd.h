@@ -299,10 +299,11 @@ spd_status spd_candidates_static(const spd_plan *plan, const float *d_snr,
  *   d_ws          workspace of spd_workspace_size() bytes (its tile maxima are
  *                 left alone)
  * Errors: SPD_ERR_INVALID_ARG, SPD_ERR_WORKSPACE_TOO_SMALL, SPD_ERR_CUDA.  On
- * the device, rows whose start and row length make 16-byte multiples are read
- * by bulk copies into shared memory; each wait for one is bounded (2 s), and a
- * row whose copy did not arrive in time gets NaN in every d_mu and d_sigma
- * entry (a search with that table then has NaN SNRs in the row).
+ * the device, when d_x is 16-byte aligned and ld x sample size is a multiple
+ * of 16, the rows are read by bulk copies into shared memory (other layouts by
+ * plain loads); each wait for a copy is bounded (2 s), and a row whose copy did
+ * not arrive in time gets NaN in every d_mu and d_sigma entry (a search with
+ * that table then has NaN SNRs in the row).
  */
 spd_status spd_noise_stats(const spd_plan *plan, const void *d_x, float outlier_sigma,
                            int32_t max_passes, float *d_mu, float *d_sigma, void *d_ws,
