@@ -45,8 +45,13 @@ SKA_DM = 6000
 OUT_BYTES_PER_SAMPLE = 4 + 2  # f32 Y out, u16 W out (algorithmic, once each)
 DTYPES = {"f32": (0, 4), "f16": (1, 2), "bf16": (2, 2), "u8": (3, 1)}  # spd_dtype, bytes per sample
 METRIC = "DM x time samples/s"
+# The arithmetic type of the path: every input type is converted exactly to f32 on
+# load and every boxcar sum, SNR and maximum is an f32 operation (the proposal
+# network multiplies bf16 operands into f32 sums); the stored input type is
+# reported beside it as "input_dtype".
+COMPUTE_DTYPE = "f32"
 SM_MAX_HZ = 2070e6          # GB300 maximum SM clock
-ALU_BALANCE_CANDIDATES = 10  # above this many candidates per sample a grid is ALU-bound
+ALU_OPS_PER_CANDIDATE = 3    # add (the sum), scale, max: the least a boxcar candidate costs
 
 ALGOS = {
     "ig1": dict(algo=2, igrid_depth=1, igrid_layers=4),
@@ -58,7 +63,8 @@ ALGOS = {
     "bd32": dict(algo=1, boxdit_lmax=32),
     "exh": dict(algo=0),
 }
-SEARCH_SOURCES = ["paper_1910_08324_gb300/csrc/spd_igrid.cu", "paper_1910_08324_gb300/csrc/spd_search.cu",
+SEARCH_SOURCES = ["paper_1910_08324_gb300/csrc/spd_igrid.cu", "paper_1910_08324_gb300/csrc/spd_igrid.cuh",
+                  "paper_1910_08324_gb300/csrc/spd_igrid_coded.cu", "paper_1910_08324_gb300/csrc/spd_search.cu",
                   "paper_1910_08324_gb300/csrc/spd_boxdit.cu", "paper_1910_08324_gb300/csrc/spd_common.cuh",
                   "paper_1910_08324_gb300/csrc/spd_internal.h"]
 # uneven DM ranges of one batched search: (DM trials, time decimation) of a 2,097,152-sample base
@@ -115,6 +121,36 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def alu_peak_candidates(sm_count):
+    """Candidates per second at the ALU roofline: every FP32 lane of every SM at
+    the maximum clock, 3 lane operations per candidate."""
+    return sm_count * 128 * SM_MAX_HZ / ALU_OPS_PER_CANDIDATE
+
+
+def binding_roofline(cand_per_sample, bytes_per_sample, samples, kernel_ms, sm_count, hbm_peak_gbs):
+    """Roofline of one search launch against the bound that binds it: the larger
+    of its HBM time (algorithmic bytes at the measured copy rate) and its ALU time
+    (candidates at the ALU peak).  ``frac`` is that bound's time over the measured
+    time; both fractions are returned, with the balance point (candidates per
+    sample at which the two times are equal)."""
+    alu_peak = alu_peak_candidates(sm_count)
+    t = kernel_ms / 1e3
+    t_hbm = bytes_per_sample * samples / (hbm_peak_gbs * 1e9)
+    t_alu = cand_per_sample * samples / alu_peak
+    gbs = bytes_per_sample * samples / t / 1e9
+    cps = cand_per_sample * samples / t
+    r = {"frac_hbm": gbs / hbm_peak_gbs, "frac_alu": cps / alu_peak, "hbm_GBps": gbs, "candidates_per_s": cps,
+         "balance_candidates_per_sample": alu_peak * bytes_per_sample / (hbm_peak_gbs * 1e9),
+         "alu_peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz / %d ops per candidate"
+                            % (sm_count, SM_MAX_HZ / 1e6, ALU_OPS_PER_CANDIDATE)}
+    if t_hbm >= t_alu:
+        r.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak_gbs, "unit": "GB/s", "frac": gbs / hbm_peak_gbs})
+    else:
+        r.update({"bound": "alu", "achieved": cps, "peak": alu_peak, "unit": "candidates/s",
+                  "frac": cps / alu_peak})
+    return r
+
+
 def source_hash():
     h = hashlib.sha256()
     for s in SEARCH_SOURCES:
@@ -160,29 +196,45 @@ def recorded_msd_traffic(dtype, ndm, nt):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling (every 20 ms) around the timed region.
 
-    def __init__(self, index):
+    Each sample carries nvidia-smi's timestamp; ``begin()``/``end()`` mark the
+    timed region on the host clock and the summary keeps the samples taken
+    between the two marks (all samples when none fell inside, e.g. a region
+    shorter than the sampling period)."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, period_ms=20):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         time.sleep(0.3)
         return self
 
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
     def __exit__(self, *a):
+        if self.t0 is not None and self.t1 is None:
+            self.t1 = time.time()
         if self.proc:
             self.proc.terminate()
             try:
@@ -190,28 +242,43 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
     def summary(self):
         if not self.path or not os.path.exists(self.path):
             return None
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             f = [c.strip() for c in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                rows.append((self._stamp(f[0]), float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
+        os.unlink(self.path)
+        inside = [r for r in rows if r[0] is not None and self.t0 is not None and self.t1 is not None
+                  and self.t0 <= r[0] <= self.t1]
+        use = inside or rows
+        if not use:
+            return None
+        reasons = set()
+        for r in use:
+            for n, v in zip(names, r[3]):
                 if v.lower() == "active":
                     reasons.add(n)
-        os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted(reasons), "samples": len(use), "in_timed_region": bool(inside),
+                "period_ms": self.period_ms}
 
 
 def cpu_model() -> str:
@@ -346,12 +413,14 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        clk.begin()
         with torch.cuda.stream(stream):
             for k in range(args.steps):
                 ev[2 * k].record(stream)
                 graph.replay()
                 ev[2 * k + 1].record(stream)
         torch.cuda.synchronize(dev)
+        clk.end()
     total_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
     if world > 1:
         total_ms = shard.max_over_ranks(total_ms, dist)
@@ -362,14 +431,13 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
                                        algo=a, **kw).widths()
     cand_per_sample = float(np.sum(1.0 / seps))
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak = sm_count * 128 * SM_MAX_HZ / 3.0
-    achieved = cand_per_sample * samples / (search_ms / 1e3)
     bps = esize + OUT_BYTES_PER_SAMPLE
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "candidates/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz / 3 ops per candidate" % (sm_count, SM_MAX_HZ / 1e6),
-                "hbm_GBps": bps * samples / (search_ms / 1e3) / 1e9, "kernel": "batched search (%s)" % algo,
-                "kernel_ms": search_ms, "algorithmic_bytes_per_launch": bps * samples}
+    peak, peak_kind = measured_peaks()
+    roofline = binding_roofline(cand_per_sample, bps, samples, search_ms, sm_count, peak)
+    roofline.update({"traffic": None, "kernel": "batched search (%s)" % algo, "kernel_ms": search_ms,
+                     "algorithmic_bytes_per_launch": bps * samples,
+                     "hbm_peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                     if peak_kind == "measured" else "fallback 6800 GB/s"})
     n_cand = sum(int(c.item()) for c in cnts)
     # end to end: host inputs of every range (pinned).  The persistent search is
     # launched first and each range's units wait for its ready flag (a bounded
@@ -416,11 +484,11 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
             t0 = time.perf_counter()
             e2e_step()
             per_step.append(time.perf_counter() - t0)
-        dt = statistics.median(per_step)
+        dt = statistics.mean(per_step)
         b.set_wait_ns(10 ** 9)
         e2e = {"value": samples / dt, "unit": "samples/s", "h2d_bytes_per_step": esize * samples,
                "d2h_bytes_per_step": 8 * len(shapes), "steps": args.e2e_steps, "ms_per_step": 1e3 * dt,
-               "ms_steps": [round(1e3 * v, 2) for v in per_step],
+               "ms_median": 1e3 * statistics.median(per_step), "ms_steps": [round(1e3 * v, 2) for v in per_step],
                "api": "spd_batch_execute launched first with per-range ready flags; torch pinned H2D of each "
                       "range on a copy stream followed by its flag; spd_batch_candidates; D2H of counts"}
         del hs
@@ -441,7 +509,7 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": COMPUTE_DTYPE, "input_dtype": args.dtype, "data": "synthetic",
             "config": {"workload": "batched: 5 DM ranges %s at decimations 1/2/4/8/16 of %d samples, one "
                                    "graph-captured persistent launch" % ("/".join(str(n) for n, _ in BATCH_RANGES),
                                                                          BATCH_BASE),
@@ -495,12 +563,14 @@ def run_noise_stats(args, torch, dist, spd, rank, world, local, dev):
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        clk.begin()
         with torch.cuda.stream(stream):
             for k in range(args.steps):
                 ev[2 * k].record(stream)
                 step()
                 ev[2 * k + 1].record(stream)
         torch.cuda.synchronize(dev)
+        clk.end()
     total_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
     if world > 1:
         total_ms = shard.max_over_ranks(total_ms, dist)
@@ -545,9 +615,10 @@ def run_noise_stats(args, torch, dist, spd, rank, world, local, dev):
             t0 = time.perf_counter()
             e2e_step()
             per.append(time.perf_counter() - t0)
-        dt = statistics.median(per)
+        dt = statistics.mean(per)
         e2e = {"value": samples / dt, "unit": "samples/s", "h2d_bytes_per_step": esize * samples,
                "d2h_bytes_per_step": 8 * ndm * nw, "steps": args.e2e_steps, "ms_per_step": 1e3 * dt,
+               "ms_median": 1e3 * statistics.median(per), "ms_steps": [round(1e3 * v, 2) for v in per],
                "api": "pinned H2D of the rows, spd_noise_stats (one pass), D2H of the mu and sigma tables"}
         del hx
     cpu = None
@@ -572,7 +643,7 @@ def run_noise_stats(args, torch, dist, spd, rank, world, local, dev):
         line = {
             "metric": "noise-statistics samples/s (one pass)", "value": value, "unit": "samples/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": COMPUTE_DTYPE, "input_dtype": args.dtype, "data": "synthetic",
             "config": {"workload": "noise statistics %d DM x %d samples" % (ndm, nt), "input_dtype": args.dtype,
                        "algo": args.algo, "s_end": args.s_end, "widths": nw, "ms_3_passes_2sigma": ms_3,
                        "parallelism": "dp%d (rows per GPU)" % world,
@@ -673,12 +744,14 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
         dist.barrier()
     times = []
     with ClockSampler(local) as clk:
+        clk.begin()
         for _ in range(args.steps):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             rec, nflag = prop_step()
             torch.cuda.synchronize(dev)
             times.append(time.perf_counter() - t0)
+        clk.end()
     total = sum(times)
     if world > 1:
         total = shard.max_over_ranks(total, dist)
@@ -778,10 +851,11 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
             t0 = time.perf_counter()
             nrec.append(len(e2e_step()))
             per.append(time.perf_counter() - t0)
-        dt = statistics.median(per)
+        dt = statistics.mean(per)
         e2e = {"value": ndm * nt / dt, "unit": "samples/s", "h2d_bytes_per_step": 2 * ndm * nt,
                "d2h_bytes_per_step": int(24 * statistics.mean(nrec) + 16), "steps": args.e2e_steps,
-               "ms_per_step": 1e3 * dt, "ms_steps": [round(1e3 * v, 2) for v in per], "chunks": nchunk,
+               "ms_per_step": 1e3 * dt, "ms_median": 1e3 * statistics.median(per),
+               "ms_steps": [round(1e3 * v, 2) for v in per], "chunks": nchunk,
                "records_equal_unchunked": same,
                "api": "torch pinned H2D per row chunk (copy stream) + proposal.propose_and_search per chunk "
                       "(C ABI calls, after its copy) + records to the host"}
@@ -821,7 +895,7 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "vs_baseline": None, "dtype": COMPUTE_DTYPE, "input_dtype": "f16", "data": "synthetic",
             "config": {"workload": "proposal %d DM x %d FP16 samples, white + 1/f noise, 0.1%% zero-DM spikes, "
                                    "500 pulses (widths 1..2048, SNR 5..20)" % (ndm, nt),
                        "algo": "network proposals + bd16 (table noise)", "s_end": 4096,
@@ -919,6 +993,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        clk.begin()
         for k in range(args.steps):
             if flush is not None:
                 flush.zero_()
@@ -930,6 +1005,7 @@ def main():
                                out.data_ptr(), cap, cnt.data_ptr(), ws.data_ptr(), ws.numel(), 1, sp)
             ev[3 * k + 2].record(stream)
         torch.cuda.synchronize(dev)
+        clk.end()
     if world > 1:
         dist.barrier()
     search_ms = [ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(args.steps)]
@@ -942,31 +1018,19 @@ def main():
     value = samples_step / (ms_per_step / 1e3)
     n_cand = int(cnt.item())
 
-    # roofline of the dominant kernel (the search): algorithmic work / event time.
-    # A grid is HBM-bound when the ALU work of its candidates fits in the time of
-    # its 10 bytes per sample (machine balance: about 55 lane operations per sample
-    # at the measured HBM rate, i.e. about 10 candidates at 3 operations each);
-    # dense grids are reported against the ALU peak in candidates/s (3 lane
-    # operations per candidate: add, scale, compare).
+    # roofline of the dominant kernel (the search): algorithmic work / event time,
+    # against the bound that binds the grid: its HBM time (input once, Y and W once)
+    # or its ALU time (candidates x 3 lane operations), whichever is longer
     peak, peak_kind = measured_peaks()
     s_avg = statistics.mean(search_ms)
     traffic = recorded_traffic(args.algo if args.dtype == "f32" else "%s_%s" % (args.algo, args.dtype),
                                ndm, nt)
-    if cand_per_sample <= ALU_BALANCE_CANDIDATES:
-        achieved = bytes_per_sample * ndm * nt / (s_avg / 1e3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic, "frac_of_nominal_7900": achieved / 7900.0,
-                    "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
-                    if peak_kind == "measured" else "fallback 6800 GB/s"}
-    else:
-        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-        alu_peak = sm_count * 128 * SM_MAX_HZ / 3.0
-        achieved = cand_per_sample * ndm * nt / (s_avg / 1e3)
-        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "candidates/s",
-                    "frac": achieved / alu_peak, "traffic": traffic,
-                    "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz / 3 ops per candidate"
-                                   % (sm_count, SM_MAX_HZ / 1e6),
-                    "hbm_GBps": bytes_per_sample * ndm * nt / (s_avg / 1e3) / 1e9}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    roofline = binding_roofline(cand_per_sample, bytes_per_sample, ndm * nt, s_avg, sm_count, peak)
+    roofline.update({"traffic": traffic, "frac_of_nominal_7900": roofline["hbm_GBps"] / 7900.0,
+                     "peak_source": ("%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                                     if peak_kind == "measured" else "fallback 6800 GB/s")
+                     if roofline["bound"] == "hbm" else roofline["alu_peak_source"]})
     roofline.update({"kernel": "search (%s)" % args.algo, "kernel_ms": s_avg,
                      "candidates_ms": statistics.mean(cand_ms),
                      "algorithmic_bytes_per_launch": bytes_per_sample * ndm * nt})
@@ -1039,8 +1103,8 @@ def main():
             t0 = time.perf_counter()
             d2h.append(e2e_step())
             per_step.append(time.perf_counter() - t0)
-        # the host link is shared with the machine's other work: the median step
-        dt = statistics.median(per_step)
+        # every step counts: the mean step time (the median and each step are in the line too)
+        dt = statistics.mean(per_step)
         if world > 1:
             dt = shard.max_over_ranks(dt, dist)
         torch.cuda.synchronize(dev)
@@ -1050,7 +1114,8 @@ def main():
         h2d_gbps = esize * ndm * nt / (time.perf_counter() - t1) / 1e9
         e2e = {"value": samples_step / dt, "unit": "samples/s", "h2d_bytes_per_step": esize * ndm * nt,
                "d2h_bytes_per_step": int(statistics.mean(d2h)), "steps": args.e2e_steps,
-               "ms_per_step": 1e3 * dt, "ms_steps": [round(1e3 * v, 2) for v in per_step], "chunks": nck,
+               "ms_per_step": 1e3 * dt, "ms_median": 1e3 * statistics.median(per_step),
+               "ms_steps": [round(1e3 * v, 2) for v in per_step], "chunks": nck,
                "h2d_GBps_one_copy": h2d_gbps,
                "api": "torch pinned H2D per row chunk (copy stream) + spd_search per chunk (C ABI, compute "
                       "stream, after its copy) + D2H of counts and records"}
@@ -1084,7 +1149,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": COMPUTE_DTYPE, "input_dtype": args.dtype,
             "data": "synthetic",
             "config": {"workload": ("ska_mid %d DM x %d samples, 64 us, 500 pulses" % (ndm, nt))
                        if args.workload == "ska_mid" else

@@ -216,7 +216,8 @@ spd_status spd_execute(const spd_plan *plan, const void *d_x, const spd_noise *n
  * (0 = plain threshold, at most 64).  Records are written in (row, start)
  * order; the first min(cap, total) are stored in d_out and the total count is
  * stored in *d_count (device int64).  When *d_count > cap the list is
- * truncated; the call itself still returns SPD_OK (it does not synchronise).
+ * truncated; the call itself still returns SPD_OK (it does not synchronise):
+ * spd_candidates_status reports the overflow as SPD_ERR_BUFFER_TOO_SMALL.
  *   d_snr, d_width_idx  device outputs of spd_execute ([ndm][ld])
  *   d_out               device array of cap records (may be NULL if cap == 0)
  *   d_ws                workspace as for spd_execute
@@ -231,6 +232,22 @@ spd_status spd_candidates(const spd_plan *plan, const float *d_snr,
                           const uint16_t *d_width_idx, float threshold, int32_t peak_radius,
                           spd_candidate *d_out, int64_t cap, int64_t *d_count, void *d_ws,
                           size_t ws_bytes, int32_t use_tile_max, spd_stream_t stream);
+
+/*
+ * The synchronous overflow report of a candidate step (Sec. 4.5 candidate
+ * list): waits for the stream, reads the true record count that spd_candidates,
+ * spd_candidates_static, spd_search or spd_batch_candidates wrote to *d_count,
+ * stores it in *total (host; may be NULL) and returns SPD_ERR_BUFFER_TOO_SMALL
+ * when it exceeds cap (the list holds the first cap records in (row, start)
+ * order), SPD_OK when every record was stored.  The candidate calls themselves
+ * never synchronise, so that a search and its candidate step can be captured in
+ * a CUDA graph; a caller that wants the error at once calls this after them.
+ *   d_count  device int64 written by the candidate call (8-byte aligned)
+ *   cap      the cap that call was given (>= 0)
+ * Errors: SPD_ERR_INVALID_ARG, SPD_ERR_CUDA (an asynchronous error of work
+ * queued on the stream, or the copy), SPD_ERR_BUFFER_TOO_SMALL.
+ */
+spd_status spd_candidates_status(const int64_t *d_count, int64_t cap, int64_t *total, spd_stream_t stream);
 
 /*
  * spd_execute followed by spd_candidates(..., use_tile_max = 1) on the same
@@ -259,9 +276,11 @@ spd_status spd_search(const spd_plan *plan, const void *d_x, const spd_noise *no
  * library until the process exits).
  * A plan with more tiles is rejected with SPD_ERR_UNSUPPORTED before any work
  * is queued.  The call itself allocates nothing.
- *   - The first call on a device looks up the array's device address (once per
- *     device, with that device current); make that first call before any
- *     stream capture.
+ *   - Each call looks up the array's device address with the device current;
+ *     inside a stream capture it cannot, and uses the address found by the last
+ *     call on that device outside a capture: make a first call on each device
+ *     before any stream capture (and again after the device's context was
+ *     destroyed and created anew, e.g. by cudaDeviceReset).
  *   - All calls on a device share the array: calls whose work overlaps on the
  *     GPU (different streams, no ordering between them) race and give wrong
  *     results.  Calls ordered on one stream are safe; nothing carries over

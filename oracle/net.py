@@ -12,6 +12,9 @@ file is its definition, written plainly in numpy:
   head    z = b_4 + sum_c W_4[c] g[c],  p = sigmoid(z)
   loss    BCE(p, y) = softplus(z) - y z
 
+The input blocks come from ``decimate``: 16-sample sums of a row, centred and
+scaled to unit variance.
+
 bf16(v) rounds to the nearest bfloat16 (ties to even); bf16=False drops the
 rounding (the exact function, used to check the gradients by finite
 differences).  Gradients pass the roundings unchanged (straight-through); the
@@ -28,6 +31,28 @@ C, K, P, PAD = 16, 9, 256, 4
 SHAPES = [("W1", (C, 1, K)), ("b1", (C,)), ("W2", (C, C, K)), ("b2", (C,)), ("W3", (C, C, K)),
           ("b3", (C,)), ("W4", (C,)), ("b4", (1,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+
+
+def decimate(x, mu, sigma, factor=16):
+    """The network's input series: x16 decimation of each row, normalised.
+
+    d[r][j] = (sum_{i < factor} x[r][factor j + i] - factor mu_r) / (sqrt(factor) sigma_r)
+    for j < nt // factor (a trailing partial block is dropped): the sum of a
+    block of white noise N(mu_r, sigma_r^2) has mean factor mu_r and deviation
+    sqrt(factor) sigma_r, so d is N(0, 1) noise.  Plain loops in FP64."""
+    x = np.asarray(x, np.float64)
+    ndm, nt = x.shape
+    mu = np.broadcast_to(np.asarray(mu, np.float64), (ndm,))
+    sigma = np.broadcast_to(np.asarray(sigma, np.float64), (ndm,))
+    nb = nt // factor
+    out = np.empty((ndm, nb))
+    for r in range(ndm):
+        for j in range(nb):
+            acc = 0.0
+            for i in range(factor):
+                acc += x[r, factor * j + i]
+            out[r, j] = (acc - factor * mu[r]) / (np.sqrt(factor) * sigma[r])
+    return out
 
 
 def unpack(theta):

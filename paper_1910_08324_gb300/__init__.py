@@ -50,6 +50,7 @@ from ._binding import (  # noqa: F401
     spd_batch_status,
     spd_candidates,
     spd_candidates_static,
+    spd_candidates_status,
     spd_execute,
     spd_net_param_count,
     spd_noise_stats,

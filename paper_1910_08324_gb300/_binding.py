@@ -60,7 +60,7 @@ _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_des
             "spd_batch_set_wait_ns", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
             "spd_batch_candidates", "spd_net_decimate", "spd_net_forward", "spd_net_gradient",
             "spd_net_adam", "spd_net_select", "spd_net_gather", "spd_plan_set_starts", "spd_plan_create_grid",
-            "spd_net_gradient_ordered"]
+            "spd_net_gradient_ordered", "spd_candidates_status"]
 
 
 def library_path() -> str:
@@ -90,6 +90,7 @@ def load_library():
                                    i64, vp, vp, sz, vp]
         lib.spd_sync_status.argtypes = [vp, vp]
         lib.spd_candidates_static.argtypes = [vp, vp, vp, ctypes.c_float, i32, vp, i64, vp, vp]
+        lib.spd_candidates_status.argtypes = [vp, i64, ctypes.POINTER(i64), vp]
         lib.spd_noise_stats.argtypes = [vp, vp, ctypes.c_float, i32, vp, vp, vp, sz, vp]
         lib.spd_plan_set_segment.argtypes = [vp, i32]
         lib.spd_plan_set_starts.argtypes = [vp, i64]
@@ -224,6 +225,15 @@ def spd_candidates(plan: Plan, snr: int, width_idx: int, threshold: float, peak_
                                          int(cap), count, ws, ws_bytes, int(use_tile_max),
                                          stream or None),
            "spd_candidates")
+
+
+def spd_candidates_status(count: int, cap: int, stream: int = 0) -> int:
+    """Waits for the stream and returns the true record count at device address
+    ``count``; raises SpdError (SPD_ERR_BUFFER_TOO_SMALL) when it exceeds cap."""
+    total = ctypes.c_int64(-1)
+    _check(load_library().spd_candidates_status(count, int(cap), ctypes.byref(total), stream or None),
+           "spd_candidates_status")
+    return int(total.value)
 
 
 def spd_candidates_static(plan: Plan, snr: int, width_idx: int, threshold: float,

@@ -173,8 +173,8 @@ void fill_grid(spd::SearchParams& p, const spd_plan& plan) {
     for (int j = 0; j <= plan.top; ++j)
       for (int m = 1; m <= plan.k; ++m)
         p.bscale[j][m] = (float)(1.0 / std::sqrt((double)plan.lvl_base[j] + (double)m * (double)(1 << j)));
-  } else if (plan.family == kIgrid) {  // fine levels 0..3: 1/sqrt(m 2^j) in one constant
-    for (int j = 0; j <= 3 && j <= plan.top; ++j)
+  } else if (plan.family == kIgrid) {  // 1/sqrt(m 2^j) in one constant (block count m of level j)
+    for (int j = 0; j <= plan.top && j < spd::kMaxLevels; ++j)
       for (int m = 1; m <= 32; ++m) p.bscale[j][m] = (float)(1.0 / std::sqrt((double)m * (double)(1 << j)));
   }
 }
@@ -886,6 +886,18 @@ spd_status spd_sync_status(const spd_plan* plan, spd_stream_t stream) {
   cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
   if (e == cudaSuccess) e = cudaPeekAtLastError();
   return check_cuda(e);
+}
+
+spd_status spd_candidates_status(const int64_t* d_count, int64_t cap, int64_t* total, spd_stream_t stream) {
+  if (!d_count || ((uintptr_t)d_count % 8) || cap < 0) return SPD_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaPeekAtLastError();
+  int64_t n = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&n, d_count, sizeof(n), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return SPD_ERR_CUDA;
+  if (total) *total = n;
+  return n > cap ? SPD_ERR_BUFFER_TOO_SMALL : SPD_OK;
 }
 
 }  // extern "C"

@@ -111,27 +111,24 @@ struct BdDyn {
 // One coarse position: widths c_j + m 2^j, m = 1..K (ranks >= nu masked out).
 // A points at the window's first aligned block (SKIP0: one block earlier, for
 // the level whose base is K - 2 blocks), R at R_j[n]; sc[m - 1] is the scale of
-// block count m (a float, or a float2 (a, b) for table noise).
+// block count m (a float, or a float2 (a, b) for table noise).  Returns the
+// maximum SNR coded with its rank m - 1 (see enc_w), kept running.
 template <int K, bool HAS_R, bool SKIP0, class SC>
-__device__ __forceinline__ void bd_coarse_eval(const float* A, const float* R, const SC* sc,
-                                               int nu, float& bv, int& bq) {
+__device__ __forceinline__ float bd_coarse_eval(const float* A, const float* R, const SC* sc, int nu) {
   float S = SKIP0 ? 0.0f : A[0];
   static_for<1, K - 1>([&](auto T) { S += A[decltype(T)::value]; });
-  float v[K];
+  float acc = ninf(), c = ninf();
   static_for<1, K + 1>([&](auto M) {
     constexpr int m = decltype(M)::value;
     S += A[K - 2 + m];
     const float X = HAS_R ? S + R[K - 1 + m] : S;
-    v[m - 1] = (m == 1 || m - 1 < nu) ? snr_of(X, sc[m - 1]) : ninf();
+    const float e = (m == 1 || m - 1 < nu) ? enc_w<5>(snr_of(X, sc[m - 1]), 32 - m) : ninf();
+    if constexpr (m & 1)
+      c = e;
+    else
+      acc = fmax3(acc, c, e);
   });
-  const float best = tree_max<K>(v);
-  int q = K - 1;
-  static_for<0, K - 1>([&](auto C) {
-    constexpr int c = K - 2 - decltype(C)::value;
-    if (v[c] == best) q = c;
-  });
-  bv = best;
-  bq = q;
+  return acc;
 }
 
 // Table noise with K = 32 keeps 32 (a, b) pairs of level 0 live: one CTA per
@@ -305,23 +302,24 @@ __device__ __forceinline__ void boxdit_unit(const SearchParams& p, const Unit& U
     }
     if (ar >= srel || !cj) return;
     const int n = cn - ((k * kC) >> cj);
-    float bv;
-    int bq;
+    float cv;
     auto run = [&](const auto* sc) {
       if (cj > KAP) {
-        bd_coarse_eval<K, true, false>(smem + ca + (n & cmask), smem + cr + (n & cmask), sc, cnu, bv, bq);
+        cv = bd_coarse_eval<K, true, false>(smem + ca + (n & cmask), smem + cr + (n & cmask), sc, cnu);
       } else if (K == 32 && cj == 4) {  // c_4 / 16 = K - 2 blocks: window starts one block early
-        bd_coarse_eval<K, false, true>(smem + ca + ((n - 1) & cmask), nullptr, sc, cnu, bv, bq);
+        cv = bd_coarse_eval<K, false, true>(smem + ca + ((n - 1) & cmask), nullptr, sc, cnu);
       } else {
-        bd_coarse_eval<K, false, false>(smem + ca + (n & cmask), nullptr, sc, cnu, bv, bq);
+        cv = bd_coarse_eval<K, false, false>(smem + ca + (n & cmask), nullptr, sc, cnu);
       }
     };
     if constexpr (TABLE)
       run(static_cast<const float2*>(AB + cfirst));
     else
       run(static_cast<const float*>(STAB + cj * (K + 1) + 1));
+    // a position with no valid candidate (every sum -inf) gives NaN: -inf instead
+    const float bv = cv == cv ? dec_v<5>(cv) : ninf();
     RESY[(k & 1) * kResN + t] = bv;
-    RESW[(k & 1) * kResN + t] = (uint16_t)(cfirst + bq);
+    RESW[(k & 1) * kResN + t] = (uint16_t)(cfirst + dec_w<5>(cv));
     atomicMax(BCM + (k & 1) * kBcm + cbcm, (fkey(bv) & ~15) | ccode);
   };
 
@@ -348,51 +346,59 @@ __device__ __forceinline__ void boxdit_unit(const SearchParams& p, const Unit& U
     const int buf = k % S::NBUF;
     float y[8], f0[8];
     int w[8];
+    // every level's maximum is coded with its rank (eval_bd_enc); a level is
+    // decoded once per position and merged with the levels below by a strict '>'
+    // (the smaller width wins a tie)
+    auto merge_coded = [&](float& yv, int& wv, float c, int first) {
+      merge1(yv, wv, dec_v<5>(c), first + dec_w<5>(c));
+    };
     {
-      float win[S::NW0 * 4];
+      float win[S::NW0 * 4], o[8];
       load_window4<S::NW0>(smem + S::f0(buf) + 8 * t, win);
       if (!COARSE && top == 0)
-        eval_window<8, K, AllM, true, false>(win, p.n_top, sc0, nullptr, y, w, f0);
+        eval_bd_enc<8, K, false, true>(win, nullptr, p.n_top, sc0, o, f0);
       else
-        eval_window_mxb<8, K, AllM, false>(win, nullptr, sc0, y, w, f0);
+        eval_bd_enc<8, K, false, false>(win, nullptr, p.n_top, sc0, o, f0);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {  // level 0 starts at width index 0
+        y[r] = dec_v<5>(o[r]);
+        w[r] = dec_w<5>(o[r]);
+      }
     }
     float f1[4], f2[2];
     if (COARSE || top >= 1) {
-      float win[S::NW1 * 4], bv[4];
-      int bq[4];
+      float win[S::NW1 * 4], o[4];
       const float b[4] = {f0[0], f0[2], f0[4], f0[6]};
       load_window4<S::NW1>(smem + S::f1(buf) + 4 * t + S::OF1, win);
       if (!COARSE && top == 1)
-        eval_window<4, K, AllM, true, true>(win, p.n_top, sc1, b, bv, bq, f1);
+        eval_bd_enc<4, K, true, true>(win, b, p.n_top, sc1, o, f1);
       else
-        eval_window_mxb<4, K, AllM, true>(win, b, sc1, bv, bq, f1);
+        eval_bd_enc<4, K, true, false>(win, b, p.n_top, sc1, o, f1);
       const int first = p.lvl_first[1];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) merge1(y[2 * r], w[2 * r], bv[r], first + bq[r]);
+      for (int r = 0; r < 4; ++r) merge_coded(y[2 * r], w[2 * r], o[r], first);
     }
     if (COARSE || top >= 2) {
-      float win[S::NW2 * 2], bv[2];
-      int bq[2];
+      float win[S::NW2 * 2], o[2];
       const float b[2] = {f1[0], f1[2]};
       load_window2<S::NW2>(smem + S::f2(buf) + 2 * t + S::OF2, win);
       if (!COARSE && top == 2)
-        eval_window<2, K, AllM, true, true>(win, p.n_top, sc2, b, bv, bq, f2);
+        eval_bd_enc<2, K, true, true>(win, b, p.n_top, sc2, o, f2);
       else
-        eval_window_mxb<2, K, AllM, true>(win, b, sc2, bv, bq, f2);
+        eval_bd_enc<2, K, true, false>(win, b, p.n_top, sc2, o, f2);
       const int first = p.lvl_first[2];
-      merge1(y[0], w[0], bv[0], first + bq[0]);
-      merge1(y[4], w[4], bv[1], first + bq[1]);
+      merge_coded(y[0], w[0], o[0], first);
+      merge_coded(y[4], w[4], o[1], first);
     }
     if (COARSE || top >= 3) {
-      float win[S::NW3], bv[1], f3[1];
-      int bq[1];
+      float win[S::NW3], o[1], f3[1];
       const float b[1] = {f2[0]};
       load_window1<S::NW3>(smem + S::f3(buf) + t + S::OF3, win);
       if (!COARSE && top == 3)
-        eval_window<1, K, AllM, true, true>(win, p.n_top, sc3, b, bv, bq, f3);
+        eval_bd_enc<1, K, true, true>(win, b, p.n_top, sc3, o, f3);
       else
-        eval_window_mxb<1, K, AllM, true>(win, b, sc3, bv, bq, f3);
-      merge1(y[0], w[0], bv[0], p.lvl_first[3] + bq[0]);
+        eval_bd_enc<1, K, true, false>(win, b, p.n_top, sc3, o, f3);
+      merge_coded(y[0], w[0], o[0], p.lvl_first[3]);
     }
     if (COARSE) {  // best coarse level at start 8t (even t: 8t = 0 mod 16)
       int* kp = BCM + (k & 1) * kBcm + (t >> 1);

@@ -44,7 +44,7 @@ namespace {
 
 constexpr int kCandThreads = 256;
 constexpr int kScanThreads = 1024;
-constexpr int kCandCtas = 152 * 8;  // persistent CTAs of the count and write passes (upper bound)
+constexpr int kCandCtasPerSm = 8;  // persistent CTAs per SM of the count and write passes
 static_assert(kCandGroup == 32, "a group is one tile per lane");
 static_assert(sizeof(spd_candidate) == 24 && offsetof(spd_candidate, row) == 0 &&
                   offsetof(spd_candidate, width_idx) == 4 && offsetof(spd_candidate, start) == 8 &&
@@ -212,29 +212,53 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_addr[kMaxDevices] = {};  // device address of the scratch, per device
+int g_sm_count[kMaxDevices] = {};       // multiprocessors of each device
 }  // namespace
 
 // The host-side name g_static_cand_scratch is not a device address: the address
-// is looked up once per device (with that device current) and cached.
-cudaError_t static_cand_scratch(void** out) {
+// is looked up with the device current.  Outside a stream capture it is looked
+// up on every call (so a context that was torn down and created again gets the
+// new address); during a capture the address of the last call outside one is
+// used, so the first call on a device must come before any capture.
+cudaError_t static_cand_scratch(cudaStream_t s, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* a = nullptr;
     e = cudaGetSymbolAddress(&a, g_static_cand_scratch);
     if (e != cudaSuccess) return e;
     g_static_addr[dev] = a;
   }
+  if (!g_static_addr[dev]) return cudaErrorStreamCaptureUnsupported;
   *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+// Multiprocessor count of the current device, queried on its first use and kept
+// (the query is not a stream operation, so capture does not prevent it).
+cudaError_t device_sm_count(int* n) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_sm_count[dev]) {
+    e = cudaDeviceGetAttribute(&g_sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  *n = g_sm_count[dev];
   return cudaSuccess;
 }
 
 cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s) {
   void* base = nullptr;
-  const cudaError_t e = static_cand_scratch(&base);
+  const cudaError_t e = static_cand_scratch(s, &base);
   if (e != cudaSuccess) return e;
   char* b = static_cast<char*>(base);
   p.counts = reinterpret_cast<int32_t*>(b);
@@ -248,10 +272,13 @@ cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaSt
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s) {
   const int64_t ntiles = plan.desc.ndm * plan.cand_tiles_per_row;
   const int64_t ngroups = (ntiles + kCandGroup - 1) / kCandGroup;
+  int sms = 0;
+  cudaError_t e = device_sm_count(&sms);
+  if (e != cudaSuccess) return e;
   int64_t ctas = (ngroups + kCandThreads / 32 - 1) / (kCandThreads / 32);
-  if (ctas > kCandCtas) ctas = kCandCtas;
+  if (ctas > (int64_t)sms * kCandCtasPerSm) ctas = (int64_t)sms * kCandCtasPerSm;
   cand_count_kernel<<<(unsigned)ctas, kCandThreads, 0, s>>>(p, ntiles, ngroups);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   cand_scan_kernel<<<1, kScanThreads, 0, s>>>(p, ngroups);
   e = cudaGetLastError();

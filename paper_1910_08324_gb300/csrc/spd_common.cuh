@@ -240,8 +240,9 @@ __device__ __forceinline__ Raw8 load_raw8(const unsigned char* __restrict__ row,
   return r;
 }
 
-// The samples of load_raw8 as floats, normalised to (x - mu) * inv; samples at
-// or past n are -inf.
+// The samples of load_raw8 as floats, normalised to (x - mu) * inv (NORM; the
+// raw values otherwise); samples at or past n are -inf.
+template <bool NORM = true>
 __device__ __forceinline__ void cvt8(const Raw8& r, int pos, int n, int dtype, float mu, float inv,
                                      float4& v0, float4& v1) {
   float f[8];
@@ -269,8 +270,15 @@ __device__ __forceinline__ void cvt8(const Raw8& r, int pos, int n, int dtype, f
 #pragma unroll
     for (int i = 0; i < 8; ++i) f[i] = __uint2float_rn((wa[i >> 2] >> (8 * (i & 3))) & 0xffu);
   }
+  if constexpr (NORM) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) f[i] = (f[i] - mu) * inv;
+    for (int i = 0; i < 8; i += 2) {  // packed pairs: x + (-mu) rounds as x - mu
+      const float2 z =
+          __fmul2_rn(__fadd2_rn(make_float2(f[i], f[i + 1]), make_float2(-mu, -mu)), make_float2(inv, inv));
+      f[i] = z.x;
+      f[i + 1] = z.y;
+    }
+  }
   if (pos + 8 > n) {
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -460,9 +468,23 @@ __device__ __forceinline__ void eval_window(const float* w, int n_used, Scale&& 
 // then single max instructions.  A -inf candidate becomes a NaN, which max
 // ignores; a maximum over NaNs only is the canonical (positive) NaN, which
 // callers must treat as "no candidate" before using it as an ordered key.
+//
+// The code is set with one logic instruction: (v | low) & (~low | code), where
+// low = 2^B - 1 sits in a register (opaque to the compiler, so that it is not
+// folded back into the two-instruction (v & ~low) | code) and ~low | code is the
+// instruction's immediate.
+__device__ __forceinline__ int opaque_int(int v) {
+  int r;
+  asm("mov.b32 %0, %1;" : "=r"(r) : "r"(v));
+  return r;
+}
 template <int B>
 __device__ __forceinline__ float enc_w(float v, int code) {
-  return __int_as_float((__float_as_int(v) & ~((1 << B) - 1)) | code);
+  int r;
+  asm("lop3.b32 %0, %1, %2, %3, 0xC8;"
+      : "=r"(r)
+      : "r"(__float_as_int(v)), "r"(~((1 << B) - 1) | code), "r"(opaque_int((1 << B) - 1)));
+  return __int_as_float(r);
 }
 template <int B>
 __device__ __forceinline__ int dec_w(float v) {
@@ -560,7 +582,10 @@ __device__ __forceinline__ void enc_post(float x, int code0, int n_used, float (
     v[RK] = c;
 }
 
-template <int NP, int MMAX, class Pred, int B, bool PARTIAL, class Scale>
+//
+// UNIT1: the scale of block count 1 is exactly 1 (white noise, width 1), so that
+// candidate is the sum itself, with no multiplication.
+template <int NP, int MMAX, class Pred, int B, bool PARTIAL, bool UNIT1 = false, class Scale>
 __device__ __forceinline__ void eval_window_enc(const float* w, int n_used, Scale&& scale, int code0,
                                                 float (&out)[NP]) {
   constexpr int NC = count_in<Pred, MMAX>();
@@ -590,7 +615,7 @@ __device__ __forceinline__ void eval_window_enc(const float* w, int n_used, Scal
           Sm = (m == 1) ? make_float2(w[r], w[r + 1]) : __fadd2_rn(Se, make_float2(w[r + m - 1], w[r + m]));
         }
         if constexpr (Pred::in(m)) {
-          const float2 x = snr_of2(Sm, scale(M));
+          const float2 x = (UNIT1 && m == 1) ? Sm : snr_of2(Sm, scale(M));
           enc_post<B, PARTIAL, Pred::rank(m)>(x.x, code0, n_used, v0);
           enc_post<B, PARTIAL, Pred::rank(m)>(x.y, code0, n_used, v1);
         }
@@ -617,9 +642,80 @@ __device__ __forceinline__ void eval_window_enc(const float* w, int n_used, Scal
         } else {
           Sm = 0.0f;  // not formed
         }
-        if constexpr (Pred::in(m)) enc_post<B, PARTIAL, Pred::rank(m)>(snr_of(Sm, scale(M)), code0, n_used, v);
+        if constexpr (Pred::in(m))
+          enc_post<B, PARTIAL, Pred::rank(m)>((UNIT1 && m == 1) ? Sm : snr_of(Sm, scale(M)), code0, n_used, v);
       });
       out[r] = tree_max<NC>(v);
+    });
+  }
+}
+
+// Coded evaluation of one BoxDIT level (Alg. 1: block counts m = 1..K, every
+// one a candidate) at NP consecutive positions: S_m = base[r] + w[r] + ... +
+// w[r + m - 1] (added in block order, as the shifted decimation adds them), the
+// SNR S_m * scale(m) coded with its rank m - 1 (code 31 - (m - 1), see enc_w),
+// and out[r] = the coded maximum over m (PARTIAL: ranks >= n_used count as
+// -inf); full[r] = S_K, the level's widest boxcar, the base of the next level.
+// Two positions share each scale instruction (packed f32x2; the sums are added
+// in packed form where the two addends are an aligned pair), and the maximum is
+// kept running, so no candidate outlives its step.
+template <int NP, int K, bool HAS_BASE, bool PARTIAL, class Scale>
+__device__ __forceinline__ void eval_bd_enc(const float* w, const float* base, int n_used, Scale&& scale,
+                                            float (&out)[NP], float (&full)[NP]) {
+  static_assert(K <= 32 && K % 2 == 0, "5-bit codes, block counts in pairs");
+  auto keep = [&](float c, auto M) {
+    constexpr int m = decltype(M)::value;
+    if constexpr (PARTIAL && m > 1)
+      return (m - 1 < n_used) ? c : ninf();
+    else
+      return c;
+  };
+  if constexpr (NP % 2 == 0) {
+    static_for<0, NP / 2>([&](auto R2) {
+      constexpr int r = 2 * decltype(R2)::value;
+      float2 S = HAS_BASE ? make_float2(base[r], base[r + 1]) : make_float2(0.0f, 0.0f);
+      float a0 = ninf(), a1 = ninf(), c0 = ninf(), c1 = ninf();
+      static_for<1, K + 1>([&](auto M) {
+        constexpr int m = decltype(M)::value;
+        if constexpr (m == 1 && !HAS_BASE) {
+          S = make_float2(w[r], w[r + 1]);
+        } else if constexpr (((r + m - 1) & 1) == 0) {
+          S = __fadd2_rn(S, make_float2(w[r + m - 1], w[r + m]));
+        } else {
+          S.x += w[r + m - 1];
+          S.y += w[r + m];
+        }
+        const float2 x = snr_of2(S, scale(M));
+        const float e0 = keep(enc_w<5>(x.x, 32 - m), M), e1 = keep(enc_w<5>(x.y, 32 - m), M);
+        if constexpr (m & 1) {
+          c0 = e0;
+          c1 = e1;
+        } else {
+          a0 = fmax3(a0, c0, e0);
+          a1 = fmax3(a1, c1, e1);
+        }
+      });
+      out[r] = a0;
+      out[r + 1] = a1;
+      full[r] = S.x;
+      full[r + 1] = S.y;
+    });
+  } else {
+    static_for<0, NP>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      float S = HAS_BASE ? base[r] : 0.0f;
+      float a = ninf(), c = ninf();
+      static_for<1, K + 1>([&](auto M) {
+        constexpr int m = decltype(M)::value;
+        S = (m == 1 && !HAS_BASE) ? w[r] : S + w[r + m - 1];
+        const float e = keep(enc_w<5>(snr_of(S, scale(M)), 32 - m), M);
+        if constexpr (m & 1)
+          c = e;
+        else
+          a = fmax3(a, c, e);
+      });
+      out[r] = a;
+      full[r] = S;
     });
   }
 }

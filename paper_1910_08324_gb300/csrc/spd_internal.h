@@ -83,7 +83,7 @@ struct SearchParams {
   int32_t lvl_first[kMaxLevels];  // width-table index of each level's first width
   float lvl_scale[kMaxLevels];    // IGRID: 2^(-j/2), the unit factor of level j
   float rs[64];                   // rs[m] = 1/sqrt(m) (IGRID block-count factor)
-  float bscale[kMaxLevels][33];   // BoxDIT: 1/sqrt(c_j + m 2^j), m = 1..K; IGRID levels 0..3: 1/sqrt(m 2^j)
+  float bscale[kMaxLevels][33];   // BoxDIT: 1/sqrt(c_j + m 2^j), m = 1..K; IGRID: 1/sqrt(m 2^j), every level
   int32_t table;                  // 1: per-row, per-width noise statistics (spd_noise mode 1)
   int32_t n_widths;               // widths of the plan
   int32_t unit_widths;            // 1: width index w is width w + 1 (exhaustive grid)
@@ -152,9 +152,10 @@ struct spd_plan {
 };
 
 namespace spd {
-// kernel launchers (spd_search.cu, spd_igrid.cu, spd_boxdit.cu, spd_candidates.cu, spd_msd.cu)
+// kernel launchers (spd_search.cu, spd_igrid.cu, spd_igrid_coded.cu, spd_boxdit.cu, spd_candidates.cu, spd_msd.cu)
 cudaError_t launch_search(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_igrid(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
+cudaError_t launch_igrid_coded(const spd_plan& plan, const SearchParams& p, size_t smem, cudaStream_t s);
 size_t igrid_smem_bytes(const spd_plan& plan, bool table);
 cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 size_t boxdit_smem_bytes(const spd_plan& plan, bool table);

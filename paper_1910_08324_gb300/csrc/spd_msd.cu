@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
     float v0, v1;
     {
       float4 a, b;
-      cvt8(load_raw8(xrow, 8 * t, n0, DT, vx), 8 * t, n0, DT, 0.0f, 1.0f, a, b);
+      cvt8<false>(load_raw8(xrow, 8 * t, n0, DT, vx), 8 * t, n0, DT, 0.0f, 1.0f, a, b);
       float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
       v0 = 0.0f;
 #pragma unroll
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
     float f[8];
     {
       float4 a, b;
-      cvt8(cx, o, rem, DT, 0.0f, 1.0f, a, b);
+      cvt8<false>(cx, o, rem, DT, 0.0f, 1.0f, a, b);
       f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w, f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
       if (!whole) {
 #pragma unroll

@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(256) net_decimate_kernel(const void* __restric
   const int64_t r = i / nd, j = i % nd;
   const unsigned char* row = static_cast<const unsigned char*>(x) + (r * ld + 16 * j) * esize;
   float4 a, b, c, d;
-  cvt8(load_raw8(row, 0, 16, dtype, vec != 0), 0, 16, dtype, 0.f, 1.f, a, b);
-  cvt8(load_raw8(row, 8, 16, dtype, vec != 0), 8, 16, dtype, 0.f, 1.f, c, d);
+  cvt8<false>(load_raw8(row, 0, 16, dtype, vec != 0), 0, 16, dtype, 0.f, 1.f, a, b);
+  cvt8<false>(load_raw8(row, 8, 16, dtype, vec != 0), 8, 16, dtype, 0.f, 1.f, c, d);
   const float s = ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w)) + ((c.x + c.y) + (c.z + c.w)) +
                   ((d.x + d.y) + (d.z + d.w));
   out[i] = (s - 16.f * mu[r]) / (4.f * sigma[r]);

@@ -28,6 +28,15 @@ def test_library_exports_every_declared_symbol():
         assert ctypes.cast(getattr(lib, n), ctypes.c_void_p).value
 
 
+def test_candidates_status_validates_before_any_device_work():
+    lib = spd.load_library()
+    total = ctypes.c_int64(-7)
+    assert lib.spd_candidates_status(None, 10, ctypes.byref(total), None) == 1  # NULL count
+    assert lib.spd_candidates_status(ctypes.c_void_p(8), -1, ctypes.byref(total), None) == 1  # cap < 0
+    assert lib.spd_candidates_status(ctypes.c_void_p(12), 0, None, None) == 1  # misaligned
+    assert total.value == -7
+
+
 def test_version_and_status_strings():
     assert spd.spd_version() == "0.1"
     for s in range(8):

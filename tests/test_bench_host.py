@@ -52,20 +52,49 @@ def test_traffic_record_of_other_sources_or_types_is_null(bench, tmp_path, monke
 
 
 def test_clock_summary_reports_median_and_throttle_reasons(bench, tmp_path):
-    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
-            "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
-            "0, 2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+    rows = ["2026/12/04 10:00:00.000, 0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "2026/12/04 10:00:00.100, 0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "2026/12/04 10:00:00.200, 0, 2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active",
             "garbage line"]
     p = tmp_path / "clocks.csv"
     p.write_text("\n".join(rows) + "\n")
     cs = bench.ClockSampler(0)
     cs.path = str(p)
-    s = cs.summary()
+    s = cs.summary()  # no timed region marked: every sample
     assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
-    assert s["reasons"] == ["sw_power_cap"]
-    p.write_text("0, 1500, 2070, 1000, 0x8, Active, Not Active, Active, Not Active\n")
+    assert s["reasons"] == ["sw_power_cap"] and not s["in_timed_region"]
+    p.write_text("2026/12/04 10:00:00.000, 0, 1500, 2070, 1000, 0x8, Active, Not Active, Active, Not Active\n")
     cs.path = str(p)
     assert cs.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_keeps_the_samples_of_the_timed_region(bench, tmp_path):
+    # samples before the region (an idle clock, a throttle reason) are left out
+    rows = ["2026/12/04 10:00:00.000, 0, 990, 2070, 100.0, 0x1, Not Active, Not Active, Not Active, Active",
+            "2026/12/04 10:00:01.000, 0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "2026/12/04 10:00:01.020, 0, 2055, 2070, 910.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "2026/12/04 10:00:01.040, 0, 2070, 2070, 905.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    p = tmp_path / "clocks.csv"
+    p.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.path = str(p)
+    cs.t0 = bench.ClockSampler._stamp("2026/12/04 10:00:00.900")
+    cs.t1 = bench.ClockSampler._stamp("2026/12/04 10:00:01.050")
+    s = cs.summary()
+    assert s["samples"] == 3 and s["in_timed_region"] and s["reasons"] == [] and s["sm_mhz"] == 2070.0
+
+
+def test_binding_roofline_takes_the_longer_of_hbm_and_alu_time(bench):
+    # 152 SMs: ALU peak 1.3422e13 candidates/s; at 6784.5 GB/s and 10 B/sample the
+    # balance point is ~19.8 candidates per sample
+    r = bench.binding_roofline(7.0, 10, 1 << 30, 2.0, 152, 6784.5)
+    assert r["bound"] == "hbm" and abs(r["balance_candidates_per_sample"] - 19.78) < 0.05
+    assert r["frac"] == pytest.approx(r["frac_hbm"]) and r["frac_alu"] < r["frac_hbm"]
+    r = bench.binding_roofline(31.9, 10, 1 << 30, 5.0, 152, 6784.5)
+    assert r["bound"] == "alu" and r["frac"] == pytest.approx(31.9 * (1 << 30) / 5e-3 / 1.3422e13, rel=1e-3)
+    # IG(2) (15 candidates per sample) and BD-8 (16) sit below the balance: HBM-bound
+    for c in (15.0, 16.0):
+        assert bench.binding_roofline(c, 10, 1 << 30, 5.0, 152, 6784.5)["bound"] == "hbm"
 
 
 def test_workloads_and_defaults(bench, monkeypatch):

@@ -60,6 +60,22 @@ def test_truncation_keeps_first_records_and_true_count():
     assert n0 == n_all
 
 
+def test_candidates_status_reports_overflow_synchronously():
+    # the candidate call itself returns SPD_OK; spd_candidates_status waits for the
+    # stream and turns a count above cap into SPD_ERR_BUFFER_TOO_SMALL
+    t = torch()
+    plan, x, Yh, Wh, (Y, W, ws, *_), _ = _setup()
+    out = t.zeros(17 * 24, dtype=t.uint8, device="cuda")
+    cnt = t.zeros(1, dtype=t.int64, device="cuda")
+    spd.candidates(plan, Y, W, 3.0, 0, out, cnt, ws)
+    stream = t.cuda.current_stream().cuda_stream
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_candidates_status(cnt.data_ptr(), 17, stream)
+    assert e.value.status == 5  # SPD_ERR_BUFFER_TOO_SMALL
+    n = int(cnt.item())
+    assert n > 17 and spd.spd_candidates_status(cnt.data_ptr(), n, stream) == n
+
+
 @pytest.mark.parametrize("name,s_end", [("ig1", 8192), ("bd16", 8192), ("exh", 256), ("ig3", 512)])
 def test_fused_search_equals_execute_then_candidates(name, s_end):
     t = torch()

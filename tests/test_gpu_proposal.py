@@ -1,9 +1,12 @@
 """Proposal path on the GPU: block selection and gather against numpy, the
 restricted search equal to the plain search on the selected blocks, and what a
 network trained on the GPU gains over the plain search on red noise with
-zero-DM spikes (judged by the ideal exhaustive search)."""
+zero-DM spikes, judged by the ideal exhaustive search of the FP64 CPU oracle on
+each pulse's neighbourhood (the GPU's exhaustive judge is checked against it)."""
 import numpy as np
 import pytest
+
+import oracle
 
 import paper_1910_08324_gb300 as spd
 import spd_synth
@@ -108,6 +111,37 @@ def test_search_flagged_equals_plain_search_on_those_blocks(name):
     assert np.array_equal(rec, ref[keep])
 
 
+def oracle_pulse_snr(x, pulses, mu, sigma, plan, width_ratio=4.0):
+    """The ideal search's SNR of each injected pulse, from the FP64 oracle: the
+    exhaustive grid of ``plan`` searched (table noise mu, sigma of the pulse's row)
+    over the pulse's neighbourhood [s0 - w, s0 + w] plus the widest boxcar past
+    it; the largest SNR at a start in [s0 - w, s0 + w] whose best width lies
+    within a factor ``width_ratio`` of w (0 where none), as ``proposal.pulse_snr``.
+    Windows of one length go to the oracle together (its threads split rows)."""
+    w_tab, s_tab = plan.widths()
+    g = oracle.Grid(w_tab, s_tab)
+    lend = int(w_tab[-1])
+    nt = x.shape[1]
+    mu_h, sg_h = mu.cpu().numpy().astype(np.float64), sigma.cpu().numpy().astype(np.float64)
+    rows = pulses["row"].astype(np.int64)
+    s0 = pulses["start"].astype(np.int64)
+    w = pulses["width"].astype(np.int64)
+    a = np.maximum(s0 - w, 0)
+    span = int(2 * w.max() + 1 + lend)
+    a = np.minimum(a, max(nt - span, 0))  # the window stays inside the row (it still covers the pulse)
+    n = min(span, nt)
+    xh = x.float().cpu().numpy()
+    xs = np.stack([xh[r, i:i + n] for r, i in zip(rows, a)]).astype(np.float64)
+    Y, W, _ = oracle.search(xs, g, mu_h[rows], sg_h[rows], noise_mode=1)
+    out = np.zeros(len(pulses))
+    for k in range(len(pulses)):
+        j = np.arange(max(s0[k] - w[k], 0) - a[k], min(s0[k] + w[k] - a[k], n - 1) + 1)
+        cw = w_tab[W[k, j]].astype(np.float64)
+        ok = (cw <= width_ratio * w[k]) & (cw * width_ratio >= w[k])
+        out[k] = max(0.0, float(Y[k, j][ok].max())) if ok.any() else 0.0
+    return out
+
+
 def test_trained_network_gain_on_red_noise_with_spikes():
     """Train the network on the GPU (labels from the plain BoxDIT search), then
     search only the blocks it flags.  Against the plain search of every block,
@@ -162,7 +196,10 @@ def test_trained_network_gain_on_red_noise_with_spikes():
     xev = series(nev, 32, pev)
     plan, mu, sg, ws = tables(grid, xev)
     planx, mux, sgx, _ = tables(gx, xev)
-    sj = P.pulse_snr(xev, pev, mux, sgx, gx)
+    sj_gpu = P.pulse_snr(xev, pev, mux, sgx, gx)
+    sj = oracle_pulse_snr(xev, pev, mux, sgx, planx)
+    # the GPU's exhaustive judge equals the oracle's (parity bar of the search)
+    assert np.all(np.abs(sj_gpu - sj) <= 1e-5 * np.maximum(np.abs(sj), 1.0)), np.abs(sj_gpu - sj).max()
     s_plain = P.score(plain(plan, xev, mu, sg, ws), pev, sj, nev, nt)
     rec, nsearched = P.propose_and_search(params, xev, mu, sg, grid, logit_threshold=0.0)
     s_prop = P.score(rec, pev, sj, nev, nt)

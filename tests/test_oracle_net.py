@@ -54,3 +54,26 @@ def test_adam_step_by_hand():
     # first step: m_hat = g, v_hat = g^2, update = lr * sign(g) (up to eps)
     assert np.allclose(th1, th - 0.1 * np.sign(g), atol=1e-7)
     assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
+
+
+def test_decimate_closed_forms():
+    # a constant row c: every output is (16 c - 16 mu) / (4 sigma) = 4 (c - mu) / sigma
+    x = np.full((2, 16 * 7 + 5), 2.5)
+    d = net.decimate(x, np.array([0.5, 2.5]), np.array([2.0, 1.0]))
+    assert d.shape == (2, 7)
+    assert np.allclose(d[0], 4.0 * (2.5 - 0.5) / 2.0) and np.allclose(d[1], 0.0)
+    # a ramp x[i] = i: block j sums 16 * 16 j + 120 (the trailing 5 samples are dropped)
+    r = np.arange(16 * 7 + 5, dtype=np.float64)[None, :]
+    d = net.decimate(r, 0.0, 1.0)
+    assert np.allclose(d[0], (256.0 * np.arange(7) + 120.0) / 4.0)
+
+
+def test_decimate_whitens_gaussian_noise():
+    # white noise N(mu, sigma^2) becomes unit-variance, zero-mean blocks; the
+    # neighbouring blocks are independent (disjoint sums)
+    rng = np.random.default_rng(7)
+    mu, sigma = 3.0, 0.7
+    x = mu + sigma * rng.normal(size=(1, 16 * 20000))
+    d = net.decimate(x, mu, sigma)[0]
+    assert abs(d.mean()) < 0.03 and abs(d.var() - 1.0) < 0.03
+    assert abs(np.corrcoef(d[:-1], d[1:])[0, 1]) < 0.03

@@ -53,6 +53,36 @@ def test_static_scratch_candidates_equal_workspace_version(name, s_end, thr, rad
         assert np.array_equal(_records(out, n, cap), ref)
 
 
+def test_static_scratch_at_its_maximum():
+    """262,144 candidate tiles, the static maximum: one tile per short row, so the
+    array's group sums and offsets past the first group and the scan's carry
+    across passes of 1,024 groups are all used; records and count equal
+    spd_candidates', on two calls in a row."""
+    t = torch()
+    ndm, nt = 262144, 64
+    x = spd_synth.gaussian_noise(ndm, nt, 2718, dtype=np.float32)
+    plan = spd.spd_plan_create(ndm=ndm, nt=nt, **ALGOS["ig1"](8))
+    _, _, (Y, W, ws, *_) = run_gpu(plan, x, 0.0, 1.0, return_ws=True)
+    cap = 1 << 21
+    stream = t.cuda.current_stream().cuda_stream
+    ref_out = t.zeros(cap * 24, dtype=t.uint8, device="cuda")
+    ref_cnt = t.zeros(1, dtype=t.int64, device="cuda")
+    spd.candidates(plan, Y, W, 2.5, 1, ref_out, ref_cnt, ws)
+    t.cuda.synchronize()
+    n_ref = int(ref_cnt.item())
+    assert 10000 < n_ref <= cap
+    ref = _records(ref_out, n_ref, cap)
+    assert ref["row"].max() > 250000  # records from the last groups of tiles
+    for _ in range(2):
+        out = t.zeros(cap * 24, dtype=t.uint8, device="cuda")
+        cnt = t.full((1,), -1, dtype=t.int64, device="cuda")
+        spd.spd_candidates_static(plan, Y.data_ptr(), W.data_ptr(), 2.5, 1, out.data_ptr(), cap,
+                                  cnt.data_ptr(), stream)
+        spd.spd_sync_status(plan, stream)
+        assert int(cnt.item()) == n_ref
+        assert np.array_equal(_records(out, n_ref, cap), ref)
+
+
 def test_static_scratch_rejects_plans_beyond_its_size():
     # 262,144 candidate tiles of 16,384 starts is the static maximum
     plan = spd.spd_plan_create(ndm=262145, nt=16, **ALGOS["ig1"](8))
