@@ -81,7 +81,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ska_mid", choices=["ska_mid", "exhaustive_small", "batched", "proposal", "noise_stats"],
+    ap.add_argument("--workload", default="ska_mid",
+                    choices=["ska_mid", "exhaustive_small", "batched", "proposal", "noise_stats", "host_link"],
                     help="ska_mid: 4096 x 1M lossy search (default); exhaustive_small: 64 x 65536, widths 1..256")
     ap.add_argument("--algo", default="ig1", choices=sorted(ALGOS))
     ap.add_argument("--ndm", type=int, default=spd_synth.SKA_MID["ndm"])
@@ -525,6 +526,48 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
     return 0
 
 
+def run_host_link(args, torch, rank, dev):
+    """The host link that bounds the end-to-end figures: plain torch copies of the
+    workload's input bytes (ndm x nt f32) between pinned host memory and the device,
+    each copy timed alone (synchronised wall time), with no library kernel in the
+    process.  Prints the GB/s of every copy."""
+    if rank != 0:
+        return 0
+    n = args.ndm * args.nt
+    x = torch.empty(n, dtype=torch.float32, device=dev)
+    h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    h.fill_(1.0)
+    q = n // 4
+
+    def rates(dst, src, reps):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            out.append(round(src.numel() * src.element_size() / (time.perf_counter() - t0) / 1e9, 1))
+        return out
+
+    side = torch.cuda.Stream(dev)
+    chunked = []
+    for _ in range(6):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(side):
+            for c in range(4):
+                x[c * q:(c + 1) * q].copy_(h[c * q:(c + 1) * q], non_blocking=True)
+        torch.cuda.synchronize(dev)
+        chunked.append(round(4 * n / (time.perf_counter() - t0) / 1e9, 1))
+    res = {"h2d_whole": rates(x, h, 6), "h2d_first_quarter": rates(x[:q], h[:q], 6),
+           "h2d_last_quarter": rates(x[3 * q:], h[3 * q:], 6), "h2d_4_chunks_side_stream": chunked,
+           "d2h_whole": rates(h, x, 3), "h2d_whole_after_d2h": rates(x, h, 6)}
+    line = {"metric": "host link GB/s per copy", "unit": "GB/s", "bytes": 4 * n, "workload": "host_link",
+            "higher_is_better": True, "copies": res, "host_cores": os.cpu_count() or 1, "cpu_model": cpu_model()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_noise_stats(args, torch, dist, spd, rank, world, local, dev):
     """Noise statistics (Sec. 4.5) of the search's input: one step = one
     ``spd_noise_stats`` call of one pass (every decimation level of every row,
@@ -939,6 +982,8 @@ def main():
         return run_proposal(args, torch, dist, spd, rank, world, local, dev)
     if args.workload == "noise_stats":
         return run_noise_stats(args, torch, dist, spd, rank, world, local, dev)
+    if args.workload == "host_link":
+        return run_host_link(args, torch, rank, dev)
     ndm, nt = args.ndm, args.nt
     kw = dict(ALGOS[args.algo])
     dt_code, esize = DTYPES[args.dtype]

@@ -20,10 +20,20 @@
 // input is the previous layer's output in shared memory, so the warp-level MMA
 // keeps a block's three layers inside one CTA without TMEM round trips.
 //
-// Gradients: the max pool passes one position per channel, so the backward
-// pass is a few dense FP32 loops per block in shared memory (straight-through
-// for the bf16 roundings); each CTA accumulates its blocks' gradients in shared
-// memory and adds them to the global sum once.
+// Gradients (straight-through for the bf16 roundings; the max pool passes its
+// gradient to one position per channel): the layer-3 terms touch only the 16
+// pooled positions and stay FP32 loops; the three dense contractions run on the
+// tensor cores as the same bf16 mma.sync implicit GEMMs with FP32 accumulate:
+//   dW2[co][ci][k] = sum_p dh2[p][co] a1[p + k - 4][ci]     (M = co, N = ci, K = p per tap)
+//   da1[p][ci]     = sum_{k, co} W2[8 - k][co][ci] dh2[p + k - 4][co]   (the forward's
+//                    convolution with the taps flipped and the channels swapped)
+//   dW1[c][k], db1[c] = sum_p dh1[p][c] (bf16(x[p + k - 4]), 1)   (M = c, N = 9 taps and a ones column)
+// The activations and weights are bf16 values already; the upstream gradient dh
+// is split into two bf16 terms, hi = bf16(dh) and lo = bf16(dh - hi), each
+// multiplied on the tensor cores, so a product keeps ~16 significant bits.
+// Each CTA accumulates its blocks' gradients in shared memory (every entry
+// written by one thread or one warp, in a fixed order) and adds them to the
+// global sum once.
 #include <cuda_bf16.h>
 
 #include "spd_common.cuh"
@@ -59,9 +69,12 @@ struct NetSmem {
 
 struct GradSmem {  // training only
   float G[kNetParams];
-  float dh2[NP][NC];
-  float dh1[NP][NC];
+  // upstream gradient of a layer's output as two bf16 terms (hi, lo), rows
+  // p + PAD (zero padding rows) like the activations: dh2, then dh1
+  alignas(16) __nv_bfloat16 dh[2][NPP][NC];
+  alignas(16) __nv_bfloat16 w2t[NK][NC][NC];  // [8 - tap][ci][co, swizzled by ci]: W2 for da1
   float dh3[NC];
+  float db2[kNetThreads / 32][NC];  // per-warp partial sums of the layer-2 bias gradient
 };
 
 __device__ __forceinline__ float bf(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -103,6 +116,14 @@ __device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const __nv_bfloat16* p) 
                : "r"(a));
 }
 
+// As ldsm4, transposed: thread (g, q) receives rows 2q and 2q + 1 of column g.
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const __nv_bfloat16* p) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -114,16 +135,20 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 
 // One tensor-core layer: out[p][co] = sum_{k, ci} w[k][co][ci] in[p + k - 4][ci]
 // for the warp's 4 tiles of 16 positions and both tiles of 8 channels.
+// ZERO: start from 0 (else add to acc).
+template <bool ZERO = true>
 __device__ __forceinline__ void conv_mma(const __nv_bfloat16 (*in)[NC], const __nv_bfloat16 (*w)[NC][NC],
                                          float (&acc)[4][2][4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lr = lane & 7, lm = lane >> 3;  // row within, and index of, the 8x8 matrix this lane addresses
+  if constexpr (ZERO) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+      for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+        for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  }
 #pragma unroll
   for (int k = 0; k < NK; ++k) {
     // B of both channel tiles: matrices (tile 0, in 0-7), (tile 0, in 8-15), (tile 1, ...), (tile 1, ...)
@@ -299,9 +324,39 @@ __global__ void __launch_bounds__(kNetThreads, 7) net_forward_kernel(const float
   }
 }
 
+// Split v into two bf16 terms: hi = bf16(v), lo = bf16(v - hi).
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// C[m][n] += sum over the 256 positions p of A[p][m] B[p + boff][n] for the
+// 16 x 16 block (m, n), where A rows are those of dh (split h: rows p + PAD) and
+// B rows those of `bmat` (rows p + boff); both operands are read transposed
+// (ldmatrix .trans), so that M and N index channels and K positions.  One warp;
+// c[nt][e]: the m16n8 fragment of n-tile nt.
+__device__ __forceinline__ void gemm_pos(const __nv_bfloat16 (*dh)[NPP][NC], const __nv_bfloat16 (*bmat)[NC],
+                                         int boff, float (&c)[2][4]) {
+  const int lane = threadIdx.x & 31, lr = lane & 7, lm = lane >> 3;
+#pragma unroll 4
+  for (int st = 0; st < NP / 16; ++st) {
+    uint32_t bb[4];
+    const int brow = 16 * st + boff + 8 * (lm & 1) + lr;  // matrices: (p 0-7, n 0-7), (p 8-15, n 0-7), (p 0-7, n 8-15), ...
+    ldsm4t(bb, &bmat[brow][swz(brow, 8 * (lm >> 1))]);
+    const int arow = 16 * st + PAD + 8 * (lm >> 1) + lr;  // matrices: (p 0-7, m 0-7), (p 0-7, m 8-15), (p 8-15, m 0-7), ...
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t aa[4];
+      ldsm4t(aa, &dh[h][arow][swz(arow, 8 * (lm & 1))]);
+      mma_bf16(c[0], aa[0], aa[1], aa[2], aa[3], bb[0], bb[1]);
+      mma_bf16(c[1], aa[0], aa[1], aa[2], aa[3], bb[2], bb[3]);
+    }
+  }
+}
+
 // Forward + backward of the CTA's blocks; gradients summed into G (global) and
-// the summed loss into *loss.
-__global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* __restrict__ P,
+// the summed loss into *loss (or, ordered, into this CTA's row of partials).
+__global__ void __launch_bounds__(kNetThreads, 3) net_grad_kernel(const float* __restrict__ P,
                                                                 const float* __restrict__ X,
                                                                 const float* __restrict__ Y, int64_t nb,
                                                                 float* __restrict__ Gout, float* __restrict__ loss,
@@ -309,9 +364,17 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* _
   extern __shared__ __align__(16) unsigned char raw[];
   NetSmem& s = *reinterpret_cast<NetSmem*>(raw);
   GradSmem& q = *reinterpret_cast<GradSmem*>(raw + ((sizeof(NetSmem) + 15) / 16) * 16);
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, gq = lane >> 2, tq = lane & 3;
   load_weights(P, s);
   for (int i = t; i < kNetParams; i += kNetThreads) q.G[i] = 0.f;
+  for (int i = t; i < NK * NC * NC; i += kNetThreads) {  // w2t[8 - k][ci][co] = W2[co][ci][k]
+    const int co = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
+    q.w2t[NK - 1 - k][ci][swz(ci, co)] = __float2bfloat16_rn(P[oW2 + i]);
+  }
+  for (int i = t; i < 2 * 2 * PAD * NC; i += kNetThreads) {  // zero padding rows of dh
+    const int h = i / (2 * PAD * NC), r = (i / NC) % (2 * PAD), c = i % NC;
+    q.dh[h][r < PAD ? r : NP + r][c] = __float2bfloat16_rn(0.f);
+  }
   float lsum = 0.f;
   for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
     __syncthreads();
@@ -329,59 +392,100 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_grad_kernel(const float* _
       q.dh3[t] = s.g[t] > 0.f ? dz * s.w4[t] : 0.f;
     }
     __syncthreads();
-    // layer 3: weights and bias from the pooled positions; d(a2) gathered
+    // layer 3: weights and bias from the pooled positions
     for (int i = t; i < NC * NC * NK; i += kNetThreads) {
       const int c = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
       q.G[oW3 + i] += q.dh3[c] * bf(s.a2[s.arg[c] + k][swz(s.arg[c] + k, ci)]);
     }
     if (t < NC) q.G[ob3 + t] += q.dh3[t];
-    for (int i = t; i < NP * NC; i += kNetThreads) {
-      const int p = i >> 4, ci = i & 15;
-      float d = 0.f;
+    // dh2 = (a2 > 0) (W3^T dh3 at the taps of the pooled positions), split into two
+    // bf16 terms; this thread's channel is t % 16 (its bias-gradient partial sum)
+    {
+      float db = 0.f;
+      for (int i = t; i < NP * NC; i += kNetThreads) {
+        const int p = i >> 4, ci = i & 15;
+        float d = 0.f;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int k = p - s.arg[c] + PAD;  // a2[p] feeds h3[c][arg] through tap k
-        if (k >= 0 && k < NK) d = fmaf(bf(s.w3[k][c][swz(c, ci)]), q.dh3[c], d);
+        for (int c = 0; c < NC; ++c) {
+          const int k = p - s.arg[c] + PAD;  // a2[p] feeds h3[c][arg] through tap k
+          if (k >= 0 && k < NK) d = fmaf(bf(s.w3[k][c][swz(c, ci)]), q.dh3[c], d);
+        }
+        d = bf(s.a2[p + PAD][swz(p + PAD, ci)]) > 0.f ? d : 0.f;
+        db += d;
+        __nv_bfloat16 hi, lo;
+        split_bf16(d, hi, lo);
+        q.dh[0][p + PAD][swz(p + PAD, ci)] = hi;
+        q.dh[1][p + PAD][swz(p + PAD, ci)] = lo;
       }
-      q.dh2[p][ci] = bf(s.a2[p + PAD][swz(p + PAD, ci)]) > 0.f ? d : 0.f;
+      db += __shfl_xor_sync(kFull, db, 16);  // the two threads of the warp with this channel
+      if (lane < NC) q.db2[warp][lane] = db;
     }
     __syncthreads();
-    // layer 2
-    for (int i = t; i < NC * NC * NK; i += kNetThreads) {
-      const int co = i / (NC * NK), ci = (i / NK) % NC, k = i % NK;
-      float acc = 0.f;
-      for (int p = 0; p < NP; ++p) acc = fmaf(q.dh2[p][co], bf(s.a1[p + k][swz(p + k, ci)]), acc);
-      q.G[oW2 + i] += acc;
-    }
-    if (t < NC) {
-      float acc = 0.f;
-      for (int p = 0; p < NP; ++p) acc += q.dh2[p][t];
-      q.G[ob2 + t] += acc;
-    }
-    for (int i = t; i < NP * NC; i += kNetThreads) {
-      const int p = i >> 4, ci = i & 15;
-      float d = 0.f;
-      for (int k = 0; k < NK; ++k) {
-        const int pp = p - k + PAD;  // output position fed by a1[p] through tap k
-        if (pp >= 0 && pp < NP)
+    if (t < NC) q.G[ob2 + t] += (q.db2[0][t] + q.db2[1][t]) + (q.db2[2][t] + q.db2[3][t]);
+    // layer 2 on the tensor cores: dW2 (taps warp, warp + 4, warp + 8 of this warp)
+    // and da1 (this warp's 64 positions)
+    {
+#pragma unroll 1
+      for (int k = warp; k < NK; k += kNetThreads / 32) {
+        float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        gemm_pos(q.dh, s.a1, k, c);  // a1[p + k - 4] sits in row p + k
 #pragma unroll
-          for (int co = 0; co < NC; ++co) d = fmaf(bf(s.w2[k][co][swz(co, ci)]), q.dh2[pp][co], d);
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int co = gq + 8 * (e >> 1), ci = 8 * nt + 2 * tq + (e & 1);
+            q.G[oW2 + (co * NC + ci) * NK + k] += c[nt][e];
+          }
       }
-      q.dh1[p][ci] = bf(s.a1[p + PAD][swz(p + PAD, ci)]) > 0.f ? d : 0.f;
     }
-    __syncthreads();
-    // layer 1
-    for (int i = t; i < NC * NK + NC; i += kNetThreads) {
-      float acc = 0.f;
-      if (i < NC * NK) {
-        const int c = i / NK, k = i % NK;
-        for (int p = 0; p < NP; ++p) acc = fmaf(q.dh1[p][c], bf(__float2bfloat16_rn(s.x[p + k])), acc);
-        q.G[oW1 + i] += acc;
-      } else {
-        const int c = i - NC * NK;
-        for (int p = 0; p < NP; ++p) acc += q.dh1[p][c];
-        q.G[ob1 + c] += acc;
+    float acc[4][2][4];
+    conv_mma<true>(q.dh[0], q.w2t, acc);
+    conv_mma<false>(q.dh[1], q.w2t, acc);
+    // the layer-1 im2col (bf16 input taps 0..8, a ones column 9 for the bias) in the
+    // rows of a2, which the backward no longer reads
+    for (int r = t; r < NP; r += kNetThreads) {
+      uint32_t v[8];
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const float x0 = 2 * h < NK ? s.x[r + 2 * h] : (2 * h == NK ? 1.f : 0.f);
+        const float x1 = 2 * h + 1 < NK ? s.x[r + 2 * h + 1] : (2 * h + 1 == NK ? 1.f : 0.f);
+        const __nv_bfloat162 pr = __floats2bfloat162_rn(x0, x1);
+        v[h] = *reinterpret_cast<const uint32_t*>(&pr);
       }
+      const int row = r + PAD, sw = (row >> 2) & 1;
+      uint4* dst = reinterpret_cast<uint4*>(&s.a2[row][0]);
+      dst[sw] = make_uint4(v[0], v[1], v[2], v[3]);
+      dst[sw ^ 1] = make_uint4(v[4], v[5], v[6], v[7]);
+    }
+    __syncthreads();  // every warp is done with dh2: it becomes dh1
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int p = 64 * warp + 16 * i + gq + 8 * (e >> 1), ci = 8 * j + 2 * tq + (e & 1);
+          const float d = bf(s.a1[p + PAD][swz(p + PAD, ci)]) > 0.f ? acc[i][j][e] : 0.f;
+          __nv_bfloat16 hi, lo;
+          split_bf16(d, hi, lo);
+          q.dh[0][p + PAD][swz(p + PAD, ci)] = hi;
+          q.dh[1][p + PAD][swz(p + PAD, ci)] = lo;
+        }
+    __syncthreads();
+    // layer 1 on the tensor cores (one warp): dW1 (columns 0..8) and db1 (column 9)
+    if (warp == 0) {
+      float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      gemm_pos(q.dh, s.a2, PAD, c);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int co = gq + 8 * (e >> 1), n = 8 * nt + 2 * tq + (e & 1);
+          if (n < NK)
+            q.G[oW1 + co * NK + n] += c[nt][e];
+          else if (n == NK)
+            q.G[ob1 + co] += c[nt][e];
+        }
     }
   }
   __syncthreads();
