@@ -97,8 +97,9 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=96)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="oracle time the cpu_baseline sample accumulates")
-    ap.add_argument("--train-rows", type=int, default=1024, help="proposal: rows of 1M samples to train on")
-    ap.add_argument("--train-steps", type=int, default=6000, help="proposal: Adam steps of 512 blocks")
+    ap.add_argument("--train-rows", type=int, default=3907,
+                    help="proposal: rows of 1M samples to train on (3907 rows = 10^6 blocks of 4096 samples)")
+    ap.add_argument("--train-steps", type=int, default=8000, help="proposal: Adam steps of 512 blocks")
     ap.add_argument("--logit-threshold", type=float, default=0.0, help="proposal: blocks above it are searched")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -399,8 +400,8 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
     with torch.cuda.stream(stream):
         step(stream)  # first launches outside any capture
         key = autotune.key_of(a, BATCH_S_END, dt_code, shapes, boxdit_lmax=kw.get("boxdit_lmax", 0))
-        seg, timings = autotune.tune_segment(key, b.set_segment, lambda: time_ms(search), cache_path=TUNE_CACHE,
-                                             reps=2, force=True)
+        (seg, ctas), timings = autotune.tune_launch(key, b.set_segment, b.set_ctas_per_sm, lambda: time_ms(search),
+                                                    ctas=(0, 1, 2), cache_path=TUNE_CACHE, reps=2, force=True)
         step(stream)
     stream.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -515,7 +516,10 @@ def run_batched(args, torch, dist, spd, rank, world, local, dev):
                                    "graph-captured persistent launch" % ("/".join(str(n) for n, _ in BATCH_RANGES),
                                                                          BATCH_BASE),
                        "algo": algo, "input_dtype": args.dtype, "s_end": BATCH_S_END, "samples": samples,
-                       "candidates_per_sample": cand_per_sample, "segment": seg,
+                       "candidates_per_sample": cand_per_sample,
+                       "tuned": {"segment": seg, "ctas_per_sm": ctas if ctas else "as many as fit",
+                                 "threads_per_cta": 256, "starts_per_thread": 8,
+                                 "fixed": "threads and starts per thread: the level layout of a 2048-sample chunk"},
                        "autotune_ms": timings, "candidates_found": n_cand,
                        "parallelism": "dp%d (ranges per GPU)" % world,
                        "l2": "inputs larger than L2 (%.1f GB per GPU); no flush" % (esize * samples / 1e9)},
@@ -731,7 +735,9 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
         spd.noise_stats(plan, x, mu, sg, ws)
         return plan, mu, sg, ws
 
-    cap = 1 << 25
+    # the labels' plain search of 10^6 training blocks of red noise with spikes
+    # finds ~8e7 candidates above SNR 6: room for 1.3e8 records (3.2 GB)
+    cap = 1 << 27
     out = torch.empty(cap * 24, dtype=torch.uint8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
 

@@ -390,6 +390,10 @@ spd_status spd_batch_destroy(spd_batch *batch);
 spd_status spd_batch_set_segment(spd_batch *batch, int32_t segment);
 /* Limit of one ready-flag wait, in nanoseconds (0..60 s). */
 spd_status spd_batch_set_wait_ns(spd_batch *batch, int64_t wait_ns);
+/* CTAs per SM of the persistent launch (0..64; 0, the default: as many as fit,
+ * and never more than fit).  A launch-shape parameter for the autotuner; the
+ * results do not depend on it. */
+spd_status spd_batch_set_ctas_per_sm(spd_batch *batch, int32_t ctas_per_sm);
 /* Device workspace of spd_batch_execute / spd_batch_candidates (256-byte aligned base). */
 spd_status spd_batch_workspace_size(const spd_batch *batch, size_t *bytes);
 /* Searches every range (io: host array of the batch's n_ranges entries), with

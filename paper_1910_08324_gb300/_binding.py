@@ -57,7 +57,7 @@ _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_des
             "spd_plan_widths", "spd_workspace_size", "spd_execute", "spd_candidates",
             "spd_search", "spd_sync_status", "spd_candidates_static", "spd_noise_stats",
             "spd_plan_set_segment", "spd_batch_create", "spd_batch_destroy", "spd_batch_set_segment",
-            "spd_batch_set_wait_ns", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
+            "spd_batch_set_wait_ns", "spd_batch_set_ctas_per_sm", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
             "spd_batch_candidates", "spd_net_decimate", "spd_net_forward", "spd_net_gradient",
             "spd_net_adam", "spd_net_select", "spd_net_gather", "spd_plan_set_starts", "spd_plan_create_grid",
             "spd_net_gradient_ordered", "spd_candidates_status"]
@@ -110,6 +110,7 @@ def load_library():
         lib.spd_batch_destroy.argtypes = [vp]
         lib.spd_batch_set_segment.argtypes = [vp, i32]
         lib.spd_batch_set_wait_ns.argtypes = [vp, i64]
+        lib.spd_batch_set_ctas_per_sm.argtypes = [vp, i32]
         lib.spd_batch_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
         lib.spd_batch_execute.argtypes = [vp, ctypes.POINTER(_RangeIO), vp, sz, vp]
         lib.spd_batch_status.argtypes = [vp, vp, vp]
@@ -297,6 +298,10 @@ class Batch:
     def set_segment(self, segment: int):
         _check(load_library().spd_batch_set_segment(ctypes.c_void_p(self.handle), int(segment)),
                "spd_batch_set_segment")
+
+    def set_ctas_per_sm(self, n: int):
+        _check(load_library().spd_batch_set_ctas_per_sm(ctypes.c_void_p(self.handle), int(n)),
+               "spd_batch_set_ctas_per_sm")
 
     def set_wait_ns(self, ns: int):
         _check(load_library().spd_batch_set_wait_ns(ctypes.c_void_p(self.handle), int(ns)),

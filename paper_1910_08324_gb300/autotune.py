@@ -1,12 +1,18 @@
-"""Segment-length autotuner for the streaming searches (plans and batches).
+"""Launch-shape autotuner for the streaming searches (plans and batches).
 
 A CTA of the BoxDIT/IGRID kernels searches one segment of a row; the segment
 length trades the re-read of the widest boxcar after each segment (shorter
 segments re-read more) against the number of CTAs (longer segments give fewer,
-and a ragged last wave).  ``tune_segment`` times each candidate length with a
-caller-supplied timing function, keeps the fastest, and caches the choice in a
-JSON file keyed by the search's description (grid, dtype, range shapes), so a
-later run with the same key reuses it without timing.
+and a ragged last wave).  A batched search also sets how many persistent CTAs
+share an SM (fewer leave each CTA more of the SM's issue slots and caches,
+more hide more latency).  ``tune_segment`` times each candidate segment length,
+``tune_launch`` each (segment, CTAs per SM) pair, with a caller-supplied timing
+function; the fastest is kept and cached in a JSON file keyed by the search's
+description (grid, dtype, range shapes), so a later run with the same key
+reuses it without timing.  A CTA's thread count (256) and starts per thread (8)
+are not tuned: one CTA step covers a 2 048-sample chunk, 8 starts per thread,
+and the kernels' level layout (which thread owns which coarse position, which
+warp builds levels 9 to 11) is built on that chunk.
 """
 from __future__ import annotations
 
@@ -74,3 +80,45 @@ def tune_segment(key: str, set_segment, time_ms, candidates=DEFAULT_CANDIDATES, 
         cache[key] = {"segment": int(best), "timings": timings}
         save_cache(cache_path, cache)
     return int(best), timings
+
+
+DEFAULT_CTAS = (0, 1, 2, 3)  # 0: as many as fit
+
+
+def tune_launch(key: str, set_segment, set_ctas, time_ms, segments=DEFAULT_CANDIDATES, ctas=DEFAULT_CTAS,
+                cache_path=None, reps: int = 3, force: bool = False):
+    """Returns ``((segment, ctas_per_sm), timings)``: every pair of a segment
+    length and a CTAs-per-SM setting is applied (set_segment / set_ctas; pairs
+    either call rejects are skipped) and timed with time_ms() (minimum over
+    ``reps``); the fastest is applied and, with a cache path, stored under
+    ``key`` (a cached choice is applied without timing unless ``force``).
+    Timings are keyed "segment/ctas"."""
+    cache = load_cache(cache_path) if cache_path else {}
+    if not force and key in cache and "ctas_per_sm" in cache[key]:
+        seg, c = int(cache[key]["segment"]), int(cache[key]["ctas_per_sm"])
+        set_segment(seg)
+        set_ctas(c)
+        return (seg, c), cache[key].get("timings", {})
+    timings = {}
+    for seg in segments:
+        try:
+            set_segment(int(seg))
+        except Exception:
+            continue
+        for c in ctas:
+            try:
+                set_ctas(int(c))
+            except Exception:
+                continue
+            timings["%d/%d" % (int(seg), int(c))] = min(float(time_ms()) for _ in range(max(1, reps)))
+    if not timings:
+        raise RuntimeError("no launch shape could be applied")
+    best = min(timings, key=lambda k: timings[k])
+    seg, c = (int(v) for v in best.split("/"))
+    set_segment(seg)
+    set_ctas(c)
+    if cache_path:
+        cache = load_cache(cache_path)
+        cache[key] = {"segment": seg, "ctas_per_sm": c, "timings": timings}
+        save_cache(cache_path, cache)
+    return (seg, c), timings

@@ -286,6 +286,7 @@ struct spd_batch {
   int64_t ndm[spd::kMaxRanges], nt[spd::kMaxRanges], ld[spd::kMaxRanges];
   int32_t segment;
   int64_t wait_ns;
+  int32_t ctas_per_sm = 0;  // persistent CTAs per SM of spd_batch_execute (0: as many as fit)
 };
 
 namespace {
@@ -700,6 +701,12 @@ spd_status spd_batch_set_wait_ns(spd_batch* batch, int64_t wait_ns) {
   return SPD_OK;
 }
 
+spd_status spd_batch_set_ctas_per_sm(spd_batch* batch, int32_t ctas_per_sm) {
+  if (!batch || ctas_per_sm < 0 || ctas_per_sm > 64) return SPD_ERR_INVALID_ARG;
+  batch->ctas_per_sm = ctas_per_sm;
+  return SPD_OK;
+}
+
 spd_status spd_batch_workspace_size(const spd_batch* batch, size_t* bytes) {
   if (!batch || !bytes) return SPD_ERR_INVALID_ARG;
   *bytes = BatchLayout(*batch).total;
@@ -728,6 +735,7 @@ spd_status spd_batch_execute(const spd_batch* batch, const spd_range_io* io, voi
   p.table = 0;
   p.n_ranges = batch->n;
   p.wait_ns = batch->wait_ns;
+  p.ctas_per_sm = batch->ctas_per_sm;
   char* ws = static_cast<char*>(d_ws);
   p.status = reinterpret_cast<int32_t*>(ws + bl.status);
   int64_t units = 0;

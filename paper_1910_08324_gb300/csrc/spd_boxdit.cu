@@ -503,6 +503,7 @@ cudaError_t launch_persistent(KernelT kern, size_t smem, int64_t units, const Se
   int per_sm = 0, sms = 0;
   const cudaError_t e = persistent_config(reinterpret_cast<const void*>(kern), smem, &per_sm, &sms);
   if (e != cudaSuccess) return e;
+  if (p.ctas_per_sm > 0 && per_sm > p.ctas_per_sm) per_sm = p.ctas_per_sm;
   int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   if (grid > units) grid = units;
   kern<<<(unsigned)grid, kThreads, smem, s>>>(p);

@@ -720,6 +720,62 @@ __device__ __forceinline__ void eval_bd_enc(const float* w, const float* base, i
   }
 }
 
+// Coded evaluation of one level of an arbitrary block-count set at NP
+// consecutive positions, for sets whose largest count MMAX is too large for
+// eval_window_enc's pair sums: S_m = w[r] + ... + w[r + m - 1] added in block
+// order, and at every count m of the set the SNR S_m * scale(m) coded with its
+// rank in the set (code 31 - rank, B = 5: at most 32 counts), kept as a running
+// maximum; out[r] is that coded maximum (PARTIAL: ranks >= n_used, except rank
+// 0, count as -inf).  Two positions share each scale instruction (packed f32x2).
+template <int NP, int MMAX, class Pred, bool PARTIAL, class Scale>
+__device__ __forceinline__ void eval_set_enc(const float* w, int n_used, Scale&& scale, float (&out)[NP]) {
+  static_assert(count_in<Pred, MMAX>() <= 32, "5-bit codes");
+  auto code = [&](float x, auto M) {
+    constexpr int rk = Pred::rank(decltype(M)::value);
+    const float c = enc_w<5>(x, 31 - rk);
+    if constexpr (PARTIAL && rk > 0)
+      return rk < n_used ? c : ninf();
+    else
+      return c;
+  };
+  if constexpr (NP % 2 == 0) {
+    static_for<0, NP / 2>([&](auto R2) {
+      constexpr int r = 2 * decltype(R2)::value;
+      float2 S = make_float2(w[r], w[r + 1]);
+      float a0 = ninf(), a1 = ninf();
+      static_for<1, MMAX + 1>([&](auto M) {
+        constexpr int m = decltype(M)::value;
+        if constexpr (m > 1) {
+          if constexpr (((r + m - 1) & 1) == 0) {
+            S = __fadd2_rn(S, make_float2(w[r + m - 1], w[r + m]));
+          } else {
+            S.x += w[r + m - 1];
+            S.y += w[r + m];
+          }
+        }
+        if constexpr (Pred::in(m)) {
+          const float2 x = snr_of2(S, scale(M));
+          a0 = fmaxf(a0, code(x.x, M));
+          a1 = fmaxf(a1, code(x.y, M));
+        }
+      });
+      out[r] = a0;
+      out[r + 1] = a1;
+    });
+  } else {
+    static_for<0, NP>([&](auto R) {
+      constexpr int r = decltype(R)::value;
+      float S = w[r], a = ninf();
+      static_for<1, MMAX + 1>([&](auto M) {
+        constexpr int m = decltype(M)::value;
+        if constexpr (m > 1) S += w[r + m - 1];
+        if constexpr (Pred::in(m)) a = fmaxf(a, code(snr_of(S, scale(M)), M));
+      });
+      out[r] = a;
+    });
+  }
+}
+
 // Like eval_window_mx for one position, but only ranks below n_used count
 // (the last level of a grid); the others are set to -inf without branching.
 template <int MMAX, class Pred, class Scale>

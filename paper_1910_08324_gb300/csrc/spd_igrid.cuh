@@ -452,11 +452,10 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
         for (int r = 0; r < 4; ++r)
           atomicMax(KB + ((qq + r) << (qj - 4)), out[r] == out[r] ? fkey(out[r]) : INT_MIN);
       } else {
-        float bv[4], full[4];
-        int bq[4];
-        eval_window<4, MMAX, SM, true, false>(win, nu, scl(AB + first, SM{}), nullptr, bv, bq, full);
+        float o[4];
+        eval_set_enc<4, MMAX, SM, true>(win, nu, scl(AB + first, SM{}), o);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) put(qj, qq + r, bv[r] * f, first + bq[r]);
+        for (int r = 0; r < 4; ++r) put(qj, qq + r, o[r] == o[r] ? dec_v<5>(o[r]) * f : ninf(), first + dec_w<5>(o[r]));
       }
     }
     if (sj) {
@@ -556,53 +555,59 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
         y[r] = dec_v<S::EB>(y[r]);
       }
     } else {
+      // more than 32 widths: every level's maximum is coded with its rank within
+      // the level (eval_set_enc), decoded once per position and merged with the
+      // levels below by a strict '>' (the smaller width wins a tie)
+      auto merge_coded = [&](float& yv, int& wv, float c, int first) {
+        merge1(yv, wv, dec_v<5>(c), first + dec_w<5>(c));
+      };
       {
-        float win[S::NW0 * 4];
+        float win[S::NW0 * 4], o[8];
         load_window4_ab<S::NW0>(smem + FX::f0(buf) + 4 * t, FX::OB, win);
         const auto sc0 = scl(AB, S0{});
-        if (!COARSE && top == 0) {
-          float full[8];
-          eval_window<8, MMAX, S0, true, false>(win, p.n_top, sc0, nullptr, y, w, full);
-        } else {
-          eval_window_mx<8, MMAX, S0>(win, sc0, y, w);
+        if (!COARSE && top == 0)
+          eval_set_enc<8, MMAX, S0, true>(win, p.n_top, sc0, o);
+        else
+          eval_set_enc<8, MMAX, S0, false>(win, p.n_top, sc0, o);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {  // level 0 starts at width index 0
+          y[r] = dec_v<5>(o[r]);
+          w[r] = dec_w<5>(o[r]);
         }
       }
       if (COARSE || top >= 1) {
-        float win[S::NW1 * 4], bv[4], full[4];
-        int bq[4];
+        float win[S::NW1 * 4], o[4];
         load_window4<S::NW1>(smem + FX::f1(buf) + 4 * t, win);
         const auto scj = scl_fine(std::integral_constant<int, 1>{}, SM{});
         if (!COARSE && top == 1)
-          eval_window<4, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+          eval_set_enc<4, MMAX, SM, true>(win, p.n_top, scj, o);
         else
-          eval_window<4, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+          eval_set_enc<4, MMAX, SM, false>(win, p.n_top, scj, o);
         const int first = p.lvl_first[1];
-  #pragma unroll
-        for (int r = 0; r < 4; ++r) merge1(y[2 * r], w[2 * r], bv[r], first + bq[r]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) merge_coded(y[2 * r], w[2 * r], o[r], first);
       }
       if (COARSE || top >= 2) {
-        float win[S::NW2 * 2], bv[2], full[2];
-        int bq[2];
+        float win[S::NW2 * 2], o[2];
         load_window2<S::NW2>(smem + FX::f2(buf) + 2 * t, win);
         const auto scj = scl_fine(std::integral_constant<int, 2>{}, SM{});
         if (!COARSE && top == 2)
-          eval_window<2, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+          eval_set_enc<2, MMAX, SM, true>(win, p.n_top, scj, o);
         else
-          eval_window<2, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+          eval_set_enc<2, MMAX, SM, false>(win, p.n_top, scj, o);
         const int first = p.lvl_first[2];
-        merge1(y[0], w[0], bv[0], first + bq[0]);
-        merge1(y[4], w[4], bv[1], first + bq[1]);
+        merge_coded(y[0], w[0], o[0], first);
+        merge_coded(y[4], w[4], o[1], first);
       }
       if (COARSE || top >= 3) {
-        float win[S::NW3], bv[1], full[1];
-        int bq[1];
+        float win[S::NW3], o[1];
         load_window1<S::NW3>(smem + FX::f3(buf) + t, win);
         const auto scj = scl_fine(std::integral_constant<int, 3>{}, SM{});
         if (!COARSE && top == 3)
-          eval_window<1, MMAX, SM, true, false>(win, p.n_top, scj, nullptr, bv, bq, full);
+          eval_set_enc<1, MMAX, SM, true>(win, p.n_top, scj, o);
         else
-          eval_window<1, MMAX, SM, false, false>(win, p.n_top, scj, nullptr, bv, bq, full);
-        merge1(y[0], w[0], bv[0], p.lvl_first[3] + bq[0]);
+          eval_set_enc<1, MMAX, SM, false>(win, p.n_top, scj, o);
+        merge_coded(y[0], w[0], o[0], p.lvl_first[3]);
       }
       if (COARSE) {  // best coarse level at start 8t (even t: 8t = 0 mod 16), without branching
         int* kp = BCM + (k & 1) * kBcm + (t >> 1);
@@ -687,6 +692,7 @@ cudaError_t launch_persistent(KernelT kern, size_t smem, int64_t units, const Se
   int per_sm = 0, sms = 0;
   const cudaError_t e = persistent_config(reinterpret_cast<const void*>(kern), smem, &per_sm, &sms);
   if (e != cudaSuccess) return e;
+  if (p.ctas_per_sm > 0 && per_sm > p.ctas_per_sm) per_sm = p.ctas_per_sm;
   int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   if (grid > units) grid = units;
   kern<<<(unsigned)grid, kThreads, smem, s>>>(p);

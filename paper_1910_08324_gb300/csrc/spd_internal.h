@@ -95,6 +95,7 @@ struct SearchParams {
   int64_t n_units;
   int32_t* status;                // bit r: a wait for range r's ready flag ran out
   int64_t wait_ns;                // limit of one wait
+  int32_t ctas_per_sm;            // persistent CTAs per SM (0: as many as fit)
   BatchRange ranges[kMaxRanges];
 };
 

@@ -228,9 +228,15 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
 
   float sw[4], sw2[4], cw[4], cw2[4];  // levels 0..3: compensated sums over chunks
   float pw[4], pw2[4];                 // ... and over the steps of the current chunk
+  float2 qw = make_float2(0.0f, 0.0f), qw2 = qw;  // level 0 in packed pairs (first pass)
   int cn[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) sw[k] = sw2[k] = cw[k] = cw2[k] = pw[k] = pw2[k] = 0.0f, cn[k] = 0;
+  // First pass (no limits yet): a whole step whose 256 samples are finite keeps
+  // every value of levels 0..8, so its sums need no compare and no select and
+  // run in packed pairs; other steps (and later passes) take the general form.
+  const bool keep_all = pass == 0 && nlev > 8;
+  const bool has_a = jl < 5;
   float sa = 0.0f, sa2 = 0.0f, sb = 0.0f, sb2 = 0.0f, blk = 0.0f, q = 0.0f;
   int na = 0, nb = 0, bad = 0;
 
@@ -248,6 +254,43 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
         for (int i = 0; i < 8; ++i) f[i] = (o + i < rem) ? f[i] : 0.0f;  // sums stay finite
       }
     }
+    float p1[4], p2[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p1[i] = f[2 * i] + f[2 * i + 1];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) p2[i] = p1[2 * i] + p1[2 * i + 1];
+    const float s3 = p2[0] + p2[1];
+    float s = s3, v = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      s += __shfl_xor_sync(kFull, s, 1 << j);
+      if (jl == j) v = s;
+    }
+    // s: the warp's 256-sample sum (the same in every lane); finite only when every sample is
+    if (whole && keep_all && fabsf(s) <= FLT_MAX) {
+#pragma unroll
+      for (int i = 0; i < 8; i += 2) {  // level 0: two values per instruction
+        const float2 w = __fadd2_rn(make_float2(f[i], f[i + 1]), make_float2(-sh[0], -sh[0]));
+        qw = __fadd2_rn(qw, w);
+        qw2 = __ffma2_rn(w, w, qw2);
+      }
+      auto add = [&](int k, float v) {
+        const float w = v - sh[k];
+        pw[k] += w;
+        pw2[k] = fmaf(w, w, pw2[k]);
+      };
+#pragma unroll
+      for (int i = 0; i < 4; ++i) add(1, p1[i]);
+      add(2, p2[0]);
+      add(2, p2[1]);
+      add(3, s3);
+      cn[0] += 8, cn[1] += 4, cn[2] += 2, cn[3] += 1;
+      const float wa = has_a ? v - sha : 0.0f;
+      sa += wa;
+      sa2 = fmaf(wa, wa, sa2);
+      na += has_a ? 1 : 0;
+      return s;
+    }
     // a block counts when it ends inside the row
     auto keep = [&](int k, float v, int end) {
       const float w = v - sh[k];
@@ -259,25 +302,11 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
     };
 #pragma unroll
     for (int i = 0; i < 8; ++i) keep(0, f[i], o + i + 1);
-    float p1[4], p2[2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      p1[i] = f[2 * i] + f[2 * i + 1];
-      keep(1, p1[i], o + 2 * i + 2);
-    }
+    for (int i = 0; i < 4; ++i) keep(1, p1[i], o + 2 * i + 2);
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      p2[i] = p1[2 * i] + p1[2 * i + 1];
-      keep(2, p2[i], o + 4 * i + 4);
-    }
-    float s = p2[0] + p2[1];
-    keep(3, s, o + 8);
-    float v = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      s += __shfl_xor_sync(kFull, s, 1 << j);
-      if (jl == j) v = s;
-    }
+    for (int i = 0; i < 2; ++i) keep(2, p2[i], o + 4 * i + 4);
+    keep(3, s3, o + 8);
     const float w = v - sha;
     const int end = 8 * (lane & ~((2 << jl) - 1)) + (16 << jl);
     const bool in = (whole || end <= rem) && fabsf(w) <= lima;
@@ -346,6 +375,9 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
       sb2 += inb ? wb * wb : 0.0f;
       nb += inb ? 1 : 0;
       q = 0.0f;
+      pw[0] += qw.x + qw.y;
+      pw2[0] += qw2.x + qw2.y;
+      qw = qw2 = make_float2(0.0f, 0.0f);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         kahan_add(sw[k], cw[k], pw[k]);

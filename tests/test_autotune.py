@@ -50,3 +50,31 @@ def test_corrupt_cache_is_ignored(tmp_path):
     path.write_text("{not json")
     seg, _ = autotune.tune_segment("k", lambda s: None, lambda: 1.0, candidates=(32768,), cache_path=str(path))
     assert seg == 32768 and json.load(open(path))["k"]["segment"] == 32768
+
+
+def test_launch_tuner_searches_both_dimensions_and_caches(tmp_path):
+    path = str(tmp_path / "tune.json")
+    cost = {(32768, 0): 4.0, (32768, 1): 6.0, (32768, 2): 3.5, (65536, 0): 3.0, (65536, 1): 5.0,
+            (65536, 2): 2.0}
+    state = {}
+
+    def set_segment(s):
+        if s not in (32768, 65536):
+            raise ValueError("not for this grid")
+        state["s"] = s
+
+    def set_ctas(c):
+        if c > 2:
+            raise ValueError("more CTAs than fit")
+        state["c"] = c
+
+    (seg, c), t = autotune.tune_launch("k", set_segment, set_ctas, lambda: cost[(state["s"], state["c"])],
+                                       cache_path=path, reps=2)
+    assert (seg, c) == (65536, 2) and (state["s"], state["c"]) == (65536, 2)
+    assert t["65536/2"] == 2.0 and "65536/3" not in t and not any(k.startswith("16384/") for k in t)
+    d = json.load(open(path))["k"]
+    assert (d["segment"], d["ctas_per_sm"]) == (65536, 2)
+    state.clear()
+    (seg, c), _ = autotune.tune_launch("k", set_segment, set_ctas, lambda: pytest.fail("timed again"),
+                                       cache_path=path)
+    assert (seg, c) == (65536, 2) and state == {"s": 65536, "c": 2}
