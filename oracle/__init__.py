@@ -59,6 +59,8 @@ def _load():
         lib.spdo_grid_exhaustive.restype = i32
         lib.spdo_grid_boxdit.argtypes = [i32, i32, i32, _i32p, _i32p, i32]
         lib.spdo_grid_boxdit.restype = i32
+        lib.spdo_grid_boxdit_iters.argtypes = [_i32p, i32, i32, i32, _i32p, _i32p, i32]
+        lib.spdo_grid_boxdit_iters.restype = i32
         lib.spdo_grid_igrid.argtypes = [i32, i32, i32, _i32p, _i32p, i32]
         lib.spdo_grid_igrid.restype = i32
         lib.spdo_search.argtypes = [_f64p, i64, i64, i64, _i32p, _i32p, i32, i32,
@@ -67,6 +69,9 @@ def _load():
         lib.spdo_boxdit_steps.argtypes = [_f64p, i64, i64, i64, i32, i32, i32,
                                           _f64p, _f64p, _f64p, _i32p]
         lib.spdo_boxdit_steps.restype = i32
+        lib.spdo_boxdit_steps_iters.argtypes = [_f64p, i64, i64, i64, _i32p, i32, i32, i32,
+                                                _f64p, _f64p, _f64p, _i32p]
+        lib.spdo_boxdit_steps_iters.restype = i32
         lib.spdo_igrid_steps.argtypes = [_f64p, i64, i64, i64, i32, i32, i32,
                                          _f64p, _f64p, _f64p, _i32p]
         lib.spdo_igrid_steps.restype = i32
@@ -120,9 +125,20 @@ def grid_exhaustive(lmax: int) -> Grid:
     return _grid_call(_load().spdo_grid_exhaustive, int(lmax))
 
 
-def grid_boxdit(k: int, s_end: int, n_iter: int = 0) -> Grid:
-    """BoxDIT with L^i_max = k, D = 2 (Alg. 1); stops at the first width >= s_end."""
-    return _grid_call(_load().spdo_grid_boxdit, int(k), int(s_end), int(n_iter))
+def _klist(k):
+    ks = np.atleast_1d(np.asarray(k, np.int32)).ravel()
+    return np.ascontiguousarray(ks), int(ks.size)
+
+
+def grid_boxdit(k, s_end: int, n_iter: int = 0) -> Grid:
+    """BoxDIT, D = 2 (Alg. 1); stops at the first width >= s_end.
+
+    ``k`` is L^i_max: one even number for every iteration, or a sequence with
+    one per iteration (Sec. 3.1: it may change from iteration to iteration),
+    whose last entry repeats for later iterations.
+    """
+    ks, nk = _klist(k)
+    return _grid_call(_load().spdo_grid_boxdit_iters, ks, nk, int(s_end), int(n_iter))
 
 
 def grid_igrid(d: int, P: int, s_end: int) -> Grid:
@@ -170,15 +186,19 @@ def search(x, grid: Grid, mu=0.0, sigma=1.0, noise_mode: int = 0, literal: bool 
     return Y, W, Y2
 
 
-def boxdit_steps(x, k: int, s_end: int, mu=0.0, sigma=1.0, n_iter: int = 0):
-    """Alg. 1 run literally (O2).  Returns ``(Y, Wlen)``; ``Wlen`` holds widths."""
+def boxdit_steps(x, k, s_end: int, mu=0.0, sigma=1.0, n_iter: int = 0):
+    """Alg. 1 run literally (O2).  Returns ``(Y, Wlen)``; ``Wlen`` holds widths.
+
+    ``k``: L^i_max, one even number or one per iteration (as in grid_boxdit).
+    """
     x = _rows(x)
     ndm, nt = x.shape
     mu, sigma = _noise_arrays(ndm, mu, sigma)
     Y = np.empty((ndm, nt), np.float64)
     Wl = np.empty((ndm, nt), np.int32)
-    rc = _load().spdo_boxdit_steps(x.reshape(-1), ndm, nt, nt, int(k), int(s_end),
-                                   int(n_iter), mu, sigma, Y.reshape(-1), Wl.reshape(-1))
+    ks, nk = _klist(k)
+    rc = _load().spdo_boxdit_steps_iters(x.reshape(-1), ndm, nt, nt, ks, nk, int(s_end),
+                                         int(n_iter), mu, sigma, Y.reshape(-1), Wl.reshape(-1))
     if rc != 0:
         raise RuntimeError("spdo_boxdit_steps failed (%d)" % rc)
     return Y, Wl

@@ -12,12 +12,13 @@
  * passage of the paper it follows.
  *
  * Contents
- *   grids      spdo_grid_exhaustive / spdo_grid_boxdit / spdo_grid_igrid
+ *   grids      spdo_grid_exhaustive / spdo_grid_boxdit(_iters) / spdo_grid_igrid
  *              (Sec. 2.2.1 parameters B and L_s; Alg. 1 and the BoxDIT width
- *              formula of Sec. 3.1; Sec. 3.2 layers, Eq. boxcarsize, Table 1)
+ *              formula of Sec. 3.1, with one L^i_max per iteration or the
+ *              same for all; Sec. 3.2 layers, Eq. boxcarsize, Table 1)
  *   O1         spdo_search: the definition, Eq. boxcar + Eq. SNRlong (+ Eq.
  *              whitenoise), Y = max over the grid (Eq. MSD03), for every start
- *   O2         spdo_boxdit_steps: Alg. 1 run literally (boxcars on the
+ *   O2         spdo_boxdit_steps(_iters): Alg. 1 run literally (boxcars on the
  *              decimated series x^i extended from X^{i-1}, shifted decimation)
  *              spdo_igrid_steps: Sec. 3.2 run literally (binary tree of shifted
  *              decimated layers, depth extensions from ancestor layers)
@@ -70,22 +71,29 @@ SPDO_EXPORT int32_t spdo_grid_exhaustive(int32_t lmax, int32_t *L, int32_t *Ls,
 /*
  * BoxDIT grid (Alg. 1 and the width formula of Sec. 3.1), decimation D = 2.
  * Iteration i computes, on x^i, the widths
- *     L = L^{i-1}_MAX + D^i * m,   m = 1 .. L^i_max (= k here),
+ *     L = L^{i-1}_MAX + D^i * m,   m = 1 .. L^i_max,
  * at every point of x^i, i.e. at every D^i-th sample of x^0 (L_s = D^i), and
  *     L^i_MAX = L^{i-1}_MAX + D^i * L^i_max,   L^{-1}_MAX = 0.
+ * L^i_max may differ from iteration to iteration (Sec. 3.1, discussion of
+ * BoxDIT's single implementation): iteration i uses k[i], and iterations past
+ * the list repeat its last entry.  Each L^i_max must be even (divisible by D).
  * Iterations continue until a width >= s_end has been produced, which is the
  * last width kept.  If n_iter > 0 exactly n_iter full iterations are produced
  * instead (the paper's BD-8 footnote counts iterations this way).
  */
-SPDO_EXPORT int32_t spdo_grid_boxdit(int32_t k, int32_t s_end, int32_t n_iter,
-                                     int32_t *L, int32_t *Ls, int32_t cap) {
-  if (k < 2 || (k % 2) != 0 || s_end < 1) return -1;
+SPDO_EXPORT int32_t spdo_grid_boxdit_iters(const int32_t *k, int32_t nk, int32_t s_end,
+                                           int32_t n_iter, int32_t *L, int32_t *Ls,
+                                           int32_t cap) {
+  if (nk < 1 || s_end < 1) return -1;
+  for (int32_t i = 0; i < nk; ++i)
+    if (k[i] < 2 || (k[i] % 2) != 0) return -1;
   int32_t n = 0;
   int64_t lmax_cum = 0; /* L^{i-1}_MAX */
   int64_t Di = 1;       /* D^i */
   for (int32_t i = 0;; ++i) {
     if (n_iter > 0 && i >= n_iter) return n;
-    for (int32_t m = 1; m <= k; ++m) {
+    const int32_t ki = k[i < nk ? i : nk - 1];
+    for (int32_t m = 1; m <= ki; ++m) {
       int64_t w = lmax_cum + Di * m;
       if (w > 2147483647LL) return -3;
       if (n >= cap) return -2;
@@ -94,10 +102,16 @@ SPDO_EXPORT int32_t spdo_grid_boxdit(int32_t k, int32_t s_end, int32_t n_iter,
       ++n;
       if (n_iter <= 0 && w >= s_end) return n;
     }
-    lmax_cum += Di * k;
+    lmax_cum += Di * ki;
     Di *= 2;
     if (Di > (1LL << 30)) return -3;
   }
+}
+
+/* The same with one L^i_max = k for every iteration (BD-k of Sec. 4). */
+SPDO_EXPORT int32_t spdo_grid_boxdit(int32_t k, int32_t s_end, int32_t n_iter,
+                                     int32_t *L, int32_t *Ls, int32_t cap) {
+  return spdo_grid_boxdit_iters(&k, 1, s_end, n_iter, L, Ls, cap);
 }
 
 /*
@@ -222,7 +236,8 @@ SPDO_EXPORT int32_t spdo_search(const double *x, int64_t ndm, int64_t nt, int64_
 /* ------------------------------------------------------------------------ */
 
 /*
- * Alg. 1 for one row, D = 2, L^i_max = k for every iteration:
+ * Alg. 1 for one row, D = 2, L^i_max = k = kl[i] (the last entry of kl
+ * repeats for later iterations):
  *   - iteration i holds x^i (length len_i) and X^{i-1} at every D^i-th sample
  *     (X^{-1} = 0, L^{-1}_MAX = 0);
  *   - Boxcars(): for every point n of x^i and m = 1..k,
@@ -238,8 +253,8 @@ SPDO_EXPORT int32_t spdo_search(const double *x, int64_t ndm, int64_t nt, int64_
  * (max SNR, smallest width on ties); Wlen holds the width itself.
  * White noise per row (mu[r], sigma[r]).
  */
-static void boxdit_row(const double *x0, int64_t nt, int32_t k, int32_t s_end,
-                       int32_t n_iter, double mu, double sigma, double *Y,
+static void boxdit_row(const double *x0, int64_t nt, const int32_t *kl, int32_t nk,
+                       int32_t s_end, int32_t n_iter, double mu, double sigma, double *Y,
                        int32_t *Wlen) {
   for (int64_t s = 0; s < nt; ++s) {
     Y[s] = -HUGE_VAL;
@@ -254,6 +269,7 @@ static void boxdit_row(const double *x0, int64_t nt, int32_t k, int32_t s_end,
   int done = 0;
   for (int32_t i = 0; !done; ++i) {
     if (n_iter > 0 && i >= n_iter) break;
+    const int32_t k = kl[i < nk ? i : nk - 1]; /* L^i_max */
     /* Boxcars() */
     for (int64_t nn = 0; nn < len; ++nn) {
       int64_t s = nn * Di;
@@ -297,16 +313,25 @@ static void boxdit_row(const double *x0, int64_t nt, int32_t k, int32_t s_end,
   free(Xcur);
 }
 
+SPDO_EXPORT int32_t spdo_boxdit_steps_iters(const double *x, int64_t ndm, int64_t nt,
+                                            int64_t ld, const int32_t *k, int32_t nk,
+                                            int32_t s_end, int32_t n_iter, const double *mu,
+                                            const double *sigma, double *Y, int32_t *Wlen) {
+  if (nk < 1 || nt < 1 || ld < nt) return -1;
+  for (int32_t i = 0; i < nk; ++i)
+    if (k[i] < 2 || (k[i] % 2) != 0) return -1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < ndm; ++r)
+    boxdit_row(x + r * ld, nt, k, nk, s_end, n_iter, mu[r], sigma[r], Y + r * nt,
+               Wlen + r * nt);
+  return 0;
+}
+
 SPDO_EXPORT int32_t spdo_boxdit_steps(const double *x, int64_t ndm, int64_t nt,
                                       int64_t ld, int32_t k, int32_t s_end,
                                       int32_t n_iter, const double *mu,
                                       const double *sigma, double *Y, int32_t *Wlen) {
-  if (k < 2 || (k % 2) != 0 || nt < 1 || ld < nt) return -1;
-#pragma omp parallel for schedule(dynamic, 1)
-  for (int64_t r = 0; r < ndm; ++r)
-    boxdit_row(x + r * ld, nt, k, s_end, n_iter, mu[r], sigma[r], Y + r * nt,
-               Wlen + r * nt);
-  return 0;
+  return spdo_boxdit_steps_iters(x, ndm, nt, ld, &k, 1, s_end, n_iter, mu, sigma, Y, Wlen);
 }
 
 /* ------------------------------------------------------------------------ */

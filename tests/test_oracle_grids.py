@@ -13,6 +13,22 @@ def test_boxdit_worked_example():
     assert [[int(a), int(b)] for a, b in zip(g.L, g.Ls)] == want
 
 
+def test_boxdit_per_iteration_lmax():
+    # Sec. 3.1: BoxDIT's maximum width may differ from iteration to iteration; the
+    # golden grid is evaluated by hand from the width formula (see its header).
+    want = read_table("boxdit_lmax_per_iter.txt")
+    g = oracle.grid_boxdit([2, 4, 6], 45)
+    assert [[int(a), int(b)] for a, b in zip(g.L, g.Ls)] == want
+    # a list whose entries are all k is the uniform grid; n_iter counts iterations
+    for k in (2, 6, 8, 10):
+        for n_iter in (0, 3):
+            u = oracle.grid_boxdit(k, 700, n_iter)
+            v = oracle.grid_boxdit([k, k, k], 700, n_iter)
+            assert np.array_equal(u.L, v.L) and np.array_equal(u.Ls, v.Ls)
+    g = oracle.grid_boxdit([4, 2], 1, 3)  # exactly three iterations: 1..4 | 6, 8 | 12, 16
+    assert list(g.L) == [1, 2, 3, 4, 6, 8, 12, 16] and list(g.Ls) == [1] * 4 + [2] * 2 + [4] * 2
+
+
 def test_igrid_table1_depths():
     # Table 1: widths produced from base 16 by depth d.  In the IG(d) grid the step
     # whose base width is 16 must produce exactly that row.
@@ -68,5 +84,7 @@ def test_exhaustive():
 def test_invalid_parameters_rejected():
     with pytest.raises(ValueError):
         oracle.grid_boxdit(3, 100)  # L^i_max must be divisible by D = 2 (Sec. 3.1)
+    with pytest.raises(ValueError):
+        oracle.grid_boxdit([4, 6, 5], 100)  # ... in every iteration
     with pytest.raises(ValueError):
         oracle.grid_igrid(1, 3, 100)  # layers must be a power of two

@@ -92,6 +92,30 @@ def test_boxdit_paper_form_equals_definition(k, s_end, nt):
     assert np.array_equal(g.L[W], Wl)
 
 
+@pytest.mark.parametrize("k,s_end,nt", [((2, 4, 6), 300, 700), ((12,), 400, 901), ((6, 2), 100, 333),
+                                        ((2,), 1000, 1500), ((10, 4, 14, 2), 250, 64)])
+def test_boxdit_per_iteration_paper_form_equals_definition(k, s_end, nt):
+    # Alg. 1 with L^i_max changing per iteration (Sec. 3.1): the shifted decimation by
+    # L^i_max / D per iteration against the definition on the grid of the width formula.
+    x = _rand(3, nt, 77 + len(k))
+    mu, sigma = np.array([0.0, 0.5, -2.0]), np.array([1.0, 2.0, 0.5])
+    g = oracle.grid_boxdit(list(k), s_end)
+    Y, W, _ = oracle.search(x, g, mu, sigma)
+    Yp, Wl = oracle.boxdit_steps(x, list(k), s_end, mu, sigma)
+    np.testing.assert_allclose(Yp, Y, rtol=0, atol=1e-11)
+    assert np.array_equal(g.L[W], Wl)
+
+
+def test_boxdit_per_iteration_brute_force():
+    # literal running sums over the grid (no prefix sums) on a tiny row
+    x = _rand(2, 97, 5)
+    g = oracle.grid_boxdit([6, 2, 4], 60)
+    Y, W, _ = oracle.search(x, g, literal=True)
+    Yp, Wl = oracle.boxdit_steps(x, [6, 2, 4], 60)
+    np.testing.assert_allclose(Yp, Y, rtol=0, atol=1e-11)
+    assert np.array_equal(g.L[W], Wl)
+
+
 @pytest.mark.parametrize("d,P,s_end,nt", [(0, 1, 256, 700), (1, 4, 300, 1025), (2, 8, 200, 999),
                                           (3, 16, 400, 1300), (1, 2, 64, 200), (2, 4, 100, 77),
                                           (1, 4, 5000, 600)])
