@@ -61,11 +61,14 @@ ALGOS = {
     "bd8": dict(algo=1, boxdit_lmax=8),
     "bd16": dict(algo=1, boxdit_lmax=16),
     "bd32": dict(algo=1, boxdit_lmax=32),
+    "bd12": dict(algo=1, boxdit_lmax=12),  # any other even L^i_max: the general BoxDIT kernel
+    "bd24": dict(algo=1, boxdit_lmax=24),
     "exh": dict(algo=0),
 }
 SEARCH_SOURCES = ["paper_1910_08324_gb300/csrc/spd_igrid.cu", "paper_1910_08324_gb300/csrc/spd_igrid.cuh",
                   "paper_1910_08324_gb300/csrc/spd_igrid_coded.cu", "paper_1910_08324_gb300/csrc/spd_search.cu",
-                  "paper_1910_08324_gb300/csrc/spd_boxdit.cu", "paper_1910_08324_gb300/csrc/spd_common.cuh",
+                  "paper_1910_08324_gb300/csrc/spd_boxdit.cu", "paper_1910_08324_gb300/csrc/spd_boxdit_gen.cu",
+                  "paper_1910_08324_gb300/csrc/spd_common.cuh",
                   "paper_1910_08324_gb300/csrc/spd_internal.h"]
 # uneven DM ranges of one batched search: (DM trials, time decimation) of a 2,097,152-sample base
 BATCH_RANGES = [(1024, 1), (1024, 2), (768, 4), (512, 8), (256, 16)]
@@ -906,8 +909,8 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
                "ms_per_step": 1e3 * dt, "ms_median": 1e3 * statistics.median(per),
                "ms_steps": [round(1e3 * v, 2) for v in per], "chunks": nchunk,
                "records_equal_unchunked": same,
-               "api": "torch pinned H2D per row chunk (copy stream) + proposal.propose_and_search per chunk "
-                      "(C ABI calls, after its copy) + records to the host"}
+               "api": "torch pinned H2D per row chunk (copy stream) + one spd_propose_search C-ABI call per "
+                      "chunk (proposal.propose_and_search, after its copy) + records to the host"}
         del xh
 
     cpu = None
@@ -957,7 +960,8 @@ def run_proposal(args, torch, dist, spd, rank, world, local, dev):
             "proposal": s_prop, "plain": dict(s_plain, ms_per_step=plain_ms,
                                               value=ndm * nt / (plain_ms / 1e3)),
             "speedup_vs_plain": plain_ms / ms_per_step, "training": training,
-            "e2e": e2e, "gpu_launches": 8 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            # per step: decimate, forward, select, gather, two row gathers, search, candidate count/scan/write
+            "e2e": e2e, "gpu_launches": 10 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

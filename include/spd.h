@@ -84,8 +84,12 @@ typedef enum spd_dtype {
  *                 grid is the first one >= s_end ("nearest longer", L_end).
  *                 For SPD_ALGO_EXHAUSTIVE it is L_max itself (1..4096).
  *                 L_end must not exceed 32768.
- *   boxdit_lmax   BoxDIT: widths computed per iteration, L^i_max (Alg. 1);
- *                 one of 8, 16, 32 (BD-8/16/32 of Sec. 4).
+ *   boxdit_lmax   BoxDIT: widths computed per iteration, L^i_max (Alg. 1), the
+ *                 same for every iteration: any even value 2..256 (Sec. 3.1
+ *                 requires only divisibility by D = 2).  8, 16 and 32 (BD-8/16/32
+ *                 of Sec. 4) run on dedicated streaming kernels, every other
+ *                 value on the general BoxDIT kernel; spd_plan_create_boxdit
+ *                 takes one value per iteration.
  *   igrid_depth   IGRID: depth d of Eq. boxcarsize, 0..3.
  *   igrid_layers  IGRID: layers per step P (power of two, 2^d <= P, P <= 2^(d+1));
  *                 IG(1), IG(2), IG(3) of Sec. 3.2.1 use 4, 8, 16; DIT uses d=0, P=1.
@@ -151,6 +155,28 @@ const char *spd_version(void);
  * SPD_ERR_HOST_ALLOC.  *out is NULL on error.
  */
 spd_status spd_plan_create(const spd_plan_desc *desc, spd_plan **out);
+
+/*
+ * Build a BoxDIT plan with a maximum width per iteration (Alg. 1; Sec. 3.1 lets
+ * L^i_max change from iteration to iteration, to trade signal loss between
+ * pulse widths).  Iteration i uses lmax[i]; iterations past n_lmax use
+ * lmax[n_lmax - 1].  Iteration i computes the widths L^{i-1}_MAX + 2^i m,
+ * m = 1..L^i_max, at every 2^i-th start, with L^i_MAX = L^{i-1}_MAX + 2^i L^i_max.
+ *   lmax     host array of n_lmax even values, each 2..256 (read during the call)
+ *   n_lmax   1..24
+ *   n_iter   0: iterate up to the first width >= desc->s_end (nearest longer,
+ *            as spd_plan_create); 1..24: exactly n_iter full iterations
+ *            (desc->s_end is then ignored; the paper counts BD-8's iterations
+ *            this way in Sec. 4)
+ * desc supplies dtype, ndm, nt, ld (and s_end when n_iter is 0); its algo and
+ * boxdit_lmax are ignored.  The widest width must not exceed 32768 and the grid
+ * must have at most 512 widths.  A plan whose L^i_max are all 8, all 16 or all
+ * 32 runs on the BD-K streaming kernels, any other on the general BoxDIT
+ * kernel (tiles of 2048 or 4096 starts; spd_plan_set_segment then returns
+ * SPD_ERR_UNSUPPORTED).  Host only.  Errors as spd_plan_create.
+ */
+spd_status spd_plan_create_boxdit(const spd_plan_desc *desc, const int32_t *lmax, int32_t n_lmax,
+                                  int32_t n_iter, spd_plan **out);
 
 /*
  * Build a plan over an explicit grid: Sec. 2.2 characterises a search by its
@@ -335,7 +361,8 @@ spd_status spd_noise_stats(const spd_plan *plan, const void *d_x, float outlier_
  * multiple of 16384 and of 2^top (top: the plan's last level), at most 2^24;
  * the default is the longest of 524288, 262144 and 131072 that gives at least
  * 2432 segments (ndm x segments per row).  Host only.  SPD_ERR_INVALID_ARG otherwise (and for
- * exhaustive plans).
+ * exhaustive plans); SPD_ERR_UNSUPPORTED for a BoxDIT plan on the general kernel
+ * (its tiles are fixed by the plan).
  */
 spd_status spd_plan_set_segment(spd_plan *plan, int32_t segment);
 
@@ -468,6 +495,66 @@ spd_status spd_net_select(const float *d_logits, int64_t n, float threshold, int
 spd_status spd_net_gather(const void *d_x, int32_t dtype, int64_t ndm, int64_t nt, int64_t ld,
                           const int64_t *d_list, int64_t n, int32_t block, int32_t left, int32_t width,
                           void *d_out, int64_t ld_out, spd_stream_t stream);
+
+/*
+ * Proposal search: the network above flags 4096-sample blocks, and only the
+ * flagged blocks are searched at full resolution with the plan grid; all of it
+ * runs on the device, records come back in the series' own (row, start).
+ *
+ * spd_proposal_create: grid is a plan description of the series (algo, dtype,
+ * s_end, boxdit_lmax, igrid_*, ndm, nt, ld) with nt a multiple of 4096 and
+ * dtype F32, F16 or BF16 (U8: SPD_ERR_UNSUPPORTED); peak_radius (0..64) is the
+ * candidate rule's R; max_blocks (>= 1; clamped to ndm * nt / 4096) bounds the
+ * flagged blocks one call can search and sizes the workspace.  Each flagged
+ * block is searched in a compact row holding L samples before it (L the
+ * smallest multiple of the grid's largest start separation >= max(R, 1)), the
+ * block, and R + the widest boxcar after it (-inf outside the series), so every
+ * start of the block and of its peak-test neighbours gets the outputs of a
+ * search of the whole row.  The grid's
+ * start separations must divide 4096 (else SPD_ERR_UNSUPPORTED).  Host only.
+ */
+typedef struct spd_proposal spd_proposal;
+spd_status spd_proposal_create(const spd_plan_desc *grid, int32_t peak_radius, int64_t max_blocks,
+                               spd_proposal **out);
+spd_status spd_proposal_destroy(spd_proposal *prop);
+/* Device workspace of spd_propose_search in bytes (256-byte aligned base). */
+spd_status spd_proposal_workspace_size(const spd_proposal *prop, size_t *bytes);
+/* The grid's widths and separations (as spd_plan_widths); the width indices of
+ * the records and the width order of a noise table refer to it. */
+spd_status spd_proposal_widths(const spd_proposal *prop, int32_t *widths, int32_t *seps, int32_t cap,
+                               int32_t *n);
+/*
+ * One proposal search of the series d_x ([ndm][ld] of the grid's dtype):
+ *   1. decimated blocks (spd_net_decimate with the width-1 statistics of
+ *      `noise`), logits (spd_net_forward with d_params), and the ids of the
+ *      blocks whose logit > logit_threshold (spd_net_select);
+ *   2. the number of flagged blocks is read back (the stream is synchronised
+ *      once) and written to *n_blocks (host, may be NULL); more than max_blocks:
+ *      SPD_ERR_BUFFER_TOO_SMALL, nothing searched; none: *d_count = 0;
+ *   3. the flagged blocks and their rows' statistics are gathered, searched
+ *      (spd_execute on the compact rows) and their candidates selected with
+ *      threshold and the proposal's peak radius (spd_candidates rule), only
+ *      starts inside a block counting; records carry the series' row and start,
+ *      in (row, start) order, with the grid's width index and width.
+ * noise: mode 0, mu/sigma [ndm]; mode 1, [ndm][n_widths] of the grid (device).
+ * d_out, cap, d_count as spd_candidates (first cap records, true count; see
+ * spd_candidates_status).  Asynchronous after step 2; errors as spd_execute.
+ */
+spd_status spd_propose_search(const spd_proposal *prop, const float *d_params, const void *d_x,
+                              const spd_noise *noise, float logit_threshold, float threshold,
+                              spd_candidate *d_out, int64_t cap, int64_t *d_count, int64_t *n_blocks,
+                              void *d_ws, size_t ws_bytes, spd_stream_t stream);
+/*
+ * Step 3 of spd_propose_search alone, for blocks the caller chose: d_ids
+ * (device int64[n_ids], increasing) are block ids r * (nt / 4096) + b of the
+ * series.  n_ids above the proposal's max_blocks: SPD_ERR_BUFFER_TOO_SMALL;
+ * 0: *d_count = 0.  An id outside [0, ndm * nt / 4096) is searched as a block
+ * of -inf samples (no records).  Asynchronous; other arguments and errors as
+ * spd_propose_search.
+ */
+spd_status spd_search_blocks(const spd_proposal *prop, const void *d_x, const spd_noise *noise,
+                             const int64_t *d_ids, int64_t n_ids, float threshold, spd_candidate *d_out,
+                             int64_t cap, int64_t *d_count, void *d_ws, size_t ws_bytes, spd_stream_t stream);
 
 /*
  * Wait for the stream and report any asynchronous CUDA error of work queued

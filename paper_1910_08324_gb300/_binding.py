@@ -60,7 +60,9 @@ _SYMBOLS = ["spd_status_string", "spd_version", "spd_plan_create", "spd_plan_des
             "spd_batch_set_wait_ns", "spd_batch_set_ctas_per_sm", "spd_batch_workspace_size", "spd_batch_execute", "spd_batch_status",
             "spd_batch_candidates", "spd_net_decimate", "spd_net_forward", "spd_net_gradient",
             "spd_net_adam", "spd_net_select", "spd_net_gather", "spd_plan_set_starts", "spd_plan_create_grid",
-            "spd_net_gradient_ordered", "spd_candidates_status"]
+            "spd_net_gradient_ordered", "spd_candidates_status", "spd_plan_create_boxdit",
+            "spd_proposal_create", "spd_proposal_destroy", "spd_proposal_workspace_size",
+            "spd_proposal_widths", "spd_propose_search", "spd_search_blocks"]
 
 
 def library_path() -> str:
@@ -95,6 +97,16 @@ def load_library():
         lib.spd_plan_set_segment.argtypes = [vp, i32]
         lib.spd_plan_set_starts.argtypes = [vp, i64]
         lib.spd_plan_create_grid.argtypes = [ctypes.POINTER(_Desc), vp, vp, i32, ctypes.POINTER(vp)]
+        lib.spd_plan_create_boxdit.argtypes = [ctypes.POINTER(_Desc), vp, i32, i32, ctypes.POINTER(vp)]
+        lib.spd_proposal_create.argtypes = [ctypes.POINTER(_Desc), i32, ctypes.c_int64, ctypes.POINTER(vp)]
+        lib.spd_proposal_destroy.argtypes = [vp]
+        lib.spd_proposal_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.spd_proposal_widths.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i32)]
+        lib.spd_propose_search.argtypes = [vp, vp, vp, ctypes.POINTER(_Noise), ctypes.c_float, ctypes.c_float,
+                                           vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_int64), vp,
+                                           ctypes.c_size_t, vp]
+        lib.spd_search_blocks.argtypes = [vp, vp, ctypes.POINTER(_Noise), vp, ctypes.c_int64, ctypes.c_float,
+                                          vp, ctypes.c_int64, vp, vp, ctypes.c_size_t, vp]
         lib.spd_net_param_count.argtypes = []
         lib.spd_net_param_count.restype = ctypes.c_int32
         lib.spd_net_decimate.argtypes = [vp, i32, i64, i64, i64, vp, vp, vp, vp]
@@ -169,6 +181,98 @@ def spd_plan_create(algo: int, s_end: int, ndm: int, nt: int, ld: int | None = N
               int(igrid_layers), int(ndm), int(nt), int(nt if ld is None else ld))
     h = ctypes.c_void_p()
     _check(lib.spd_plan_create(ctypes.byref(d), ctypes.byref(h)), "spd_plan_create")
+    return Plan(h.value, d)
+
+
+class Proposal:
+    """Owns an ``spd_proposal*`` (``spd_proposal_create``); destroyed with the object."""
+
+    def __init__(self, handle: int, desc: _Desc, radius: int, max_blocks: int):
+        self.handle = handle
+        self.desc = desc
+        self.radius = int(radius)
+        self.max_blocks = int(max_blocks)
+        self.ndm, self.nt, self.ld = int(desc.ndm), int(desc.nt), int(desc.ld)
+
+    def workspace_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(load_library().spd_proposal_workspace_size(ctypes.c_void_p(self.handle), ctypes.byref(n)),
+               "spd_proposal_workspace_size")
+        return int(n.value)
+
+    def widths(self):
+        lib = load_library()
+        n = ctypes.c_int32()
+        h = ctypes.c_void_p(self.handle)
+        _check(lib.spd_proposal_widths(h, None, None, 0, ctypes.byref(n)), "spd_proposal_widths")
+        w = np.zeros(n.value, np.int32)
+        sp = np.zeros(n.value, np.int32)
+        _check(lib.spd_proposal_widths(h, w.ctypes.data, sp.ctypes.data, n.value, ctypes.byref(n)),
+               "spd_proposal_widths")
+        return w, sp
+
+    def close(self):
+        if self.handle:
+            _check(load_library().spd_proposal_destroy(ctypes.c_void_p(self.handle)), "spd_proposal_destroy")
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spd_proposal_create(algo: int, s_end: int, ndm: int, nt: int, ld: int | None = None, boxdit_lmax: int = 0,
+                        igrid_depth: int = 0, igrid_layers: int = 0, dtype: int = SPD_F32, peak_radius: int = 1,
+                        max_blocks: int = 1 << 16) -> Proposal:
+    """A proposal search of [ndm, nt] series (nt a multiple of 4096) with the given grid."""
+    lib = load_library()
+    d = _Desc(int(algo), int(dtype), int(s_end), int(boxdit_lmax), int(igrid_depth),
+              int(igrid_layers), int(ndm), int(nt), int(nt if ld is None else ld))
+    h = ctypes.c_void_p()
+    _check(lib.spd_proposal_create(ctypes.byref(d), int(peak_radius), int(max_blocks), ctypes.byref(h)),
+           "spd_proposal_create")
+    return Proposal(h.value, d, peak_radius, max_blocks)
+
+
+def spd_propose_search(prop: Proposal, params: int, x: int, mu: int, sigma: int, logit_threshold: float,
+                       threshold: float, out: int, cap: int, count: int, ws: int, ws_bytes: int, stream: int = 0,
+                       noise_mode: int = 0) -> int:
+    """Runs ``spd_propose_search``; returns the number of flagged blocks (raises
+    SPD_ERR_BUFFER_TOO_SMALL when it exceeds the proposal's max_blocks)."""
+    nz = _Noise(int(noise_mode), mu, sigma)
+    nb = ctypes.c_int64(0)
+    st = load_library().spd_propose_search(ctypes.c_void_p(prop.handle), params, x, ctypes.byref(nz),
+                                           float(logit_threshold), float(threshold), out or None, int(cap),
+                                           count, ctypes.byref(nb), ws, ws_bytes, stream or None)
+    if st != 0:
+        err = SpdError(st, "spd_propose_search")
+        err.n_blocks = int(nb.value)  # the flagged blocks (when there were more than max_blocks)
+        raise err
+    return int(nb.value)
+
+
+def spd_search_blocks(prop: Proposal, x: int, mu: int, sigma: int, ids: int, n_ids: int, threshold: float,
+                      out: int, cap: int, count: int, ws: int, ws_bytes: int, stream: int = 0, noise_mode: int = 0):
+    nz = _Noise(int(noise_mode), mu, sigma)
+    _check(load_library().spd_search_blocks(ctypes.c_void_p(prop.handle), x, ctypes.byref(nz), ids or None,
+                                            int(n_ids), float(threshold), out or None, int(cap), count, ws,
+                                            ws_bytes, stream or None), "spd_search_blocks")
+
+
+def spd_plan_create_boxdit(lmax, s_end: int, ndm: int, nt: int, ld: int | None = None, n_iter: int = 0,
+                           dtype: int = SPD_F32) -> Plan:
+    """BoxDIT plan with one maximum width L^i_max per iteration (``lmax``, a
+    sequence of even values; the last repeats), up to the first width >= s_end,
+    or exactly ``n_iter`` iterations when n_iter > 0."""
+    lib = load_library()
+    k = np.ascontiguousarray(np.atleast_1d(np.asarray(lmax, np.int32)).ravel())
+    d = _Desc(SPD_ALGO_BOXDIT, int(dtype), int(s_end), int(k[0]) if k.size else 0, 0, 0, int(ndm), int(nt),
+              int(nt if ld is None else ld))
+    h = ctypes.c_void_p()
+    _check(lib.spd_plan_create_boxdit(ctypes.byref(d), k.ctypes.data, int(k.size), int(n_iter), ctypes.byref(h)),
+           "spd_plan_create_boxdit")
     return Plan(h.value, d)
 
 
@@ -492,6 +596,29 @@ def net_gather(x, block_ids, n: int, block: int, left: int, width: int, out, dty
     _check(load_library().spd_net_gather(_ptr(x), int(dtype), ndm, nt, ld, _ptr(block_ids), int(n), int(block),
                                          int(left), int(width), _ptr(out), out.shape[1],
                                          _stream(stream) or None), "spd_net_gather")
+
+
+def propose_search(prop: Proposal, params, x, mu, sigma, out, count, ws, logit_threshold: float = 0.0,
+                   threshold: float = 6.0, noise_mode: int = 0, stream=None) -> int:
+    """Run ``spd_propose_search`` on torch CUDA tensors (``x`` [ndm, ld] of the
+    proposal's dtype; ``out`` uint8 of cap * 24 bytes; ``count`` int64[1]).
+    Returns the number of flagged blocks."""
+    if not x.is_contiguous() or x.numel() < prop.ndm * prop.ld:
+        raise SpdError(5, "propose_search: x must be contiguous with ndm * ld elements")
+    cap = 0 if out is None else out.numel() * out.element_size() // CANDIDATE_DTYPE.itemsize
+    return spd_propose_search(prop, _ptr(params), _ptr(x), _ptr(mu), _ptr(sigma), logit_threshold, threshold,
+                              _ptr(out), cap, _ptr(count), _ptr(ws), ws.numel() * ws.element_size(),
+                              _stream(stream), noise_mode=noise_mode)
+
+
+def search_blocks(prop: Proposal, x, mu, sigma, ids, out, count, ws, threshold: float = 6.0, noise_mode: int = 0,
+                  stream=None):
+    """Run ``spd_search_blocks`` on torch CUDA tensors (``ids`` int64, increasing)."""
+    if not x.is_contiguous() or x.numel() < prop.ndm * prop.ld:
+        raise SpdError(5, "search_blocks: x must be contiguous with ndm * ld elements")
+    cap = 0 if out is None else out.numel() * out.element_size() // CANDIDATE_DTYPE.itemsize
+    spd_search_blocks(prop, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(ids), ids.numel(), threshold, _ptr(out), cap,
+                      _ptr(count), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream), noise_mode=noise_mode)
 
 
 def records(out_tensor, count: int):

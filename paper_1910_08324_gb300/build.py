@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libspd.so")
-SOURCES = ["spd_api.cu", "spd_search.cu", "spd_igrid.cu", "spd_igrid_coded.cu", "spd_boxdit.cu", "spd_candidates.cu",
+SOURCES = ["spd_api.cu", "spd_search.cu", "spd_igrid.cu", "spd_igrid_coded.cu", "spd_boxdit.cu", "spd_boxdit_gen.cu",
+           "spd_candidates.cu",
            "spd_msd.cu", "spd_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -3,6 +3,7 @@
 // include/spd.h for the contract of every entry point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -44,23 +45,54 @@ bool add_level(spd_plan* p, int level, const int* widths, int n, int sep) {
   return false;
 }
 
-// BoxDIT (Alg. 1, D = 2, L^i_max = k): iteration i has separation 2^i and the
-// widths L^{i-1}_MAX + 2^i m, m = 1..k, with L^{i-1}_MAX = k (2^i - 1).
-spd_status build_boxdit(spd_plan* p) {
-  const int k = p->k;
-  int w[64];
+// BoxDIT (Alg. 1, D = 2): iteration i has separation 2^i and the widths
+// L^{i-1}_MAX + 2^i m, m = 1..k_i, with L^{i-1}_MAX = sum_{j<i} k_j 2^j.  k_i is
+// k[i] (the last entry repeats for later iterations; Sec. 3.1 lets L^i_max
+// change from iteration to iteration).  n_iter > 0: exactly n_iter full
+// iterations; otherwise up to the first width >= s_end.  A plan whose k_i are
+// all 8, all 16 or all 32 is streamed by the BD-K kernels (spd_boxdit.cu),
+// every other one by the general kernel (spd_boxdit_gen.cu).
+spd_status build_boxdit(spd_plan* p, const int32_t* k, int nk, int n_iter) {
+  std::vector<int> w;
+  int64_t c = 0;
+  bool uniform = true;
   for (int i = 0; i < spd::kMaxLevels; ++i) {
-    const int64_t c = (int64_t)k * ((1LL << i) - 1);
-    for (int m = 1; m <= k; ++m) {
+    const int ki = k[i < nk ? i : nk - 1];
+    uniform = uniform && ki == k[0];
+    w.clear();
+    for (int m = 1; m <= ki; ++m) {
       const int64_t v = c + ((int64_t)m << i);
       if (v > (1LL << 30)) return SPD_ERR_INVALID_ARG;
-      w[m - 1] = (int)v;
+      w.push_back((int)v);
     }
     p->lvl_base.push_back((int32_t)c);
-    if (add_level(p, i, w, k, 1 << i)) return SPD_OK;
+    p->lvl_k.push_back(ki);
+    bool last;
+    if (n_iter > 0) {
+      p->lvl_first.push_back((int32_t)p->widths.size());
+      for (int q = 0; q < ki; ++q) {
+        p->widths.push_back(w[q]);
+        p->seps.push_back(1 << i);
+      }
+      last = i == n_iter - 1;
+      if (last) {
+        p->top = i;
+        p->n_top = ki;
+      }
+    } else {
+      last = add_level(p, i, w.data(), ki, 1 << i);
+    }
+    if (last) {
+      p->bd_general = !(uniform && (k[0] == 8 || k[0] == 16 || k[0] == 32));
+      p->k = p->bd_general ? 0 : k[0];
+      return SPD_OK;
+    }
+    c += (int64_t)ki << i;
   }
   return SPD_ERR_INVALID_ARG;
 }
+
+bool boxdit_k_ok(int k) { return k >= 2 && k <= spd::kMaxBoxditK && k % 2 == 0; }
 
 // IGRID IG(d) with P = 2^p layers (Sec. 3.2).  Steps 0..p all have boxcar
 // separation 2^i / P <= 1, so they form level 0 together: step i contributes
@@ -169,7 +201,12 @@ void fill_grid(spd::SearchParams& p, const spd_plan& plan) {
   p.grid = plan.explicit_grid ? 1 : 0;
   if (plan.explicit_grid)
     for (size_t i = 0; i < plan.seps.size() && i < (size_t)spd::kMaxGridWidths; ++i) p.wsep[i] = plan.seps[i];
-  if (plan.family == kBoxdit) {
+  if (plan.family == kBoxdit && plan.bd_general) {
+    for (int j = 0; j <= plan.top; ++j) p.lvl_k[j] = plan.lvl_k[j];
+    spd::bdg_layout(plan, plan.tile, true, p.gen_len, p.gen_off);
+    for (size_t i = 0; i < plan.widths.size() && i < (size_t)spd::kMaxGridWidths; ++i)
+      p.wscale[i] = (float)(1.0 / std::sqrt((double)plan.widths[i]));
+  } else if (plan.family == kBoxdit) {
     for (int j = 0; j <= plan.top; ++j)
       for (int m = 1; m <= plan.k; ++m)
         p.bscale[j][m] = (float)(1.0 / std::sqrt((double)plan.lvl_base[j] + (double)m * (double)(1 << j)));
@@ -252,12 +289,26 @@ void fill_cand_params(spd::CandParams& p, const spd_plan* plan, const float* d_s
   p.width_mode = (plan->family == kExhaustive && !plan->explicit_grid) ? 0 : 1;
   if (p.width_mode)
     for (size_t i = 0; i < plan->widths.size() && i < 512; ++i) p.width_tab[i] = plan->widths[i];
+  p.s_lo = 0;
+  p.s_hi = p.nt;
+  p.row_ids = nullptr;
+  p.map_bpr = 1;
+  p.map_nt = 0;
+  p.map_block = 0;
 }
+
+// Candidate window and block map of a proposal search (CandParams).
+struct BlockMap {
+  int64_t s_lo, s_hi;
+  const int64_t* ids;
+  int64_t bpr, nt;
+  int32_t block;
+};
 
 spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_t* d_width_idx,
                          float threshold, int32_t peak_radius, spd_candidate* d_out, int64_t cap,
                          int64_t* d_count, void* d_ws, size_t ws_bytes, bool use_tile_max,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, const BlockMap* map = nullptr) {
   spd_status st = check_cand_args(plan, d_snr, d_width_idx, threshold, peak_radius, d_out, cap, d_count);
   if (st != SPD_OK) return st;
   st = validate_ws(plan, d_ws, ws_bytes);
@@ -272,6 +323,14 @@ spd_status do_candidates(const spd_plan* plan, const float* d_snr, const uint16_
   p.counts = reinterpret_cast<int32_t*>(base + wl.counts);
   p.gsum = reinterpret_cast<int32_t*>(base + wl.gsum);
   p.goff = reinterpret_cast<int64_t*>(base + wl.goff);
+  if (map) {
+    p.s_lo = map->s_lo;
+    p.s_hi = map->s_hi;
+    p.row_ids = map->ids;
+    p.map_bpr = map->bpr;
+    p.map_nt = map->nt;
+    p.map_block = map->block;
+  }
   const cudaError_t e = spd::launch_candidates(*plan, p, stream);
   delete cp;
   return check_cuda(e);
@@ -318,7 +377,7 @@ spd_plan range_plan(const spd_batch& b, int r) {
   p.desc.ndm = b.ndm[r];
   p.desc.nt = b.nt[r];
   p.desc.ld = b.ld[r];
-  p.tile = segment_tile(b.nt[r], b.segment);
+  p.tile = b.grid.bd_general ? b.grid.tile : segment_tile(b.nt[r], b.segment);
   p.n_starts = b.nt[r];
   p.tiles_per_row = (b.nt[r] + p.tile - 1) / p.tile;
   p.cand_tiles_per_row = (b.nt[r] + spd::kCandTile - 1) / spd::kCandTile;
@@ -382,7 +441,7 @@ spd_status finish_plan(spd_plan* p, spd_plan** out) {
     // BoxDIT and IGRID: one CTA streams a segment of 131072 to 524288 starts (a
     // multiple of the candidate tile; default_segment); the halo is the widest
     // boxcar, rounded to whole chunks
-    if (p->family == kBoxdit && p->top > 11) {  // unreachable below kMaxLend; the kernel stops at 11
+    if (p->family == kBoxdit && !p->bd_general && p->top > 11) {  // unreachable below kMaxLend
       delete p;
       return SPD_ERR_UNSUPPORTED;
     }
@@ -394,6 +453,13 @@ spd_status finish_plan(spd_plan* p, spd_plan** out) {
     }
     p->tile = segment_tile(d.nt, default_segment(d.ndm, d.nt));
     p->halo = ((p->lend + spd::kChunk - 1) / spd::kChunk) * spd::kChunk;
+    if (p->bd_general) {
+      // tiles of 4096 starts when two CTAs still fit on an SM, else 2048
+      int32_t len[spd::kMaxLevels], off[spd::kBdgOffsets];
+      p->tile = 4096;
+      if (sizeof(float) * (size_t)spd::bdg_layout(*p, 4096, true, len, off) > 113 * 1024) p->tile = 2048;
+      p->halo = p->lend;
+    }
   }
   p->n_starts = d.nt;
   p->tiles_per_row = (d.nt + p->tile - 1) / p->tile;
@@ -406,6 +472,57 @@ spd_status finish_plan(spd_plan* p, spd_plan** out) {
   *out = p;
   return SPD_OK;
 }
+}  // namespace
+
+// A proposal search (spd_propose_search): the network flags 4096-sample blocks
+// of the series; the flagged blocks, each with `left` samples before it and the
+// widest boxcar after it, are copied into compact rows of `width` samples
+// (stride ld_c) and searched with `plan` (rows: up to max_blocks).
+struct spd_proposal {
+  spd_plan plan;       // the grid over compact rows (desc.ndm = max_blocks)
+  spd_plan_desc src;   // the series (ndm, nt, ld, dtype)
+  int32_t radius, left, width;
+  int64_t ld_c, max_blocks, bpr;
+};
+
+namespace {
+constexpr int kPropBlock = 4096;  // input samples per block
+constexpr int kPropDec = 16;      // the network reads blocks decimated x16
+
+struct PropLayout {  // workspace of a proposal search
+  size_t dec, logits, ids, cnt, mu0, sg0, xc, yc, wc, muc, sgc, ws, ws_bytes, total;
+  explicit PropLayout(const spd_proposal& q) {
+    const int64_t ndm = q.src.ndm, nblk = ndm * q.bpr, mb = q.max_blocks;
+    const size_t nw = q.plan.widths.size();
+    const size_t rows = (size_t)mb * (size_t)q.ld_c;
+    size_t o = 0;
+    dec = o;
+    o = align_up(o + (size_t)ndm * (size_t)(q.src.nt / kPropDec) * sizeof(float));
+    logits = o;
+    o = align_up(o + (size_t)nblk * sizeof(float));
+    ids = o;
+    o = align_up(o + (size_t)nblk * sizeof(int64_t));
+    cnt = o;
+    o = align_up(o + sizeof(int64_t));
+    mu0 = o;
+    o = align_up(o + (size_t)ndm * sizeof(float));
+    sg0 = o;
+    o = align_up(o + (size_t)ndm * sizeof(float));
+    xc = o;
+    o = align_up(o + rows * (size_t)dtype_size(q.src.dtype));
+    yc = o;
+    o = align_up(o + rows * sizeof(float));
+    wc = o;
+    o = align_up(o + rows * sizeof(uint16_t));
+    muc = o;
+    o = align_up(o + (size_t)mb * nw * sizeof(float));
+    sgc = o;
+    o = align_up(o + (size_t)mb * nw * sizeof(float));
+    ws = o;
+    ws_bytes = WsLayout(q.plan).total;
+    total = align_up(o + ws_bytes);
+  }
+};
 }  // namespace
 
 extern "C" {
@@ -455,12 +572,11 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
         p->n_top = d.s_end;
       }
     } else if (d.algo == SPD_ALGO_BOXDIT) {
-      if (d.boxdit_lmax != 8 && d.boxdit_lmax != 16 && d.boxdit_lmax != 32) {
+      if (!boxdit_k_ok(d.boxdit_lmax)) {
         st = SPD_ERR_INVALID_ARG;
       } else {
         p->family = kBoxdit;
-        p->k = d.boxdit_lmax;
-        st = build_boxdit(p);
+        st = build_boxdit(p, &d.boxdit_lmax, 1, 0);
       }
     } else {
       const int dd = d.igrid_depth, P = d.igrid_layers;
@@ -480,6 +596,39 @@ spd_status spd_plan_create(const spd_plan_desc* desc, spd_plan** out) {
     delete p;
     return st;
   }
+  return finish_plan(p, out);
+}
+
+spd_status spd_plan_create_boxdit(const spd_plan_desc* desc, const int32_t* lmax, int32_t n_lmax,
+                                  int32_t n_iter, spd_plan** out) {
+  if (!out) return SPD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc || !lmax || n_lmax < 1 || n_lmax > spd::kMaxLevels || n_iter < 0 || n_iter > spd::kMaxLevels)
+    return SPD_ERR_INVALID_ARG;
+  const spd_plan_desc& d = *desc;
+  if (d.ndm < 1 || d.nt < 1 || d.ld < d.nt || (n_iter == 0 && d.s_end < 1)) return SPD_ERR_INVALID_ARG;
+  if (d.ndm > (int64_t)1 << 24 || d.nt > (int64_t)1 << 40) return SPD_ERR_INVALID_ARG;
+  if (d.dtype < SPD_F32 || d.dtype > SPD_U8) return SPD_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n_lmax; ++i)
+    if (!boxdit_k_ok(lmax[i])) return SPD_ERR_INVALID_ARG;
+  spd_plan* p = new (std::nothrow) spd_plan();
+  if (!p) return SPD_ERR_HOST_ALLOC;
+  p->desc = d;
+  p->desc.algo = SPD_ALGO_BOXDIT;
+  p->desc.boxdit_lmax = lmax[0];
+  if (n_iter > 0) p->desc.s_end = 1;  // not used: the iteration count decides the grid
+  spd_status st = SPD_OK;
+  try {
+    p->family = kBoxdit;
+    st = build_boxdit(p, lmax, n_lmax, n_iter);
+  } catch (const std::bad_alloc&) {
+    st = SPD_ERR_HOST_ALLOC;
+  }
+  if (st != SPD_OK) {
+    delete p;
+    return st;
+  }
+  if (n_iter > 0) p->desc.s_end = p->widths.back();
   return finish_plan(p, out);
 }
 
@@ -627,6 +776,7 @@ spd_status spd_noise_stats(const spd_plan* plan, const void* d_x, float outlier_
 }
 
 spd_status spd_plan_set_segment(spd_plan* plan, int32_t segment) {
+  if (plan && plan->bd_general) return SPD_ERR_UNSUPPORTED;  // the general kernel has tiles of its own
   if (!plan || plan->family == kExhaustive || !segment_ok(*plan, segment)) return SPD_ERR_INVALID_ARG;
   plan->tile = segment_tile(plan->desc.nt, segment);
   plan->tiles_per_row = (plan->n_starts + plan->tile - 1) / plan->tile;
@@ -753,7 +903,7 @@ spd_status spd_batch_execute(const spd_batch* batch, const spd_range_io* io, voi
     R.ndm = batch->ndm[r];
     R.nt = batch->nt[r];
     R.ld = batch->ld[r];
-    R.tile = segment_tile(R.nt, batch->segment);
+    R.tile = g.bd_general ? g.tile : segment_tile(R.nt, batch->segment);
     R.tiles_per_row = (int32_t)((R.nt + R.tile - 1) / R.tile);
     R.cand_tiles_per_row = (int32_t)((R.nt + spd::kCandTile - 1) / spd::kCandTile);
     R.tile_max = reinterpret_cast<float*>(ws + bl.tile_max[r]);
@@ -906,6 +1056,192 @@ spd_status spd_candidates_status(const int64_t* d_count, int64_t cap, int64_t* t
   if (e != cudaSuccess) return SPD_ERR_CUDA;
   if (total) *total = n;
   return n > cap ? SPD_ERR_BUFFER_TOO_SMALL : SPD_OK;
+}
+
+spd_status spd_proposal_create(const spd_plan_desc* grid, int32_t peak_radius, int64_t max_blocks,
+                               spd_proposal** out) {
+  if (!out) return SPD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!grid || peak_radius < 0 || peak_radius > spd::kMaxPeakRadius || max_blocks < 1) return SPD_ERR_INVALID_ARG;
+  const spd_plan_desc& g = *grid;
+  if (g.ndm < 1 || g.nt < kPropBlock || g.nt % kPropBlock || g.ld < g.nt || g.ndm > ((int64_t)1 << 24) ||
+      g.nt > ((int64_t)1 << 40))
+    return SPD_ERR_INVALID_ARG;
+  if (g.dtype < SPD_F32 || g.dtype > SPD_U8) return SPD_ERR_INVALID_ARG;
+  if (g.dtype == SPD_U8) return SPD_ERR_UNSUPPORTED;  // the compact rows need -inf past a row's ends
+  const int64_t bpr = g.nt / kPropBlock;
+  if (max_blocks > g.ndm * bpr) max_blocks = g.ndm * bpr;
+  // geometry of the grid: widest width and largest start separation
+  spd_plan_desc d = g;
+  d.ndm = 1;
+  d.nt = 1 << 16;
+  d.ld = d.nt;
+  spd_plan* probe = nullptr;
+  spd_status st = spd_plan_create(&d, &probe);
+  if (st != SPD_OK) return st;
+  const int lend = probe->lend;
+  int sep = 1;
+  for (int32_t v : probe->seps) sep = v > sep ? v : sep;
+  spd_plan_destroy(probe);
+  if (kPropBlock % sep) return SPD_ERR_UNSUPPORTED;  // every level's starts must fall on block starts
+  const int left = ((std::max(peak_radius, 1) + sep - 1) / sep) * sep;
+  // after the block: its right-hand peak-test neighbours and their widest boxcars
+  const int width = left + kPropBlock + peak_radius + lend;
+  const int64_t ld_c = ((int64_t)width + 63) / 64 * 64;  // 16-byte aligned rows of any input type
+  d = g;
+  d.ndm = max_blocks;
+  d.nt = width;
+  d.ld = ld_c;
+  spd_plan* plan = nullptr;
+  st = spd_plan_create(&d, &plan);
+  if (st != SPD_OK) return st;
+  spd_proposal* q = new (std::nothrow) spd_proposal();
+  if (!q) {
+    spd_plan_destroy(plan);
+    return SPD_ERR_HOST_ALLOC;
+  }
+  q->plan = *plan;
+  spd_plan_destroy(plan);
+  // the block's starts and the right-hand neighbours of its peak test; the
+  // samples after them only feed boxcars
+  const int64_t ns = (int64_t)left + kPropBlock + peak_radius;
+  q->plan.n_starts = ns;
+  q->plan.tiles_per_row = (ns + q->plan.tile - 1) / q->plan.tile;
+  q->src = g;
+  q->radius = peak_radius;
+  q->left = left;
+  q->width = width;
+  q->ld_c = ld_c;
+  q->max_blocks = max_blocks;
+  q->bpr = bpr;
+  *out = q;
+  return SPD_OK;
+}
+
+spd_status spd_proposal_destroy(spd_proposal* prop) {
+  delete prop;
+  return SPD_OK;
+}
+
+spd_status spd_proposal_workspace_size(const spd_proposal* prop, size_t* bytes) {
+  if (!prop || !bytes) return SPD_ERR_INVALID_ARG;
+  *bytes = PropLayout(*prop).total;
+  return SPD_OK;
+}
+
+spd_status spd_proposal_widths(const spd_proposal* prop, int32_t* widths, int32_t* seps, int32_t cap, int32_t* n) {
+  if (!prop) return SPD_ERR_INVALID_ARG;
+  return spd_plan_widths(&prop->plan, widths, seps, cap, n);
+}
+
+}  // extern "C"
+
+namespace {
+spd_status check_proposal_args(const spd_proposal* prop, const void* d_x, const spd_noise* noise, float threshold,
+                               spd_candidate* d_out, int64_t cap, int64_t* d_count, void* d_ws, size_t ws_bytes) {
+  if (!prop || !d_x || !noise || !d_count || cap < 0 || (cap > 0 && !d_out) || std::isnan(threshold))
+    return SPD_ERR_INVALID_ARG;
+  if (noise->mode != 0 && noise->mode != 1) return SPD_ERR_INVALID_ARG;
+  if (!noise->mu || !noise->sigma || ((uintptr_t)noise->mu % 4) || ((uintptr_t)noise->sigma % 4) ||
+      ((uintptr_t)d_count % 8) || ((uintptr_t)d_out % 8) || ((uintptr_t)d_x % dtype_size(prop->src.dtype)))
+    return SPD_ERR_INVALID_ARG;
+  if (ws_bytes < PropLayout(*prop).total) return SPD_ERR_WORKSPACE_TOO_SMALL;
+  if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0) return SPD_ERR_INVALID_ARG;
+  return SPD_OK;
+}
+
+// Steps 3 of spd_propose_search (also spd_search_blocks): gather the n blocks
+// `ids` (device, increasing) and their rows' statistics, search them and select
+// their candidates with the block map.  Arguments already checked; n >= 1.
+spd_status search_blocks(const spd_proposal* prop, const void* d_x, const spd_noise* noise, const int64_t* ids,
+                         int64_t n, float threshold, spd_candidate* d_out, int64_t cap, int64_t* d_count,
+                         void* d_ws, cudaStream_t s) {
+  const spd_plan_desc& g = prop->src;
+  const PropLayout L(*prop);
+  char* ws = static_cast<char*>(d_ws);
+  const int esize = dtype_size(g.dtype);
+  const bool vec = (uintptr_t)d_x % 16 == 0 && (g.ld * esize) % 16 == 0;
+  void* xc = ws + L.xc;
+  float* yc = reinterpret_cast<float*>(ws + L.yc);
+  uint16_t* wc = reinterpret_cast<uint16_t*>(ws + L.wc);
+  float* muc = reinterpret_cast<float*>(ws + L.muc);
+  float* sgc = reinterpret_cast<float*>(ws + L.sgc);
+  cudaError_t e = spd::launch_net_gather(d_x, g.dtype, esize, g.ndm, g.nt, g.ld, ids, n, kPropBlock, prop->left,
+                                         prop->width, xc, prop->ld_c, vec, s);
+  const int64_t len = noise->mode == 1 ? (int64_t)prop->plan.widths.size() : 1;
+  if (e == cudaSuccess) e = spd::launch_gather_rows(noise->mu, len, ids, n, prop->bpr, g.ndm, 0.0f, muc, s);
+  if (e == cudaSuccess) e = spd::launch_gather_rows(noise->sigma, len, ids, n, prop->bpr, g.ndm, 1.0f, sgc, s);
+  if (e != cudaSuccess) return SPD_ERR_CUDA;
+  spd_plan q = prop->plan;  // the compact rows of this call
+  q.desc.ndm = n;
+  const spd_noise nc{noise->mode, muc, sgc};
+  spd_status st = do_execute(&q, xc, &nc, yc, wc, ws + L.ws, L.ws_bytes, s);
+  if (st != SPD_OK) return st;
+  const BlockMap map{prop->left, prop->left + kPropBlock, ids, prop->bpr, g.nt, kPropBlock};
+  return do_candidates(&q, yc, wc, threshold, prop->radius, d_out, cap, d_count, ws + L.ws, L.ws_bytes, true, s,
+                       &map);
+}
+}  // namespace
+
+extern "C" {
+
+spd_status spd_search_blocks(const spd_proposal* prop, const void* d_x, const spd_noise* noise,
+                             const int64_t* d_ids, int64_t n_ids, float threshold, spd_candidate* d_out,
+                             int64_t cap, int64_t* d_count, void* d_ws, size_t ws_bytes, spd_stream_t stream) {
+  spd_status st = check_proposal_args(prop, d_x, noise, threshold, d_out, cap, d_count, d_ws, ws_bytes);
+  if (st != SPD_OK) return st;
+  if (n_ids < 0 || (n_ids > 0 && (!d_ids || ((uintptr_t)d_ids % 8)))) return SPD_ERR_INVALID_ARG;
+  if (n_ids > prop->max_blocks) return SPD_ERR_BUFFER_TOO_SMALL;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n_ids == 0) return check_cuda(cudaMemsetAsync(d_count, 0, sizeof(int64_t), s));
+  return search_blocks(prop, d_x, noise, d_ids, n_ids, threshold, d_out, cap, d_count, d_ws, s);
+}
+
+spd_status spd_propose_search(const spd_proposal* prop, const float* d_params, const void* d_x,
+                              const spd_noise* noise, float logit_threshold, float threshold,
+                              spd_candidate* d_out, int64_t cap, int64_t* d_count, int64_t* n_blocks,
+                              void* d_ws, size_t ws_bytes, spd_stream_t stream) {
+  if (n_blocks) *n_blocks = 0;
+  spd_status st = check_proposal_args(prop, d_x, noise, threshold, d_out, cap, d_count, d_ws, ws_bytes);
+  if (st != SPD_OK) return st;
+  if (!d_params || ((uintptr_t)d_params % 4) || std::isnan(logit_threshold)) return SPD_ERR_INVALID_ARG;
+  const spd_plan_desc& g = prop->src;
+  const PropLayout L(*prop);
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(d_ws);
+  const int64_t nw = (int64_t)prop->plan.widths.size();
+  const int64_t nblk = g.ndm * prop->bpr;
+  const int esize = dtype_size(g.dtype);
+  const bool vec = (uintptr_t)d_x % 16 == 0 && (g.ld * esize) % 16 == 0;
+  float* dec = reinterpret_cast<float*>(ws + L.dec);
+  float* logits = reinterpret_cast<float*>(ws + L.logits);
+  int64_t* ids = reinterpret_cast<int64_t*>(ws + L.ids);
+  int64_t* cnt = reinterpret_cast<int64_t*>(ws + L.cnt);
+  // the network reads each row normalised by its width-1 statistics
+  const float* mu0 = noise->mu;
+  const float* sg0 = noise->sigma;
+  cudaError_t e = cudaSuccess;
+  if (noise->mode == 1) {
+    mu0 = reinterpret_cast<const float*>(ws + L.mu0);
+    sg0 = reinterpret_cast<const float*>(ws + L.sg0);
+    e = cudaMemcpy2DAsync(ws + L.mu0, sizeof(float), noise->mu, nw * sizeof(float), sizeof(float), g.ndm,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(ws + L.sg0, sizeof(float), noise->sigma, nw * sizeof(float), sizeof(float), g.ndm,
+                            cudaMemcpyDeviceToDevice, s);
+  }
+  if (e == cudaSuccess) e = spd::launch_net_decimate(d_x, g.dtype, esize, g.ndm, g.nt, g.ld, vec, mu0, sg0, dec, s);
+  if (e == cudaSuccess) e = spd::launch_net_forward(d_params, dec, nblk, logits, s);
+  if (e == cudaSuccess) e = spd::launch_net_select(logits, nblk, logit_threshold, ids, nblk, cnt, s);
+  // the number of flagged blocks sizes the rest: read it back
+  int64_t n = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n, cnt, sizeof(n), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return SPD_ERR_CUDA;
+  if (n_blocks) *n_blocks = n;
+  if (n > prop->max_blocks) return SPD_ERR_BUFFER_TOO_SMALL;
+  if (n == 0) return check_cuda(cudaMemsetAsync(d_count, 0, sizeof(int64_t), s));
+  return search_blocks(prop, d_x, noise, ids, n, threshold, d_out, cap, d_count, d_ws, s);
 }
 
 }  // extern "C"

@@ -486,6 +486,7 @@ cudaError_t launch_bd(const spd_plan& plan, const SearchParams& p, size_t smem, 
 }  // namespace
 
 size_t boxdit_smem_bytes(const spd_plan& plan, bool table) {
+  if (plan.bd_general) return boxdit_gen_smem_bytes(plan, table);
   const int nab = table ? (int)plan.widths.size() : 0;
   switch (plan.k) {
     case 8: return bd_smem<8>(plan.top, nab);
@@ -512,6 +513,7 @@ cudaError_t launch_persistent(KernelT kern, size_t smem, int64_t units, const Se
 }  // namespace
 
 cudaError_t launch_boxdit_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
+  if (plan.bd_general) return launch_boxdit_gen_batch(plan, p, s);
   const size_t smem = boxdit_smem_bytes(plan, false);
   const bool coarse = plan.top >= kRing0;
   switch (plan.k) {
@@ -529,6 +531,7 @@ cudaError_t launch_boxdit_batch(const spd_plan& plan, const SearchParams& p, cud
 }
 
 cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
+  if (plan.bd_general) return launch_boxdit_gen(plan, p, s);
   const bool table = p.table != 0;
   const size_t smem = boxdit_smem_bytes(plan, table);
   switch (plan.k) {

@@ -53,16 +53,20 @@ static_assert(sizeof(spd_candidate) == 24 && offsetof(spd_candidate, row) == 0 &
 
 __device__ __forceinline__ float key_to_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
 
-__device__ __forceinline__ bool is_cand(const float* __restrict__ y, int64_t s, int64_t nt,
+// neighbours are read only inside [lo, hi) (the row, or for a mapped row the
+// part of it that lies inside the original series)
+__device__ __forceinline__ bool is_cand(const float* __restrict__ y, int64_t s, int64_t lo, int64_t hi,
                                         float thr, int R) {
   const float v = y[s];
   if (!(v >= thr)) return false;
   for (int q = 1; q <= R; ++q) {
-    if (s - q >= 0 && !(v > y[s - q])) return false;
-    if (s + q < nt && !(v >= y[s + q])) return false;
+    if (s - q >= lo && !(v > y[s - q])) return false;
+    if (s + q < hi && !(v >= y[s + q])) return false;
   }
   return true;
 }
+
+__device__ __forceinline__ bool in_window(const CandParams& p, int64_t s) { return s >= p.s_lo && s < p.s_hi; }
 
 __device__ __forceinline__ int warp_sum(int v) {
 #pragma unroll
@@ -75,12 +79,20 @@ struct TileSpan {
   const float* y;
   const uint16_t* w;
   int64_t row, t0, end;
+  int64_t lo, hi;  // the starts whose SNRs the peak test may read
   __device__ TileSpan(const CandParams& p, int64_t tile) {
     row = tile / p.tiles_per_row;
     t0 = (tile % p.tiles_per_row) * (int64_t)p.tile;
     end = (t0 + p.tile < p.nt) ? t0 + p.tile : p.nt;
     y = p.snr + row * p.ld;
     w = p.widx + row * p.ld;
+    lo = 0;
+    hi = p.nt;
+    if (p.row_ids) {  // start s of this row is start s + off of the original one
+      const int64_t off = (p.row_ids[row] % p.map_bpr) * p.map_block - p.s_lo;
+      lo = -off > 0 ? -off : 0;
+      hi = p.map_nt - off < p.nt ? p.map_nt - off : p.nt;
+    }
   }
 };
 
@@ -115,7 +127,8 @@ __global__ void __launch_bounds__(kCandThreads) cand_count_kernel(const CandPara
         load_block(ts, b, lane, v);
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
-          if (v[u] >= p.thr) c += is_cand(ts.y, b + u * 32 + lane, p.nt, p.thr, p.radius) ? 1 : 0;
+          if (v[u] >= p.thr && in_window(p, b + u * 32 + lane))
+            c += is_cand(ts.y, b + u * 32 + lane, ts.lo, ts.hi, p.thr, p.radius) ? 1 : 0;
       }
       c = warp_sum(c);
       if (lane == src) mine = c;
@@ -186,16 +199,22 @@ __global__ void __launch_bounds__(kCandThreads, 1) cand_write_kernel(const CandP
         static_for<0, kUnroll>([&](auto U) {
           constexpr int u = decltype(U)::value;
           const int64_t s = b + u * 32 + lane;
-          const bool f = v[u] >= p.thr && is_cand(ts.y, s, p.nt, p.thr, p.radius);
+          const bool f = v[u] >= p.thr && in_window(p, s) && is_cand(ts.y, s, ts.lo, ts.hi, p.thr, p.radius);
           const unsigned bal = __ballot_sync(kFull, f);
           if (f) {
             const int64_t pos = base + __popc(bal & below);
             if (pos < p.cap) {  // the 24-byte record as three 8-byte stores
               const int wi = (int)ts.w[s];
               const int wd = p.width_mode ? p.width_tab[wi] : wi + 1;
+              int64_t orow = ts.row, ostart = s;
+              if (p.row_ids) {  // a searched block back to its row and start
+                const int64_t blk = p.row_ids[ts.row];
+                orow = blk / p.map_bpr;
+                ostart = (blk % p.map_bpr) * p.map_block + (s - p.s_lo);
+              }
               int2* o = reinterpret_cast<int2*>(p.out + pos);
-              o[0] = make_int2((int)ts.row, wi);
-              *reinterpret_cast<long long*>(o + 1) = (long long)s;
+              o[0] = make_int2((int)orow, wi);
+              *reinterpret_cast<long long*>(o + 1) = (long long)ostart;
               o[2] = make_int2(__float_as_int(v[u]), wd);
             }
           }

@@ -59,6 +59,11 @@ constexpr int64_t kStaticCandTiles = 262144;  // candidate tiles spd_candidates_
 
 enum Family { kExhaustive = 0, kBoxdit = 1, kIgrid = 2 };
 
+// General BoxDIT kernel (spd_boxdit_gen.cu): offsets of its shared-memory
+// regions in SearchParams::gen_off, and the largest L^i_max of a plan.
+enum BdgRegion { kBdgX0 = 0, kBdgXA, kBdgXB, kBdgBA, kBdgBB, kBdgY, kBdgW, kBdgAB, kBdgOffsets };
+constexpr int kMaxBoxditK = 256;
+
 // Search kernel parameters (passed by value; lives in the constant bank).
 struct SearchParams {
   const void* x;        // [ndm][ld] samples of type dtype
@@ -96,6 +101,12 @@ struct SearchParams {
   int32_t* status;                // bit r: a wait for range r's ready flag ran out
   int64_t wait_ns;                // limit of one wait
   int32_t ctas_per_sm;            // persistent CTAs per SM (0: as many as fit)
+  // general BoxDIT: block counts k_i of every level, window lengths of the
+  // decimated series, shared-memory offsets (floats) and 1/sqrt(L) per width
+  int32_t lvl_k[kMaxLevels];
+  int32_t gen_len[kMaxLevels];
+  int32_t gen_off[kBdgOffsets];
+  float wscale[kMaxGridWidths];
   BatchRange ranges[kMaxRanges];
 };
 
@@ -129,6 +140,17 @@ struct CandParams {
   float thr;
   int32_t width_mode;      // 0: width = index + 1 (exhaustive); 1: width_tab[index]
   int32_t width_tab[512];  // plan widths (index -> samples) when width_mode == 1
+  // only starts in [s_lo, s_hi) are candidates (their peak test still reads the
+  // neighbours below nt); default [0, nt)
+  int64_t s_lo, s_hi;
+  // proposal search (spd_propose_search): row k of the searched series is block
+  // row_ids[k] = r * map_bpr + b of the original one; records are written with
+  // row r and start b * map_block + s - s_lo.  nullptr: records as searched.
+  // The peak test of a mapped row only reads neighbours inside the original
+  // series (map_nt samples per row), as a search of the whole row would.
+  const int64_t* row_ids;
+  int64_t map_bpr, map_nt;
+  int32_t map_block;
 };
 
 }  // namespace spd
@@ -136,7 +158,9 @@ struct CandParams {
 struct spd_plan {
   spd_plan_desc desc;
   int family;
-  int k;          // BoxDIT L^i_max
+  int k;          // BoxDIT L^i_max of the streaming kernel (8, 16 or 32); 0: general kernel
+  bool bd_general = false;  // BoxDIT served by the general kernel (spd_boxdit_gen.cu)
+  std::vector<int32_t> lvl_k;  // BoxDIT L^i_max of every level
   int d, pl;      // IGRID depth and log2(layers)
   int top;        // last level index
   int n_top;      // block counts used on the last level
@@ -160,6 +184,12 @@ cudaError_t launch_igrid_coded(const spd_plan& plan, const SearchParams& p, size
 size_t igrid_smem_bytes(const spd_plan& plan, bool table);
 cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
+// general BoxDIT (spd_boxdit_gen.cu): layout of a plan with tiles of T starts
+// (window lengths into len[kMaxLevels], offsets into off[kBdgOffsets]; returns floats)
+int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off);
+size_t boxdit_gen_smem_bytes(const spd_plan& plan, bool table);
+cudaError_t launch_boxdit_gen(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
+cudaError_t launch_boxdit_gen_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 // Shared-memory attribute, CTAs per SM (of `threads` threads each) and SM count
 // of a persistent kernel, set and queried on the first call per (kernel, device,
 // shared memory, threads) and
@@ -181,6 +211,8 @@ cudaError_t launch_net_select(const float* logits, int64_t n, float thr, int64_t
 cudaError_t launch_net_gather(const void* x, int dtype, int esize, int64_t ndm, int64_t nt, int64_t ld,
                               const int64_t* list, int64_t n, int block, int left, int width, void* out,
                               int64_t ld_out, bool vec, cudaStream_t s);
+cudaError_t launch_gather_rows(const float* src, int64_t len, const int64_t* ids, int64_t n, int64_t bpr,
+                               int64_t ndm, float fill, float* dst, cudaStream_t s);
 cudaError_t launch_boxdit_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_candidates(const spd_plan& plan, CandParams& p, cudaStream_t s);
 cudaError_t launch_candidates_static(const spd_plan& plan, CandParams& p, cudaStream_t s);

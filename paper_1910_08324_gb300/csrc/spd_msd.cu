@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
   __shared__ double red[kThreads / 32][kMsdMaxLevels][2];
   __shared__ long long redn[kThreads / 32][kMsdMaxLevels];
   __shared__ int done, failed;
+  __shared__ float kahan[16 * kThreads];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t row = blockIdx.x;
   const int nlev = p.nlev;
@@ -226,12 +227,18 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
   const float limb = (kb && kb < nlev) ? clim[kb] : -1.0f;
   const int endb = (lane >= 1 && lane < 8) ? ((lane >> (jl + 1)) + 1) << kb : kC;  // block end in its chunk
 
-  float sw[4], sw2[4], cw[4], cw2[4];  // levels 0..3: compensated sums over chunks
-  float pw[4], pw2[4];                 // ... and over the steps of the current chunk
-  float2 qw = make_float2(0.0f, 0.0f), qw2 = qw;  // level 0 in packed pairs (first pass)
-  int cn[4];
+  // levels 0..3: compensated sums over chunks (shared memory, one column per
+  // thread: they change once per chunk), and sums over the steps of the
+  // current chunk (registers)
+  float* kc = kahan + t;  // [4 sums][4 levels][kThreads]
 #pragma unroll
-  for (int k = 0; k < 4; ++k) sw[k] = sw2[k] = cw[k] = cw2[k] = pw[k] = pw2[k] = 0.0f, cn[k] = 0;
+  for (int i = 0; i < 16; ++i) kc[i * kThreads] = 0.0f;
+  float pw[4], pw2[4];
+  float2 qw = make_float2(0.0f, 0.0f), qw2 = qw;  // levels 0, 1, 2 in packed pairs (first pass)
+  float2 q1 = qw, q12 = qw, q2 = qw, q22 = qw;
+  int cn[4], nfast = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) pw[k] = pw2[k] = 0.0f, cn[k] = 0;
   // First pass (no limits yet): a whole step whose 256 samples are finite keeps
   // every value of levels 0..8, so its sums need no compare and no select and
   // run in packed pairs; other steps (and later passes) take the general form.
@@ -274,17 +281,21 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
         qw = __fadd2_rn(qw, w);
         qw2 = __ffma2_rn(w, w, qw2);
       }
-      auto add = [&](int k, float v) {
-        const float w = v - sh[k];
-        pw[k] += w;
-        pw2[k] = fmaf(w, w, pw2[k]);
-      };
 #pragma unroll
-      for (int i = 0; i < 4; ++i) add(1, p1[i]);
-      add(2, p2[0]);
-      add(2, p2[1]);
-      add(3, s3);
-      cn[0] += 8, cn[1] += 4, cn[2] += 2, cn[3] += 1;
+      for (int i = 0; i < 4; i += 2) {
+        const float2 w = __fadd2_rn(make_float2(p1[i], p1[i + 1]), make_float2(-sh[1], -sh[1]));
+        q1 = __fadd2_rn(q1, w);
+        q12 = __ffma2_rn(w, w, q12);
+      }
+      {
+        const float2 w = __fadd2_rn(make_float2(p2[0], p2[1]), make_float2(-sh[2], -sh[2]));
+        q2 = __fadd2_rn(q2, w);
+        q22 = __ffma2_rn(w, w, q22);
+      }
+      const float w3 = s3 - sh[3];
+      pw[3] += w3;
+      pw2[3] = fmaf(w3, w3, pw2[3]);
+      ++nfast;  // 8, 4, 2, 1 values of levels 0..3
       const float wa = has_a ? v - sha : 0.0f;
       sa += wa;
       sa2 = fmaf(wa, wa, sa2);
@@ -377,11 +388,19 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
       q = 0.0f;
       pw[0] += qw.x + qw.y;
       pw2[0] += qw2.x + qw2.y;
-      qw = qw2 = make_float2(0.0f, 0.0f);
+      pw[1] += q1.x + q1.y;
+      pw2[1] += q12.x + q12.y;
+      pw[2] += q2.x + q2.y;
+      pw2[2] += q22.x + q22.y;
+      qw = qw2 = q1 = q12 = q2 = q22 = make_float2(0.0f, 0.0f);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        kahan_add(sw[k], cw[k], pw[k]);
-        kahan_add(sw2[k], cw2[k], pw2[k]);
+        float s1 = kc[k * kThreads], c1 = kc[(8 + k) * kThreads];
+        float s2 = kc[(4 + k) * kThreads], c2 = kc[(12 + k) * kThreads];
+        kahan_add(s1, c1, pw[k]);
+        kahan_add(s2, c2, pw2[k]);
+        kc[k * kThreads] = s1, kc[(8 + k) * kThreads] = c1;
+        kc[(4 + k) * kThreads] = s2, kc[(12 + k) * kThreads] = c2;
         pw[k] = pw2[k] = 0.0f;
       }
     }
@@ -405,9 +424,9 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
     double a, b;
     long long n;
     if (k < 4) {
-      a = (double)sw[k] - (double)cw[k];
-      b = (double)sw2[k] - (double)cw2[k];
-      n = cn[k];
+      a = (double)kc[k * kThreads] - (double)kc[(8 + k) * kThreads];
+      b = (double)kc[(4 + k) * kThreads] - (double)kc[(12 + k) * kThreads];
+      n = cn[k] + ((long long)nfast << (3 - k));
     } else if (k < 9) {
       a = ka == k ? sa : 0.0, b = ka == k ? sa2 : 0.0, n = ka == k ? na : 0;
     } else {

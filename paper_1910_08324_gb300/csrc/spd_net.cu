@@ -724,6 +724,32 @@ cudaError_t launch_net_gather(const void* x, int dtype, int esize, int64_t ndm, 
   return cudaGetLastError();
 }
 
+namespace {
+// dst[k][j] = src[ids[k] / bpr][j], j < len: the noise statistics of each
+// flagged block's row (len 1 for white noise, the plan's widths for a table);
+// `fill` for an id outside [0, ndm * bpr) (its gathered samples are all -inf)
+__global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restrict__ src, int64_t len,
+                                                          const int64_t* __restrict__ ids, int64_t n, int64_t bpr,
+                                                          int64_t ndm, float fill, float* __restrict__ dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * len; i += stride) {
+    const int64_t k = i / len, j = i - k * len;
+    const int64_t id = ids[k];
+    dst[i] = (id >= 0 && id < ndm * bpr) ? src[(id / bpr) * len + j] : fill;
+  }
+}
+}  // namespace
+
+cudaError_t launch_gather_rows(const float* src, int64_t len, const int64_t* ids, int64_t n, int64_t bpr,
+                               int64_t ndm, float fill, float* dst, cudaStream_t s) {
+  const int64_t total = n * len;
+  if (total == 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  gather_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, len, ids, n, bpr, ndm, fill, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_net_decimate(const void* x, int dtype, int esize, int64_t ndm, int64_t nt, int64_t ld,
                                 bool vec, const float* mu, const float* sigma, float* out, cudaStream_t s) {
   const int64_t n = ndm * (nt / 16);

@@ -4,13 +4,16 @@ trained network flags.
 A block is 4096 input samples of one row; the network reads it as 256
 samples after an x16 decimation.  ``flag_blocks`` decimates the series and
 scores every block (``spd_net_decimate``, ``spd_net_forward``).
-``search_flagged`` then searches the flagged blocks at full resolution.  Each
-flagged block is copied into one compact series, together with
+``search_flagged`` then searches the flagged blocks at full resolution
+(``propose_and_search`` runs both as one C-ABI call, ``spd_propose_search``,
+with the same geometry and the record map on the device).  Each flagged block
+is copied into one compact series, together with
 
 * the ``radius`` samples before it, so that the peak test of its first start
   sees its left neighbours;
-* the samples that a boxcar starting in the block can reach (up to the plan's
-  widest width).
+* the ``radius`` starts after it (the right-hand neighbours of its peak test)
+  and the samples that a boxcar starting at any of these can reach (up to the
+  plan's widest width).
 
 Samples past the row's ends are -inf, the same value the kernels use past a
 row's end, so boxcars that would need them never count.  The compact series
@@ -107,66 +110,75 @@ def search_flagged(x, ids, mu, sigma, grid: dict, threshold: float = 6.0, radius
                    cap: int = 1 << 22, noise_mode: int = 0, stream=None):
     """Search the blocks ``ids`` (``select_blocks``) of ``x`` ([ndm, nt]) with the
     plan grid ``grid`` (``spd_plan_create`` keywords: algo, s_end, boxdit_lmax,
-    ..., dtype).  ``mu``/``sigma`` are the full series' statistics: [ndm] (white)
-    or [ndm, n_widths] of the same grid (``noise_mode`` 1).  The context before a
-    block is a whole number of the grid's largest start separation, so every
-    level's starts fall where they fall in a search of the whole row and each
-    block gets the outputs the plain search gives it.  Returns the candidate
-    records (numpy, rows and starts of ``x``, sorted by row and start)."""
+    ..., dtype): one ``spd_search_blocks`` call (gather, search, candidates with
+    the record map, on the device).  ``mu``/``sigma`` are the full series'
+    statistics: [ndm] (white) or [ndm, n_widths] of the same grid (``noise_mode``
+    1).  The context before a block is a whole number of the grid's largest
+    start separation, so every level's starts fall where they fall in a search
+    of the whole row and each block gets the outputs the plain search gives it.
+    Returns the candidate records (numpy, rows and starts of ``x``, sorted by row
+    and start)."""
     import torch
-    ndm, nt = x.shape
     n = ids.numel()
     if n == 0:
         return np.zeros(0, B.CANDIDATE_DTYPE)
     lend, sep = plan_geometry(grid)
     if BLOCK % sep:
         raise ValueError("grid start separation %d does not divide the %d-sample block" % (sep, BLOCK))
-    left = -(-max(radius, 1) // sep) * sep
-    xs, width = gather_blocks(x, ids, left, lend, grid.get("dtype", B.SPD_F32), stream=stream)
-    plan = B.spd_plan_create(ndm=n, nt=width, ld=xs.shape[1], **grid)
-    # evaluate only the block's starts (and the right-hand neighbours its peak test
-    # needs): the context after them only supplies samples
-    B.spd_plan_set_starts(plan, left + BLOCK + radius)
-    try:
-        Y = torch.empty(xs.shape, dtype=torch.float32, device=x.device)  # outputs share the row stride
-        W = torch.empty(xs.shape, dtype=torch.int16, device=x.device)
-        ws = torch.empty(plan.workspace_size(), dtype=torch.uint8, device=x.device)
-        bpr = nt // BLOCK
-        rows = ids // bpr
-        mu_r = mu[rows].contiguous()
-        sg_r = sigma[rows].contiguous()
-        out = torch.empty(cap * B.CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device=x.device)
-        cnt = torch.zeros(1, dtype=torch.int64, device=x.device)
-        B.search(plan, xs, mu_r, sg_r, Y, W, threshold, radius, out, cnt, ws, stream=stream,
-                 noise_mode=noise_mode)
-        k = int(cnt.item())
-        if k > cap:
-            raise B.SpdError(5, "search_flagged: %d candidates exceed cap %d" % (k, cap))
-        rec = B.records(out, k).copy()
-    finally:
-        plan.close()
-    # starts inside the blocks; the ids increase, so the records (in compact row,
-    # start order) come out in (row, start) order of the series
-    st = rec["start"]
-    rec = rec[(st >= left) & (st < left + BLOCK)]
-    blk = ids.cpu().numpy()[rec["row"]]
-    rec["start"] += (blk % bpr) * BLOCK - left
-    rec["row"] = blk // bpr
-    return rec
+    prop, ws = _proposal(grid, x, radius, need=n)
+    out = torch.empty(cap * B.CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device=x.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=x.device)
+    B.search_blocks(prop, x, mu, sigma, ids.contiguous(), out, cnt, ws, threshold, noise_mode=noise_mode,
+                    stream=stream)
+    k = int(cnt.item())
+    if k > cap:
+        raise B.SpdError(5, "search_flagged: %d candidates exceed cap %d" % (k, cap))
+    return B.records(out, k).copy()
+
+
+_PROPOSALS = {}  # (grid, shape, radius, device) -> (spd_proposal, its workspace)
+
+
+def _proposal(grid: dict, x, radius: int, need: int = 0):
+    import torch
+    ndm, nt = x.shape
+    key = (tuple(sorted(grid.items())), ndm, nt, x.stride(0), radius, str(x.device))
+    e = _PROPOSALS.get(key)
+    if e is None or e[0].max_blocks < need:
+        total = ndm * (nt // BLOCK)
+        mb = min(total, max(need, 4096, total // 16))
+        prop = B.spd_proposal_create(ndm=ndm, nt=nt, ld=x.stride(0), peak_radius=radius, max_blocks=mb, **grid)
+        e = (prop, torch.empty(prop.workspace_size(), dtype=torch.uint8, device=x.device))
+        _PROPOSALS[key] = e
+    return e
 
 
 def propose_and_search(params, x, mu_tab, sigma_tab, grid: dict, logit_threshold: float = 0.0,
                        threshold: float = 6.0, radius: int = 1, cap: int = 1 << 22, stream=None):
-    """The proposal path: decimate and score every block, select those above
-    ``logit_threshold`` and search them with per-width noise tables ``mu_tab``,
-    ``sigma_tab`` ([ndm, n_widths] of ``grid``; the network reads the width-1
-    entries).  Returns (records, number of searched blocks)."""
-    dtype = grid.get("dtype", B.SPD_F32)
-    logits, _ = flag_blocks(params, x, mu_tab[:, 0].contiguous(), sigma_tab[:, 0].contiguous(), dtype=dtype,
-                            stream=stream)
-    ids = select_blocks(logits, logit_threshold, stream=stream)
-    rec = search_flagged(x, ids, mu_tab, sigma_tab, grid, threshold, radius, cap, noise_mode=1, stream=stream)
-    return rec, ids.numel()
+    """The proposal path through one C-ABI call (``spd_propose_search``):
+    decimate and score every block, select those above ``logit_threshold`` and
+    search them with per-width noise tables ``mu_tab``, ``sigma_tab`` ([ndm,
+    n_widths] of ``grid``; the network reads the width-1 entries); records come
+    back in the series' (row, start).  The proposal object and its workspace are
+    kept per shape and grid (room for 1/16 of the blocks, grown when more are
+    flagged).  Returns (records, number of searched blocks)."""
+    import torch
+    out = torch.empty(cap * B.CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device=x.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=x.device)
+    prop, ws = _proposal(grid, x, radius)
+    try:
+        nb = B.propose_search(prop, params, x, mu_tab, sigma_tab, out, cnt, ws, logit_threshold, threshold,
+                              noise_mode=1, stream=stream)
+    except B.SpdError as err:
+        if err.status != 5:
+            raise
+        prop, ws = _proposal(grid, x, radius, need=err.n_blocks)  # more blocks flagged than it holds
+        nb = B.propose_search(prop, params, x, mu_tab, sigma_tab, out, cnt, ws, logit_threshold, threshold,
+                              noise_mode=1, stream=stream)
+    k = int(cnt.item())
+    if k > cap:
+        raise B.SpdError(5, "propose_and_search: %d candidates exceed cap %d" % (k, cap))
+    return B.records(out, k).copy(), nb
 
 
 def score(rec, pulses, snr_judge, ndm: int, nt: int, judge_threshold: float = 6.0):

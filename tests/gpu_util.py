@@ -22,6 +22,11 @@ ALGOS = {
     "bd8": lambda s: dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=8),
     "bd16": lambda s: dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=16),
     "bd32": lambda s: dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=32),
+    # other even L^i_max: the general BoxDIT kernel
+    "bd2": lambda s: dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=2),
+    "bd6": lambda s: dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=6),
+    "bd12": lambda s: dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=12),
+    "bd64": lambda s: dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=64),
     "dit": lambda s: dict(algo=spd.SPD_ALGO_IGRID, s_end=s, igrid_depth=0, igrid_layers=1),
     "ig0p2": lambda s: dict(algo=spd.SPD_ALGO_IGRID, s_end=s, igrid_depth=0, igrid_layers=2),
     "ig1p2": lambda s: dict(algo=spd.SPD_ALGO_IGRID, s_end=s, igrid_depth=1, igrid_layers=2),

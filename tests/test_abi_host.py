@@ -50,7 +50,8 @@ GRIDS = [
 ] + [
     ("bd%d_%d" % (k, s), dict(algo=spd.SPD_ALGO_BOXDIT, s_end=s, boxdit_lmax=k),
      (lambda k=k, s=s: oracle.grid_boxdit(k, s)))
-    for k in (8, 16, 32) for s in (1, 5, 32, 33, 100, 8192, 20000)
+    for k in (2, 6, 8, 12, 16, 32, 64) for s in (1, 5, 32, 33, 100, 8192, 20000)
+    if not (k == 64 and s == 20000)  # 576 widths: above the 512 a plan may hold
 ] + [
     ("ig%d_%d_%d" % (d, P, s), dict(algo=spd.SPD_ALGO_IGRID, s_end=s, igrid_depth=d, igrid_layers=P),
      (lambda d=d, P=P, s=s: oracle.grid_igrid(d, P, s)))
@@ -69,8 +70,10 @@ def test_plan_widths_equal_oracle_grid(name, kw, og):
 
 
 @pytest.mark.parametrize("kw", [
-    dict(algo=spd.SPD_ALGO_BOXDIT, s_end=100, boxdit_lmax=12),
     dict(algo=spd.SPD_ALGO_BOXDIT, s_end=100, boxdit_lmax=7),
+    dict(algo=spd.SPD_ALGO_BOXDIT, s_end=100, boxdit_lmax=0),
+    dict(algo=spd.SPD_ALGO_BOXDIT, s_end=100, boxdit_lmax=258),
+    dict(algo=spd.SPD_ALGO_BOXDIT, s_end=20000, boxdit_lmax=64),  # 576 widths
     dict(algo=spd.SPD_ALGO_IGRID, s_end=100, igrid_depth=1, igrid_layers=3),
     dict(algo=spd.SPD_ALGO_IGRID, s_end=100, igrid_depth=2, igrid_layers=2),
     dict(algo=spd.SPD_ALGO_IGRID, s_end=100, igrid_depth=4, igrid_layers=16),
@@ -166,6 +169,71 @@ def test_batch_validation():
     with pytest.raises(spd.SpdError) as e:
         spd.spd_batch_execute(b, [4096] * 5, [4096] * 5, [4096] * 5, [4096] * 5, [4096] * 5, 4096, 16)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("lmax,s_end,n_iter", [([2, 4, 6], 45, 0), ([6, 2], 3000, 0), ([32, 16, 8], 8192, 0),
+                                              ([8], 1, 10), ([12], 1, 6), ([4, 2], 1, 3), ([64, 2], 9000, 0)])
+def test_per_iteration_boxdit_plan_equals_oracle_grid(lmax, s_end, n_iter):
+    plan = spd.spd_plan_create_boxdit(lmax, s_end, ndm=2, nt=50000, n_iter=n_iter)
+    w, s = plan.widths()
+    g = oracle.grid_boxdit(lmax, s_end, n_iter)
+    assert np.array_equal(w, g.L) and np.array_equal(s, g.Ls)
+    assert plan.workspace_size() > 0
+
+
+def test_per_iteration_boxdit_plan_rules():
+    for lmax, n_iter in (([3], 0), ([4, 5], 0), ([0], 0), ([260], 0), ([], 0), ([8], 25), ([8], -1),
+                         ([2] * 25, 0)):
+        with pytest.raises(spd.SpdError) as e:
+            spd.spd_plan_create_boxdit(lmax if lmax else np.zeros(0, np.int32), 100, ndm=2, nt=1000,
+                                       n_iter=n_iter)
+        assert e.value.status == 1, (lmax, n_iter)
+    # widest width above 32768 or more than 512 widths
+    for lmax, s_end in (([2], 40000), ([256], 1000)):
+        with pytest.raises(spd.SpdError):
+            spd.spd_plan_create_boxdit(lmax, s_end, ndm=2, nt=1000)
+    # the general kernel's tiles are fixed: no segment length
+    plan = spd.spd_plan_create_boxdit([6, 2], 1000, ndm=2, nt=1 << 20)
+    with pytest.raises(spd.SpdError) as e:
+        spd.spd_plan_set_segment(plan, 16384)
+    assert e.value.status == 2
+
+
+def test_proposal_rules():
+    kw = dict(algo=spd.SPD_ALGO_IGRID, s_end=4096, igrid_depth=1, igrid_layers=4)
+    p = spd.spd_proposal_create(ndm=4, nt=1 << 16, max_blocks=10, **kw)
+    assert p.workspace_size() > 0 and len(p.widths()[0]) == len(oracle.grid_igrid(1, 4, 4096))
+    for bad, status in ((dict(nt=5000), 1), (dict(nt=4095), 1), (dict(dtype=spd.SPD_U8), 2),
+                        (dict(s_end=30000), 2), (dict(peak_radius=65), 1), (dict(max_blocks=0), 1),
+                        (dict(ndm=0), 1)):
+        a = dict(ndm=4, nt=1 << 16, max_blocks=10, **kw)
+        a.update(bad)
+        with pytest.raises(spd.SpdError) as e:
+            spd.spd_proposal_create(**a)
+        assert e.value.status == status, bad
+    lib = spd.load_library()
+    # argument checks come before any device work
+    import ctypes
+    nb = ctypes.c_int64(7)
+    assert lib.spd_propose_search(None, 256, 256, None, ctypes.c_float(0), ctypes.c_float(6), 256, 1, 256,
+                                  ctypes.byref(nb), 256, 1 << 30, None) == 1
+    assert nb.value == 0
+    ws = p.workspace_size()
+    nz = spd._binding._Noise(0, 256, 256)
+    h = ctypes.c_void_p(p.handle)
+    assert lib.spd_propose_search(h, 256, 256, ctypes.byref(nz), ctypes.c_float(0), ctypes.c_float(6), 256, 1,
+                                  256, None, 256, ws - 1, None) == 4  # workspace too small
+    assert lib.spd_propose_search(h, 256, 256, ctypes.byref(nz), ctypes.c_float(float("nan")),
+                                  ctypes.c_float(6), 256, 1, 256, None, 256, ws, None) == 1
+    assert lib.spd_propose_search(h, 256, 256, ctypes.byref(nz), ctypes.c_float(0), ctypes.c_float(6), 256, 1,
+                                  260, None, 256, ws, None) == 1  # misaligned count
+    # block search: more ids than the proposal holds, misaligned ids, short workspace
+    assert lib.spd_search_blocks(h, 256, ctypes.byref(nz), 256, 11, ctypes.c_float(6), 256, 1, 256, 256, ws,
+                                 None) == 5
+    assert lib.spd_search_blocks(h, 256, ctypes.byref(nz), 260, 3, ctypes.c_float(6), 256, 1, 256, 256, ws,
+                                 None) == 1
+    assert lib.spd_search_blocks(h, 256, ctypes.byref(nz), 256, 3, ctypes.c_float(6), 256, 1, 256, 256, ws - 1,
+                                 None) == 4
 
 
 def test_plan_segment_rules():

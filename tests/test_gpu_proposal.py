@@ -111,6 +111,71 @@ def test_search_flagged_equals_plain_search_on_those_blocks(name):
     assert np.array_equal(rec, ref[keep])
 
 
+GRIDS_ABI = dict(GRIDS)
+GRIDS_ABI["bd12_f32_table"] = (dict(algo=spd.SPD_ALGO_BOXDIT, s_end=3000, boxdit_lmax=12, dtype=spd.SPD_F32), 1)
+
+
+@pytest.mark.parametrize("name", list(GRIDS_ABI))
+def test_propose_search_abi_equals_plain_search_on_flagged_blocks(name):
+    """spd_propose_search (network, selection, gather, search and the record map
+    all on the device) gives exactly the plain search's candidates in the blocks
+    the network flags, in the series' (row, start) order."""
+    t = torch()
+    grid, mode = GRIDS_ABI[name]
+    ndm, nt = 6, 16 * P.BLOCK
+    x = spd_synth.device_noise(ndm, nt, 91)
+    tab = spd_synth.pulse_table(40, ndm, nt, 92, width_range=(1, 2048), snr_range=(6, 30))
+    spd_synth.device_inject_many(x, tab)
+    xs = x if grid["dtype"] == spd.SPD_F32 else x.half()
+    plan = spd.spd_plan_create(ndm=ndm, nt=nt, **grid)
+    ws = t.empty(plan.workspace_size(), dtype=t.uint8, device="cuda")
+    nw = len(plan.widths()[0])
+    if mode == 1:
+        mu, sg = t.empty((ndm, nw), device="cuda"), t.empty((ndm, nw), device="cuda")
+        spd.noise_stats(plan, xs, mu, sg, ws)
+    else:
+        mu, sg = t.zeros(ndm, device="cuda"), t.ones(ndm, device="cuda")
+    Y = t.empty((ndm, nt), device="cuda")
+    W = t.empty((ndm, nt), dtype=t.int16, device="cuda")
+    cap = 1 << 18
+    out = t.empty(cap * 24, dtype=t.uint8, device="cuda")
+    cnt = t.zeros(1, dtype=t.int64, device="cuda")
+    spd.search(plan, xs, mu, sg, Y, W, 3.0, 2, out, cnt, ws, noise_mode=mode)
+    ref = spd.records(out, int(cnt.item())).copy()
+    params = t.from_numpy(net.init_params(11)).cuda()
+    # the blocks the network flags, from the separate calls
+    mu1 = (mu[:, 0] if mode == 1 else mu).contiguous()
+    sg1 = (sg[:, 0] if mode == 1 else sg).contiguous()
+    logits, _ = P.flag_blocks(params, xs, mu1, sg1, dtype=grid["dtype"])
+    thr = float(np.quantile(logits.cpu().numpy(), 0.6))
+    sel = P.select_blocks(logits, thr).cpu().numpy()
+    assert 10 < len(sel) < ndm * (nt // P.BLOCK)
+    prop = spd.spd_proposal_create(ndm=ndm, nt=nt, peak_radius=2, max_blocks=64, **grid)
+    assert np.array_equal(prop.widths()[0], plan.widths()[0])
+    pws = t.empty(prop.workspace_size(), dtype=t.uint8, device="cuda")
+    pout = t.empty(cap * 24, dtype=t.uint8, device="cuda")
+    pcnt = t.full((1,), -1, dtype=t.int64, device="cuda")
+    nb = spd.propose_search(prop, params, xs, mu, sg, pout, pcnt, pws, logit_threshold=thr, threshold=3.0,
+                            noise_mode=mode)
+    assert nb == len(sel)
+    rec = spd.records(pout, int(pcnt.item()))
+    keep = np.isin(ref["row"].astype(np.int64) * (nt // P.BLOCK) + ref["start"] // P.BLOCK, sel)
+    assert len(rec) > 20
+    assert np.array_equal(rec, ref[keep])
+    # a short record buffer keeps the first records and the true count
+    short = t.empty(7 * 24, dtype=t.uint8, device="cuda")
+    spd.propose_search(prop, params, xs, mu, sg, short, pcnt, pws, logit_threshold=thr, threshold=3.0,
+                       noise_mode=mode)
+    assert int(pcnt.item()) == len(rec) and np.array_equal(spd.records(short, 7), rec[:7])
+    # nothing flagged: no records; more flagged blocks than max_blocks: refused
+    assert spd.propose_search(prop, params, xs, mu, sg, pout, pcnt, pws, logit_threshold=1e30,
+                              noise_mode=mode) == 0
+    assert int(pcnt.item()) == 0
+    with pytest.raises(spd.SpdError) as e:
+        spd.propose_search(prop, params, xs, mu, sg, pout, pcnt, pws, logit_threshold=-1e30, noise_mode=mode)
+    assert e.value.status == 5
+
+
 def oracle_pulse_snr(x, pulses, mu, sigma, plan, width_ratio=4.0):
     """The ideal search's SNR of each injected pulse, from the FP64 oracle: the
     exhaustive grid of ``plan`` searched (table noise mu, sigma of the pulse's row)
