@@ -65,11 +65,22 @@ ALGOS = {
     "bd24": dict(algo=1, boxdit_lmax=24),
     "exh": dict(algo=0),
 }
-SEARCH_SOURCES = ["paper_1910_08324_gb300/csrc/spd_igrid.cu", "paper_1910_08324_gb300/csrc/spd_igrid.cuh",
-                  "paper_1910_08324_gb300/csrc/spd_igrid_coded.cu", "paper_1910_08324_gb300/csrc/spd_search.cu",
-                  "paper_1910_08324_gb300/csrc/spd_boxdit.cu", "paper_1910_08324_gb300/csrc/spd_boxdit_gen.cu",
-                  "paper_1910_08324_gb300/csrc/spd_common.cuh",
-                  "paper_1910_08324_gb300/csrc/spd_internal.h"]
+# the sources each search kernel family compiles from (a traffic record applies
+# only while they are unchanged)
+_CSRC = "paper_1910_08324_gb300/csrc/"
+_COMMON = [_CSRC + "spd_common.cuh", _CSRC + "spd_internal.h"]
+FAMILY_SOURCES = {
+    "igrid": [_CSRC + "spd_igrid.cu", _CSRC + "spd_igrid.cuh", _CSRC + "spd_igrid_coded.cu"] + _COMMON,
+    "boxdit": [_CSRC + "spd_boxdit.cu", _CSRC + "spd_boxdit_gen.cu"] + _COMMON,
+    "exhaustive": [_CSRC + "spd_search.cu"] + _COMMON,
+}
+SEARCH_SOURCES = sorted({f for v in FAMILY_SOURCES.values() for f in v})
+
+
+def algo_family(algo):
+    return {0: "exhaustive", 1: "boxdit", 2: "igrid"}[ALGOS[algo]["algo"]]
+
+
 # uneven DM ranges of one batched search: (DM trials, time decimation) of a 2,097,152-sample base
 BATCH_RANGES = [(1024, 1), (1024, 2), (768, 4), (512, 8), (256, 16)]
 BATCH_BASE = 2097152
@@ -156,9 +167,9 @@ def binding_roofline(cand_per_sample, bytes_per_sample, samples, kernel_ms, sm_c
     return r
 
 
-def source_hash():
+def source_hash(algo="ig1"):
     h = hashlib.sha256()
-    for s in SEARCH_SOURCES:
+    for s in FAMILY_SOURCES[algo_family(algo)]:
         with open(os.path.join(ROOT, s), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -174,7 +185,7 @@ def recorded_traffic(algo, ndm, nt):
     with open(p) as f:
         d = json.load(f)
     e = d.get(algo)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(algo.split("_")[0]):
         return None
     return float(e["bytes_per_sample"]) * ndm * nt
 

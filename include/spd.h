@@ -172,8 +172,8 @@ spd_status spd_plan_create(const spd_plan_desc *desc, spd_plan **out);
  * boxdit_lmax are ignored.  The widest width must not exceed 32768 and the grid
  * must have at most 512 widths.  A plan whose L^i_max are all 8, all 16 or all
  * 32 runs on the BD-K streaming kernels, any other on the general BoxDIT
- * kernel (tiles of 2048 or 4096 starts; spd_plan_set_segment then returns
- * SPD_ERR_UNSUPPORTED).  Host only.  Errors as spd_plan_create.
+ * kernel (tiles of 2048 to 8192 starts, see spd_plan_set_segment).  Host only.
+ * Errors as spd_plan_create.
  */
 spd_status spd_plan_create_boxdit(const spd_plan_desc *desc, const int32_t *lmax, int32_t n_lmax,
                                   int32_t n_iter, spd_plan **out);
@@ -361,8 +361,10 @@ spd_status spd_noise_stats(const spd_plan *plan, const void *d_x, float outlier_
  * multiple of 16384 and of 2^top (top: the plan's last level), at most 2^24;
  * the default is the longest of 524288, 262144 and 131072 that gives at least
  * 2432 segments (ndm x segments per row).  Host only.  SPD_ERR_INVALID_ARG otherwise (and for
- * exhaustive plans); SPD_ERR_UNSUPPORTED for a BoxDIT plan on the general kernel
- * (its tiles are fixed by the plan).
+ * exhaustive plans).  A BoxDIT plan on the general kernel (spd_plan_create_boxdit)
+ * takes tiles of 2048, 4096 or 8192 starts here instead (one CTA per tile; the
+ * default is 4096 when two CTAs fit on an SM, else 2048); SPD_ERR_UNSUPPORTED
+ * when a tile's shared memory would exceed 227 KB.
  */
 spd_status spd_plan_set_segment(spd_plan *plan, int32_t segment);
 

@@ -12,7 +12,10 @@ description (grid, dtype, range shapes), so a later run with the same key
 reuses it without timing.  A CTA's thread count (256) and starts per thread (8)
 are not tuned: one CTA step covers a 2 048-sample chunk, 8 starts per thread,
 and the kernels' level layout (which thread owns which coarse position, which
-warp builds levels 9 to 11) is built on that chunk.
+warp builds levels 9 to 11) is built on that chunk.  The general BoxDIT kernel
+(any other L^i_max) is the exception: its starts per CTA, a tile of
+``BOXDIT_GENERAL_TILES``, are what ``spd_plan_set_segment`` sets for its plans,
+and ``tune_segment`` tunes them like segment lengths.
 """
 from __future__ import annotations
 
@@ -21,6 +24,7 @@ import os
 import tempfile
 
 DEFAULT_CANDIDATES = (16384, 32768, 65536, 131072, 262144)
+BOXDIT_GENERAL_TILES = (2048, 4096, 8192)  # starts per CTA of the general BoxDIT kernel
 
 
 def key_of(algo: int, s_end: int, dtype: int, shapes, boxdit_lmax: int = 0, igrid_depth: int = 0,

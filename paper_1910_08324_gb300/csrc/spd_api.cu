@@ -776,7 +776,15 @@ spd_status spd_noise_stats(const spd_plan* plan, const void* d_x, float outlier_
 }
 
 spd_status spd_plan_set_segment(spd_plan* plan, int32_t segment) {
-  if (plan && plan->bd_general) return SPD_ERR_UNSUPPORTED;  // the general kernel has tiles of its own
+  if (plan && plan->bd_general) {  // the general BoxDIT kernel: tiles of 2048, 4096 or 8192 starts
+    if (segment != 2048 && segment != 4096 && segment != 8192) return SPD_ERR_INVALID_ARG;
+    int32_t len[spd::kMaxLevels], off[spd::kBdgOffsets];
+    if (sizeof(float) * (size_t)spd::bdg_layout(*plan, segment, true, len, off) > 227 * 1024)
+      return SPD_ERR_UNSUPPORTED;
+    plan->tile = segment;
+    plan->tiles_per_row = (plan->n_starts + plan->tile - 1) / plan->tile;
+    return SPD_OK;
+  }
   if (!plan || plan->family == kExhaustive || !segment_ok(*plan, segment)) return SPD_ERR_INVALID_ARG;
   plan->tile = segment_tile(plan->desc.nt, segment);
   plan->tiles_per_row = (plan->n_starts + plan->tile - 1) / plan->tile;

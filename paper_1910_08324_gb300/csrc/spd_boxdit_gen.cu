@@ -5,19 +5,25 @@
 // Iteration i (level i) has unit 2^i, starts s = n 2^i and the widths
 // c_i + m 2^i, m = 1..k_i, with c_i = sum_{j<i} k_j 2^j (= L^{i-1}_MAX).  The
 // kernel runs Alg. 1 as the paper states it, on one tile of T starts of one
-// row (T = 2048 or 4096, chosen per plan so that two CTAs fit on an SM):
+// row (T = 4096 when two CTAs fit on an SM, else 2048; spd_plan_set_segment
+// picks 2048, 4096 or 8192):
 //   * the shifted decimated series x^i of the tile live in shared memory:
-//     x^0 over the tile and its level-0 lookahead, x^1 summed in pairs straight
-//     from the input (x^1[u] = x^0[2u + k_0] + x^0[2u + k_0 + 1], the
-//     decimation of Sec. 3.1 with its shift of L^0_max / D), and each x^{i+1}
+//     x^0 over the tile and its level-0 lookahead, x^1 summed in pairs
+//     (x^1[u] = x^0[2u + k_0] + x^0[2u + k_0 + 1], the decimation of Sec. 3.1
+//     with its shift of L^0_max / D: from x^0's window where it reaches, past it
+//     straight from the input, 8 loads in flight per thread), and each x^{i+1}
 //     from x^i in shared memory (x^{i+1}[u] = x^i[2u + k_i] + x^i[2u + k_i + 1]),
 //     every series as long as the levels above still need it;
-//   * level i evaluates its T / 2^i positions (one per thread at a time,
-//     consecutive positions on consecutive lanes): the sum starts from the
-//     base X^{i-1} at the position (kept by level i - 1) and adds
-//     x^i[n], x^i[n + 1], ... in order, each partial sum times the width's
-//     scale being a candidate (strict '>', so the smaller width wins a tie);
-//     the full sum of k_i blocks at an even position is the next level's base;
+//   * level i evaluates its T / 2^i positions.  With 2, 4 or 8 or more per
+//     thread, a thread takes tasks of 2, 4 or 8 consecutive positions and runs
+//     them together on register windows of 16 block counts, each candidate
+//     coded with its rank in the window (bdg_task); with fewer, one position
+//     per thread, consecutive positions on consecutive lanes.  Either way the
+//     sum starts from the base X^{i-1} at the position (kept by level i - 1)
+//     and adds x^i[n], x^i[n + 1], ... in order, each partial sum times the
+//     width's scale (a shared-memory table) being a candidate (strict '>', so
+//     the smaller width wins a tie); the full sum of k_i blocks at an even
+//     position is the next level's base;
 //   * each level merges its maxima into the tile's Y and W in shared memory
 //     (levels in increasing width order, strict '>'), one barrier per level;
 //     the tile is then stored with vector stores, and its maximum goes to the
@@ -33,6 +39,8 @@ namespace spd {
 
 // Window lengths and shared-memory offsets (floats) of a general BoxDIT plan
 // with tiles of T starts (see the kernel's comment).
+constexpr int kWinPad = 32;
+
 int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off) {
   int lt = 0;
   while ((2 << lt) <= T) ++lt;  // log2 T
@@ -54,13 +62,15 @@ int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* o
     else
       mb = mb > len[i] + 1 ? mb : len[i] + 1;
   }
+  // each series buffer is padded: a task's last register window may read up to
+  // kGMC values past the series (never used)
   int o = 0;
   off[kBdgX0] = o;
-  o += al4(len[0]);
+  o += al4(len[0]) + kWinPad;
   off[kBdgXA] = o;
-  o += al4(ma);
+  o += al4(ma) + kWinPad;
   off[kBdgXB] = o;
-  o += al4(mb);
+  o += al4(mb) + kWinPad;
   off[kBdgBA] = o;
   o += al4(T / 2);
   off[kBdgBB] = o;
@@ -69,12 +79,154 @@ int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* o
   o += T;
   off[kBdgW] = o;
   o += T / 2;
-  off[kBdgAB] = o;
-  o += table ? al4(2 * ((int)plan.widths.size() + kAbPad)) : 0;
+  off[kBdgAB] = o;  // table noise: (a, b) per width; white noise: 1/sqrt(L) per width
+  o += table ? al4(2 * ((int)plan.widths.size() + kAbPad)) : al4((int)plan.widths.size());
   return o;
 }
 
 namespace {
+
+constexpr int kGMC = 16;       // block counts per register window (4-bit ranks)
+constexpr int kLoadBatch = 8;  // input loads in flight per thread
+
+// NP consecutive values at a 4 NP-byte aligned address (float4 or float2 loads)
+template <int N, int NP>
+__device__ __forceinline__ void load_run(const float* src, float (&w)[N]) {
+  if constexpr (NP % 4 == 0) {
+    static_assert(N % 4 == 0, "whole float4s");
+    load_window4<N / 4>(src, w);
+  } else {
+    static_assert(N % 2 == 0, "whole float2s");
+    load_window2<N / 2>(src, w);
+  }
+}
+
+// Level i at the NP consecutive positions n0.. of a task (n0 a multiple of NP):
+// running sums from the base (level 0: none), every partial sum times its
+// width's scale a candidate.  The block counts go in windows of kGMC: a
+// window's NP + kGMC - 1 values come in with vector loads, each candidate
+// carries its rank in the window in the 4 low mantissa bits (enc_w, smaller
+// rank wins a tie) and the window's maximum is kept running with three-input
+// max instructions; at the end of a window it is decoded and taken when
+// strictly larger than the best of the earlier windows.  S[] ends as the sum of
+// mend blocks (the next level's base); bv[], bq[] are the best SNR and its
+// block count - 1.  SC: the widths' scales (white noise) or (a, b) pairs.
+template <bool TABLE, bool BASE, int NP>
+__device__ __forceinline__ void bdg_task(const float* __restrict__ Xi, const float* __restrict__ Bi,
+                                         const float* __restrict__ SC, int n0, int first, int nu, int mend,
+                                         float (&S)[NP], float (&bv)[NP], int (&bq)[NP]) {
+  if constexpr (BASE) {
+    load_run<NP, NP>(Bi + n0, S);
+  } else {
+#pragma unroll
+    for (int r = 0; r < NP; ++r) S[r] = 0.0f;
+  }
+#pragma unroll
+  for (int r = 0; r < NP; ++r) {
+    bv[r] = ninf();
+    bq[r] = 0;
+  }
+  constexpr int NW = NP + kGMC;  // NP + kGMC - 1 values used
+  for (int m0 = 0; m0 < mend; m0 += kGMC) {
+    float w[NW];
+    load_run<NW, NP>(Xi + n0 + m0, w);
+    float acc[NP], c[NP];  // c: the candidate of the previous (even) rank, for a three-input max
+#pragma unroll
+    for (int r = 0; r < NP; ++r) acc[r] = ninf();
+    static_for<0, kGMC>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      const int m = m0 + j;
+      if (m < mend) {
+#pragma unroll
+        for (int r = 0; r < NP; ++r) S[r] += w[r + j];
+      }
+      if (m < nu) {  // (nu <= mend)
+        float sc, sb = 0.0f;
+        if constexpr (TABLE) {
+          const float2 ab = reinterpret_cast<const float2*>(SC)[first + m];
+          sc = ab.x;
+          sb = ab.y;
+        } else {
+          sc = SC[first + m];
+        }
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+          const float e = enc_w<4>(TABLE ? fmaf(S[r], sc, sb) : S[r] * sc, (kGMC - 1) - j);
+          if constexpr ((j & 1) == 0)
+            c[r] = e;
+          else
+            acc[r] = fmax3(acc[r], c[r], e);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+          if constexpr ((j & 1) == 0)
+            c[r] = ninf();
+          else
+            acc[r] = fmaxf(acc[r], c[r]);
+        }
+      }
+    });
+    static_assert(kGMC % 2 == 0, "ranks are taken in pairs");
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {  // a NaN (no candidate in the window) never passes '>'
+      const float v = dec_v<4>(acc[r]);
+      const bool take = v > bv[r];
+      bv[r] = take ? v : bv[r];
+      bq[r] = take ? m0 + dec_w<4>(acc[r]) : bq[r];
+    }
+  }
+}
+
+// All tasks of NP positions of level i (every thread takes P / (NP kThreads)),
+// their bases for level i + 1 and their merge into the tile's Y, W.
+template <bool TABLE, int NP>
+__device__ __forceinline__ void bdg_level(int i, int P, bool next, const float* Xi, const float* Bi, float* Bn,
+                                          const float* SC, int first, int nu, int mend, float* Y, uint16_t* W) {
+  for (int n0 = NP * (int)threadIdx.x; n0 < P; n0 += NP * kThreads) {
+    float S[NP], bv[NP];
+    int bq[NP];
+    if (i == 0)
+      bdg_task<TABLE, false, NP>(Xi, Bi, SC, n0, first, nu, mend, S, bv, bq);
+    else
+      bdg_task<TABLE, true, NP>(Xi, Bi, SC, n0, first, nu, mend, S, bv, bq);
+    if (next) {  // even positions: the next level's base
+      if constexpr (NP == 8)
+        *reinterpret_cast<float4*>(Bn + (n0 >> 1)) = make_float4(S[0], S[2], S[4], S[6]);
+      else if constexpr (NP == 4)
+        *reinterpret_cast<float2*>(Bn + (n0 >> 1)) = make_float2(S[0], S[2]);
+      else
+        Bn[n0 >> 1] = S[0];
+    }
+    if (NP == 8 && i == 0) {  // level 0 writes its starts outright
+      *reinterpret_cast<float4*>(Y + n0) = make_float4(bv[0], bv[1], bv[2], bv[3]);
+      *reinterpret_cast<float4*>(Y + n0 + 4) = make_float4(bv[4 % NP], bv[5 % NP], bv[6 % NP], bv[7 % NP]);
+      uint4 pk;
+      pk.x = (uint32_t)(first + bq[0]) | ((uint32_t)(first + bq[1]) << 16);
+      pk.y = (uint32_t)(first + bq[2 % NP]) | ((uint32_t)(first + bq[3 % NP]) << 16);
+      pk.z = (uint32_t)(first + bq[4 % NP]) | ((uint32_t)(first + bq[5 % NP]) << 16);
+      pk.w = (uint32_t)(first + bq[6 % NP]) | ((uint32_t)(first + bq[7 % NP]) << 16);
+      *reinterpret_cast<uint4*>(W + n0) = pk;
+    } else {
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const int s = (n0 + r) << i;
+        if (i == 0 || bv[r] > Y[s]) {
+          Y[s] = bv[r];
+          W[s] = (uint16_t)(first + bq[r]);
+        }
+      }
+    }
+  }
+}
+
+// x^1[u] for u < x1_split comes from x^0's window in shared memory (its pairs
+// 2u + k_0, 2u + k_0 + 1 lie below T + k_0 - 1), the rest from the input; even,
+// so the input part starts on a whole pair of pairs.
+__device__ __forceinline__ int x1_split(int T, int n1) {
+  const int u = T / 2 - 2;
+  return u < n1 ? u : (n1 & ~1);
+}
 
 template <bool TABLE>
 __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, float* smem) {
@@ -82,9 +234,13 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
   const int T = U.T;
   const int64_t t0 = U.t0;
   const int dt = p.dtype;
-  float2* AB = reinterpret_cast<float2*>(smem + p.gen_off[kBdgAB]);
+  // scales of the widths in shared memory: (a, b) pairs of table noise, or
+  // 1/sqrt(L) of white noise
+  float* SC = smem + p.gen_off[kBdgAB];
   float mu, inv;
-  row_noise<TABLE>(p, U.mu, U.sigma, U.row, AB, mu, inv);
+  row_noise<TABLE>(p, U.mu, U.sigma, U.row, reinterpret_cast<float2*>(SC), mu, inv);
+  if constexpr (!TABLE)
+    for (int w = t; w < p.n_widths; w += kThreads) SC[w] = p.wscale[w];
   float* X0 = smem + p.gen_off[kBdgX0];
   float* XA = smem + p.gen_off[kBdgXA];
   float* XB = smem + p.gen_off[kBdgXB];
@@ -101,15 +257,30 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
 
   // ---- x^0 over the tile's level-0 window, x^1 in pairs from the input ----
   {
-    const int n0 = p.gen_len[0];
-    for (int q = t; 4 * q < n0; q += kThreads)
-      *reinterpret_cast<float4*>(X0 + 4 * q) = load_z4d(U.xrow, t0 + 4 * q, U.nt, dt, U.vec_x, mu, inv);
-    if (tt >= 1) {
-      const int k0 = p.lvl_k[0], n1 = p.gen_len[1];
-      const bool v1 = U.vec_x && (k0 & 3) == 0;
-      for (int q = t; 2 * q < n1; q += kThreads) {
-        const float4 v = load_z4d(U.xrow, t0 + k0 + 4 * q, U.nt, dt, v1, mu, inv);
-        *reinterpret_cast<float2*>(XA + 2 * q) = make_float2(v.x + v.y, v.z + v.w);
+    const int nq0 = (p.gen_len[0] + 3) / 4;  // quads of x^0
+    const int k0 = p.lvl_k[0], n1 = p.gen_len[1];
+    const int q1 = tt >= 1 ? x1_split(T, n1) >> 1 : 0;                // first quad of x^1 from the input
+    const int nq1 = tt >= 1 ? (n1 + 1) / 2 - q1 : 0;                   // ... and their number
+    const bool v1 = U.vec_x && (k0 & 3) == 0;
+    // one index space over both: quad j < nq0 of x^0, else quad q1 + j - nq0 of x^1's input;
+    // kLoadBatch loads per thread are issued before any is used
+    const int nq = nq0 + nq1;
+    for (int j0 = t; j0 < nq; j0 += kLoadBatch * kThreads) {
+      float4 v[kLoadBatch];
+#pragma unroll
+      for (int b = 0; b < kLoadBatch; ++b) {
+        const int j = j0 + b * kThreads;
+        const bool is0 = j < nq0;
+        const int64_t pos = is0 ? t0 + 4 * j : t0 + k0 + 4 * (q1 + j - nq0);
+        v[b] = j < nq ? load_z4d(U.xrow, pos, U.nt, dt, is0 ? U.vec_x : v1, mu, inv) : make_float4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int b = 0; b < kLoadBatch; ++b) {
+        const int j = j0 + b * kThreads;
+        if (j < nq0)
+          *reinterpret_cast<float4*>(X0 + 4 * j) = v[b];
+        else if (j < nq)
+          *reinterpret_cast<float2*>(XA + 2 * (q1 + j - nq0)) = make_float2(v[b].x + v[b].y, v[b].z + v[b].w);
       }
     }
   }
@@ -125,7 +296,14 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
     const float* Xi = (i == 0) ? X0 : ((i & 1) ? XA : XB);
     const float* Bi = (i & 1) ? BA : BB;
     float* Bn = (i & 1) ? BB : BA;
-    for (int n = t; n < P; n += kThreads) {
+    const int per = P / kThreads;  // positions per thread (P and kThreads are powers of two)
+    if (per >= 8) {
+      bdg_level<TABLE, 8>(i, P, i < tt, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+    } else if (per == 4) {
+      bdg_level<TABLE, 4>(i, P, i < tt, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+    } else if (per == 2) {
+      bdg_level<TABLE, 2>(i, P, i < tt, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+    } else for (int n = t; n < P; n += kThreads) {  // at most one position per thread
       float S = i ? Bi[n] : 0.0f;
       float best = ninf();
       int bq = 0;
@@ -136,10 +314,10 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
         S += xs[m];
         float v;
         if constexpr (TABLE) {
-          const float2 ab = AB[first + m];
+          const float2 ab = reinterpret_cast<const float2*>(SC)[first + m];
           v = fmaf(S, ab.x, ab.y);
         } else {
-          v = S * p.wscale[first + m];
+          v = S * SC[first + m];
         }
         if (v > best) {
           best = v;
@@ -152,6 +330,13 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
       if (i == 0 || best > Y[s]) {
         Y[s] = best;
         W[s] = (uint16_t)(first + bq);
+      }
+    }
+    if (i == 0 && tt >= 1) {  // x^1[u] for u below the split, from x^0's window
+      const int u1 = x1_split(T, p.gen_len[1]);
+      for (int u = t; u < u1; u += kThreads) {
+        const float2 v = *reinterpret_cast<const float2*>(X0 + 2 * u + k);  // k even: aligned pair
+        XA[u] = v.x + v.y;
       }
     }
     if (i >= 1 && i < tt) {  // x^{i+1} from x^i, shifted by k_i (Sec. 3.1's decimation)

@@ -848,6 +848,40 @@ __device__ __forceinline__ void load_window1(const float* src, float (&w)[NW]) {
   });
 }
 
+// store8 with the eight 16-bit widths already packed in pairs (pk[q]: width of
+// start 2q in the low half, 2q + 1 in the high half).
+__device__ __forceinline__ void store8_pk(float* __restrict__ yrow, uint16_t* __restrict__ wrow,
+                                          int64_t s0, int64_t nt, bool vec, const float (&y)[8],
+                                          const uint32_t (&pk)[4]) {
+  if (vec && s0 + 8 <= nt) {
+    __stcs(reinterpret_cast<float4*>(yrow + s0), make_float4(y[0], y[1], y[2], y[3]));
+    __stcs(reinterpret_cast<float4*>(yrow + s0 + 4), make_float4(y[4], y[5], y[6], y[7]));
+    if ((reinterpret_cast<uintptr_t>(wrow + s0) & 15) == 0) {
+      __stcs(reinterpret_cast<uint4*>(wrow + s0), make_uint4(pk[0], pk[1], pk[2], pk[3]));
+    } else {
+      __stcs(reinterpret_cast<uint2*>(wrow + s0), make_uint2(pk[0], pk[1]));
+      __stcs(reinterpret_cast<uint2*>(wrow + s0 + 4), make_uint2(pk[2], pk[3]));
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (s0 + k < nt) {
+        yrow[s0 + k] = y[k];
+        wrow[s0 + k] = (uint16_t)(pk[k >> 1] >> (16 * (k & 1)));
+      }
+  }
+}
+
+// The width indices of two coded SNRs (code = 2^B - 1 - index, B <= 8) packed as
+// 16-bit halves: one byte permute gathers both low bytes, one logic instruction
+// inverts and masks them (2^B - 1 - c == ~c & (2^B - 1)).
+template <int B>
+__device__ __forceinline__ uint32_t dec_w_pair(float lo, float hi) {
+  static_assert(B <= 8, "the code must fit in the low byte");
+  const uint32_t m = (1u << B) - 1u;
+  return ~__byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x5410) & (m | (m << 16));
+}
+
 __device__ __forceinline__ void merge1(float& y, int& w, float ny, int nw) {
   if (ny > y) {
     y = ny;

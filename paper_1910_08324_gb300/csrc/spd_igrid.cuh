@@ -495,6 +495,7 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
     const int buf = k % FX::NBUF;
     float y[8];
     int w[8];
+    uint32_t pk[4];  // coded grids: the widths, packed in pairs
     if constexpr (ENC) {
       // coded SNRs: every maximum and merge is a max instruction; level j >= 1
       // starts at width index NC0 + (j-1) MM (compile-time)
@@ -550,10 +551,9 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
         y[0] = fmaxf(y[0], (t & 1) ? ninf() : fkey_inv(key));
       }
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        w[r] = dec_w<S::EB>(y[r]);
-        y[r] = dec_v<S::EB>(y[r]);
-      }
+      for (int q = 0; q < 4; ++q) pk[q] = dec_w_pair<S::EB>(y[2 * q], y[2 * q + 1]);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) y[r] = dec_v<S::EB>(y[r]);
     } else {
       // more than 32 widths: every level's maximum is coded with its rank within
       // the level (eval_set_enc), decoded once per position and merged with the
@@ -632,7 +632,10 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
       for (int r = 0; r < 8; ++r)
         if (s0 + r < srel) tmax = fmaxf(tmax, y[r]);
     }
-    store8(yseg, wseg, s0, srel, vec, y, w);
+    if constexpr (ENC)
+      store8_pk(yseg, wseg, s0, srel, vec, y, pk);
+    else
+      store8(yseg, wseg, s0, srel, vec, y, w);
     if ((ar & (kCandTile - 1)) == 0) {  // last chunk of a candidate tile (we walk backwards)
       tile_max_atomic(U.tm_row, t0 + ar, tmax);
       tmax = ninf();

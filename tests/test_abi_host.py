@@ -192,11 +192,16 @@ def test_per_iteration_boxdit_plan_rules():
     for lmax, s_end in (([2], 40000), ([256], 1000)):
         with pytest.raises(spd.SpdError):
             spd.spd_plan_create_boxdit(lmax, s_end, ndm=2, nt=1000)
-    # the general kernel's tiles are fixed: no segment length
+    # the general kernel takes tiles of 2048, 4096 or 8192 starts as its segment
     plan = spd.spd_plan_create_boxdit([6, 2], 1000, ndm=2, nt=1 << 20)
-    with pytest.raises(spd.SpdError) as e:
-        spd.spd_plan_set_segment(plan, 16384)
-    assert e.value.status == 2
+    for seg in (2048, 4096, 8192):
+        spd.spd_plan_set_segment(plan, seg)
+    for seg in (1024, 16384, 3000):
+        with pytest.raises(spd.SpdError) as e:
+            spd.spd_plan_set_segment(plan, seg)
+        assert e.value.status == 1
+    wide = spd.spd_plan_create_boxdit([2], 30000, ndm=2, nt=1 << 20)
+    spd.spd_plan_set_segment(wide, 8192)  # 8192 starts + a 32766-sample halo still fit in 227 KB
 
 
 def test_proposal_rules():

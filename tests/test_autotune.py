@@ -78,3 +78,22 @@ def test_launch_tuner_searches_both_dimensions_and_caches(tmp_path):
     (seg, c), _ = autotune.tune_launch("k", set_segment, set_ctas, lambda: pytest.fail("timed again"),
                                        cache_path=path)
     assert (seg, c) == (65536, 2) and state == {"s": 65536, "c": 2}
+
+
+def test_general_boxdit_tile_is_tuned_through_the_plan(tmp_path):
+    # the general BoxDIT kernel's starts per CTA are what spd_plan_set_segment
+    # sets for its plans; the library accepts exactly the tuner's tiles
+    spd = pytest.importorskip("paper_1910_08324_gb300")
+    plan = spd.spd_plan_create_boxdit([6, 2], 8192, ndm=4, nt=1 << 20)
+    cost = {2048: 3.0, 4096: 2.0, 8192: 2.5}
+    state = {}
+
+    def set_segment(s):
+        spd.spd_plan_set_segment(plan, s)  # raises for a length that is not a tile
+        state["s"] = s
+
+    key = autotune.key_of(1, 8192, 0, [(4, 1 << 20)], boxdit_lmax=6)
+    seg, t = autotune.tune_segment(key, set_segment, lambda: cost[state["s"]],
+                                   candidates=autotune.BOXDIT_GENERAL_TILES + (16384,),
+                                   cache_path=str(tmp_path / "t.json"), reps=1)
+    assert seg == 4096 and set(t) == {"2048", "4096", "8192"}  # 16384 is not a tile: skipped
