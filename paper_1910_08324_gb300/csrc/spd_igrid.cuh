@@ -248,18 +248,24 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
 
   // Ring writes of levels 4..8: the 31 blocks a warp completes per chunk (16 of
   // level 4, 8 of 5, 4 of 6, 2 of 7, 1 of 8) are written by one lane each:
-  // lane l writes block wb of level wj, whose sum it fetches from lane wsrc.
-  const int wj = lane < 16 ? 4 : lane < 24 ? 5 : lane < 28 ? 6 : lane < 30 ? 7 : 8;
-  const int wb = lane < 16 ? lane : lane < 24 ? lane - 16 : lane < 28 ? lane - 24 : lane < 30 ? lane - 28 : 0;
-  const bool wput = COARSE && lane < 31 && wj <= top;
+  // lane l writes block wb of level wj.  The lane that writes a block is one
+  // that holds its sum after the warp's
+  // butterfly: block b of level 4 on lane 2b + 1, of level 5 on 4b, of level 6
+  // on 8b + 2, of level 7 on 16b + 6, level 8's on lane 14 (lane 30 has none),
+  // so no lane fetches another lane's sum.
+  const int wj = (lane & 1) ? 4 : (lane & 3) == 0 ? 5 : (lane & 7) == 2 ? 6 : (lane & 15) == 6 ? 7 : 8;
+  const int wb = lane >> (wj - 3);
+  const bool wput = COARSE && lane != 30 && wj <= top;
   int wn = 0;
   // Coarse evaluation: quads of 4 consecutive positions (float4 ring windows) for
   // levels 4..8 on the 62 first threads (32, 16, 8, 4, 2 quads); single positions
   // of levels 9, 10, 11 on lanes 0..6 of the last warp (after it has built those
   // levels; one code path for all seven), levels above 11 on its lane 7.
   const int ctop = top < kChunkLog ? top : kChunkLog;
-  // (ring offsets, masks and level constants are re-read per chunk from the
-  // ring table and the kernel parameters rather than held in registers)
+  // (the coarse quads and singles of grids with more than 32 widths re-read
+  // their ring offsets, masks and level constants per chunk from the ring table
+  // and the kernel parameters; the ring writes and the coded grids' coarse
+  // positions hold theirs in registers)
   int qj = 0, qn = 0, qq = 0;
   int sj = 0, sn = 0, sq = 0;
   // Coded grids: one coarse position per thread and chunk.  The chunk has
@@ -280,6 +286,10 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
       cq = u;
     }
   }
+  // the ring of this thread's coarse level: offset and mask (the table is set)
+  const int wbase = wput ? RTAB[2 * wj] : 0, wmask = wput ? RTAB[2 * wj + 1] : 0;  // this lane's ring writes
+  const int cbase = (COARSE && ENC && cj) ? RTAB[2 * cj] : 0;
+  const int cmask = (COARSE && ENC && cj) ? RTAB[2 * cj + 1] : 0;
   if (COARSE && wput) wn = ((a0 + 256 * warp) >> wj) + wb;  // block index at chunk 0 (relative to the segment)
   if (COARSE && !ENC) {
     int j = 0, u = -1;
@@ -305,23 +315,23 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
       }
     }
   }
-  // level-9..11 blocks of a chunk: lane L of the last warp builds block lb of level lj
-  // as the sum of lw level-8 blocks (lanes 0..3: level 9, 4..5: level 10, 6: level 11)
-  const int lj = lane < 4 ? 9 : (lane < 6 ? 10 : 11);
-  const int lb = lane < 4 ? lane : (lane < 6 ? lane - 4 : 0);
-  const int lw = 1 << (lj - 8);
-  const bool lbuild = COARSE && warp == kThreads / 32 - 1 && lane < 7 && lj <= top;
+  // level-9..11 blocks of a chunk: lanes 0..7 of the last warp hold the chunk's
+  // eight level-8 blocks and a butterfly over them gives the sums; block b of
+  // level 9 is put by lane 2b + 1, of level 10 by lane 4b, level 11's by lane 2
+  const int lj = (lane & 1) ? 9 : (lane & 3) == 0 ? 10 : 11;
+  const int lb = lane >> (lj - 8);
+  const bool lbuild = COARSE && warp == kThreads / 32 - 1 && lane < 8 && lane != 6 && lj <= top;
 
   // ---- building chunk k: levels 0..3 into buffer k % 3 (+ tails), rings 4..8 ----
   // The lookahead tail of chunk k is the head of chunk k-1 (built one iteration
   // earlier, before the last barrier), copied from its buffer.  Writing it into
   // the next buffer from registers instead would race with a slow warp still
   // evaluating the chunk that buffer held three chunks ago.
-  auto build = [&](int k, const Raw8& raw) {
+  // (buf: k mod 3, the buffer set of chunk k, kept by the pipeline loop)
+  auto build = [&](int k, int buf, const Raw8& raw) {
     const int ar = a0 - k * kC;
-    const int buf = k % FX::NBUF;
     if (k > 0 && warp == kTailWarp) {  // lookahead tails, one value per lane of one warp
-      const int pb = (k - 1) % FX::NBUF;
+      const int pb = buf == 0 ? FX::NBUF - 1 : buf - 1;
       for (int i = lane; i < S::TLALL; i += 32) {
         int src, dst;
         tail_offsets<S, FX>(i, src, dst);
@@ -348,12 +358,8 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
       const float s6 = s5 + __shfl_xor_sync(kFull, s5, 4);
       const float s7 = s6 + __shfl_xor_sync(kFull, s6, 8);
       const float s8 = s7 + __shfl_xor_sync(kFull, s7, 16);
-      const float v4 = __shfl_sync(kFull, s4, (2 * lane) & 31);
-      const float v5 = __shfl_sync(kFull, s5, (4 * lane) & 31);
-      const float v6 = __shfl_sync(kFull, s6, (8 * lane) & 31);
-      const float v7 = __shfl_sync(kFull, s7, (16 * lane) & 31);
-      const float v = lane < 16 ? v4 : lane < 24 ? v5 : lane < 28 ? v6 : lane < 30 ? v7 : s8;
-      if (wput) ring_put(RTAB[2 * wj], RTAB[2 * wj + 1], wn - ((k * kC) >> wj), v);
+      const float v = wj == 4 ? s4 : wj == 5 ? s5 : wj == 6 ? s6 : wj == 7 ? s7 : s8;
+      if (wput) ring_put(wbase, wmask, wn - ((k * kC) >> wj), v);
     }
   };
 
@@ -364,17 +370,12 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
   auto coarse = [&](int k) {
     const int ar = a0 - k * kC;
     if (warp == kThreads / 32 - 1 && top >= 9) {  // blocks of levels 9.. need every warp's level 8
-      if (lbuild) {
-        float acc = 0.f;
-        const float* R8 = smem + RTAB[2 * 8];
-        const int m8 = RTAB[2 * 8 + 1];
-        const int n8 = (ar >> 8) + lb * lw;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float v = R8[(n8 + i) & m8];
-          acc += (i < lw) ? v : 0.f;
-        }
-        ring_put(RTAB[2 * lj], RTAB[2 * lj + 1], (ar >> lj) + lb, acc);
+      {
+        const float v8 = lane < 8 ? smem[RTAB[2 * 8] + (((ar >> 8) + lane) & RTAB[2 * 8 + 1])] : 0.0f;
+        const float s9 = v8 + __shfl_xor_sync(kFull, v8, 1);
+        const float s10 = s9 + __shfl_xor_sync(kFull, s9, 2);
+        const float s11 = s10 + __shfl_xor_sync(kFull, s10, 4);
+        if (lbuild) ring_put(RTAB[2 * lj], RTAB[2 * lj + 1], (ar >> lj) + lb, lj == 9 ? s9 : lj == 10 ? s10 : s11);
       }
       for (int j = kChunkLog + 1; j <= top; ++j) {  // blocks longer than a chunk (rare)
         __syncwarp();
@@ -394,7 +395,7 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
     if constexpr (ENC) {
       if (cj) {  // this thread's position: a window of MMAX blocks
         const int first = p.lvl_first[cj];
-        const float* R = smem + RTAB[2 * cj] + (((ar >> cj) + cq) & RTAB[2 * cj + 1]);  // mirrored ring: no wrap
+        const float* R = smem + cbase + (((ar >> cj) + cq) & cmask);  // mirrored ring: no wrap
         float win[MMAX];
         load_window1<MMAX>(R, win);
         auto scq = [&](auto M) {
@@ -489,10 +490,9 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
 
   // ---- fine levels, merge and store of chunk k -----------------------------
   float tmax = ninf();
-  auto fine = [&](int k) {
+  auto fine = [&](int k, int buf) {
     const int ar = a0 - k * kC;
     if (ar >= srel) return;
-    const int buf = k % FX::NBUF;
     float y[8];
     int w[8];
     uint32_t pk[4];  // coded grids: the widths, packed in pairs
@@ -649,20 +649,23 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
   {
     const Raw8 cx = nx;
     if (nch > 1) nx = load_raw8(xseg, a0 - kC + 8 * t, nrel, dt, vx);
-    build(0, cx);
+    build(0, 0, cx);
   }
   __syncthreads();
   if (COARSE) coarse(0);
+  int b0 = 0, b1 = 1;  // buffer sets of chunks k and k + 1
   for (int k = 0; k < nch; ++k) {
     const bool more = k + 1 < nch;
     if (more) {
       const Raw8 cx = nx;
       if (k + 2 < nch) nx = load_raw8(xseg, a0 - (k + 2) * kC + 8 * t, nrel, dt, vx);
-      build(k + 1, cx);
+      build(k + 1, b1, cx);
     }
     __syncthreads();
     if (COARSE && more) coarse(k + 1);
-    fine(k);
+    fine(k, b0);
+    b0 = b1;
+    b1 = b1 == FX::NBUF - 1 ? 0 : b1 + 1;
   }
 }
 
