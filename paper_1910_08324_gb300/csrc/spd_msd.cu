@@ -11,7 +11,9 @@
 //   * one CTA per row; each of its 8 warps streams its own contiguous share of
 //     the row in steps of 256 samples (8 per lane), the samples of 16-byte
 //     aligned rows arriving by bulk copies (cp.async.bulk) into a per-warp ring
-//     of shared-memory stages completed on mbarriers; no barrier of the CTA
+//     of shared-memory stages of two steps each (one copy and one mbarrier wait
+//     per two steps; a waiting warp sleeps in the wait instead of spinning on
+//     the issue slots); no barrier of the CTA
 //     until the final reduction;
 //   * levels 0..3 from each lane's samples, 4..8 from the warp's shuffle tree,
 //     9..11 from a tree over the level-8 sums of the 8 steps of a 2048-sample
@@ -79,15 +81,16 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 
 // Wait until the phase of parity `par` of `bar` has completed; false when that
 // takes longer than kMsdWaitNs.
+constexpr uint32_t kSuspendNs = 20000;  // a waiting warp sleeps (no issue slots) until the copy lands, at most this long
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t par) {
   const uint32_t a = smem_addr(bar);
   uint32_t ok;
   uint64_t t0 = 0;
   for (int it = 0;; ++it) {
     asm volatile(
-        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(ok)
-        : "r"(a), "r"(par)
+        : "r"(a), "r"(par), "r"(kSuspendNs)
         : "memory");
     if (ok) return true;
     uint64_t now;
@@ -197,15 +200,20 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
   const int64_t u0 = (ng * warp / kWarps) * gs;
   const int64_t u1 = min((ng * (warp + 1) / kWarps) * gs, nsub);
   constexpr int sbytes = kSub * ES;
-  constexpr int lgs = ES == 4 ? 2 : (ES == 2 ? 3 : 4);  // stages: kWarpRing / sbytes
+  constexpr int lgs = ES == 4 ? 2 : (ES == 2 ? 3 : 4);  // steps in the ring: kWarpRing / sbytes
+  constexpr int lgp = lgs - 1;                          // stages of two steps each, one copy per stage
   const int64_t ub = BULK ? min(u1, nfs) : u0;  // steps [u0, ub) arrive staged
   unsigned char* wring = ring + (BULK ? warp * kWarpRing : 0);
   if (BULK) {
     if (lane == 0) {
-      for (int i = 0; i < (1 << lgs); ++i) bar_init(&full[warp][i]);
+      for (int i = 0; i < (1 << lgp); ++i) bar_init(&full[warp][i]);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      for (int64_t u = u0; u < ub && u < u0 + (1 << lgs); ++u)
-        bulk_load(wring + (u - u0) * sbytes, xrow + u * sbytes, (uint32_t)sbytes, &full[warp][u - u0]);
+      for (int i = 0; i < (1 << lgp); ++i) {
+        const int64_t us = u0 + 2 * i;
+        if (us < ub)
+          bulk_load(wring + 2 * i * sbytes, xrow + us * sbytes, (uint32_t)((us + 2 <= ub ? 2 : 1) * sbytes),
+                    &full[warp][i]);
+      }
     }
   }
   __syncthreads();
@@ -336,10 +344,11 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
   uint32_t kk = 0;  // steps done by this warp (mod 2^32: ring stage, phase parity, step within its chunk)
   for (int64_t u = u0; u < u1; ++u, ++kk) {
     Raw8 cx;
-    const int stg = (int)(kk & ((1u << lgs) - 1));
+    const uint32_t pk = kk >> 1;  // the stage (pair of steps) of this step
+    const int stg = (int)(pk & ((1u << lgp) - 1));
     if (BULK && u < ub) {
-      bad |= bar_wait(&full[warp][stg], (kk >> lgs) & 1u) ? 0 : 1;
-      cx = read_stage(wring + stg * sbytes, lane, DT);
+      if ((kk & 1u) == 0) bad |= bar_wait(&full[warp][stg], (pk >> lgp) & 1u) ? 0 : 1;
+      cx = read_stage(wring + (2 * stg + (int)(kk & 1u)) * sbytes, lane, DT);
     } else if (BULK) {
       cx = load_raw8(xrow + u * sbytes, 8 * lane, (int)(nt - u * kSub), DT, vx);
     } else {
@@ -351,17 +360,22 @@ __global__ void __launch_bounds__(kThreads, 3) msd_pass_kernel(const MsdParams p
     }
     const float s = u < nfs ? step(std::true_type{}, cx, u) : step(std::false_type{}, cx, u);
     if (lane == (int)(kk & 7u)) q = s;
-    if (BULK) {
-      if (__any_sync(kFull, bad)) {  // a step did not arrive: wait (bounded) for this warp's copies in flight
+    if (BULK && u < ub) {
+      if ((kk & 1u) == 0 && __any_sync(kFull, bad)) {  // a stage did not arrive: wait (bounded) for the copies in flight
         if (lane == 0)
-          for (uint32_t r = 0; r < (1u << lgs) && u + r < ub; ++r)
-            bar_wait(&full[warp][(kk + r) & ((1u << lgs) - 1)], ((kk + r) >> lgs) & 1u);
+          for (uint32_t r = 0; r < (1u << lgp); ++r)
+            if (u0 + 2 * (int64_t)(pk + r) < ub)
+              bar_wait(&full[warp][(pk + r) & ((1u << lgp) - 1)], ((pk + r) >> lgp) & 1u);
         if (lane == 0) failed = 1;
         break;
       }
-      __syncwarp();  // every lane has used the stage: refill it
-      if (lane == 0 && u + (1 << lgs) < ub)
-        bulk_load(wring + stg * sbytes, xrow + (u + (1 << lgs)) * sbytes, (uint32_t)sbytes, &full[warp][stg]);
+      if ((kk & 1u) == 1 || u + 1 == ub) {  // both steps of the stage used (or the last one): refill it
+        __syncwarp();
+        const int64_t us = u - (int64_t)(kk & 1u) + 2 * (1 << lgp);
+        if (lane == 0 && us < ub)
+          bulk_load(wring + 2 * stg * sbytes, xrow + us * sbytes, (uint32_t)((us + 2 <= ub ? 2 : 1) * sbytes),
+                    &full[warp][stg]);
+      }
     }
     if ((kk & 7u) == 7u || u + 1 == u1) {  // end of a 2048-sample chunk (or of the warp's share)
       const int64_t ch = u >> 3;
