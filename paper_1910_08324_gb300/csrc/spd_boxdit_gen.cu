@@ -16,7 +16,7 @@
 //     every series as long as the levels above still need it;
 //   * level i evaluates its T / 2^i positions.  With 2, 4 or 8 or more per
 //     thread, a thread takes tasks of 2, 4 or 8 consecutive positions and runs
-//     them together on register windows of 16 block counts, each candidate
+//     them together on register windows of 8 block counts, each candidate
 //     coded with its rank in the window (bdg_task); with fewer, one position
 //     per thread, consecutive positions on consecutive lanes.  Either way the
 //     sum starts from the base X^{i-1} at the position (kept by level i - 1)
@@ -86,7 +86,7 @@ int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* o
 
 namespace {
 
-constexpr int kGMC = 16;       // block counts per register window (4-bit ranks)
+constexpr int kGMC = 8;        // block counts per register window (3-bit ranks)
 constexpr int kLoadBatch = 8;  // input loads in flight per thread
 
 // NP consecutive values at a 4 NP-byte aligned address (float4 or float2 loads)
@@ -105,7 +105,7 @@ __device__ __forceinline__ void load_run(const float* src, float (&w)[N]) {
 // running sums from the base (level 0: none), every partial sum times its
 // width's scale a candidate.  The block counts go in windows of kGMC: a
 // window's NP + kGMC - 1 values come in with vector loads, each candidate
-// carries its rank in the window in the 4 low mantissa bits (enc_w, smaller
+// carries its rank in the window in the 3 low mantissa bits (enc_w, smaller
 // rank wins a tie) and the window's maximum is kept running with three-input
 // max instructions; at the end of a window it is decoded and taken when
 // strictly larger than the best of the earlier windows.  S[] ends as the sum of
@@ -151,7 +151,7 @@ __device__ __forceinline__ void bdg_task(const float* __restrict__ Xi, const flo
         }
 #pragma unroll
         for (int r = 0; r < NP; ++r) {
-          const float e = enc_w<4>(TABLE ? fmaf(S[r], sc, sb) : S[r] * sc, (kGMC - 1) - j);
+          const float e = enc_w<3>(TABLE ? fmaf(S[r], sc, sb) : S[r] * sc, (kGMC - 1) - j);
           if constexpr ((j & 1) == 0)
             c[r] = e;
           else
@@ -170,10 +170,10 @@ __device__ __forceinline__ void bdg_task(const float* __restrict__ Xi, const flo
     static_assert(kGMC % 2 == 0, "ranks are taken in pairs");
 #pragma unroll
     for (int r = 0; r < NP; ++r) {  // a NaN (no candidate in the window) never passes '>'
-      const float v = dec_v<4>(acc[r]);
+      const float v = dec_v<3>(acc[r]);
       const bool take = v > bv[r];
       bv[r] = take ? v : bv[r];
-      bq[r] = take ? m0 + dec_w<4>(acc[r]) : bq[r];
+      bq[r] = take ? m0 + dec_w<3>(acc[r]) : bq[r];
     }
   }
 }
