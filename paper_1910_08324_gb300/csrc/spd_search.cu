@@ -12,7 +12,9 @@
 // every start) runs one CTA per 2048-start tile: the tile and its lookahead are
 // staged once in shared memory, each thread owns 4 starts and extends their
 // running sums width by width in register windows (32 widths per window),
-// with 1/sqrt(L) from a shared table.  The tile maximum goes to the workspace
+// with 1/sqrt(L) from a shared table; each candidate of a window carries its
+// rank in the 5 low mantissa bits, so the window's maximum is one three-input
+// max per two candidates, decoded and merged with a strict '>' after the window.  The tile maximum goes to the workspace
 // for the candidate step.  Only starts below the plan's n_starts are stored;
 // samples up to nt feed them.  BoxDIT and IGRID have streaming kernels of their
 // own (spd_boxdit.cu, spd_igrid.cu).
@@ -98,6 +100,7 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
   for (int k = 0; k < kItems0; ++k) {
     const int p0 = (tid + k * kThreads) * 4;
     float S[4] = {0.f, 0.f, 0.f, 0.f}, best[4];
+    float acc[4] = {ninf(), ninf(), ninf(), ninf()}, cw[4];  // the coded window maxima (explicit set: unused)
     int q[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int r = 0; r < 4; ++r) best[r] = ninf();
@@ -142,24 +145,48 @@ __global__ void __launch_bounds__(kThreads, 2) exhaustive_kernel(const SearchPar
               });
             }
           }
-        } else if (!tail || m <= lmax) {
-          const auto sc = [&] {
-            if constexpr (TABLE)
-              return AB[m - 1];
-            else
-              return RS[m];
-          }();
-          static_for<0, 4>([&](auto R) {
-            constexpr int r = decltype(R)::value;
-            S[r] += w[r + mi];
-            const float v = snr_of(S[r], sc);
-            if (v > best[r]) {
-              best[r] = v;
-              q[r] = m - 1;
-            }
-          });
+        } else {
+          // every candidate of the window carries its rank mi in the 5 low
+          // mantissa bits (enc_w: the smaller rank wins a tie), the window's
+          // maximum is kept running with three-input max instructions and merged
+          // with a strict '>' after the window
+          if (!tail || m <= lmax) {
+            const auto sc = [&] {
+              if constexpr (TABLE)
+                return AB[m - 1];
+              else
+                return RS[m];
+            }();
+            static_for<0, 4>([&](auto R) {
+              constexpr int r = decltype(R)::value;
+              S[r] += w[r + mi];
+              const float e = enc_w<5>(snr_of(S[r], sc), 31 - mi);
+              if constexpr ((mi & 1) == 0)
+                cw[r] = e;
+              else
+                acc[r] = fmax3(acc[r], cw[r], e);
+            });
+          } else {
+            static_for<0, 4>([&](auto R) {
+              constexpr int r = decltype(R)::value;
+              if constexpr ((mi & 1) == 0)
+                cw[r] = ninf();
+              else
+                acc[r] = fmaxf(acc[r], cw[r]);
+            });
+          }
         }
       });
+      if constexpr (!GRID) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {  // a NaN (no candidate) never passes '>'
+          const float v = dec_v<5>(acc[r]);
+          const bool take = v > best[r];
+          best[r] = take ? v : best[r];
+          q[r] = take ? mbase + dec_w<5>(acc[r]) : q[r];
+          acc[r] = ninf();
+        }
+      }
     }
     const int64_t s0 = t0 + p0;
 #pragma unroll
