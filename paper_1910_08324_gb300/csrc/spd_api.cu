@@ -160,8 +160,11 @@ int dtype_size(int dtype) {
 // Workspace: tile maxima (written by the search, read by the candidate step),
 // per-tile candidate counts, per-group sums and offsets, and the level
 // statistics of spd_noise_stats.
+// General BoxDIT plans above level kBdgSplit also keep the series x^h and the
+// bases X^{h-1} of every row between their two kernels.
 struct WsLayout {
-  size_t tile_max, counts, gsum, goff, msd, total;
+  size_t tile_max, counts, gsum, goff, msd, gen, total;
+  int64_t gen_ldh;
   explicit WsLayout(const spd_plan& p) {
     const size_t nt = (size_t)(p.desc.ndm * p.cand_tiles_per_row);
     const size_t ng = (nt + spd::kCandGroup - 1) / spd::kCandGroup;
@@ -170,7 +173,9 @@ struct WsLayout {
     gsum = align_up(counts + nt * sizeof(int32_t));
     goff = align_up(gsum + ng * sizeof(int32_t));
     msd = align_up(goff + ng * sizeof(int64_t));
-    total = align_up(msd + spd::msd_state_bytes(p.desc.ndm));
+    gen = align_up(msd + spd::msd_state_bytes(p.desc.ndm));
+    gen_ldh = spd::bdg_two_part(p) ? spd::bdg_ldh(p.desc.nt, p.tile) : 0;
+    total = align_up(gen + 2 * sizeof(float) * (size_t)(p.desc.ndm * gen_ldh));
   }
 };
 
@@ -204,6 +209,8 @@ void fill_grid(spd::SearchParams& p, const spd_plan& plan) {
   if (plan.family == kBoxdit && plan.bd_general) {
     for (int j = 0; j <= plan.top; ++j) p.lvl_k[j] = plan.lvl_k[j];
     spd::bdg_layout(plan, plan.tile, true, p.gen_len, p.gen_off);
+    p.gen_part = 0;
+    p.gen_h = spd::kBdgSplit;
     for (size_t i = 0; i < plan.widths.size() && i < (size_t)spd::kMaxGridWidths; ++i)
       p.wscale[i] = (float)(1.0 / std::sqrt((double)plan.widths[i]));
   } else if (plan.family == kBoxdit) {
@@ -249,6 +256,11 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
               ? 1
               : 0;
   fill_grid(p, *plan);
+  if (wl.gen_ldh > 0) {
+    p.gen_xh = reinterpret_cast<float*>(static_cast<char*>(d_ws) + wl.gen);
+    p.gen_bh = p.gen_xh + plan->desc.ndm * wl.gen_ldh;
+    p.gen_ldh = wl.gen_ldh;
+  }
   p.table = noise->mode == 1 ? 1 : 0;
   // tile maxima start at a key below every float (0x80808080)
   cudaError_t e = cudaMemsetAsync(p.tile_max, 0x80,

@@ -33,6 +33,8 @@
 // samples.  Samples past the end of the row are -inf, so a boxcar needing them
 // never wins (the s + L <= nt rule); starts at or past the plan's n_starts are
 // not stored.
+#include <memory>
+
 #include "spd_common.cuh"
 
 namespace spd {
@@ -41,20 +43,21 @@ namespace spd {
 // with tiles of T starts (see the kernel's comment).
 constexpr int kWinPad = 32;
 
-int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off) {
+int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off, int part, int h) {
   int lt = 0;
   while ((2 << lt) <= T) ++lt;  // log2 T
   auto P = [&](int i) { return i <= lt ? T >> i : 1; };
-  const int top = plan.top;
+  const int lo = part == 2 ? h : 0;                 // first plan level of this kernel
+  const int top = part == 1 ? h : plan.top - lo;    // its last (part 1: x^h, written out)
+  auto K = [&](int i) { return plan.lvl_k[i + lo]; };
   for (int i = 0; i < kMaxLevels; ++i) len[i] = 0;
-  len[top] = P(top) + plan.n_top - 1;
+  len[top] = part == 1 ? P(top) : P(top) + plan.n_top - 1;
   for (int i = top - 1; i >= 0; --i) {
-    const int k = plan.lvl_k[i];
-    const int a = P(i) + k - 1, b = 2 * len[i + 1] + k;
+    const int a = P(i) + K(i) - 1, b = 2 * len[i + 1] + K(i);
     len[i] = a > b ? a : b;
   }
   // level 0 keeps only its own window: x^1 is summed straight from the input
-  len[0] = T + (top == 0 ? plan.n_top : plan.lvl_k[0]) - 1;
+  len[0] = T + (top == 0 ? plan.n_top : K(0)) - 1;
   int ma = 0, mb = 0;
   for (int i = 1; i <= top; ++i) {
     if (i & 1)
@@ -74,7 +77,7 @@ int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* o
   off[kBdgBA] = o;
   o += al4(T / 2);
   off[kBdgBB] = o;
-  o += al4(T / 4);
+  o += al4(part == 2 ? T : T / 4);  // part 2: the bases of its level 0 (X^{h-1}) come in here
   off[kBdgY] = o;
   o += T;
   off[kBdgW] = o;
@@ -179,14 +182,17 @@ __device__ __forceinline__ void bdg_task(const float* __restrict__ Xi, const flo
 }
 
 // All tasks of NP positions of level i (every thread takes P / (NP kThreads)),
-// their bases for level i + 1 and their merge into the tile's Y, W.
+// their bases for level i + 1 and their merge into the tile's Y, W (ow: the
+// level writes its starts outright, the tile's first level; base: its sums
+// start from the bases Bi).
 template <bool TABLE, int NP>
-__device__ __forceinline__ void bdg_level(int i, int P, bool next, const float* Xi, const float* Bi, float* Bn,
-                                          const float* SC, int first, int nu, int mend, float* Y, uint16_t* W) {
+__device__ __forceinline__ void bdg_level(int i, int P, bool next, bool ow, bool base, const float* Xi,
+                                          const float* Bi, float* Bn, const float* SC, int first, int nu, int mend,
+                                          float* Y, uint16_t* W) {
   for (int n0 = NP * (int)threadIdx.x; n0 < P; n0 += NP * kThreads) {
     float S[NP], bv[NP];
     int bq[NP];
-    if (i == 0)
+    if (!base)
       bdg_task<TABLE, false, NP>(Xi, Bi, SC, n0, first, nu, mend, S, bv, bq);
     else
       bdg_task<TABLE, true, NP>(Xi, Bi, SC, n0, first, nu, mend, S, bv, bq);
@@ -198,7 +204,7 @@ __device__ __forceinline__ void bdg_level(int i, int P, bool next, const float* 
       else
         Bn[n0 >> 1] = S[0];
     }
-    if (NP == 8 && i == 0) {  // level 0 writes its starts outright
+    if (NP == 8 && ow) {  // the first level writes its starts outright
       *reinterpret_cast<float4*>(Y + n0) = make_float4(bv[0], bv[1], bv[2], bv[3]);
       *reinterpret_cast<float4*>(Y + n0 + 4) = make_float4(bv[4 % NP], bv[5 % NP], bv[6 % NP], bv[7 % NP]);
       uint4 pk;
@@ -211,7 +217,7 @@ __device__ __forceinline__ void bdg_level(int i, int P, bool next, const float* 
 #pragma unroll
       for (int r = 0; r < NP; ++r) {
         const int s = (n0 + r) << i;
-        if (i == 0 || bv[r] > Y[s]) {
+        if (ow || bv[r] > Y[s]) {
           Y[s] = bv[r];
           W[s] = (uint16_t)(first + bq[r]);
         }
@@ -228,12 +234,19 @@ __device__ __forceinline__ int x1_split(int T, int n1) {
   return u < n1 ? u : (n1 & ~1);
 }
 
-template <bool TABLE>
+// One tile.  PART 0: every level of the plan on T starts of the input; PART 1:
+// levels 0..h-1 on T starts, and x^h and the bases X^{h-1} of the tile's T / 2^h
+// level-h positions to the workspace; PART 2: levels h..top on T positions of
+// x^h (t0 and T in level-h positions), merged into the Y, W the first part wrote.
+template <bool TABLE, int PART>
 __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, float* smem) {
+  constexpr bool P1 = PART == 1, P2 = PART == 2;
   const int t = threadIdx.x;
   const int T = U.T;
   const int64_t t0 = U.t0;
   const int dt = p.dtype;
+  const int h = p.gen_h;
+  const int lo = P2 ? h : 0;  // the plan level of this tile's level 0
   // scales of the widths in shared memory: (a, b) pairs of table noise, or
   // 1/sqrt(L) of white noise
   float* SC = smem + p.gen_off[kBdgAB];
@@ -252,13 +265,15 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
   while ((2 << lt) <= T) ++lt;
   // levels with positions in this tile: a level of unit 2^i > T has one, at t0,
   // when 2^i divides t0 (and then so does every lower unit)
-  int tt = p.top;
+  int tt = P1 ? h - 1 : p.top - lo;
   while (tt > lt && (t0 & ((1LL << tt) - 1)) != 0) --tt;
+  const float* xh = P2 ? p.gen_xh + U.row * p.gen_ldh : nullptr;
+  const int64_t nxh = p.gen_ldh;  // positions of x^h per row (past them: -inf)
 
   // ---- x^0 over the tile's level-0 window, x^1 in pairs from the input ----
   {
     const int nq0 = (p.gen_len[0] + 3) / 4;  // quads of x^0
-    const int k0 = p.lvl_k[0], n1 = p.gen_len[1];
+    const int k0 = p.lvl_k[lo], n1 = p.gen_len[1];
     const int q1 = tt >= 1 ? x1_split(T, n1) >> 1 : 0;                // first quad of x^1 from the input
     const int nq1 = tt >= 1 ? (n1 + 1) / 2 - q1 : 0;                   // ... and their number
     const bool v1 = U.vec_x && (k0 & 3) == 0;
@@ -272,7 +287,21 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
         const int j = j0 + b * kThreads;
         const bool is0 = j < nq0;
         const int64_t pos = is0 ? t0 + 4 * j : t0 + k0 + 4 * (q1 + j - nq0);
-        v[b] = j < nq ? load_z4d(U.xrow, pos, U.nt, dt, is0 ? U.vec_x : v1, mu, inv) : make_float4(0, 0, 0, 0);
+        if constexpr (P2) {  // the series x^h of the first part (sums of normalised samples)
+          // rows of nxh positions, nxh and t0 multiples of 4, k0 even
+          const float4 ninf4 = make_float4(ninf(), ninf(), ninf(), ninf());
+          if (is0) {
+            v[b] = pos < nxh ? __ldg(reinterpret_cast<const float4*>(xh + pos)) : ninf4;
+          } else if (j < nq) {
+            const float2 a = pos < nxh ? __ldg(reinterpret_cast<const float2*>(xh + pos)) : make_float2(ninf(), ninf());
+            const float2 c = pos + 2 < nxh ? __ldg(reinterpret_cast<const float2*>(xh + pos + 2))
+                                           : make_float2(ninf(), ninf());
+            v[b] = make_float4(a.x, a.y, c.x, c.y);
+          } else {
+            v[b] = make_float4(0, 0, 0, 0);
+          }
+        } else
+          v[b] = j < nq ? load_z4d(U.xrow, pos, U.nt, dt, is0 ? U.vec_x : v1, mu, inv) : make_float4(0, 0, 0, 0);
       }
 #pragma unroll
       for (int b = 0; b < kLoadBatch; ++b) {
@@ -283,28 +312,40 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
           *reinterpret_cast<float2*>(XA + 2 * (q1 + j - nq0)) = make_float2(v[b].x + v[b].y, v[b].z + v[b].w);
       }
     }
+    if constexpr (P2) {  // the bases of level h, and the Y, W the first part left at its starts
+      const float* bh = p.gen_bh + U.row * p.gen_ldh;
+      for (int n = t; n < T; n += kThreads) {
+        const int64_t v = t0 + n, st = v << h;
+        BB[n] = v < nxh ? bh[v] : 0.0f;
+        const bool in = st < U.ns;
+        Y[n] = in ? U.yrow[st] : ninf();
+        W[n] = in ? U.wrow[st] : (uint16_t)0;
+      }
+    }
   }
   __syncthreads();
 
   // ---- levels 0..tt: evaluate, merge, decimate; one barrier per level ----
   for (int i = 0; i <= tt; ++i) {
     const int P = i <= lt ? T >> i : 1;
-    const int k = p.lvl_k[i];
-    const int nu = (i == p.top) ? p.n_top : k;  // block counts that are candidates
-    const int mend = (i < tt) ? k : nu;         // blocks summed (the next level needs all k)
-    const int first = p.lvl_first[i];
+    const int k = p.lvl_k[i + lo];
+    const int nu = (i + lo == p.top) ? p.n_top : k;  // block counts that are candidates
+    const bool next = i < tt || P1;                  // a next level (part 1: level h) needs the bases
+    const int mend = next ? k : nu;                  // blocks summed (the next level needs all k)
+    const int first = p.lvl_first[i + lo];
+    const bool ow = i == 0 && !P2, base = i > 0 || P2;
     const float* Xi = (i == 0) ? X0 : ((i & 1) ? XA : XB);
     const float* Bi = (i & 1) ? BA : BB;
     float* Bn = (i & 1) ? BB : BA;
     const int per = P / kThreads;  // positions per thread (P and kThreads are powers of two)
     if (per >= 8) {
-      bdg_level<TABLE, 8>(i, P, i < tt, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+      bdg_level<TABLE, 8>(i, P, next, ow, base, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
     } else if (per == 4) {
-      bdg_level<TABLE, 4>(i, P, i < tt, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+      bdg_level<TABLE, 4>(i, P, next, ow, base, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
     } else if (per == 2) {
-      bdg_level<TABLE, 2>(i, P, i < tt, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+      bdg_level<TABLE, 2>(i, P, next, ow, base, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
     } else for (int n = t; n < P; n += kThreads) {  // at most one position per thread
-      float S = i ? Bi[n] : 0.0f;
+      float S = base ? Bi[n] : 0.0f;
       float best = ninf();
       int bq = 0;
       const float* xs = Xi + n;
@@ -325,9 +366,9 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
         }
       }
       for (; m < mend; ++m) S += xs[m];
-      if (i < tt && (n & 1) == 0) Bn[n >> 1] = S;
+      if (next && (n & 1) == 0) Bn[n >> 1] = S;
       const int s = n << i;
-      if (i == 0 || best > Y[s]) {
+      if (ow || best > Y[s]) {
         Y[s] = best;
         W[s] = (uint16_t)(first + bq);
       }
@@ -339,7 +380,7 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
         XA[u] = v.x + v.y;
       }
     }
-    if (i >= 1 && i < tt) {  // x^{i+1} from x^i, shifted by k_i (Sec. 3.1's decimation)
+    if (i >= 1 && next) {  // x^{i+1} from x^i, shifted by k_i (Sec. 3.1's decimation)
       float* Xn = (i & 1) ? XB : XA;
       const int nn = p.gen_len[i + 1];
       for (int u = t; u < nn; u += kThreads) {
@@ -348,6 +389,34 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
       }
     }
     __syncthreads();
+  }
+
+  if constexpr (P1) {  // x^h and the bases of the tile's level-h positions, for the second part
+    const float* Xh = ((h - 1) & 1) ? XB : XA;
+    const float* Bh = ((h - 1) & 1) ? BB : BA;
+    const int64_t v0 = t0 >> h;
+    float* xo = p.gen_xh + U.row * p.gen_ldh + v0;
+    float* bo = p.gen_bh + U.row * p.gen_ldh + v0;
+    for (int u = t; u < (T >> h); u += kThreads) {
+      xo[u] = Xh[u];
+      bo[u] = Bh[u];
+    }
+  }
+
+  if constexpr (P2) {  // ---- store back the starts of levels h..: strided, key per warp step ----
+    const int warp = t >> 5, lane = t & 31;
+    for (int n0 = 32 * warp; n0 < T; n0 += kThreads) {
+      const int n = n0 + lane;
+      const int64_t st = (t0 + n) << h;
+      const bool in = st < U.ns;
+      if (in) {
+        U.yrow[st] = Y[n];
+        U.wrow[st] = W[n];
+      }
+      if (((t0 + n0) << h) < U.ns)  // warp-uniform: the warp's starts lie in one candidate tile
+        tile_max_atomic(U.tm_row, (t0 + n0) << h, in ? Y[n] : ninf());
+    }
+    return;
   }
 
   // ---- store the tile; its maximum goes to the candidate-tile key ----
@@ -365,13 +434,13 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
     }
     store4(U.yrow, U.wrow, t0 + 4 * q, U.ns, U.vec, y, w);
   }
-  tile_max_atomic(U.tm_row, t0, tmax);
+  if (t0 < U.ns) tile_max_atomic(U.tm_row, t0, tmax);  // (the first part covers the row up to nt)
 }
 
-template <bool TABLE>
+template <bool TABLE, int PART>
 __global__ void __launch_bounds__(kThreads, 2) boxdit_gen_kernel(const SearchParams p) {
   extern __shared__ __align__(16) float smem[];
-  bdg_unit<TABLE>(p, plan_unit(p, blockIdx.x), smem);
+  bdg_unit<TABLE, PART>(p, plan_unit(p, blockIdx.x), smem);
 }
 
 // Batched search: persistent CTAs stride over the units of every range.
@@ -381,24 +450,60 @@ __global__ void __launch_bounds__(kThreads, 2) boxdit_gen_batch_kernel(const Sea
   for (int64_t u = blockIdx.x; u < p.n_units; u += gridDim.x) {
     Unit U;
     if (!batch_unit(p, u, U, &flag)) continue;
-    bdg_unit<false>(p, U, smem);
+    bdg_unit<false, 0>(p, U, smem);
     __syncthreads();
   }
 }
 
 }  // namespace
 
+bool bdg_two_part(const spd_plan& plan) {
+  if (plan.family != kBoxdit || !plan.bd_general || plan.top <= kBdgSplit) return false;
+  int32_t len[kMaxLevels], off[kBdgOffsets];
+  return sizeof(float) * (size_t)bdg_layout(plan, plan.tile, true, len, off, 1, kBdgSplit) <= kBdgMaxSmem &&
+         sizeof(float) * (size_t)bdg_layout(plan, kBdgTile2, true, len, off, 2, kBdgSplit) <= kBdgMaxSmem;
+}
+
 size_t boxdit_gen_smem_bytes(const spd_plan& plan, bool table) {
   int32_t len[kMaxLevels], off[kBdgOffsets];
   return sizeof(float) * (size_t)bdg_layout(plan, plan.tile, table, len, off);
 }
 
+namespace {
+
+template <int PART>
+cudaError_t launch_gen_part(const SearchParams& p, size_t smem, int64_t nblk, cudaStream_t s) {
+  return p.table ? launch_one(boxdit_gen_kernel<true, PART>, smem, nblk, p, s)
+                 : launch_one(boxdit_gen_kernel<false, PART>, smem, nblk, p, s);
+}
+
+}  // namespace
+
 cudaError_t launch_boxdit_gen(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {
   const bool table = p.table != 0;
-  const size_t smem = boxdit_gen_smem_bytes(plan, table);
-  const int64_t nblk = plan.desc.ndm * plan.tiles_per_row;
-  return table ? launch_one(boxdit_gen_kernel<true>, smem, nblk, p, s)
-               : launch_one(boxdit_gen_kernel<false>, smem, nblk, p, s);
+  if (!p.gen_xh || !bdg_two_part(plan))  // every level in one kernel
+    return launch_gen_part<0>(p, boxdit_gen_smem_bytes(plan, table), plan.desc.ndm * plan.tiles_per_row, s);
+  // two kernels: levels below h on tiles covering the row (x^h is needed up to
+  // its end), then levels h..top on tiles of kBdgTile2 level-h positions
+  const int h = kBdgSplit;
+  std::unique_ptr<SearchParams> q(new (std::nothrow) SearchParams(p));
+  if (!q) return cudaErrorMemoryAllocation;
+  q->gen_part = 1;
+  q->gen_h = h;
+  const size_t smem1 = sizeof(float) * (size_t)bdg_layout(plan, plan.tile, table, q->gen_len, q->gen_off, 1, h);
+  const int64_t tiles1 = (plan.desc.nt + plan.tile - 1) / plan.tile;
+  q->tiles_per_row = (int32_t)tiles1;
+  cudaError_t e = launch_gen_part<1>(*q, smem1, plan.desc.ndm * tiles1, s);
+  if (e != cudaSuccess) return e;
+  *q = p;
+  q->gen_part = 2;
+  q->gen_h = h;
+  q->tile = kBdgTile2;
+  const size_t smem2 = sizeof(float) * (size_t)bdg_layout(plan, kBdgTile2, table, q->gen_len, q->gen_off, 2, h);
+  const int64_t nh = (plan.n_starts + (1 << h) - 1) >> h;  // level-h positions with a start
+  const int64_t tiles2 = (nh + kBdgTile2 - 1) / kBdgTile2;
+  q->tiles_per_row = (int32_t)tiles2;
+  return launch_gen_part<2>(*q, smem2, plan.desc.ndm * tiles2, s);
 }
 
 cudaError_t launch_boxdit_gen_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s) {

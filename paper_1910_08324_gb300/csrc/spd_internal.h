@@ -107,6 +107,13 @@ struct SearchParams {
   int32_t gen_len[kMaxLevels];
   int32_t gen_off[kBdgOffsets];
   float wscale[kMaxGridWidths];
+  // the two-kernel form of larger plans: gen_part 1 runs levels below gen_h and
+  // writes x^gen_h and the bases X^{gen_h - 1} of every row to gen_xh / gen_bh
+  // ([ndm][gen_ldh]); gen_part 2 runs levels gen_h..top on them
+  int32_t gen_part, gen_h;
+  float* gen_xh;
+  float* gen_bh;
+  int64_t gen_ldh;
   BatchRange ranges[kMaxRanges];
 };
 
@@ -186,7 +193,17 @@ cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStrea
 size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
 // general BoxDIT (spd_boxdit_gen.cu): layout of a plan with tiles of T starts
 // (window lengths into len[kMaxLevels], offsets into off[kBdgOffsets]; returns floats)
-int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off);
+// part 0: every level in one kernel; 1: levels below h (writing x^h and the
+// bases X^{h-1}); 2: levels h..top of the series x^h, in tiles of T positions
+int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off, int part = 0, int h = 0);
+constexpr int kBdgSplit = 4;     // general BoxDIT plans above this level run in two kernels
+constexpr int kBdgTile2 = 4096;  // level-kBdgSplit positions per tile of the second
+constexpr size_t kBdgMaxSmem = 227 * 1024;  // shared memory of one CTA at most
+// positions of x^h kept per row (the first kernel covers the row in tiles of T starts)
+inline int64_t bdg_ldh(int64_t nt, int T) { return ((nt + T - 1) / T) * (int64_t)(T >> kBdgSplit); }
+// whether a plan runs in the two-kernel form (general BoxDIT above level
+// kBdgSplit, both kernels' layouts within kBdgMaxSmem)
+bool bdg_two_part(const spd_plan& plan);
 size_t boxdit_gen_smem_bytes(const spd_plan& plan, bool table);
 cudaError_t launch_boxdit_gen(const spd_plan& plan, const SearchParams& p, cudaStream_t s);
 cudaError_t launch_boxdit_gen_batch(const spd_plan& plan, const SearchParams& p, cudaStream_t s);

@@ -204,6 +204,22 @@ def test_per_iteration_boxdit_plan_rules():
     spd.spd_plan_set_segment(wide, 8192)  # 8192 starts + a 32766-sample halo still fit in 227 KB
 
 
+def test_two_kernel_form_workspace():
+    """General BoxDIT plans above level 4 keep x^4 and the level-3 bases of every
+    row in the workspace (2 floats per 16 samples, rounded up to whole first-kernel
+    tiles); plans up to level 4 need none."""
+    ndm, nt = 3, 100000
+    low = spd.spd_plan_create_boxdit([6], 20, ndm=ndm, nt=nt)     # widths up to 42: levels 0-2
+    high = spd.spd_plan_create_boxdit([6], 8192, ndm=ndm, nt=nt)  # levels 0-10
+    base = spd.spd_plan_create(algo=spd.SPD_ALGO_BOXDIT, s_end=8192, ndm=ndm, nt=nt, boxdit_lmax=16)
+    assert low.workspace_size() == base.workspace_size()
+    for seg in (2048, 4096, 8192):
+        spd.spd_plan_set_segment(high, seg)
+        ldh = -(-nt // seg) * (seg // 16)
+        assert high.workspace_size() - base.workspace_size() >= 2 * 4 * ndm * ldh
+        assert high.workspace_size() - base.workspace_size() < 2 * 4 * ndm * ldh + 512
+
+
 def test_proposal_rules():
     kw = dict(algo=spd.SPD_ALGO_IGRID, s_end=4096, igrid_depth=1, igrid_layers=4)
     p = spd.spd_proposal_create(ndm=4, nt=1 << 16, max_blocks=10, **kw)

@@ -135,6 +135,23 @@ def test_row_stride_and_evaluated_starts():
     assert_parity(Yg[:, :ns], Wg[:, :ns], Yo[:, :ns], Wo[:, :ns], Y2o[:, :ns], ns, ctx="n_starts")
 
 
+@pytest.mark.parametrize("segment", [2048, 4096, 8192])
+def test_two_kernel_form_tiles(segment):
+    """A plan above level 4 runs levels 0-3 on tiles of 2048, 4096 or 8192
+    starts, then levels 4.. on the series x^4 in tiles of 4096 level-4 positions
+    (65 536 starts): rows of two such tiles and a ragged third, with fewer
+    evaluated starts than samples."""
+    ndm, nt, ns = 2, 150001, 140003
+    x = _data(ndm, nt, 17 + segment)
+    plan = spd.spd_plan_create_boxdit([2, 4, 6, 8, 10, 12], 8192, ndm=ndm, nt=nt)
+    spd.spd_plan_set_segment(plan, segment)
+    spd.spd_plan_set_starts(plan, ns)
+    Yg, Wg = run_gpu(plan, x, 0.1, 0.9)
+    assert np.all(Yg[:, ns:] == -12345.0)
+    Yo, Wo, Y2o = oracle.search(x.astype(np.float64), oracle_grid(plan), 0.1, 0.9)
+    assert_parity(Yg[:, :ns], Wg[:, :ns], Yo[:, :ns], Wo[:, :ns], Y2o[:, :ns], ns, ctx="tile %d" % segment)
+
+
 def test_all_zero_input_ties_to_smallest_width():
     x = np.zeros((2, 20000), np.float32)
     plan = spd.spd_plan_create(algo=spd.SPD_ALGO_BOXDIT, s_end=1024, ndm=2, nt=20000, boxdit_lmax=12)
@@ -179,7 +196,11 @@ def test_candidates_from_tile_maxima():
         assert np.array_equal(rec["width_idx"], widx) and np.array_equal(rec["snr"], snr.astype(np.float32))
 
 
-def test_batch_equals_per_range_search():
+def test_batch_agrees_with_per_range_search():
+    """The batched search runs every level in one kernel per tile; a per-range
+    search of a plan above level 4 runs the two-kernel form, which takes the
+    levels from 4 on with tasks of several positions.  Both meet the oracle; their
+    SNRs differ at most by the low 3 mantissa bits that carry a window rank."""
     t = torch()
     shapes = [(3, 50000), (2, 25001), (1, 140001)]
     xs = [_data(a, b, 950 + i) for i, (a, b) in enumerate(shapes)]
@@ -197,5 +218,10 @@ def test_batch_equals_per_range_search():
         plan = spd.spd_plan_create(algo=spd.SPD_ALGO_BOXDIT, s_end=8192, ndm=x.shape[0], nt=x.shape[1],
                                    boxdit_lmax=12)
         Ys, Ws = run_gpu(plan, x, 0.0, 1.0)
-        assert np.array_equal(ys[r].cpu().numpy(), Ys), r
-        assert np.array_equal(wis[r].cpu().numpy().view(np.uint16), Ws), r
+        Yb, Wb = ys[r].cpu().numpy(), wis[r].cpu().numpy().view(np.uint16)
+        g = oracle_grid(plan)
+        Yo, Wo, Y2o = oracle.search(x.astype(np.float64), g, 0.0, 1.0)
+        assert_parity(Yb, Wb, Yo, Wo, Y2o, x.shape[1], ctx="batched, range %d" % r)
+        fin = np.isfinite(Ys)
+        assert np.array_equal(np.isfinite(Yb), fin), r
+        assert np.all(np.abs(Yb[fin] - Ys[fin]) <= 2.0 ** -19 * np.abs(Ys[fin])), r
