@@ -466,10 +466,16 @@ spd_status finish_plan(spd_plan* p, spd_plan** out) {
     p->tile = segment_tile(d.nt, default_segment(d.ndm, d.nt));
     p->halo = ((p->lend + spd::kChunk - 1) / spd::kChunk) * spd::kChunk;
     if (p->bd_general) {
-      // tiles of 4096 starts when two CTAs still fit on an SM, else 2048
+      // tiles of 4096 starts when two CTAs still fit on an SM, else 2048 (plans
+      // above level kBdgSplit: the first of their two kernels)
       int32_t len[spd::kMaxLevels], off[spd::kBdgOffsets];
       p->tile = 4096;
-      if (sizeof(float) * (size_t)spd::bdg_layout(*p, 4096, true, len, off) > 113 * 1024) p->tile = 2048;
+      if (spd::bdg_two_part(*p)) {
+        if (sizeof(float) * (size_t)spd::bdg_layout(*p, 4096, true, len, off, 1, spd::kBdgSplit) > 113 * 1024)
+          p->tile = 2048;
+      } else if (sizeof(float) * (size_t)spd::bdg_layout(*p, 4096, true, len, off) > 113 * 1024) {
+        p->tile = 2048;
+      }
       p->halo = p->lend;
     }
   }
@@ -790,10 +796,16 @@ spd_status spd_noise_stats(const spd_plan* plan, const void* d_x, float outlier_
 spd_status spd_plan_set_segment(spd_plan* plan, int32_t segment) {
   if (plan && plan->bd_general) {  // the general BoxDIT kernel: tiles of 2048, 4096 or 8192 starts
     if (segment != 2048 && segment != 4096 && segment != 8192) return SPD_ERR_INVALID_ARG;
-    int32_t len[spd::kMaxLevels], off[spd::kBdgOffsets];
-    if (sizeof(float) * (size_t)spd::bdg_layout(*plan, segment, true, len, off) > 227 * 1024)
-      return SPD_ERR_UNSUPPORTED;
+    // plans above level kBdgSplit run levels 0.. kBdgSplit - 1 on these tiles
+    // (the rest on tiles of their own), the others every level
+    const int32_t old_tile = plan->tile;
     plan->tile = segment;
+    int32_t len[spd::kMaxLevels], off[spd::kBdgOffsets];
+    if (!spd::bdg_two_part(*plan) &&
+        sizeof(float) * (size_t)spd::bdg_layout(*plan, segment, true, len, off) > spd::kBdgMaxSmem) {
+      plan->tile = old_tile;
+      return SPD_ERR_UNSUPPORTED;
+    }
     plan->tiles_per_row = (plan->n_starts + plan->tile - 1) / plan->tile;
     return SPD_OK;
   }

@@ -43,6 +43,12 @@ namespace spd {
 // with tiles of T starts (see the kernel's comment).
 constexpr int kWinPad = 32;
 
+// Offset in the YC, WC regions of level i >= 1's P(i) results (P(i) = T / 2^i
+// up to level lt = log2 T, then 1): the levels one after the other from level 1.
+__host__ __device__ __forceinline__ int yc_off(int T, int lt, int i) {
+  return i - 1 <= lt ? T - (T >> (i - 1)) : T - 1 + (i - 1 - lt);
+}
+
 int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off, int part, int h) {
   int lt = 0;
   while ((2 << lt) <= T) ++lt;  // log2 T
@@ -66,7 +72,7 @@ int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* o
       mb = mb > len[i] + 1 ? mb : len[i] + 1;
   }
   // each series buffer is padded: a task's last register window may read up to
-  // kGMC values past the series (never used)
+  // kGMC - 1 values past the series (never used)
   int o = 0;
   off[kBdgX0] = o;
   o += al4(len[0]) + kWinPad;
@@ -78,10 +84,15 @@ int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* o
   o += al4(T / 2);
   off[kBdgBB] = o;
   o += al4(part == 2 ? T : T / 4);  // part 2: the bases of its level 0 (X^{h-1}) come in here
-  off[kBdgY] = o;
+  off[kBdgY] = o;  // level 0's results
   o += T;
   off[kBdgW] = o;
   o += T / 2;
+  const int nyc = yc_off(T, lt, (part == 1 ? h - 1 : top) + 1);  // levels 1.. (part 1: up to h - 1)
+  off[kBdgYC] = o;
+  o += al4(nyc);
+  off[kBdgWC] = o;
+  o += al4((nyc + 1) / 2);
   off[kBdgAB] = o;  // table noise: (a, b) per width; white noise: 1/sqrt(L) per width
   o += table ? al4(2 * ((int)plan.widths.size() + kAbPad)) : al4((int)plan.widths.size());
   return o;
@@ -104,16 +115,75 @@ __device__ __forceinline__ void load_run(const float* src, float (&w)[N]) {
   }
 }
 
+// One window of G (8 or 4) block counts m0.. of a task (see bdg_task); FULL:
+// every count of the window is summed and a candidate (no per-count tests).
+template <bool TABLE, int NP, bool FULL, int G>
+__device__ __forceinline__ void bdg_window(const float* __restrict__ Xi, const float* __restrict__ SC, int n0,
+                                           int m0, int first, int nu, int mend, float (&S)[NP], float (&bv)[NP],
+                                           int (&bq)[NP]) {
+  static_assert(G <= kGMC && G % 2 == 0, "ranks in 3 bits, taken in pairs");
+  constexpr int NW = NP + G;  // NP + G - 1 values used
+  float w[NW];
+  load_run<NW, NP>(Xi + n0 + m0, w);
+  float acc[NP], c[NP];  // c: the candidate of the previous (even) rank, for a three-input max
+#pragma unroll
+  for (int r = 0; r < NP; ++r) acc[r] = ninf();
+  static_for<0, G>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    const int m = m0 + j;
+    if (FULL || m < mend) {
+#pragma unroll
+      for (int r = 0; r < NP; ++r) S[r] += w[r + j];
+    }
+    if (FULL || m < nu) {  // (nu <= mend)
+      float sc, sb = 0.0f;
+      if constexpr (TABLE) {
+        const float2 ab = reinterpret_cast<const float2*>(SC)[first + m];
+        sc = ab.x;
+        sb = ab.y;
+      } else {
+        sc = SC[first + m];
+      }
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const float e = enc_w<3>(TABLE ? fmaf(S[r], sc, sb) : S[r] * sc, (kGMC - 1) - j);
+        if constexpr ((j & 1) == 0)
+          c[r] = e;
+        else
+          acc[r] = fmax3(acc[r], c[r], e);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        if constexpr ((j & 1) == 0)
+          c[r] = ninf();
+        else
+          acc[r] = fmaxf(acc[r], c[r]);
+      }
+    }
+  });
+  static_assert(kGMC % 2 == 0, "ranks are taken in pairs");
+#pragma unroll
+  for (int r = 0; r < NP; ++r) {  // a NaN (no candidate in the window) never passes '>'
+    const float v = dec_v<3>(acc[r]);
+    const bool take = v > bv[r];
+    bv[r] = take ? v : bv[r];
+    bq[r] = take ? m0 + dec_w<3>(acc[r]) : bq[r];
+  }
+}
+
 // Level i at the NP consecutive positions n0.. of a task (n0 a multiple of NP):
-// running sums from the base (level 0: none), every partial sum times its
-// width's scale a candidate.  The block counts go in windows of kGMC: a
-// window's NP + kGMC - 1 values come in with vector loads, each candidate
-// carries its rank in the window in the 3 low mantissa bits (enc_w, smaller
-// rank wins a tie) and the window's maximum is kept running with three-input
-// max instructions; at the end of a window it is decoded and taken when
-// strictly larger than the best of the earlier windows.  S[] ends as the sum of
-// mend blocks (the next level's base); bv[], bq[] are the best SNR and its
-// block count - 1.  SC: the widths' scales (white noise) or (a, b) pairs.
+// running sums from the base (level 0 of the row: none), every partial sum
+// times its width's scale a candidate.  The block counts go in windows of G = 8
+// or 4 (bdg_window): a window's NP + G - 1 values come in with vector loads,
+// each candidate carries its rank in the window in the 3 low mantissa bits
+// (enc_w, smaller rank wins a tie) and the window's maximum is kept running
+// with three-input max instructions; at the end of a window it is decoded and
+// taken when strictly larger than the best of the earlier windows.  Windows of
+// 8, then one of 4, take counts that are all candidates, without per-count
+// tests; the rest go in windows of 4 with tests.  S[] ends as the sum of mend
+// blocks (the next level's base); bv[], bq[] are the best SNR and its block
+// count - 1.  SC: the widths' scales (white noise) or (a, b) pairs.
 template <bool TABLE, bool BASE, int NP>
 __device__ __forceinline__ void bdg_task(const float* __restrict__ Xi, const float* __restrict__ Bi,
                                          const float* __restrict__ SC, int n0, int first, int nu, int mend,
@@ -129,66 +199,25 @@ __device__ __forceinline__ void bdg_task(const float* __restrict__ Xi, const flo
     bv[r] = ninf();
     bq[r] = 0;
   }
-  constexpr int NW = NP + kGMC;  // NP + kGMC - 1 values used
-  for (int m0 = 0; m0 < mend; m0 += kGMC) {
-    float w[NW];
-    load_run<NW, NP>(Xi + n0 + m0, w);
-    float acc[NP], c[NP];  // c: the candidate of the previous (even) rank, for a three-input max
-#pragma unroll
-    for (int r = 0; r < NP; ++r) acc[r] = ninf();
-    static_for<0, kGMC>([&](auto J) {
-      constexpr int j = decltype(J)::value;
-      const int m = m0 + j;
-      if (m < mend) {
-#pragma unroll
-        for (int r = 0; r < NP; ++r) S[r] += w[r + j];
-      }
-      if (m < nu) {  // (nu <= mend)
-        float sc, sb = 0.0f;
-        if constexpr (TABLE) {
-          const float2 ab = reinterpret_cast<const float2*>(SC)[first + m];
-          sc = ab.x;
-          sb = ab.y;
-        } else {
-          sc = SC[first + m];
-        }
-#pragma unroll
-        for (int r = 0; r < NP; ++r) {
-          const float e = enc_w<3>(TABLE ? fmaf(S[r], sc, sb) : S[r] * sc, (kGMC - 1) - j);
-          if constexpr ((j & 1) == 0)
-            c[r] = e;
-          else
-            acc[r] = fmax3(acc[r], c[r], e);
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < NP; ++r) {
-          if constexpr ((j & 1) == 0)
-            c[r] = ninf();
-          else
-            acc[r] = fmaxf(acc[r], c[r]);
-        }
-      }
-    });
-    static_assert(kGMC % 2 == 0, "ranks are taken in pairs");
-#pragma unroll
-    for (int r = 0; r < NP; ++r) {  // a NaN (no candidate in the window) never passes '>'
-      const float v = dec_v<3>(acc[r]);
-      const bool take = v > bv[r];
-      bv[r] = take ? v : bv[r];
-      bq[r] = take ? m0 + dec_w<3>(acc[r]) : bq[r];
-    }
+  // windows of 8 candidates, one of 4, then windows of 4 with tests
+  int m0 = 0;
+  for (; m0 + 8 <= nu; m0 += 8) bdg_window<TABLE, NP, true, 8>(Xi, SC, n0, m0, first, nu, mend, S, bv, bq);
+  if (m0 + 4 <= nu) {
+    bdg_window<TABLE, NP, true, 4>(Xi, SC, n0, m0, first, nu, mend, S, bv, bq);
+    m0 += 4;
   }
+  for (; m0 < mend; m0 += 4) bdg_window<TABLE, NP, false, 4>(Xi, SC, n0, m0, first, nu, mend, S, bv, bq);
 }
 
-// All tasks of NP positions of level i (every thread takes P / (NP kThreads)),
-// their bases for level i + 1 and their merge into the tile's Y, W (ow: the
-// level writes its starts outright, the tile's first level; base: its sums
-// start from the bases Bi).
+// All tasks of NP positions of level i (every thread takes P / (NP kThreads)):
+// the bases of level i + 1 (next) and the level's best SNR and width index at
+// each of its P positions, into Yo, Wo (base: the sums start from the bases Bi;
+// merge: Yo, Wo already hold results of smaller widths, replaced only where
+// strictly exceeded).
 template <bool TABLE, int NP>
-__device__ __forceinline__ void bdg_level(int i, int P, bool next, bool ow, bool base, const float* Xi,
-                                          const float* Bi, float* Bn, const float* SC, int first, int nu, int mend,
-                                          float* Y, uint16_t* W) {
+__device__ __forceinline__ void bdg_level(int P, bool next, bool base, bool merge, const float* Xi, const float* Bi,
+                                          float* Bn, const float* SC, int first, int nu, int mend, float* Yo,
+                                          uint16_t* Wo) {
   for (int n0 = NP * (int)threadIdx.x; n0 < P; n0 += NP * kThreads) {
     float S[NP], bv[NP];
     int bq[NP];
@@ -196,32 +225,34 @@ __device__ __forceinline__ void bdg_level(int i, int P, bool next, bool ow, bool
       bdg_task<TABLE, false, NP>(Xi, Bi, SC, n0, first, nu, mend, S, bv, bq);
     else
       bdg_task<TABLE, true, NP>(Xi, Bi, SC, n0, first, nu, mend, S, bv, bq);
-    if (next) {  // even positions: the next level's base
-      if constexpr (NP == 8)
-        *reinterpret_cast<float4*>(Bn + (n0 >> 1)) = make_float4(S[0], S[2], S[4], S[6]);
-      else if constexpr (NP == 4)
-        *reinterpret_cast<float2*>(Bn + (n0 >> 1)) = make_float2(S[0], S[2]);
-      else
-        Bn[n0 >> 1] = S[0];
-    }
-    if (NP == 8 && ow) {  // the first level writes its starts outright
-      *reinterpret_cast<float4*>(Y + n0) = make_float4(bv[0], bv[1], bv[2], bv[3]);
-      *reinterpret_cast<float4*>(Y + n0 + 4) = make_float4(bv[4 % NP], bv[5 % NP], bv[6 % NP], bv[7 % NP]);
-      uint4 pk;
-      pk.x = (uint32_t)(first + bq[0]) | ((uint32_t)(first + bq[1]) << 16);
-      pk.y = (uint32_t)(first + bq[2 % NP]) | ((uint32_t)(first + bq[3 % NP]) << 16);
-      pk.z = (uint32_t)(first + bq[4 % NP]) | ((uint32_t)(first + bq[5 % NP]) << 16);
-      pk.w = (uint32_t)(first + bq[6 % NP]) | ((uint32_t)(first + bq[7 % NP]) << 16);
-      *reinterpret_cast<uint4*>(W + n0) = pk;
-    } else {
+#pragma unroll
+    for (int r = 0; r < NP; ++r) bq[r] += first;
+    if (merge) {  // keep the SNRs already there unless strictly exceeded (they have the smaller widths)
+      float yo[NP];
+      load_run<NP, NP>(Yo + n0, yo);
 #pragma unroll
       for (int r = 0; r < NP; ++r) {
-        const int s = (n0 + r) << i;
-        if (ow || bv[r] > Y[s]) {
-          Y[s] = bv[r];
-          W[s] = (uint16_t)(first + bq[r]);
-        }
+        const bool keep = !(bv[r] > yo[r]);
+        bv[r] = keep ? yo[r] : bv[r];
+        bq[r] = keep ? (int)Wo[n0 + r] : bq[r];
       }
+    }
+    uint32_t pk[NP / 2];
+#pragma unroll
+    for (int r = 0; r < NP / 2; ++r) pk[r] = (uint32_t)bq[2 * r] | ((uint32_t)bq[2 * r + 1] << 16);
+    if constexpr (NP == 8) {
+      if (next) *reinterpret_cast<float4*>(Bn + (n0 >> 1)) = make_float4(S[0], S[2], S[4], S[6]);
+      *reinterpret_cast<float4*>(Yo + n0) = make_float4(bv[0], bv[1], bv[2], bv[3]);
+      *reinterpret_cast<float4*>(Yo + n0 + 4) = make_float4(bv[4 % NP], bv[5 % NP], bv[6 % NP], bv[7 % NP]);
+      *reinterpret_cast<uint4*>(Wo + n0) = make_uint4(pk[0], pk[1 % (NP / 2)], pk[2 % (NP / 2)], pk[3 % (NP / 2)]);
+    } else if constexpr (NP == 4) {
+      if (next) *reinterpret_cast<float2*>(Bn + (n0 >> 1)) = make_float2(S[0], S[2 % NP]);
+      *reinterpret_cast<float4*>(Yo + n0) = make_float4(bv[0], bv[1], bv[2 % NP], bv[3 % NP]);
+      *reinterpret_cast<uint2*>(Wo + n0) = make_uint2(pk[0], pk[1 % (NP / 2)]);
+    } else {
+      if (next) Bn[n0 >> 1] = S[0];
+      *reinterpret_cast<float2*>(Yo + n0) = make_float2(bv[0], bv[1 % NP]);
+      *reinterpret_cast<uint32_t*>(Wo + n0) = pk[0];
     }
   }
 }
@@ -259,8 +290,12 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
   float* XB = smem + p.gen_off[kBdgXB];
   float* BA = smem + p.gen_off[kBdgBA];
   float* BB = smem + p.gen_off[kBdgBB];
+  // level 0's best SNR and width index at each of its T positions; levels 1..
+  // in YC, WC, level i at offset yc_off(i)
   float* Y = smem + p.gen_off[kBdgY];
   uint16_t* W = reinterpret_cast<uint16_t*>(smem + p.gen_off[kBdgW]);
+  float* YC = smem + p.gen_off[kBdgYC];
+  uint16_t* WC = reinterpret_cast<uint16_t*>(smem + p.gen_off[kBdgWC]);
   int lt = 0;
   while ((2 << lt) <= T) ++lt;
   // levels with positions in this tile: a level of unit 2^i > T has one, at t0,
@@ -312,11 +347,15 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
           *reinterpret_cast<float2*>(XA + 2 * (q1 + j - nq0)) = make_float2(v[b].x + v[b].y, v[b].z + v[b].w);
       }
     }
-    if constexpr (P2) {  // the bases of level h, and the Y, W the first part left at its starts
+    if constexpr (P2) {  // the bases of level h, and the SNRs and widths the first part stored at its starts
       const float* bh = p.gen_bh + U.row * p.gen_ldh;
+      for (int n = 4 * t; n < T; n += 4 * kThreads) {  // (nxh and t0 multiples of 4)
+        const int64_t v = t0 + n;
+        *reinterpret_cast<float4*>(BB + n) =
+            v < nxh ? __ldg(reinterpret_cast<const float4*>(bh + v)) : make_float4(0, 0, 0, 0);
+      }
       for (int n = t; n < T; n += kThreads) {
-        const int64_t v = t0 + n, st = v << h;
-        BB[n] = v < nxh ? bh[v] : 0.0f;
+        const int64_t st = (t0 + n) << h;
         const bool in = st < U.ns;
         Y[n] = in ? U.yrow[st] : ninf();
         W[n] = in ? U.wrow[st] : (uint16_t)0;
@@ -325,7 +364,7 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
   }
   __syncthreads();
 
-  // ---- levels 0..tt: evaluate, merge, decimate; one barrier per level ----
+  // ---- levels 0..tt: evaluate, decimate; one barrier per level ----
   for (int i = 0; i <= tt; ++i) {
     const int P = i <= lt ? T >> i : 1;
     const int k = p.lvl_k[i + lo];
@@ -333,17 +372,21 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
     const bool next = i < tt || P1;                  // a next level (part 1: level h) needs the bases
     const int mend = next ? k : nu;                  // blocks summed (the next level needs all k)
     const int first = p.lvl_first[i + lo];
-    const bool ow = i == 0 && !P2, base = i > 0 || P2;
+    const bool base = i > 0 || P2;
     const float* Xi = (i == 0) ? X0 : ((i & 1) ? XA : XB);
     const float* Bi = (i & 1) ? BA : BB;
     float* Bn = (i & 1) ? BB : BA;
+    const int yo = yc_off(T, lt, i);
+    float* Yo = i == 0 ? Y : YC + yo;
+    uint16_t* Wo = i == 0 ? W : WC + yo;
     const int per = P / kThreads;  // positions per thread (P and kThreads are powers of two)
+    const bool merge = P2 && i == 0;  // merged into the stored SNRs of the first part
     if (per >= 8) {
-      bdg_level<TABLE, 8>(i, P, next, ow, base, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+      bdg_level<TABLE, 8>(P, next, base, merge, Xi, Bi, Bn, SC, first, nu, mend, Yo, Wo);
     } else if (per == 4) {
-      bdg_level<TABLE, 4>(i, P, next, ow, base, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+      bdg_level<TABLE, 4>(P, next, base, merge, Xi, Bi, Bn, SC, first, nu, mend, Yo, Wo);
     } else if (per == 2) {
-      bdg_level<TABLE, 2>(i, P, next, ow, base, Xi, Bi, Bn, SC, first, nu, mend, Y, W);
+      bdg_level<TABLE, 2>(P, next, base, merge, Xi, Bi, Bn, SC, first, nu, mend, Yo, Wo);
     } else for (int n = t; n < P; n += kThreads) {  // at most one position per thread
       float S = base ? Bi[n] : 0.0f;
       float best = ninf();
@@ -367,10 +410,9 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
       }
       for (; m < mend; ++m) S += xs[m];
       if (next && (n & 1) == 0) Bn[n >> 1] = S;
-      const int s = n << i;
-      if (ow || best > Y[s]) {
-        Y[s] = best;
-        W[s] = (uint16_t)(first + bq);
+      if (!merge || best > Yo[n]) {
+        Yo[n] = best;
+        Wo[n] = (uint16_t)(first + bq);
       }
     }
     if (i == 0 && tt >= 1) {  // x^1[u] for u below the split, from x^0's window
@@ -403,35 +445,62 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
     }
   }
 
-  if constexpr (P2) {  // ---- store back the starts of levels h..: strided, key per warp step ----
+  // merge of the levels above level 0 at local position n of level 0 (levels in
+  // increasing width order, strict '>': the smaller width keeps a tie)
+  auto merge_up = [&](int n, int i1, float& y, int& w) {
+    for (int i = i1; i <= tt && (n & ((1 << i) - 1)) == 0; ++i) {
+      const int o = yc_off(T, lt, i) + (n >> i);
+      const float v = YC[o];
+      if (v > y) {
+        y = v;
+        w = WC[o];
+      }
+    }
+  };
+
+  if constexpr (P2) {  // ---- store the starts of levels h..: strided, key per warp step ----
     const int warp = t >> 5, lane = t & 31;
     for (int n0 = 32 * warp; n0 < T; n0 += kThreads) {
       const int n = n0 + lane;
       const int64_t st = (t0 + n) << h;
-      const bool in = st < U.ns;
-      if (in) {
-        U.yrow[st] = Y[n];
-        U.wrow[st] = W[n];
+      float y = Y[n];
+      int w = W[n];
+      merge_up(n, 1, y, w);
+      if (st < U.ns) {
+        U.yrow[st] = y;
+        U.wrow[st] = (uint16_t)w;
       }
       if (((t0 + n0) << h) < U.ns)  // warp-uniform: the warp's starts lie in one candidate tile
-        tile_max_atomic(U.tm_row, (t0 + n0) << h, in ? Y[n] : ninf());
+        tile_max_atomic(U.tm_row, (t0 + n0) << h, st < U.ns ? y : ninf());
     }
     return;
   }
 
-  // ---- store the tile; its maximum goes to the candidate-tile key ----
+  // ---- merge and store the tile; its maximum goes to the candidate-tile key ----
   const int64_t sleft = U.ns - t0;
   const int srel = (int)(sleft < (int64_t)T ? sleft : (int64_t)T);
   float tmax = ninf();
   for (int q = t; 4 * q < srel; q += kThreads) {
-    float y[4];
-    int w[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      y[r] = Y[4 * q + r];
-      w[r] = W[4 * q + r];
-      if (4 * q + r < srel) tmax = fmaxf(tmax, y[r]);
+    const float4 y4 = *reinterpret_cast<const float4*>(Y + 4 * q);
+    const uint2 w4 = *reinterpret_cast<const uint2*>(W + 4 * q);
+    float y[4] = {y4.x, y4.y, y4.z, y4.w};
+    int w[4] = {(int)(w4.x & 0xffffu), (int)(w4.x >> 16), (int)(w4.y & 0xffffu), (int)(w4.y >> 16)};
+    if (tt >= 1) {  // level 1 at the starts 4q and 4q + 2, then levels 2.. at 4q
+      const float2 y1 = *reinterpret_cast<const float2*>(YC + 2 * q);  // (level 1 at offset 0)
+      const uint32_t w1 = *reinterpret_cast<const uint32_t*>(WC + 2 * q);
+      if (y1.x > y[0]) {
+        y[0] = y1.x;
+        w[0] = (int)(w1 & 0xffffu);
+      }
+      if (y1.y > y[2]) {
+        y[2] = y1.y;
+        w[2] = (int)(w1 >> 16);
+      }
+      merge_up(4 * q, 2, y[0], w[0]);
     }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (4 * q + r < srel) tmax = fmaxf(tmax, y[r]);
     store4(U.yrow, U.wrow, t0 + 4 * q, U.ns, U.vec, y, w);
   }
   if (t0 < U.ns) tile_max_atomic(U.tm_row, t0, tmax);  // (the first part covers the row up to nt)

@@ -61,7 +61,7 @@ enum Family { kExhaustive = 0, kBoxdit = 1, kIgrid = 2 };
 
 // General BoxDIT kernel (spd_boxdit_gen.cu): offsets of its shared-memory
 // regions in SearchParams::gen_off, and the largest L^i_max of a plan.
-enum BdgRegion { kBdgX0 = 0, kBdgXA, kBdgXB, kBdgBA, kBdgBB, kBdgY, kBdgW, kBdgAB, kBdgOffsets };
+enum BdgRegion { kBdgX0 = 0, kBdgXA, kBdgXB, kBdgBA, kBdgBB, kBdgY, kBdgW, kBdgYC, kBdgWC, kBdgAB, kBdgOffsets };
 constexpr int kMaxBoxditK = 256;
 
 // Search kernel parameters (passed by value; lives in the constant bank).
