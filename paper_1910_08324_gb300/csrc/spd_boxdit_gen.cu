@@ -5,8 +5,8 @@
 // Iteration i (level i) has unit 2^i, starts s = n 2^i and the widths
 // c_i + m 2^i, m = 1..k_i, with c_i = sum_{j<i} k_j 2^j (= L^{i-1}_MAX).  The
 // kernel runs Alg. 1 as the paper states it, on one tile of T starts of one
-// row (T = 4096 when two CTAs fit on an SM, else 2048; spd_plan_set_segment
-// picks 2048, 4096 or 8192):
+// row (T = 4096 when the layout allows several CTAs per SM, else 2048;
+// spd_plan_set_segment picks 2048, 4096 or 8192):
 //   * the shifted decimated series x^i of the tile live in shared memory:
 //     x^0 over the tile and its level-0 lookahead, x^1 summed in pairs
 //     (x^1[u] = x^0[2u + k_0] + x^0[2u + k_0 + 1], the decimation of Sec. 3.1
@@ -16,7 +16,7 @@
 //     every series as long as the levels above still need it;
 //   * level i evaluates its T / 2^i positions.  With 2, 4 or 8 or more per
 //     thread, a thread takes tasks of 2, 4 or 8 consecutive positions and runs
-//     them together on register windows of 8 block counts, each candidate
+//     them together on register windows of 8 or 4 block counts, each candidate
 //     coded with its rank in the window (bdg_task); with fewer, one position
 //     per thread, consecutive positions on consecutive lanes.  Either way the
 //     sum starts from the base X^{i-1} at the position (kept by level i - 1)
@@ -24,10 +24,20 @@
 //     width's scale (a shared-memory table) being a candidate (strict '>', so
 //     the smaller width wins a tie); the full sum of k_i blocks at an even
 //     position is the next level's base;
-//   * each level merges its maxima into the tile's Y and W in shared memory
-//     (levels in increasing width order, strict '>'), one barrier per level;
-//     the tile is then stored with vector stores, and its maximum goes to the
+//   * each level writes its best SNR and width index per position into an
+//     array of its own in shared memory (level 0's over the tile's starts, the
+//     others over x^0's buffer, dead by then), one barrier per level; the tile
+//     store merges the levels at each start (increasing width order, strict
+//     '>'), stores with vector stores, and folds the maximum into the
 //     candidate-tile key.
+// Plans above level kBdgSplit (4) run in two kernels.  The first takes levels
+// 0-3 on the tiles above (three CTAs per SM) and also writes x^4 and the level-3
+// bases of its positions (X^3 at even positions) to the workspace; the second
+// takes levels 4.. on tiles of kBdgTile2 positions of x^4 (a level-4 position
+// is 16 starts), starting from those bases, and merges into the SNRs and widths
+// the first stored at its starts.  The levels above 3 then see tiles of 32768
+// starts, so their halo (the widest boxcar) is read 16 times less often and
+// their positions fill the CTA.
 // The series past the tile (the halo, up to the widest boxcar) are re-read by
 // the neighbouring tiles' CTAs; the widest boxcar of a plan is at most 32768
 // samples.  Samples past the end of the row are -inf, so a boxcar needing them
@@ -89,8 +99,12 @@ int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* o
   off[kBdgW] = o;
   o += T / 2;
   const int nyc = yc_off(T, lt, (part == 1 ? h - 1 : top) + 1);  // levels 1.. (part 1: up to h - 1)
-  off[kBdgYC] = o;
-  o += al4(nyc);
+  if (nyc <= al4(len[0]) + kWinPad) {
+    off[kBdgYC] = off[kBdgX0];  // x^0 is dead once level 0 is done
+  } else {
+    off[kBdgYC] = o;
+    o += al4(nyc);
+  }
   off[kBdgWC] = o;
   o += al4((nyc + 1) / 2);
   off[kBdgAB] = o;  // table noise: (a, b) per width; white noise: 1/sqrt(L) per width
@@ -507,7 +521,7 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
 }
 
 template <bool TABLE, int PART>
-__global__ void __launch_bounds__(kThreads, 2) boxdit_gen_kernel(const SearchParams p) {
+__global__ void __launch_bounds__(kThreads, PART == 0 ? 2 : 3) boxdit_gen_kernel(const SearchParams p) {
   extern __shared__ __align__(16) float smem[];
   bdg_unit<TABLE, PART>(p, plan_unit(p, blockIdx.x), smem);
 }

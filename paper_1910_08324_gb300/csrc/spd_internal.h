@@ -197,7 +197,7 @@ size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
 // bases X^{h-1}); 2: levels h..top of the series x^h, in tiles of T positions
 int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off, int part = 0, int h = 0);
 constexpr int kBdgSplit = 4;     // general BoxDIT plans above this level run in two kernels
-constexpr int kBdgTile2 = 4096;  // level-kBdgSplit positions per tile of the second
+constexpr int kBdgTile2 = 2048;  // level-kBdgSplit positions per tile of the second
 constexpr size_t kBdgMaxSmem = 227 * 1024;  // shared memory of one CTA at most
 // positions of x^h kept per row (the first kernel covers the row in tiles of T starts)
 inline int64_t bdg_ldh(int64_t nt, int T) { return ((nt + T - 1) / T) * (int64_t)(T >> kBdgSplit); }

@@ -138,8 +138,8 @@ def test_row_stride_and_evaluated_starts():
 @pytest.mark.parametrize("segment", [2048, 4096, 8192])
 def test_two_kernel_form_tiles(segment):
     """A plan above level 4 runs levels 0-3 on tiles of 2048, 4096 or 8192
-    starts, then levels 4.. on the series x^4 in tiles of 4096 level-4 positions
-    (65 536 starts): rows of two such tiles and a ragged third, with fewer
+    starts, then levels 4.. on the series x^4 in tiles of 2048 level-4 positions
+    (32 768 starts): rows of four such tiles and a ragged fifth, with fewer
     evaluated starts than samples."""
     ndm, nt, ns = 2, 150001, 140003
     x = _data(ndm, nt, 17 + segment)
