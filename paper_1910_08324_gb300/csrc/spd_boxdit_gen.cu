@@ -146,21 +146,36 @@ __device__ __forceinline__ void bdg_window(const float* __restrict__ Xi, const f
     constexpr int j = decltype(J)::value;
     const int m = m0 + j;
     if (FULL || m < mend) {
+      if constexpr ((j & 1) == 0) {  // aligned pairs of the window: packed f32x2 adds (the same roundings)
 #pragma unroll
-      for (int r = 0; r < NP; ++r) S[r] += w[r + j];
+        for (int q = 0; q < NP / 2; ++q) {
+          const float2 s2 = __fadd2_rn(make_float2(S[2 * q], S[2 * q + 1]), make_float2(w[2 * q + j], w[2 * q + j + 1]));
+          S[2 * q] = s2.x;
+          S[2 * q + 1] = s2.y;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < NP; ++r) S[r] += w[r + j];
+      }
     }
     if (FULL || m < nu) {  // (nu <= mend)
-      float sc, sb = 0.0f;
+      float x[NP];
       if constexpr (TABLE) {
         const float2 ab = reinterpret_cast<const float2*>(SC)[first + m];
-        sc = ab.x;
-        sb = ab.y;
+#pragma unroll
+        for (int r = 0; r < NP; ++r) x[r] = fmaf(S[r], ab.x, ab.y);
       } else {
-        sc = SC[first + m];
+        const float sc = SC[first + m];
+#pragma unroll
+        for (int q = 0; q < NP / 2; ++q) {  // two positions per scale instruction (packed f32x2)
+          const float2 x2 = __fmul2_rn(make_float2(S[2 * q], S[2 * q + 1]), make_float2(sc, sc));
+          x[2 * q] = x2.x;
+          x[2 * q + 1] = x2.y;
+        }
       }
 #pragma unroll
       for (int r = 0; r < NP; ++r) {
-        const float e = enc_w<3>(TABLE ? fmaf(S[r], sc, sb) : S[r] * sc, (kGMC - 1) - j);
+        const float e = enc_w<3>(x[r], (kGMC - 1) - j);
         if constexpr ((j & 1) == 0)
           c[r] = e;
         else
