@@ -669,10 +669,17 @@ __device__ __forceinline__ void igrid_unit(const SearchParams& p, const Unit& U,
   }
 }
 
+// CTAs per SM the registers are sized for (measured per grid on 4 096 x 1 048 576
+// rows: IG(2) 15.8 / 15.2 / 14.8 ms at 2 / 3 / 4 CTAs, IG(3) 25.2 / 24.0 / 24.4 ms)
+template <int D, int PL>
+constexpr int ig_min_ctas() {
+  return (IgS<D, PL>::MMAX <= 6 || (D == 2 && PL == 3)) ? 4 : 3;
+}
+
 // One CTA per unit of a single-series search (DT: input type fixed at compile
 // time, or -1: read from the parameters).
 template <int D, int PL, bool COARSE, bool TABLE, int DT>
-__global__ void __launch_bounds__(kThreads, (IgS<D, PL>::MMAX <= 6 ? 4 : 2)) igrid_stream_kernel(const SearchParams p) {
+__global__ void __launch_bounds__(kThreads, (ig_min_ctas<D, PL>())) igrid_stream_kernel(const SearchParams p) {
   extern __shared__ __align__(16) float smem[];
   igrid_unit<D, PL, COARSE, TABLE, DT>(p, plan_unit(p, blockIdx.x), smem);
 }
