@@ -160,8 +160,9 @@ int dtype_size(int dtype) {
 // Workspace: tile maxima (written by the search, read by the candidate step),
 // per-tile candidate counts, per-group sums and offsets, and the level
 // statistics of spd_noise_stats.
-// General BoxDIT plans above level kBdgSplit also keep the series x^h and the
-// bases X^{h-1} of every row between their two kernels.
+// General BoxDIT plans above level kBdgSplit also keep the series x^h, the
+// bases X^{h-1} and the first kernel's results at level h's starts of every row
+// between their two kernels.
 struct WsLayout {
   size_t tile_max, counts, gsum, goff, msd, gen, total;
   int64_t gen_ldh;
@@ -175,7 +176,8 @@ struct WsLayout {
     msd = align_up(goff + ng * sizeof(int64_t));
     gen = align_up(msd + spd::msd_state_bytes(p.desc.ndm));
     gen_ldh = spd::bdg_two_part(p) ? spd::bdg_ldh(p.desc.nt, p.tile) : 0;
-    total = align_up(gen + 2 * sizeof(float) * (size_t)(p.desc.ndm * gen_ldh));
+    // x^h, the bases, and the first kernel's SNRs and widths at level h's starts
+    total = align_up(gen + (3 * sizeof(float) + sizeof(uint16_t)) * (size_t)(p.desc.ndm * gen_ldh));
   }
 };
 
@@ -259,6 +261,8 @@ spd_status do_execute(const spd_plan* plan, const void* d_x, const spd_noise* no
   if (wl.gen_ldh > 0) {
     p.gen_xh = reinterpret_cast<float*>(static_cast<char*>(d_ws) + wl.gen);
     p.gen_bh = p.gen_xh + plan->desc.ndm * wl.gen_ldh;
+    p.gen_yh = p.gen_bh + plan->desc.ndm * wl.gen_ldh;
+    p.gen_wh = reinterpret_cast<uint16_t*>(p.gen_yh + plan->desc.ndm * wl.gen_ldh);
     p.gen_ldh = wl.gen_ldh;
   }
   p.table = noise->mode == 1 ? 1 : 0;

@@ -383,11 +383,13 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
         *reinterpret_cast<float4*>(BB + n) =
             v < nxh ? __ldg(reinterpret_cast<const float4*>(bh + v)) : make_float4(0, 0, 0, 0);
       }
+      const float* yh = p.gen_yh + U.row * p.gen_ldh;  // (copies of the first part's, coalesced)
+      const uint16_t* wh = p.gen_wh + U.row * p.gen_ldh;
       for (int n = t; n < T; n += kThreads) {
-        const int64_t st = (t0 + n) << h;
-        const bool in = st < U.ns;
-        Y[n] = in ? U.yrow[st] : ninf();
-        W[n] = in ? U.wrow[st] : (uint16_t)0;
+        const int64_t v = t0 + n;
+        const bool in = (v << h) < U.ns;
+        Y[n] = in ? yh[v] : ninf();
+        W[n] = in ? wh[v] : (uint16_t)0;
       }
     }
   }
@@ -488,6 +490,9 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
   };
 
   if constexpr (P2) {  // ---- store the starts of levels h..: strided, key per warp step ----
+    // only where a level above h - 1 won: a different (wider) width than the
+    // first part stored there (strided stores fill partial sectors)
+    const uint16_t* wh = p.gen_wh + U.row * p.gen_ldh;
     const int warp = t >> 5, lane = t & 31;
     for (int n0 = 32 * warp; n0 < T; n0 += kThreads) {
       const int n = n0 + lane;
@@ -495,7 +500,7 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
       float y = Y[n];
       int w = W[n];
       merge_up(n, 1, y, w);
-      if (st < U.ns) {
+      if (st < U.ns && w != (int)wh[t0 + n]) {
         U.yrow[st] = y;
         U.wrow[st] = (uint16_t)w;
       }
@@ -531,6 +536,11 @@ __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, f
     for (int r = 0; r < 4; ++r)
       if (4 * q + r < srel) tmax = fmaxf(tmax, y[r]);
     store4(U.yrow, U.wrow, t0 + 4 * q, U.ns, U.vec, y, w);
+    if (P1 && ((4 * q) & ((1 << h) - 1)) == 0) {  // a start of level h: a copy for the second part
+      const int64_t v = (t0 + 4 * q) >> h;
+      p.gen_yh[U.row * p.gen_ldh + v] = y[0];
+      p.gen_wh[U.row * p.gen_ldh + v] = (uint16_t)w[0];
+    }
   }
   if (t0 < U.ns) tile_max_atomic(U.tm_row, t0, tmax);  // (the first part covers the row up to nt)
 }

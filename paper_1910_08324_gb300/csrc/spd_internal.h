@@ -109,10 +109,13 @@ struct SearchParams {
   float wscale[kMaxGridWidths];
   // the two-kernel form of larger plans: gen_part 1 runs levels below gen_h and
   // writes x^gen_h and the bases X^{gen_h - 1} of every row to gen_xh / gen_bh
-  // ([ndm][gen_ldh]); gen_part 2 runs levels gen_h..top on them
+  // and its SNRs and width indices at the starts of level gen_h to gen_yh /
+  // gen_wh (all [ndm][gen_ldh]); gen_part 2 runs levels gen_h..top on them
   int32_t gen_part, gen_h;
   float* gen_xh;
   float* gen_bh;
+  float* gen_yh;
+  uint16_t* gen_wh;
   int64_t gen_ldh;
   BatchRange ranges[kMaxRanges];
 };

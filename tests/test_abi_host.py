@@ -205,9 +205,10 @@ def test_per_iteration_boxdit_plan_rules():
 
 
 def test_two_kernel_form_workspace():
-    """General BoxDIT plans above level 4 keep x^4 and the level-3 bases of every
-    row in the workspace (2 floats per 16 samples, rounded up to whole first-kernel
-    tiles); plans up to level 4 need none."""
+    """General BoxDIT plans above level 4 keep x^4, the level-3 bases and the first
+    kernel's SNR and width index at every 16th start of every row in the workspace
+    (3 floats and a u16 per 16 samples, rounded up to whole first-kernel tiles);
+    plans up to level 4 need none."""
     ndm, nt = 3, 100000
     low = spd.spd_plan_create_boxdit([6], 20, ndm=ndm, nt=nt)     # widths up to 42: levels 0-2
     high = spd.spd_plan_create_boxdit([6], 8192, ndm=ndm, nt=nt)  # levels 0-10
@@ -216,8 +217,8 @@ def test_two_kernel_form_workspace():
     for seg in (2048, 4096, 8192):
         spd.spd_plan_set_segment(high, seg)
         ldh = -(-nt // seg) * (seg // 16)
-        assert high.workspace_size() - base.workspace_size() >= 2 * 4 * ndm * ldh
-        assert high.workspace_size() - base.workspace_size() < 2 * 4 * ndm * ldh + 512
+        assert high.workspace_size() - base.workspace_size() >= (3 * 4 + 2) * ndm * ldh
+        assert high.workspace_size() - base.workspace_size() < (3 * 4 + 2) * ndm * ldh + 512
 
 
 def test_proposal_rules():
