@@ -81,6 +81,16 @@ def algo_family(algo):
     return {0: "exhaustive", 1: "boxdit", 2: "igrid"}[ALGOS[algo]["algo"]]
 
 
+def search_launches(algo, widths):
+    """Kernel launches of one search: the general BoxDIT kernel (an L^i_max other
+    than 8, 16 or 32) runs a plan above level 4 (more than the 5 k widths of levels
+    0-4) as two launches, every other grid as one."""
+    k = ALGOS[algo].get("boxdit_lmax")
+    if ALGOS[algo]["algo"] == 1 and k not in (8, 16, 32) and len(widths) > 5 * k:
+        return 2
+    return 1
+
+
 # uneven DM ranges of one batched search: (DM trials, time decimation) of a 2,097,152-sample base
 BATCH_RANGES = [(1024, 1), (1024, 2), (768, 4), (512, 8), (256, 16)]
 BATCH_BASE = 2097152
@@ -1266,7 +1276,7 @@ def main():
             "snr_loss": loss,
             "components": components,
             "e2e": e2e,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (search_launches(args.algo, widths) + 3) * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

@@ -31,13 +31,14 @@
 //     '>'), stores with vector stores, and folds the maximum into the
 //     candidate-tile key.
 // Plans above level kBdgSplit (4) run in two kernels.  The first takes levels
-// 0-3 on the tiles above (three CTAs per SM) and also writes x^4 and the level-3
-// bases of its positions (X^3 at even positions) to the workspace; the second
-// takes levels 4.. on tiles of kBdgTile2 positions of x^4 (a level-4 position
-// is 16 starts), starting from those bases, and merges into the SNRs and widths
-// the first stored at its starts.  The levels above 3 then see tiles of 32768
-// starts, so their halo (the widest boxcar) is read 16 times less often and
-// their positions fill the CTA.
+// 0-3 on the tiles above (three CTAs per SM) and also writes x^4, the level-3
+// bases of its positions (X^3 at even positions) and a copy of its SNR and width
+// at every 16th start to the workspace; the second takes levels 4.. on tiles of
+// kBdgTile2 positions of x^4 (a level-4 position is 16 starts), starting from
+// those bases and that copy, and rewrites a start only where a wider level won
+// (strided stores touch partial sectors, so the fewer the better).  The levels
+// above 3 then see tiles of 32768 starts, so their halo (the widest boxcar) is
+// read 16 times less often and their positions fill the CTA.
 // The series past the tile (the halo, up to the widest boxcar) are re-read by
 // the neighbouring tiles' CTAs; the widest boxcar of a plan is at most 32768
 // samples.  Samples past the end of the row are -inf, so a boxcar needing them

@@ -104,3 +104,12 @@ def test_workloads_and_defaults(bench, monkeypatch):
     assert (a.ndm, a.nt, a.s_end) == (4096, 1 << 20, 8192)
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "noise_stats"])
     assert bench.parse().workload == "noise_stats"
+
+
+def test_search_launches_of_each_grid(bench):
+    import paper_1910_08324_gb300 as spd
+    for algo, n in (("ig1", 1), ("bd16", 1), ("bd12", 2), ("bd24", 2)):
+        plan = spd.spd_plan_create(ndm=1, nt=1 << 16, s_end=8192, **bench.ALGOS[algo])
+        assert bench.search_launches(algo, plan.widths()[0]) == n, algo
+    low = spd.spd_plan_create(ndm=1, nt=1 << 16, s_end=40, **bench.ALGOS["bd12"])  # levels 0-1 only
+    assert bench.search_launches("bd12", low.widths()[0]) == 1
