@@ -2,7 +2,8 @@
 bench.py times.
 
 * exhaustive_small (64 x 65,536, widths 1..256): full element-wise parity.
-* ska_mid (4,096 x 1,048,576, IGRID IG(1) / BoxDIT BD-32, S_end = 8192): parity on
+* ska_mid (4,096 x 1,048,576, IGRID IG(1) / BoxDIT BD-32 / BoxDIT with L^i_max = 12
+  on the general kernel's two launches, S_end = 8192): parity on
   sampled rows (the pulse rows, the first and the last), properties that hold at
   any size on every row (Y >= the width-1 SNR, widths in range), and recall of
   the injected pulses through the fused candidate step.
@@ -35,7 +36,7 @@ def test_exhaustive_small_full_parity():
     assert hits == len(tab)
 
 
-@pytest.mark.parametrize("name", ["ig1", "bd32"])
+@pytest.mark.parametrize("name", ["ig1", "bd32", "bd12"])
 def test_ska_mid_full_size(name):
     t = torch()
     cfg = spd_synth.SKA_MID
