@@ -87,6 +87,16 @@ def test_tiny_and_tile_edge_rows(nt):
     assert np.array_equal(Wg[:, nt - 1], [0, 0])  # the last sample only has width 1
 
 
+@pytest.mark.parametrize("nt", [1, 37, 4097, 16385, 33000])
+def test_two_kernel_form_short_rows(nt):
+    # a plan above level 4 on rows shorter than its widest boxcars, than one
+    # first-kernel tile or than one second-kernel tile (32 768 starts)
+    x = _data(2, nt, 31 + nt, max_w=300)
+    plan = spd.spd_plan_create(algo=spd.SPD_ALGO_BOXDIT, s_end=2000, ndm=2, nt=nt, boxdit_lmax=6)
+    assert oracle_grid(plan).L[-1] > 16 * 6  # widths above level 4
+    _check(plan, x, 0.0, 1.0, "nt=%d" % nt)
+
+
 @pytest.mark.parametrize("name", ["bd2", "bd12", "bd64"])
 def test_table_noise_parity(name):
     ndm, nt = 3, 30001
