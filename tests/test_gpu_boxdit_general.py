@@ -65,6 +65,8 @@ PER_ITER = [
     ((2, 4, 6), 8192, 0, 2, 40000), ((6, 2), 3000, 0, 2, 20001), ((32, 16, 8), 8192, 0, 2, 40000),
     ((64, 2), 9000, 0, 2, 30000), ((8, 8, 8, 8, 16), 8192, 0, 2, 33333), ((4, 6, 8, 10, 12), 5000, 0, 2, 25000),
     ((12,), 1, 6, 2, 30000), ((2, 30), 1, 9, 2, 33000), ((8,), 1, 10, 2, 20000),
+    # the second of the two kernels with many block counts per level, the first with few, and the reverse
+    ((2, 2, 2, 2, 64), 8192, 0, 2, 40000), ((128, 2, 2, 2, 2, 32), 6000, 0, 2, 30000),
 ]
 
 
