@@ -97,45 +97,87 @@ struct TileSpan {
 };
 
 // The warp's SNRs at starts b + u*32 + lane, u < kUnroll (all loads issued
-// before any is used); -inf past the tile.
+// before any is used); -inf at and past lim (<= the tile's end).
 constexpr int kUnroll = 16;
-__device__ __forceinline__ void load_block(const TileSpan& ts, int64_t b, int lane, float (&v)[kUnroll]) {
+__device__ __forceinline__ void load_block(const TileSpan& ts, int64_t b, int64_t lim, int lane,
+                                           float (&v)[kUnroll]) {
 #pragma unroll
   for (int u = 0; u < kUnroll; ++u) {
     const int64_t s = b + u * 32 + lane;
-    v[u] = (s < ts.end) ? __ldcs(ts.y + s) : __int_as_float(0xff800000u);
+    v[u] = (s < lim) ? __ldcs(ts.y + s) : __int_as_float(0xff800000u);
   }
 }
 
+// A tile with candidates is scanned by all kCtaWarps warps of a CTA at once, one
+// segment each (a whole number of 32 * kUnroll-start blocks).
+constexpr int kCtaWarps = kCandThreads / 32;
+__device__ __forceinline__ int64_t seg_len(const CandParams& p) {
+  const int64_t per = (p.tile + kCtaWarps - 1) / kCtaWarps;
+  return (per + 32 * kUnroll - 1) / (32 * kUnroll) * (32 * kUnroll);
+}
+
+// Candidates among the starts [b0, b1) of a tile (one warp; the warp's total).
+__device__ __forceinline__ int count_span(const CandParams& p, const TileSpan& ts, int64_t b0, int64_t b1,
+                                         int lane) {
+  int c = 0;
+  for (int64_t b = b0; b < b1; b += 32 * kUnroll) {
+    float v[kUnroll];
+    load_block(ts, b, b1, lane, v);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (v[u] >= p.thr && in_window(p, b + u * 32 + lane))
+        c += is_cand(ts.y, b + u * 32 + lane, ts.lo, ts.hi, p.thr, p.radius) ? 1 : 0;
+  }
+  return warp_sum(c);
+}
+
+// A CTA takes kCtaWarps consecutive groups at a time: each warp reads its
+// group's 32 tile maxima, then the CTA counts the tiles at or above the
+// threshold one after the other, all warps on each (one segment per warp).
 __global__ void __launch_bounds__(kCandThreads) cand_count_kernel(const CandParams p, int64_t ntiles,
                                                                   int64_t ngroups) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (kCandThreads / 32);
-  for (int64_t g = (int64_t)blockIdx.x * (kCandThreads / 32) + (threadIdx.x >> 5); g < ngroups; g += nwarps) {
+  __shared__ unsigned hot[kCtaWarps];
+  __shared__ int segc[kCtaWarps];
+  __shared__ int gs[kCtaWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t seg = seg_len(p);
+  for (int64_t g0 = (int64_t)blockIdx.x * kCtaWarps; g0 < ngroups; g0 += (int64_t)gridDim.x * kCtaWarps) {
+    const int64_t g = g0 + warp;
     const int64_t tile = g * kCandGroup + lane;
-    bool live = tile < ntiles;
+    const bool in = g < ngroups && tile < ntiles;
+    bool live = in;
     if (live && p.tile_max) live = key_to_float(reinterpret_cast<const int*>(p.tile_max)[tile]) >= p.thr;
-    unsigned todo = __ballot_sync(kFull, live);
-    int mine = 0;
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const TileSpan ts(p, g * kCandGroup + src);
-      int c = 0;
-      for (int64_t b = ts.t0; b < ts.end; b += 32 * kUnroll) {
-        float v[kUnroll];
-        load_block(ts, b, lane, v);
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-          if (v[u] >= p.thr && in_window(p, b + u * 32 + lane))
-            c += is_cand(ts.y, b + u * 32 + lane, ts.lo, ts.hi, p.thr, p.radius) ? 1 : 0;
-      }
-      c = warp_sum(c);
-      if (lane == src) mine = c;
+    const unsigned m = __ballot_sync(kFull, live);
+    if (lane == 0) {
+      hot[warp] = m;
+      gs[warp] = 0;
     }
-    if (tile < ntiles) p.counts[tile] = mine;
-    const int gs = warp_sum(mine);
-    if (lane == 0) p.gsum[g] = gs;
+    if (in && !live) p.counts[tile] = 0;
+    __syncthreads();
+    for (int w2 = 0; w2 < kCtaWarps; ++w2) {
+      unsigned todo = hot[w2];  // (the same for every thread)
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t tl = (g0 + w2) * kCandGroup + src;
+        const TileSpan ts(p, tl);
+        const int64_t b0 = ts.t0 + warp * seg;
+        const int64_t b1 = (b0 + seg < ts.end) ? b0 + seg : ts.end;
+        const int c = (b0 < b1) ? count_span(p, ts, b0, b1, lane) : 0;
+        if (lane == 0) segc[warp] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int tot = 0;
+#pragma unroll
+          for (int i = 0; i < kCtaWarps; ++i) tot += segc[i];
+          p.counts[tl] = tot;
+          gs[w2] += tot;
+        }
+        __syncthreads();
+      }
+    }
+    if (g < ngroups && lane == 0) p.gsum[g] = gs[warp];
+    __syncthreads();  // hot and gs are reused by the next groups
   }
 }
 
@@ -171,57 +213,86 @@ __global__ void __launch_bounds__(kScanThreads) cand_scan_kernel(const CandParam
   if (threadIdx.x == 0) *p.d_count = carry;
 }
 
+// Records of the candidates among the starts [b0, b1) of a tile (one warp),
+// from offset base on, in start order (a ballot per 32 consecutive starts).
+__device__ __forceinline__ void write_span(const CandParams& p, const TileSpan& ts, int64_t b0, int64_t b1,
+                                           int lane, int64_t base) {
+  const unsigned below = (1u << lane) - 1u;
+  for (int64_t b = b0; b < b1 && base < p.cap; b += 32 * kUnroll) {
+    float v[kUnroll];
+    load_block(ts, b, b1, lane, v);
+    static_for<0, kUnroll>([&](auto U) {
+      constexpr int u = decltype(U)::value;
+      const int64_t s = b + u * 32 + lane;
+      const bool f = v[u] >= p.thr && in_window(p, s) && is_cand(ts.y, s, ts.lo, ts.hi, p.thr, p.radius);
+      const unsigned bal = __ballot_sync(kFull, f);
+      if (f) {
+        const int64_t pos = base + __popc(bal & below);
+        if (pos < p.cap) {  // the 24-byte record as three 8-byte stores
+          const int wi = (int)ts.w[s];
+          const int wd = p.width_mode ? p.width_tab[wi] : wi + 1;
+          int64_t orow = ts.row, ostart = s;
+          if (p.row_ids) {  // a searched block back to its row and start
+            const int64_t blk = p.row_ids[ts.row];
+            orow = blk / p.map_bpr;
+            ostart = (blk % p.map_bpr) * p.map_block + (s - p.s_lo);
+          }
+          int2* o = reinterpret_cast<int2*>(p.out + pos);
+          o[0] = make_int2((int)orow, wi);
+          *reinterpret_cast<long long*>(o + 1) = (long long)ostart;
+          o[2] = make_int2(__float_as_int(v[u]), wd);
+        }
+      }
+      base += __popc(bal);
+    });
+  }
+}
+
+// The same groups per CTA as the count pass; each tile with candidates is
+// written by all warps at once: each counts its segment again, takes its
+// offset from the counts of the segments before it, and writes its records.
 __global__ void __launch_bounds__(kCandThreads, 1) cand_write_kernel(const CandParams p, int64_t ntiles,
                                                                   int64_t ngroups) {
-  const int lane = threadIdx.x & 31;
-  const unsigned below = (1u << lane) - 1u;
-  const int64_t nwarps = (int64_t)gridDim.x * (kCandThreads / 32);
-  for (int64_t g = (int64_t)blockIdx.x * (kCandThreads / 32) + (threadIdx.x >> 5); g < ngroups; g += nwarps) {
+  __shared__ unsigned hot[kCtaWarps];
+  __shared__ long long toff[kCtaWarps][kCandGroup];
+  __shared__ int segc[kCtaWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t seg = seg_len(p);
+  for (int64_t g0 = (int64_t)blockIdx.x * kCtaWarps; g0 < ngroups; g0 += (int64_t)gridDim.x * kCtaWarps) {
+    const int64_t g = g0 + warp;
     const int64_t tile = g * kCandGroup + lane;
-    const int c = (tile < ntiles) ? p.counts[tile] : 0;
+    const int c = (g < ngroups && tile < ntiles) ? p.counts[tile] : 0;
     int x = c;  // inclusive warp scan of the tile counts
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int u = __shfl_up_sync(kFull, x, o);
       if (lane >= o) x += u;
     }
-    const int64_t off = p.goff[g] + (x - c);
-    unsigned todo = __ballot_sync(kFull, c > 0);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      int64_t base = __shfl_sync(kFull, off, src);
-      if (base >= p.cap) break;  // later tiles start even later
-      const TileSpan ts(p, g * kCandGroup + src);
-      for (int64_t b = ts.t0; b < ts.end && base < p.cap; b += 32 * kUnroll) {
-        float v[kUnroll];
-        load_block(ts, b, lane, v);
-        static_for<0, kUnroll>([&](auto U) {
-          constexpr int u = decltype(U)::value;
-          const int64_t s = b + u * 32 + lane;
-          const bool f = v[u] >= p.thr && in_window(p, s) && is_cand(ts.y, s, ts.lo, ts.hi, p.thr, p.radius);
-          const unsigned bal = __ballot_sync(kFull, f);
-          if (f) {
-            const int64_t pos = base + __popc(bal & below);
-            if (pos < p.cap) {  // the 24-byte record as three 8-byte stores
-              const int wi = (int)ts.w[s];
-              const int wd = p.width_mode ? p.width_tab[wi] : wi + 1;
-              int64_t orow = ts.row, ostart = s;
-              if (p.row_ids) {  // a searched block back to its row and start
-                const int64_t blk = p.row_ids[ts.row];
-                orow = blk / p.map_bpr;
-                ostart = (blk % p.map_bpr) * p.map_block + (s - p.s_lo);
-              }
-              int2* o = reinterpret_cast<int2*>(p.out + pos);
-              o[0] = make_int2((int)orow, wi);
-              *reinterpret_cast<long long*>(o + 1) = (long long)ostart;
-              o[2] = make_int2(__float_as_int(v[u]), wd);
-            }
-          }
-          base += __popc(bal);
-        });
+    toff[warp][lane] = (g < ngroups ? p.goff[g] : 0) + (x - c);
+    const unsigned m = __ballot_sync(kFull, c > 0);
+    if (lane == 0) hot[warp] = m;
+    __syncthreads();
+    for (int w2 = 0; w2 < kCtaWarps; ++w2) {
+      unsigned todo = hot[w2];  // (the same for every thread)
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t base = toff[w2][src];
+        if (base >= p.cap) break;  // later tiles of the group start even later
+        const int64_t tl = (g0 + w2) * kCandGroup + src;
+        const TileSpan ts(p, tl);
+        const int64_t b0 = ts.t0 + warp * seg;
+        const int64_t b1 = (b0 + seg < ts.end) ? b0 + seg : ts.end;
+        const int cs = (b0 < b1) ? count_span(p, ts, b0, b1, lane) : 0;
+        if (lane == 0) segc[warp] = cs;
+        __syncthreads();
+        int64_t sb = base;
+        for (int i = 0; i < warp; ++i) sb += segc[i];
+        if (b0 < b1 && cs > 0 && sb < p.cap) write_span(p, ts, b0, b1, lane, sb);
+        __syncthreads();  // segc is reused by the next tile
       }
     }
+    __syncthreads();  // hot and toff are reused by the next groups
   }
 }
 
