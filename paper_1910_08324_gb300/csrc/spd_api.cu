@@ -211,7 +211,6 @@ void fill_grid(spd::SearchParams& p, const spd_plan& plan) {
   if (plan.family == kBoxdit && plan.bd_general) {
     for (int j = 0; j <= plan.top; ++j) p.lvl_k[j] = plan.lvl_k[j];
     spd::bdg_layout(plan, plan.tile, true, p.gen_len, p.gen_off);
-    p.gen_part = 0;
     p.gen_h = spd::kBdgSplit;
     for (size_t i = 0; i < plan.widths.size() && i < (size_t)spd::kMaxGridWidths; ++i)
       p.wscale[i] = (float)(1.0 / std::sqrt((double)plan.widths[i]));

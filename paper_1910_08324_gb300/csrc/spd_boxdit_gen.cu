@@ -597,7 +597,6 @@ cudaError_t launch_boxdit_gen(const spd_plan& plan, const SearchParams& p, cudaS
   const int h = kBdgSplit;
   std::unique_ptr<SearchParams> q(new (std::nothrow) SearchParams(p));
   if (!q) return cudaErrorMemoryAllocation;
-  q->gen_part = 1;
   q->gen_h = h;
   const size_t smem1 = sizeof(float) * (size_t)bdg_layout(plan, plan.tile, table, q->gen_len, q->gen_off, 1, h);
   const int64_t tiles1 = (plan.desc.nt + plan.tile - 1) / plan.tile;
@@ -605,7 +604,6 @@ cudaError_t launch_boxdit_gen(const spd_plan& plan, const SearchParams& p, cudaS
   cudaError_t e = launch_gen_part<1>(*q, smem1, plan.desc.ndm * tiles1, s);
   if (e != cudaSuccess) return e;
   *q = p;
-  q->gen_part = 2;
   q->gen_h = h;
   q->tile = kBdgTile2;
   const size_t smem2 = sizeof(float) * (size_t)bdg_layout(plan, kBdgTile2, table, q->gen_len, q->gen_off, 2, h);

@@ -107,11 +107,11 @@ struct SearchParams {
   int32_t gen_len[kMaxLevels];
   int32_t gen_off[kBdgOffsets];
   float wscale[kMaxGridWidths];
-  // the two-kernel form of larger plans: gen_part 1 runs levels below gen_h and
-  // writes x^gen_h and the bases X^{gen_h - 1} of every row to gen_xh / gen_bh
-  // and its SNRs and width indices at the starts of level gen_h to gen_yh /
-  // gen_wh (all [ndm][gen_ldh]); gen_part 2 runs levels gen_h..top on them
-  int32_t gen_part, gen_h;
+  // the two-kernel form of larger plans: the first kernel runs levels below
+  // gen_h and writes x^gen_h and the bases X^{gen_h - 1} of every row to gen_xh /
+  // gen_bh and its SNRs and width indices at the starts of level gen_h to gen_yh
+  // / gen_wh (all [ndm][gen_ldh]); the second runs levels gen_h..top on them
+  int32_t gen_h;
   float* gen_xh;
   float* gen_bh;
   float* gen_yh;
@@ -196,8 +196,9 @@ cudaError_t launch_boxdit(const spd_plan& plan, const SearchParams& p, cudaStrea
 size_t boxdit_smem_bytes(const spd_plan& plan, bool table);
 // general BoxDIT (spd_boxdit_gen.cu): layout of a plan with tiles of T starts
 // (window lengths into len[kMaxLevels], offsets into off[kBdgOffsets]; returns floats)
-// part 0: every level in one kernel; 1: levels below h (writing x^h and the
-// bases X^{h-1}); 2: levels h..top of the series x^h, in tiles of T positions
+// part 0: every level in one kernel; 1: levels below h (writing x^h, the bases
+// X^{h-1} and a copy of the results at level h's starts); 2: levels h..top of
+// the series x^h, in tiles of T positions
 int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off, int part = 0, int h = 0);
 constexpr int kBdgSplit = 4;     // general BoxDIT plans above this level run in two kernels
 constexpr int kBdgTile2 = 2048;  // level-kBdgSplit positions per tile of the second
