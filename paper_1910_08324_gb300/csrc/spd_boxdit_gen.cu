@@ -50,9 +50,7 @@
 
 namespace spd {
 
-// Window lengths and shared-memory offsets (floats) of a general BoxDIT plan
-// with tiles of T starts (see the kernel's comment).
-constexpr int kWinPad = 32;
+constexpr int kWinPad = 32;  // floats after each series buffer (see bdg_layout)
 
 // Offset in the YC, WC regions of level i >= 1's P(i) results (P(i) = T / 2^i
 // up to level lt = log2 T, then 1): the levels one after the other from level 1.
@@ -60,6 +58,8 @@ __host__ __device__ __forceinline__ int yc_off(int T, int lt, int i) {
   return i - 1 <= lt ? T - (T >> (i - 1)) : T - 1 + (i - 1 - lt);
 }
 
+// Window lengths and shared-memory offsets (floats) of a general BoxDIT plan
+// with tiles of T starts (see the kernel's comment).
 int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* off, int part, int h) {
   int lt = 0;
   while ((2 << lt) <= T) ++lt;  // log2 T
@@ -115,7 +115,7 @@ int bdg_layout(const spd_plan& plan, int T, bool table, int32_t* len, int32_t* o
 
 namespace {
 
-constexpr int kGMC = 8;        // block counts per register window (3-bit ranks)
+constexpr int kGMC = 8;        // block counts per register window at most (3-bit ranks)
 constexpr int kLoadBatch = 8;  // input loads in flight per thread
 
 // NP consecutive values at a 4 NP-byte aligned address (float4 or float2 loads)
@@ -296,9 +296,10 @@ __device__ __forceinline__ int x1_split(int T, int n1) {
 }
 
 // One tile.  PART 0: every level of the plan on T starts of the input; PART 1:
-// levels 0..h-1 on T starts, and x^h and the bases X^{h-1} of the tile's T / 2^h
-// level-h positions to the workspace; PART 2: levels h..top on T positions of
-// x^h (t0 and T in level-h positions), merged into the Y, W the first part wrote.
+// levels 0..h-1 on T starts, and x^h, the bases X^{h-1} and a copy of the
+// results of the tile's T / 2^h level-h positions to the workspace; PART 2:
+// levels h..top on T positions of x^h (t0 and T in level-h positions), stored
+// at the starts where they beat the first part's copy.
 template <bool TABLE, int PART>
 __device__ __forceinline__ void bdg_unit(const SearchParams& p, const Unit& U, float* smem) {
   constexpr bool P1 = PART == 1, P2 = PART == 2;
