@@ -116,6 +116,24 @@ __device__ __forceinline__ int64_t seg_len(const CandParams& p) {
   return (per + 32 * kUnroll - 1) / (32 * kUnroll) * (32 * kUnroll);
 }
 
+// Whether a CTA scans its live tiles together (each tile by all warps, one after
+// the other) or each warp its own group's: together when that ends sooner.  A
+// tile scanned together costs about twice its share of one warp's time (two
+// barriers, the write pass counting its segment again, idle warps past a short
+// row's end), so together wins when the busiest warp holds more than 2 /
+// kCtaWarps of the live tiles (a few live tiles: together; most tiles live, as in
+// a search of flagged blocks: each warp its own).
+__device__ __forceinline__ bool cta_together(const unsigned (&hot)[kCtaWarps]) {
+  int n = 0, mx = 0;
+#pragma unroll
+  for (int w = 0; w < kCtaWarps; ++w) {
+    const int c = __popc(hot[w]);
+    n += c;
+    mx = c > mx ? c : mx;
+  }
+  return 2 * n < kCtaWarps * mx;
+}
+
 // Candidates among the starts [b0, b1) of a tile (one warp; the warp's total).
 __device__ __forceinline__ int count_span(const CandParams& p, const TileSpan& ts, int64_t b0, int64_t b1,
                                          int lane) {
@@ -154,6 +172,21 @@ __global__ void __launch_bounds__(kCandThreads) cand_count_kernel(const CandPara
     }
     if (in && !live) p.counts[tile] = 0;
     __syncthreads();
+    if (!cta_together(hot)) {  // each warp its own group's tiles, whole
+      unsigned todo = m;
+      int gsum = 0;
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const TileSpan ts(p, g * kCandGroup + src);
+        const int c = count_span(p, ts, ts.t0, ts.end, lane);
+        if (lane == 0) p.counts[g * kCandGroup + src] = c;
+        gsum += c;
+      }
+      if (g < ngroups && lane == 0) p.gsum[g] = gsum;
+      __syncthreads();  // hot is reused by the next groups
+      continue;
+    }
     for (int w2 = 0; w2 < kCtaWarps; ++w2) {
       unsigned todo = hot[w2];  // (the same for every thread)
       while (todo) {
@@ -272,6 +305,19 @@ __global__ void __launch_bounds__(kCandThreads, 1) cand_write_kernel(const CandP
     const unsigned m = __ballot_sync(kFull, c > 0);
     if (lane == 0) hot[warp] = m;
     __syncthreads();
+    if (!cta_together(hot)) {  // each warp its own group's tiles, whole
+      unsigned todo = m;
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t base = toff[warp][src];
+        if (base >= p.cap) break;  // later tiles of the group start even later
+        const TileSpan ts(p, g * kCandGroup + src);
+        write_span(p, ts, ts.t0, ts.end, lane, base);
+      }
+      __syncthreads();  // hot and toff are reused by the next groups
+      continue;
+    }
     for (int w2 = 0; w2 < kCtaWarps; ++w2) {
       unsigned todo = hot[w2];  // (the same for every thread)
       while (todo) {
