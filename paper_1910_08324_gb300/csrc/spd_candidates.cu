@@ -21,8 +21,10 @@
 //             the first cap records are kept.
 // A warp reads a tile 512 starts at a time (16 independent loads per lane)
 // and runs the peak test only where the threshold is met.
-// Count and write run as a grid of persistent warps (a few per SM) that stride
-// over the groups.
+// Count and write run as a grid of persistent CTAs (a few per SM) that stride
+// over the groups, eight groups (one per warp) at a time.  A CTA with few tiles
+// that have candidates scans each of them with all its warps at once, one
+// segment per warp (cta_together); otherwise each warp scans its own group's.
 #include <cuda_runtime.h>
 
 #include <cstddef>
