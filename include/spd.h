@@ -363,8 +363,12 @@ spd_status spd_noise_stats(const spd_plan *plan, const void *d_x, float outlier_
  * 2432 segments (ndm x segments per row).  Host only.  SPD_ERR_INVALID_ARG otherwise (and for
  * exhaustive plans).  A BoxDIT plan on the general kernel (spd_plan_create_boxdit)
  * takes tiles of 2048, 4096 or 8192 starts here instead (one CTA per tile; the
- * default is 4096 when two CTAs fit on an SM, else 2048); SPD_ERR_UNSUPPORTED
- * when a tile's shared memory would exceed 227 KB.
+ * default is 4096 when several CTAs fit on an SM, else 2048); SPD_ERR_UNSUPPORTED
+ * when a tile's shared memory would exceed 227 KB.  Such a plan above level 4
+ * runs in two launches: levels 0..3 on these tiles, then levels 4.. on tiles of
+ * 2048 positions of the level-4 series (32768 starts); its workspace
+ * (spd_workspace_size, which depends on the tile) then also holds 14 bytes per
+ * 16 samples of every row between the two.
  */
 spd_status spd_plan_set_segment(spd_plan *plan, int32_t segment);
 
